@@ -1,0 +1,302 @@
+"""Throughput of the CRBM proposal + Metropolis-Hastings step on GB300.
+
+Default workload ("ising-batch"): 2D Ising, L in {16, 32, 64, 128}, 4096 chains
+per L over 32 temperatures in [1.5, 3.5], CRBM with K = 4 filters 5 x 5, all
+four lattice sizes in ONE batched launch; mixed precision (FP32 with certified
+margins and FP64 recompute).  One bench step = one launch running S_STEP
+proposals of every chain.  value = chain-proposals per second over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ising-batch|ising-small|kitaev-small] [--precision mixed|fp64]
+
+--impl reference times the CPU oracle (the plain FP64 numpy restatement of
+the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import crbm_workloads as wl  # noqa: E402
+
+METRIC = "CRBM-MH proposals/s (Ising, Kitaev) vs plain FP64 path; serving p50/p99 latency"
+SEED = wl.BASE_SEED
+
+
+def workload(name):
+    """(kind, [(L, n_chains)], T-ladder fn, J, model params, S_STEP, description)."""
+    if name == "ising-batch":
+        W, hb, vb = _ising_batch_model()
+        return dict(kind=0, jobs=[(L, 4096) for L in (16, 32, 64, 128)], T=lambda n: wl.ising_ladder(n, 32),
+                    J=(1.0,), model=(W, hb, vb), S=10,
+                    desc="2D Ising L in {16,32,64,128} x 4096 chains, 32 T in [1.5,3.5], K=4 5x5 CRBM")
+    if name == "ising-small":
+        W, hb, vb = wl.gaussian_crbm(2, 3, 0.1)
+        return dict(kind=0, jobs=[(8, 16)], T=lambda n: np.full(n, 2.269), J=(1.0,), model=(W, hb, vb), S=100,
+                    desc="2D Ising L=8, 16 chains, T=2.269, K=2 3x3 CRBM N(0,0.1)")
+    if name == "kitaev-small":
+        W, hb, vb = wl.gaussian_crbm(4, 3, 0.05)
+        return dict(kind=1, jobs=[(6, 1024)], T=lambda n: wl.kitaev_ladder(n, 24), J=(1.0, 1.0, 1.0),
+                    model=(W, hb, vb), S=2,
+                    desc="Kitaev L=6 (72 sites), J=1, 1024 chains, 24 T log-spaced in [0.005,1], K=4 3x3 CRBM")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _ising_batch_model():
+    path = os.path.join(ROOT, "paper_2008_05401_gb300", "data", "ising_cd1_L16_K4_k5.npz")
+    if os.path.exists(path):
+        d = np.load(path)
+        return d["W"], d["hb"], float(d["vb"])
+    return wl.gaussian_crbm(4, 5, 0.1)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def roofline(wd, kernel_ms, clocks, K, k, n_sites_step):
+    """ALU roofline of the fused kernel: algorithmic FP32 flops = the three
+    periodic convolutions of a proposal written directly (hidden, visible and
+    free-energy pre-activations: 3 x K k^2 multiply-adds per site), against the
+    FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops) and the SM
+    clock sampled during the run."""
+    flops = 6.0 * K * k * k * n_sites_step
+    mhz = clocks.get("sm_mhz") or peaks().get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": f"FP32 FMA from unit counts x sampled SM clock {mhz:.0f} MHz"}
+
+
+def cpu_baseline_run(spec, budget_s=15.0):
+    """Time the oracle on a bounded sample of the workload (one process, BLAS 1 thread)."""
+    from oracle import chain
+    try:
+        from threadpoolctl import threadpool_limits
+        lim = threadpool_limits(1)
+    except Exception:  # noqa: BLE001
+        lim = None
+    W, hb, vb = spec["model"]
+    props, t_total, samples = 0, 0.0, []
+    for L, n in spec["jobs"]:
+        nc = min(n, 64 if spec["kind"] == 0 else 32)
+        ch = chain.make_chains(spec["kind"], W, hb, vb, L, spec["T"](nc), spec["J"], SEED, np.arange(nc))
+        t0 = time.perf_counter()
+        s = 0
+        while time.perf_counter() - t0 < budget_s / len(spec["jobs"]):
+            chain.step(ch)
+            s += 1
+        dt = time.perf_counter() - t0
+        props += nc * s * L * L
+        t_total += dt
+        samples.append(f"L={L}: {nc} chains x {s} proposals in {dt:.1f}s")
+    if lim is not None:
+        lim.unregister() if hasattr(lim, "unregister") else None
+    # scale to the workload's mix: site-weighted rate -> proposals/s of the full mix
+    sites_per_prop = sum(n * L * L for L, n in spec["jobs"]) / sum(n for _, n in spec["jobs"])
+    rate = props / t_total / sites_per_prop
+    return {"value": rate, "unit": "proposals/s", "cores": 1, "kind": "oracle",
+            "sample": "; ".join(samples) + " (site-weighted to the workload's L mix)"}
+
+
+def run_reference(args, spec):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline_run(spec, budget_s=max(5.0, 2.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "proposals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "parallelism": "chains"}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "proposals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ising-batch")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--chains", type=int, default=0, help="override chains per lattice size (profiling)")
+    ap.add_argument("--Ls", default="", help="comma list restricting the lattice sizes (profiling)")
+    args = ap.parse_args()
+    spec = workload(args.workload)
+    if args.Ls:
+        keep = {int(x) for x in args.Ls.split(",")}
+        spec["jobs"] = [(L, n) for L, n in spec["jobs"] if L in keep]
+    if args.chains:
+        spec["jobs"] = [(L, args.chains) for L, _ in spec["jobs"]]
+    if args.impl == "reference":
+        return run_reference(args, spec)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if world > 1 else 0
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2008_05401_gb300 import FP64, MIXED, Context
+    prec = MIXED if args.precision == "mixed" else FP64
+    ctx = Context(dev)
+    W, hb, vb = spec["model"]
+    mid = ctx.load_model(spec["kind"], W, vb, hb)
+    jobs = []
+    base = 0
+    for L, n in spec["jobs"]:
+        init = wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L))
+        # weak scaling: each rank owns its own chain-id range
+        jobs.append(ctx.new_job(mid, spec["kind"], L, spec["T"](n), spec["J"], SEED,
+                                rank * 10_000_000 + base, init, prec))
+        base += n
+    S = spec["S"]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(dev) as ck:
+        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            flush.zero_()                      # L2 flush between timed steps (untimed)
+            ev[i][0].record(stream)
+            ctx.run_batch(jobs, S, precision=prec, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_chains = sum(n for _, n in spec["jobs"])
+    props = n_chains * S * args.steps * world
+    value = props / (total_ms * 1e-3)
+    clocks = ck.summary()
+
+    # end to end through the C ABI with host buffers: upload lattices (pinned),
+    # run, read lattices and observable sums back
+    host_bits = []
+    for j in jobs:
+        b = torch.empty(j.state()[0].shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        b[:] = j.state()[0]
+        host_bits.append(b)
+    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        for j, hbits in zip(jobs, host_bits):
+            j.write_state(hbits, j.step)
+            h2d += hbits.nbytes
+        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+        for j in jobs:
+            bits, _ = j.state()
+            sums, _, _ = j.observables()
+            d2h += bits.nbytes + sums.nbytes
+    e2e_s = time.perf_counter() - t0
+    e2e = None if not e2e_steps else {
+        "value": n_chains * S * e2e_steps * world / e2e_s, "unit": "proposals/s",
+        "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
+
+    K, k = W.shape[0], W.shape[1]
+    sites = sum(n * L * L for L, n in spec["jobs"]) * S
+    line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == MIXED else "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "proposals_per_step": S, "chains": n_chains,
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"chains x{world}"},
+            "roofline": roofline(spec, total_ms / args.steps, clocks, K, k, sites),
+            "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(spec)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

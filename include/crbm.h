@@ -1,0 +1,169 @@
+/*
+ * crbm.h -- C ABI of the GB300 (sm_103a) CRBM-aided Monte Carlo library.
+ *
+ * Method: Alcalde Puente & Eremin, "Convolutional restricted Boltzmann
+ * machine aided Monte Carlo: an application to Ising and Kitaev models"
+ * (arXiv:2008.05401).  Every chain repeats one proposal:
+ *   g block-Gibbs steps of a convolutional RBM (Sec. II, Eqs. 12-13;
+ *   App. B.1, Eqs. B1-B4), then an exact Metropolis-Hastings correction
+ *   with log r = [log pi(v') - log pi(v)] + [F(v') - F(v)] (App. B.2,
+ *   Eq. B5 read with the target pi and P_CRBM ~ exp(-F) as the pair of
+ *   distributions), where log pi is -beta E for the 2D Ising model
+ *   (Sec. III, Eq. 14) or sum_l log 2cosh(beta eps_l / 2) for the Kitaev
+ *   honeycomb model in its Majorana / Z2-gauge form (Sec. IV, Eq. 16).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a crbm_status; details of a failure are kept in the
+ *     context and returned by crbm_last_error().  No call aborts the process.
+ *   - Host pointers are read or written only during the call.
+ *   - Device memory of a job (dev_mem) belongs to the caller (for instance a
+ *     torch tensor) and must stay allocated until crbm_release().
+ *   - crbm_run / crbm_run_batch are asynchronous on the given CUDA stream;
+ *     the crbm_read_* calls synchronise the job's last stream first.
+ *   - Lattice layout ("packed"): site n = i*L + j of the L x L lattice is bit
+ *     n % 32 of uint32 word n / 32; one chain holds ceil(L*L/32) words; bits
+ *     at n >= L*L are zero.  A set bit is v = 1 (Ising spin s = +1; Kitaev
+ *     z-bond variable eta = +1).
+ *   - Random numbers: Philox4x32-10 keyed by the 64-bit seed; the counter of
+ *     every draw is (block, tag, step, chain id), chain id = chain_id_base + c.
+ *     A chain's trajectory therefore depends only on (seed, chain id, state,
+ *     step), never on which job, batch or slot it runs in.
+ *   - Limits: 2 <= L <= 32 or L a multiple of 32 up to 256 (Ising);
+ *     2 <= L <= 12 (Kitaev); 1 <= K <= 8 filters; 1 <= k <= min(7, L).
+ */
+#ifndef CRBM_H
+#define CRBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CRBM_API __attribute__((visibility("default")))
+#else
+#define CRBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crbm_ctx crbm_ctx;
+
+typedef enum {
+    CRBM_OK = 0,
+    CRBM_EINVAL = -1,   /* bad argument, size or id                              */
+    CRBM_ENOMEM = -2,   /* job does not fit the context's HBM budget or dev_mem  */
+    CRBM_ECUDA = -3,    /* a CUDA runtime call failed (message in last_error)    */
+    CRBM_ETIMEOUT = -4, /* a device-side wait gave up after its iteration limit  */
+    CRBM_EBUSY = -5     /* job still referenced by an unfinished batch plan      */
+} crbm_status;
+
+typedef enum { CRBM_ISING = 0, CRBM_KITAEV = 1 } crbm_model_kind;
+
+/* CRBM_FP64: every pre-activation, probability, free energy and decision in
+ * FP64.  CRBM_MIXED: FP32 pre-activations (hi/lo split filters), FP32
+ * sigmoid/softplus with FP64 accumulation; every Bernoulli or accept/reject
+ * decision that lies within the FP32 error bound of its threshold is redone
+ * with the FP64 code, so the chain takes exactly the FP64 path's decisions. */
+typedef enum { CRBM_FP64 = 0, CRBM_MIXED = 1 } crbm_precision;
+
+/* Per-chain observable sums (crbm_read_observables), CRBM_NOBS per chain:
+ *   Ising : sum E, sum E^2, sum |M|, sum M^2        (E of Eq. 14, M = sum s)
+ *   Kitaev: sum e, sum e^2, sum c_f, sum n_vison
+ * with e(eta) = -sum_l (eps_l/2) tanh(beta eps_l/2), c_f(eta) =
+ * sum_l (beta eps_l/2)^2 sech^2(beta eps_l/2) (so that <E> = <e> and
+ * C = beta^2 Var(e) + <c_f>), n_vison = fraction of hexagons with flux -1.
+ * One term per proposal, taken on the state after the decision. */
+#define CRBM_NOBS 4
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the sum of
+ * crbm_job_bytes() over live jobs (0 = no cap).  *out receives the handle.
+ * Errors: CRBM_EINVAL (null out, bad device), CRBM_ECUDA. */
+CRBM_API int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context and the device buffers it owns (not the jobs' dev_mem). */
+CRBM_API int crbm_destroy(crbm_ctx* ctx);
+
+/* Last error message of the context ("" if none); valid until the next call. */
+CRBM_API const char* crbm_last_error(const crbm_ctx* ctx);
+
+/* Load a CRBM (Sec. II, Eqs. 12-13): W is K*k*k FP64, row-major W[f][a][b],
+ * h_bias has K entries, v_bias is the single visible bias.  The weight
+ * W[f][a][b] couples hidden unit (f,i,j) to visible unit ((i+a)%L,(j+b)%L)
+ * (periodic cross-correlation anchored at the top-left tap).  The values are
+ * copied; the caller keeps ownership.  *model_id receives the id.
+ * Errors: CRBM_EINVAL (kind, K, k out of range, null pointers). */
+CRBM_API int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W,
+                    double v_bias, const double* h_bias, int* model_id);
+
+/* Bytes of caller-owned device memory one job needs: packed lattices, FP64
+ * temperatures and energies, observable sums and counters, 256-byte aligned.
+ * Returns 0 for arguments out of range. */
+CRBM_API size_t crbm_job_bytes(int kind, int L, int n_chains, int precision);
+
+/* Create a job of n_chains chains of side L using model `model_id`.
+ *   T[n_chains]   temperature of each chain (beta = 1/T), host FP64.
+ *   J             Ising: J[0] (E = -J sum s_i s_j); Kitaev: J[0..2] = (Jx, Jy, Jz).
+ *   seed, chain_id_base: random stream of chain c is (seed, chain_id_base + c);
+ *                 chain ids must stay below 2^32.
+ *   init          0: v_ij = [u < 1/2] from the stream's init tag;
+ *                 1: copy init_bits (n_chains * ceil(L*L/32) packed words, host).
+ *   dev_mem       caller-owned device buffer of dev_bytes >= crbm_job_bytes().
+ * Evaluates F, log pi and the observables of the initial lattices in FP64 and
+ * resets the sums.  The call returns after the work is complete.
+ * Errors: CRBM_EINVAL, CRBM_ENOMEM (dev_bytes too small or budget exceeded),
+ * CRBM_ECUDA. */
+CRBM_API int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const double* T,
+                     const double* J, uint64_t seed, uint64_t chain_id_base, int init,
+                     const uint32_t* init_bits, void* dev_mem, size_t dev_bytes, int* job_id);
+
+/* Enqueue S proposals per chain on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream).  Each proposal is g Gibbs steps then the MH decision;
+ * correct = 0 accepts every proposal (uncorrected Gibbs sampling, the
+ * paper's Ising protocol of Sec. III).  The job's step counter advances by S.
+ * Errors: CRBM_EINVAL, CRBM_ECUDA (launch failure). */
+CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision,
+             void* cuda_stream);
+
+/* As crbm_run for n_jobs jobs of the same model kind in ONE kernel launch
+ * (chains of different L and temperature side by side).  Each job keeps its
+ * own step counter and random streams, so its result equals a crbm_run of
+ * that job alone.  At most 16 jobs per call; a job may appear once. */
+CRBM_API int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g,
+                   int correct, int precision, void* cuda_stream);
+
+/* Wait for the job's last enqueued work and check the device error flag.
+ * Errors: CRBM_ECUDA, CRBM_ETIMEOUT (a device wait hit its iteration cap). */
+CRBM_API int crbm_sync(crbm_ctx* ctx, int job_id);
+
+/* Copy per-chain FP64 values of the current states to host arrays of
+ * n_chains entries each (any may be NULL): log pi, CRBM free energy F
+ * (Eq. 13; in CRBM_MIXED this is the FP32-path value, within the bound the
+ * decisions used, unless a recompute made it exact), and E_phys (Ising E,
+ * Kitaev e(eta)). */
+CRBM_API int crbm_read_energies(crbm_ctx* ctx, int job_id, double* logpi, double* F_crbm, double* E_phys);
+
+/* Copy observable sums (n_chains * CRBM_NOBS FP64, chain-major), accepted
+ * proposal counts and FP64-recompute counts (n_chains int64 each; any
+ * pointer may be NULL). */
+CRBM_API int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int64_t* accepts,
+                          int64_t* recomputes);
+
+/* Copy the packed lattices (n_chains * ceil(L*L/32) words) and the job's
+ * step counter (proposals made so far).  Together with the seed and chain
+ * ids this is a complete checkpoint. */
+CRBM_API int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step);
+
+/* Restore a checkpoint: overwrite the lattices and the step counter, then
+ * re-evaluate F, log pi and observables in FP64 (sums are kept).  A resumed
+ * chain continues bit-identically to an uninterrupted one. */
+CRBM_API int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step);
+
+/* Forget a job (its dev_mem may be freed afterwards) and return its bytes to
+ * the context's budget. */
+CRBM_API int crbm_release(crbm_ctx* ctx, int job_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRBM_H */

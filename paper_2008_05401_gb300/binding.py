@@ -1,0 +1,236 @@
+"""Thin ctypes binding of libcrbm.so (declarations and contracts: include/crbm.h).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+library.  The module-level ``crbm_*`` functions mirror the C entry points one
+to one; ``Context`` / ``Job`` wrap them with torch tensors for device memory
+and numpy arrays for host data.  Loading fails loudly when the library has
+not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+ISING, KITAEV = 0, 1
+FP64, MIXED = 0, 1
+NOBS = 4
+STATUS = {0: "CRBM_OK", -1: "CRBM_EINVAL", -2: "CRBM_ENOMEM", -3: "CRBM_ECUDA", -4: "CRBM_ETIMEOUT",
+          -5: "CRBM_EBUSY"}
+
+_lib = None
+
+
+class CrbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_SIGS = {
+    "crbm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]),
+    "crbm_destroy": (C.c_int, [C.c_void_p]),
+    "crbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "crbm_load_model": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                                  C.c_void_p, C.POINTER(C.c_int)]),
+    "crbm_job_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
+    "crbm_init_chains": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                                   C.POINTER(C.c_int)]),
+    "crbm_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "crbm_run_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                 C.c_void_p]),
+    "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
+    "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "crbm_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
+    "crbm_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64]),
+    "crbm_release": (C.c_int, [C.c_void_p, C.c_int]),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libcrbm.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = load().crbm_last_error(ctx).decode() if ctx else ""
+        raise CrbmError(rc, msg)
+
+
+# ---- one-to-one wrappers of the C entry points --------------------------------
+def crbm_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = C.c_void_p()
+    _check(None, load().crbm_create(C.byref(h), device, hbm_budget_bytes))
+    return h
+
+
+def crbm_destroy(ctx):
+    _check(None, load().crbm_destroy(ctx))
+
+
+def crbm_last_error(ctx) -> str:
+    return load().crbm_last_error(ctx).decode()
+
+
+def crbm_load_model(ctx, kind, W, v_bias, h_bias) -> int:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    hb = np.ascontiguousarray(h_bias, dtype=np.float64)
+    K, k, _ = W.shape
+    mid = C.c_int()
+    _check(ctx, load().crbm_load_model(ctx, kind, K, k, _ptr(W), float(v_bias), _ptr(hb), C.byref(mid)))
+    return mid.value
+
+
+def crbm_job_bytes(kind, L, n_chains, precision=FP64) -> int:
+    return int(load().crbm_job_bytes(kind, L, n_chains, precision))
+
+
+def crbm_init_chains(ctx, model_id, L, T, J, seed, chain_id_base, init_bits, dev_ptr, dev_bytes) -> int:
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint32)
+    jid = C.c_int()
+    _check(ctx, load().crbm_init_chains(ctx, model_id, L, len(T), _ptr(T), _ptr(J), seed, chain_id_base,
+                                        0 if bits is None else 1, _ptr(bits), C.c_void_p(dev_ptr),
+                                        dev_bytes, C.byref(jid)))
+    return jid.value
+
+
+def crbm_run(ctx, job_id, S, g=1, correct=1, precision=FP64, stream=0):
+    _check(ctx, load().crbm_run(ctx, job_id, S, g, correct, precision, C.c_void_p(stream)))
+
+
+def crbm_run_batch(ctx, job_ids, S, g=1, correct=1, precision=FP64, stream=0):
+    ids = np.ascontiguousarray(job_ids, dtype=np.int32)
+    _check(ctx, load().crbm_run_batch(ctx, len(ids), _ptr(ids), S, g, correct, precision, C.c_void_p(stream)))
+
+
+def crbm_sync(ctx, job_id):
+    _check(ctx, load().crbm_sync(ctx, job_id))
+
+
+def crbm_read_energies(ctx, job_id, n):
+    lp, F, E = (np.empty(n) for _ in range(3))
+    _check(ctx, load().crbm_read_energies(ctx, job_id, _ptr(lp), _ptr(F), _ptr(E)))
+    return lp, F, E
+
+
+def crbm_read_observables(ctx, job_id, n):
+    sums = np.empty((n, NOBS))
+    acc = np.empty(n, dtype=np.int64)
+    rec = np.empty(n, dtype=np.int64)
+    _check(ctx, load().crbm_read_observables(ctx, job_id, _ptr(sums), _ptr(acc), _ptr(rec)))
+    return sums, acc, rec
+
+
+def crbm_read_state(ctx, job_id, n, L):
+    bits = np.empty((n, (L * L + 31) // 32), dtype=np.uint32)
+    step = C.c_uint64()
+    _check(ctx, load().crbm_read_state(ctx, job_id, _ptr(bits), C.byref(step)))
+    return bits, step.value
+
+
+def crbm_write_state(ctx, job_id, bits, step):
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    _check(ctx, load().crbm_write_state(ctx, job_id, _ptr(bits), step))
+
+
+def crbm_release(ctx, job_id):
+    _check(ctx, load().crbm_release(ctx, job_id))
+
+
+# ---- convenience layer: torch tensors hold the job memory ---------------------
+class Job:
+    def __init__(self, ctx: "Context", job_id: int, L: int, n: int, mem):
+        self.ctx, self.id, self.L, self.n, self.mem = ctx, job_id, L, n, mem
+        self.step = 0
+
+    def run(self, S, g=1, correct=True, precision=FP64, stream=None):
+        crbm_run(self.ctx.h, self.id, S, g, int(correct), precision, _stream_handle(stream))
+        self.step += S
+        return self
+
+    def sync(self):
+        crbm_sync(self.ctx.h, self.id)
+
+    def energies(self):
+        return crbm_read_energies(self.ctx.h, self.id, self.n)
+
+    def observables(self):
+        return crbm_read_observables(self.ctx.h, self.id, self.n)
+
+    def state(self):
+        return crbm_read_state(self.ctx.h, self.id, self.n, self.L)
+
+    def write_state(self, bits, step):
+        crbm_write_state(self.ctx.h, self.id, bits, step)
+        self.step = step
+
+    def release(self):
+        crbm_release(self.ctx.h, self.id)
+        self.mem = None
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.h = crbm_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            crbm_destroy(self.h)
+            self.h = None
+
+    def load_model(self, kind, W, v_bias, h_bias) -> int:
+        return crbm_load_model(self.h, kind, W, v_bias, h_bias)
+
+    def new_job(self, model_id, kind, L, T, J, seed, chain_id_base=0, init_bits=None, precision=FP64,
+                mem=None) -> Job:
+        import torch
+        T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+        nbytes = crbm_job_bytes(kind, L, len(T), precision)
+        if mem is None:
+            mem = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+        jid = crbm_init_chains(self.h, model_id, L, T, J, seed, chain_id_base, init_bits,
+                               mem.data_ptr() if len(T) else 0, mem.numel())
+        return Job(self, jid, L, len(T), mem)
+
+    def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
+        crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))
+        for j in jobs:
+            j.step += S

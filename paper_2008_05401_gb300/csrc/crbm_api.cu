@@ -1,0 +1,541 @@
+// C ABI of the CRBM-aided Monte Carlo library (declarations and contracts in
+// include/crbm.h).  Host side: contexts, models (row-sum tables of the CRBM
+// filters), jobs laid out in caller-owned device memory, and kernel launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "crbm.h"
+#include "crbm_device.cuh"
+#include "crbm_kernels.h"
+
+using namespace crbm;
+
+namespace {
+
+struct Model {
+  bool live = false;
+  int kind = 0, K = 0, k = 0;
+  double vb = 0.0;
+  std::vector<double> hb;
+  double* d_f64 = nullptr;   // forward FP64 row-sum table, then the backward one
+  float* d_f32 = nullptr;    // fd, bd, fh, fl
+  size_t nlut = 0;
+  float hb32[kMaxK] = {}, hb_hi[kMaxK] = {}, hb_lo[kMaxK] = {};
+  float vb32 = 0.f;
+  float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f;
+};
+
+struct Layout {
+  size_t bits, T, F, Fb, lp, E, ot, os, acc, rec, total;
+};
+
+struct Job {
+  bool live = false;
+  int model = -1, kind = 0, L = 0, N = 0, Wd = 0, n = 0, nc = 1, tiles = 0;
+  double J[3] = {1.0, 1.0, 1.0};
+  uint64_t seed = 0, cid_base = 0, step = 0;
+  unsigned char* mem = nullptr;
+  size_t bytes = 0;
+  Layout lay{};
+  cudaStream_t stream = nullptr;
+};
+
+Layout make_layout(int L, int n) {
+  Layout y{};
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += (b + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t Wd = ((size_t)L * L + 31) / 32;
+  y.bits = take((size_t)n * Wd * 4);
+  y.T = take((size_t)n * 8);
+  y.F = take((size_t)n * 8);
+  y.Fb = take((size_t)n * 8);
+  y.lp = take((size_t)n * 8);
+  y.E = take((size_t)n * 8);
+  y.ot = take((size_t)n * 8 * kNobs);
+  y.os = take((size_t)n * 8 * kNobs);
+  y.acc = take((size_t)n * 8);
+  y.rec = take((size_t)n * 8);
+  y.total = off;
+  return y;
+}
+
+bool valid_L(int kind, int L) {
+  if (kind == kIsing) return (L >= 2 && L <= 32) || (L % 32 == 0 && L <= 256);
+  if (kind == kKitaev) return L >= 2 && L <= 12;
+  return false;
+}
+
+// Chains per CTA: about two 4-site units per thread, a power of two in [1, 32].
+int chains_per_tile(int kind, int L) {
+  if (kind == kKitaev) return 1;
+  const int nblk = (L * L + 3) / 4;
+  int nc = 1;
+  while (nc < 32 && (nc * 2) * nblk <= 2 * kThreads) nc *= 2;
+  return nc;
+}
+
+}  // namespace
+
+struct crbm_ctx {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  std::vector<Model> models;
+  std::vector<Job> jobs;
+  std::string err;
+  int* d_err = nullptr;
+};
+
+static int fail(crbm_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+static int cuda_fail(crbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, CRBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+static Job* get_job(crbm_ctx* ctx, int id) {
+  if (!ctx || id < 0 || id >= (int)ctx->jobs.size() || !ctx->jobs[id].live) return nullptr;
+  return &ctx->jobs[id];
+}
+
+static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
+  const Model& m = ctx->models[j.model];
+  JobDev d;
+  memset(&d, 0, sizeof d);
+  d.kind = j.kind;
+  d.L = j.L;
+  d.N = j.N;
+  d.Wd = j.Wd;
+  d.P = j.Wd + 1;
+  d.K = m.K;
+  d.k = m.k;
+  d.n_chains = j.n;
+  d.nc = j.nc;
+  d.vb = m.vb;
+  for (int f = 0; f < m.K; ++f) {
+    d.hb[f] = m.hb[f];
+    d.hb32[f] = m.hb32[f];
+    d.hb_hi[f] = m.hb_hi[f];
+    d.hb_lo[f] = m.hb_lo[f];
+  }
+  for (int i = 0; i < 3; ++i) d.J[i] = j.J[i];
+  d.vb32 = m.vb32;
+  d.c0h = m.c0h;
+  d.c0v = m.c0v;
+  d.c1 = m.c1;
+  d.csp = m.csp;
+  d.f64 = m.d_f64;
+  d.b64 = m.d_f64 + m.nlut;
+  d.fd = m.d_f32;
+  d.bd = m.d_f32 + m.nlut;
+  d.fh = m.d_f32 + 2 * m.nlut;
+  d.fl = m.d_f32 + 3 * m.nlut;
+  d.seed = j.seed;
+  d.cid_base = j.cid_base;
+  d.step0 = j.step;
+  unsigned char* b = j.mem;
+  d.bits = (uint32_t*)(b + j.lay.bits);
+  d.T = (const double*)(b + j.lay.T);
+  d.F = (double*)(b + j.lay.F);
+  d.Fb = (double*)(b + j.lay.Fb);
+  d.logpi = (double*)(b + j.lay.lp);
+  d.Ephys = (double*)(b + j.lay.E);
+  d.obs_t = (double*)(b + j.lay.ot);
+  d.obs = (double*)(b + j.lay.os);
+  d.acc = (unsigned long long*)(b + j.lay.acc);
+  d.rec = (unsigned long long*)(b + j.lay.rec);
+  return d;
+}
+
+// Launch the fused kernel for a set of jobs (same kind); mode 1 = evaluate.
+static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct,
+                       int prec, int mode, cudaStream_t st) {
+  LaunchParams p;
+  memset(&p, 0, sizeof p);
+  p.n_jobs = (int)ids.size();
+  p.S = S;
+  p.g = g;
+  p.correct = correct;
+  p.mode = mode;
+  p.err = ctx->d_err;
+  size_t smem = 0;
+  int tiles = 0, kind = -1;
+  for (size_t i = 0; i < ids.size(); ++i) {
+    const Job& j = ctx->jobs[ids[i]];
+    const Model& m = ctx->models[j.model];
+    kind = j.kind;
+    p.tile_begin[i] = tiles;
+    p.job[i] = make_jobdev(ctx, j);
+    tiles += j.tiles;
+    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc);
+    if (b > smem) smem = b;
+  }
+  p.tile_begin[ids.size()] = tiles;
+  if (tiles == 0) return CRBM_OK;
+  CK(launch_step(kind, prec, p, tiles, smem, st), "kernel launch");
+  return CRBM_OK;
+}
+
+extern "C" {
+
+int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return CRBM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return CRBM_EINVAL;
+  crbm_ctx* ctx = new crbm_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    e = set_smem_limits((size_t)optin);
+  }
+  if (e != cudaSuccess) {
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return CRBM_ECUDA;
+  }
+  *out = ctx;
+  return CRBM_OK;
+}
+
+int crbm_destroy(crbm_ctx* ctx) {
+  if (!ctx) return CRBM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& m : ctx->models) {
+    if (m.d_f64) cudaFree(m.d_f64);
+    if (m.d_f32) cudaFree(m.d_f32);
+  }
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return CRBM_OK;
+}
+
+const char* crbm_last_error(const crbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, double v_bias,
+                    const double* h_bias, int* model_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (kind != kIsing && kind != kKitaev) return fail(ctx, CRBM_EINVAL, "unknown model kind %d", kind);
+  if (K < 1 || K > kMaxK) return fail(ctx, CRBM_EINVAL, "K=%d outside [1,%d]", K, kMaxK);
+  if (k < 1 || k > kMaxk) return fail(ctx, CRBM_EINVAL, "k=%d outside [1,%d]", k, kMaxk);
+  if (!W || !h_bias || !model_id) return fail(ctx, CRBM_EINVAL, "null pointer");
+  for (int i = 0; i < K * k * k; ++i)
+    if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Model m;
+  m.kind = kind;
+  m.K = K;
+  m.k = k;
+  m.vb = v_bias;
+  m.hb.assign(h_bias, h_bias + K);
+  // Row-sum tables: lut[f][a][code] = sum over set bits b of code of W[f][a][b],
+  // summed in increasing b (the FP64 order of every pre-activation); the
+  // backward table is indexed by the raw window of a hidden row, whose bit
+  // k-1-b is the unit seen through tap b.
+  const int T = 1 << k;
+  const size_t nlut = (size_t)K * k * T;
+  if (nlut > 4096) return fail(ctx, CRBM_EINVAL, "K*k*2^k = %zu exceeds 4096 table entries", nlut);
+  std::vector<double> fwd(nlut), bwd(nlut);
+  for (int f = 0; f < K; ++f)
+    for (int a = 0; a < k; ++a)
+      for (int c = 0; c < T; ++c) {
+        double s = 0.0;
+        for (int b = 0; b < k; ++b)
+          if ((c >> b) & 1) s += W[((size_t)f * k + a) * k + b];
+        fwd[((size_t)f * k + a) * T + c] = s;
+      }
+  for (int f = 0; f < K; ++f)
+    for (int a = 0; a < k; ++a)
+      for (int w = 0; w < T; ++w) {
+        int rev = 0;
+        for (int b = 0; b < k; ++b)
+          if ((w >> b) & 1) rev |= 1 << (k - 1 - b);
+        bwd[((size_t)f * k + a) * T + w] = fwd[((size_t)f * k + a) * T + rev];
+      }
+  // S_h, S_v: largest possible |partial sum| of a hidden / visible pre-activation
+  double sh = 0.0, sv = std::fabs(v_bias);
+  for (int f = 0; f < K; ++f) {
+    double sf = std::fabs(h_bias[f]);
+    for (int a = 0; a < k; ++a) {
+      double mx = 0.0;
+      for (int c = 0; c < T; ++c) mx = std::fmax(mx, std::fabs(fwd[((size_t)f * k + a) * T + c]));
+      sf += mx;
+      sv += mx;
+    }
+    sh = std::fmax(sh, sf);
+  }
+  // hi/lo split for the FP32 free energy: hi on a 2^-gbits grid such that every
+  // partial sum of hi terms is exact in FP32; lo = the FP32-rounded remainder.
+  const int gbits = 23 - (int)std::ceil(std::log2(std::fmax(sh, sv) + 1.0));
+  auto split = [&](double x, float& hi, float& lo) {
+    const double h = std::ldexp(std::nearbyint(std::ldexp(x, gbits)), -gbits);
+    hi = (float)h;
+    lo = (float)(x - h);
+  };
+  std::vector<float> t32(4 * nlut);
+  for (size_t i = 0; i < nlut; ++i) {
+    t32[i] = (float)fwd[i];
+    t32[nlut + i] = (float)bwd[i];
+    split(fwd[i], t32[2 * nlut + i], t32[3 * nlut + i]);
+  }
+  for (int f = 0; f < K; ++f) {
+    m.hb32[f] = (float)h_bias[f];
+    split(h_bias[f], m.hb_hi[f], m.hb_lo[f]);
+  }
+  m.vb32 = (float)v_bias;
+  // Certified FP32 error constants.  Assumed bounds of the special-function
+  // approximations (checked exhaustively on the device by the test-suite):
+  // ex2 relative 2^-22, rcp relative 2^-23, lg2 absolute 2^-22 on [1, 2].
+  const double u24 = std::ldexp(1.0, -24), ex2 = std::ldexp(1.0, -22), rcp = std::ldexp(1.0, -23),
+               lg2 = std::ldexp(1.0, -22);
+  // decisions: |p32 - p64| <= 0.25 ex2 + 2^-24 + rcp + |u32 - u| + 0.25 dx + 2^-25 |x|,
+  // dx <= (terms + 1) 2^-24 S; factor 2 of safety
+  const double common = 0.25 * ex2 + u24 + rcp + std::ldexp(1.0, -25) + std::ldexp(1.0, -33);
+  m.c0h = (float)(2.0 * (common + 0.25 * (k + 1) * u24 * sh) + 1e-14);
+  m.c0v = (float)(2.0 * (common + 0.25 * ((double)K * k + 1) * u24 * sv) + 1e-14);
+  m.c1 = (float)(2.0 * std::ldexp(1.0, -25));
+  // free energy, per softplus term: 0.5 ex2 + 2^-24 (1 + e) + ln2 lg2 + 2^-23 ln2
+  // (ln 2 product) + error of the FP32 sum of k + 1 lo terms; factor 1.5 of safety
+  const double lo1 = std::ldexp(1.0, -(gbits + 1));
+  const double elo = (k + 2) * u24 * (k + 1) * lo1;
+  m.csp = (float)(1.5 * (0.5 * ex2 + u24 + 0.69314718055994531 * lg2 + 0.7 * std::ldexp(1.0, -23)) + elo);
+  m.nlut = nlut;
+  CK(cudaMalloc(&m.d_f64, 2 * nlut * sizeof(double)), "cudaMalloc tables");
+  CK(cudaMalloc(&m.d_f32, 4 * nlut * sizeof(float)), "cudaMalloc tables");
+  CK(cudaMemcpy(m.d_f64, fwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
+  CK(cudaMemcpy(m.d_f64 + nlut, bwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
+  CK(cudaMemcpy(m.d_f32, t32.data(), 4 * nlut * sizeof(float), cudaMemcpyHostToDevice), "table copy");
+  m.live = true;
+  ctx->models.push_back(m);
+  *model_id = (int)ctx->models.size() - 1;
+  return CRBM_OK;
+}
+
+size_t crbm_job_bytes(int kind, int L, int n_chains, int precision) {
+  if (!valid_L(kind, L) || n_chains < 0 || (precision != CRBM_FP64 && precision != CRBM_MIXED)) return 0;
+  return make_layout(L, n_chains).total;
+}
+
+static int evaluate(crbm_ctx* ctx, int id) {
+  Job& j = ctx->jobs[id];
+  int rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, j.stream);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(j.stream), "evaluate");
+  return CRBM_OK;
+}
+
+int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const double* T,
+                     const double* J, uint64_t seed, uint64_t chain_id_base, int init,
+                     const uint32_t* init_bits, void* dev_mem, size_t dev_bytes, int* job_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (!job_id) return fail(ctx, CRBM_EINVAL, "null job_id");
+  if (model_id < 0 || model_id >= (int)ctx->models.size() || !ctx->models[model_id].live)
+    return fail(ctx, CRBM_EINVAL, "bad model id %d", model_id);
+  const Model& m = ctx->models[model_id];
+  if (!valid_L(m.kind, L)) return fail(ctx, CRBM_EINVAL, "lattice side L=%d not supported", L);
+  if (m.k > L) return fail(ctx, CRBM_EINVAL, "kernel side k=%d exceeds L=%d", m.k, L);
+  if (n_chains < 0) return fail(ctx, CRBM_EINVAL, "n_chains < 0");
+  if (chain_id_base + (uint64_t)n_chains > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "chain ids must stay below 2^32");
+  if (n_chains > 0 && (!T || !J)) return fail(ctx, CRBM_EINVAL, "null T or J");
+  if (init != 0 && init != 1) return fail(ctx, CRBM_EINVAL, "init must be 0 or 1");
+  if (init == 1 && n_chains > 0 && !init_bits) return fail(ctx, CRBM_EINVAL, "null init_bits");
+  for (int c = 0; c < n_chains; ++c)
+    if (!(T[c] > 0.0) || !std::isfinite(T[c])) return fail(ctx, CRBM_EINVAL, "temperature of chain %d not > 0", c);
+  const Layout lay = make_layout(L, n_chains);
+  if (n_chains > 0 && (!dev_mem || dev_bytes < lay.total))
+    return fail(ctx, CRBM_ENOMEM, "dev_mem holds %zu bytes, job needs %zu", dev_bytes, lay.total);
+  if (((uintptr_t)dev_mem & 255) != 0) return fail(ctx, CRBM_EINVAL, "dev_mem must be 256-byte aligned");
+  if (ctx->budget && ctx->used + lay.total > ctx->budget)
+    return fail(ctx, CRBM_ENOMEM, "job of %zu bytes exceeds the HBM budget (%zu of %zu used)", lay.total,
+                ctx->used, ctx->budget);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Job j;
+  j.live = true;
+  j.model = model_id;
+  j.kind = m.kind;
+  j.L = L;
+  j.N = L * L;
+  j.Wd = (j.N + 31) / 32;
+  j.n = n_chains;
+  j.nc = chains_per_tile(m.kind, L);
+  j.tiles = (n_chains + j.nc - 1) / j.nc;
+  if (m.kind == kIsing) {
+    j.J[0] = n_chains > 0 ? J[0] : 1.0;
+  } else if (n_chains > 0) {
+    for (int i = 0; i < 3; ++i) j.J[i] = J[i];
+  }
+  j.seed = seed;
+  j.cid_base = chain_id_base;
+  j.step = 0;
+  j.mem = (unsigned char*)dev_mem;
+  j.bytes = lay.total;
+  j.lay = lay;
+  j.stream = nullptr;
+  if (n_chains > 0) {
+    unsigned char* b = j.mem;
+    CK(cudaMemcpy(b + lay.T, T, (size_t)n_chains * 8, cudaMemcpyHostToDevice), "copy T");
+    if (init == 1)
+      CK(cudaMemcpy(b + lay.bits, init_bits, (size_t)n_chains * j.Wd * 4, cudaMemcpyHostToDevice), "copy init_bits");
+    else
+      CK(launch_random_init((uint32_t*)(b + lay.bits), n_chains, j.N, j.Wd, seed, chain_id_base, nullptr),
+         "random init");
+    CK(cudaMemset(b + lay.os, 0, (size_t)n_chains * 8 * kNobs), "zero sums");
+    CK(cudaMemset(b + lay.acc, 0, (size_t)n_chains * 8), "zero accepts");
+    CK(cudaMemset(b + lay.rec, 0, (size_t)n_chains * 8), "zero recomputes");
+  }
+  ctx->jobs.push_back(j);
+  const int id = (int)ctx->jobs.size() - 1;
+  if (n_chains > 0) {
+    const int rc = evaluate(ctx, id);
+    if (rc) {
+      ctx->jobs[id].live = false;
+      return rc;
+    }
+  }
+  ctx->used += lay.total;
+  *job_id = id;
+  return CRBM_OK;
+}
+
+static int check_run_args(crbm_ctx* ctx, int64_t S, int g, int correct, int precision) {
+  if (S < 0) return fail(ctx, CRBM_EINVAL, "S < 0");
+  if (g < 1 || g > 64) return fail(ctx, CRBM_EINVAL, "g=%d outside [1,64]", g);
+  if (correct != 0 && correct != 1) return fail(ctx, CRBM_EINVAL, "correct must be 0 or 1");
+  if (precision != CRBM_FP64 && precision != CRBM_MIXED) return fail(ctx, CRBM_EINVAL, "bad precision");
+  return CRBM_OK;
+}
+
+int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g, int correct,
+                   int precision, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  int rc = check_run_args(ctx, S, g, correct, precision);
+  if (rc) return rc;
+  if (n_jobs < 1 || n_jobs > kMaxJobs || !job_ids) return fail(ctx, CRBM_EINVAL, "n_jobs=%d outside [1,%d]", n_jobs, kMaxJobs);
+  std::vector<int> ids;
+  int kind = -1;
+  for (int i = 0; i < n_jobs; ++i) {
+    Job* j = get_job(ctx, job_ids[i]);
+    if (!j) return fail(ctx, CRBM_EINVAL, "bad job id %d", job_ids[i]);
+    for (int x : ids)
+      if (x == job_ids[i]) return fail(ctx, CRBM_EINVAL, "job %d listed twice", x);
+    if (kind >= 0 && j->kind != kind) return fail(ctx, CRBM_EINVAL, "jobs of different model kinds in one batch");
+    kind = j->kind;
+    if (j->step + (uint64_t)S > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
+    ids.push_back(job_ids[i]);
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t left = S;
+  while (left > 0) {
+    const int chunk = (int)(left < (1 << 20) ? left : (1 << 20));
+    rc = launch_jobs(ctx, ids, chunk, g, correct, precision, 0, st);
+    if (rc) return rc;
+    for (int id : ids) ctx->jobs[id].step += (uint64_t)chunk;
+    left -= chunk;
+  }
+  for (int id : ids) ctx->jobs[id].stream = st;
+  return CRBM_OK;
+}
+
+int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision, void* cuda_stream) {
+  return crbm_run_batch(ctx, 1, &job_id, S, g, correct, precision, cuda_stream);
+}
+
+int crbm_sync(crbm_ctx* ctx, int job_id) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(j->stream), "stream sync");
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+  if (h == kErrTimeout) return fail(ctx, CRBM_ETIMEOUT, "a device-side wait reached its iteration limit");
+  if (h != 0) return fail(ctx, CRBM_EINVAL, "device reported configuration error %d", h);
+  return CRBM_OK;
+}
+
+static int read_back(crbm_ctx* ctx, Job* j, void* dst, size_t off, size_t bytes) {
+  if (!dst || bytes == 0) return CRBM_OK;
+  CK(cudaMemcpy(dst, j->mem + off, bytes, cudaMemcpyDeviceToHost), "device to host copy");
+  return CRBM_OK;
+}
+
+int crbm_read_energies(crbm_ctx* ctx, int job_id, double* logpi, double* F_crbm, double* E_phys) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  int rc = crbm_sync(ctx, job_id);
+  if (rc) return rc;
+  const size_t b = (size_t)j->n * 8;
+  if ((rc = read_back(ctx, j, logpi, j->lay.lp, b))) return rc;
+  if ((rc = read_back(ctx, j, F_crbm, j->lay.F, b))) return rc;
+  return read_back(ctx, j, E_phys, j->lay.E, b);
+}
+
+int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int64_t* accepts, int64_t* recomputes) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  int rc = crbm_sync(ctx, job_id);
+  if (rc) return rc;
+  if ((rc = read_back(ctx, j, sums, j->lay.os, (size_t)j->n * 8 * kNobs))) return rc;
+  if ((rc = read_back(ctx, j, accepts, j->lay.acc, (size_t)j->n * 8))) return rc;
+  return read_back(ctx, j, recomputes, j->lay.rec, (size_t)j->n * 8);
+}
+
+int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  int rc = crbm_sync(ctx, job_id);
+  if (rc) return rc;
+  if (step) *step = j->step;
+  return read_back(ctx, j, bits, j->lay.bits, (size_t)j->n * j->Wd * 4);
+}
+
+int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  if (!bits && j->n > 0) return fail(ctx, CRBM_EINVAL, "null bits");
+  if (step >= (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step must stay below 2^32");
+  int rc = crbm_sync(ctx, job_id);
+  if (rc) return rc;
+  j->step = step;
+  if (j->n == 0) return CRBM_OK;
+  CK(cudaMemcpy(j->mem + j->lay.bits, bits, (size_t)j->n * j->Wd * 4, cudaMemcpyHostToDevice), "copy bits");
+  return evaluate(ctx, job_id);
+}
+
+int crbm_release(crbm_ctx* ctx, int job_id) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(j->stream), "stream sync");
+  ctx->used -= j->bytes;
+  j->live = false;
+  return CRBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,700 @@
+// Device-side building blocks of the CRBM proposal + Metropolis-Hastings step.
+//
+// Method: arXiv:2008.05401.  CRBM joint/free energy (Sec. II, Eqs. 12-13),
+// Gibbs conditionals (App. B.1, Eqs. B1-B4), acceptance (App. B.2, Eq. B5),
+// Ising energy (Sec. III, Eq. 14), Kitaev Majorana log-weight (Sec. IV,
+// Eq. 16 and the free energy that follows it).
+//
+// Data layout in shared memory (one chain):
+//   plane = ceil(L*L/32) + 1 uint32 words, site n = i*L + j is bit n%32 of
+//   word n/32, the extra word is padding read (and masked) by row extraction.
+//   Per chain: plane[0], plane[1] (current / proposed lattice, swapped on
+//   accept), K hidden planes.
+// Work unit: a block of 4 consecutive sites n = 4q..4q+3.  One Philox call
+// gives the 4 uniforms of a unit for one tag, so a unit is owned by one thread.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace crbm {
+
+constexpr int kMaxK = 8;
+constexpr int kMaxk = 7;
+constexpr int kMaxJobs = 16;
+constexpr int kNobs = 4;
+constexpr uint32_t kTagAcc = 0xFFFFFFFEu;
+constexpr uint32_t kTagInit = 0xFFFFFFFFu;
+constexpr int kIsing = 0;
+constexpr int kKitaev = 1;
+constexpr int kFP64 = 0;
+constexpr int kMixed = 1;
+constexpr int kThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+enum DevErr : int { kErrNone = 0, kErrConfig = 1, kErrTimeout = 2 };
+
+// Everything a kernel needs about one job; passed by value in the launch
+// parameters.  Pointers into the job's caller-owned device memory.
+struct JobDev {
+  int kind, L, N, Wd, P, K, k, n_chains, nc;
+  int pad0;
+  double vb;
+  double hb[kMaxK];
+  double J[3];
+  float vb32;
+  float hb32[kMaxK], hb_hi[kMaxK], hb_lo[kMaxK];
+  float c0h, c0v, c1, csp;      // FP32 error-bound constants (see host code)
+  const double* f64;            // [K][k][2^k] row-sum tables, see struct Tabs
+  const double* b64;
+  const float* fd;
+  const float* bd;
+  const float* fh;
+  const float* fl;
+  uint64_t seed, cid_base, step0;
+  uint32_t* bits;               // [n_chains][Wd]
+  const double* T;              // [n_chains]
+  double* F;                    // [n_chains]
+  double* Fb;                   // [n_chains] bound on |F - F_fp64| (0: exact)
+  double* logpi;                // [n_chains]
+  double* Ephys;                // [n_chains]
+  double* obs_t;                // [n_chains][4] observables of the current lattice
+  double* obs;                  // [n_chains][4] running sums
+  unsigned long long* acc;      // [n_chains]
+  unsigned long long* rec;      // [n_chains]
+};
+
+struct LaunchParams {
+  int n_jobs, S, g, correct, mode;   // mode 0: S proposals; 1: evaluate current state
+  int tile_begin[kMaxJobs + 1];
+  int* err;
+  JobDev job[kMaxJobs];
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): per round the counter words x0, x2
+// are multiplied (32x32 -> 64 bit) by M0, M1; the high halves are xored with
+// the other two words and the key; the key is bumped by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4& w, int t) {
+  return t == 0 ? w.x : (t == 1 ? w.y : (t == 2 ? w.z : w.w));
+}
+
+// ------------------------------------------------------- bit-row windows
+// w bits (w <= 12) of row r starting at column c (0 <= c < L), periodic in the
+// column: bit b of the result is site (r, (c + b) mod L).  Supports L <= 32
+// and L a multiple of 32.
+__device__ __forceinline__ uint32_t row_window(const uint32_t* __restrict__ bits, int L, int r,
+                                               int c, int w) {
+  uint32_t x;
+  if ((L & 31) == 0) {
+    const int WL = L >> 5, wi = c >> 5;
+    const int wn = (wi + 1 == WL) ? 0 : wi + 1;
+    x = __funnelshift_r(bits[r * WL + wi], bits[r * WL + wn], c & 31);
+  } else {
+    const int off = r * L;
+    const uint32_t row =
+        __funnelshift_r(bits[off >> 5], bits[(off >> 5) + 1], off & 31) & ((1u << L) - 1u);
+    uint64_t rr = row;
+    for (int s = L; s < 64; s += L) rr |= (uint64_t)row << s;
+    x = (uint32_t)(rr >> c);
+  }
+  return x & ((1u << w) - 1u);
+}
+
+__device__ __forceinline__ uint32_t site_bit(const uint32_t* bits, int n) {
+  return (bits[n >> 5] >> (n & 31)) & 1u;
+}
+
+// Forward codes of unit q (sites n = 4q..4q+3): m[t][a] = a*T + (bits of
+// sites (i_t + a, j_t + b), b = 0..k-1, as bit b) -- the offset of the
+// row-sum table entry of kernel row a for the receptive field of hidden unit
+// (i_t, j_t).  When L % 4 == 0 the 4 sites share a row and one window of
+// k + 3 bits per kernel row serves all of them.
+__device__ __forceinline__ void fwd_codes(const uint32_t* bits, int L, int N, int k, int T, int q,
+                                          uint32_t (&m)[4][kMaxk]) {
+  const uint32_t mk = (1u << k) - 1u;
+  if ((L & 3) == 0) {
+    const int n0 = 4 * q, i = n0 / L, j0 = n0 - i * L;
+#pragma unroll
+    for (int a = 0; a < kMaxk; ++a) {
+      if (a < k) {
+        int r = i + a;
+        if (r >= L) r -= L;
+        const uint32_t win = row_window(bits, L, r, j0, k + 3);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) m[t][a] = (uint32_t)(a * T) + ((win >> t) & mk);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int n = 4 * q + t;
+      if (n >= N) n = 0;
+      const int i = n / L, j = n - i * L;
+#pragma unroll
+      for (int a = 0; a < kMaxk; ++a) {
+        if (a < k) {
+          int r = i + a;
+          if (r >= L) r -= L;
+          m[t][a] = (uint32_t)(a * T) + row_window(bits, L, r, j, k);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------ Bernoulli decisions
+// FP64: h = [u < sigma(x)], u = (w + 1/2) 2^-32 exactly (App. B.1 sampling).
+__device__ __forceinline__ uint32_t decide64(double x, uint32_t w) {
+  const double p = 1.0 / (1.0 + exp(-x));
+  const double u = ((double)w + 0.5) * 0x1p-32;
+  return u < p ? 1u : 0u;
+}
+
+// Special-function-unit approximations (PTX ex2/rcp/lg2, flush-to-zero).
+// Their error bounds are part of the certified margins below and are checked
+// exhaustively on the device by the test-suite.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// sigma(x) in FP32: e = 2^(-x log2 e), p = 1/(1 + e).
+__device__ __forceinline__ float sigmoid32(float x) {
+  return rcp_approx(1.0f + ex2_approx(x * -1.4426950408889634f));
+}
+
+// FP32 decision with a certified margin: |p32 - p64| <= c0 + c1 |x| covers the
+// FP32 pre-activation error, the ex2/rcp errors, the conversion of the Philox
+// word, and the FP64 path's own rounding.  Returns 0/1 when the FP64 path
+// takes the same decision, 2 when the FP64 code has to decide.
+__device__ __forceinline__ uint32_t decide32(float x, uint32_t w, float c0, float c1) {
+  const float d = sigmoid32(x) - __uint2float_rn(w) * 0x1p-32f;
+  const float delta = fmaf(c1, fabsf(x), c0);
+  return d > delta ? 1u : (d < -delta ? 0u : 2u);
+}
+
+// log(1 + e^x) without overflow.
+__device__ __forceinline__ double softplus64(double x) {
+  return fmax(x, 0.0) + log1p(exp(-fabs(x)));
+}
+// FP32: max(x, 0) + ln 2 * log2(1 + 2^(-|x| log2 e)).
+__device__ __forceinline__ float softplus32(float x) {
+  const float e = ex2_approx(fabsf(x) * -1.4426950408889634f);
+  return fmaxf(x, 0.0f) + 0.69314718055994531f * lg2_approx(1.0f + e);
+}
+
+// Store the 4-bit result of unit q: 8 consecutive lanes own the 8 units of
+// one word and OR their nibbles together.  Every lane of the warp must call.
+__device__ __forceinline__ void store_nibble(uint32_t* plane, int q, uint32_t nib, bool act) {
+  uint32_t x = act ? (nib << (4 * (q & 7))) : 0u;
+  x |= __shfl_xor_sync(kFull, x, 1);
+  x |= __shfl_xor_sync(kFull, x, 2);
+  x |= __shfl_xor_sync(kFull, x, 4);
+  if (act && (q & 7) == 0) plane[q >> 3] = x;
+}
+
+// One chain's thread group: tpc threads (a power of two >= 8), rank r.
+struct Grp {
+  int c;          // chain index within the job
+  int gl;         // group index within the CTA
+  int r, tpc;
+  bool active;    // c < n_chains
+  uint32_t cid;   // chain id (Philox counter word 3)
+};
+
+// Deterministic sum of NV doubles over a chain's group; the result is valid in
+// the leader (r == 0).  Every thread of the CTA must call (it may sync).
+template <int NV>
+__device__ __forceinline__ void grp_reduce(double (&x)[NV], const Grp& g, double* scratch) {
+  const int span = g.tpc < 32 ? g.tpc : 32;
+  for (int o = 1; o < span; o <<= 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] += __shfl_xor_sync(kFull, x[v], o);
+  }
+  if (g.tpc > 32) {
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) scratch[warp * NV + v] = x[v];
+    }
+    __syncthreads();
+    if (g.r == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0;
+        for (int w = 0; w < g.tpc / 32; ++w) s += scratch[(warp + w) * NV + v];
+        x[v] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Deterministic block-wide sum, result returned to every thread.
+__device__ __forceinline__ double block_sum(double x, double* scratch) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) scratch[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += scratch[w];
+  __syncthreads();
+  return s;
+}
+
+// Row-sum tables of one model (index (f*k + a)*T + code, T = 2^k):
+//   f64/b64   FP64, forward code / raw backward window (FP64 path; global
+//             copies of them serve the mixed path's FP64 recomputes)
+//   fd/bd     FP32 roundings of f64/b64 (mixed-path decisions)
+//   fh/fl     hi/lo split of f64 (mixed-path free energy)
+struct Tabs {
+  const double* f64;
+  const double* b64;
+  const float* fd;
+  const float* bd;
+  const float* fh;
+  const float* fl;
+  int T;
+};
+
+// FP64 recomputes of the mixed path (rare; kept out of line so that the FP32
+// fast path keeps its registers).  Same tables (global copies), same order.
+static __device__ __noinline__ uint32_t recompute_hidden(const JobDev& jb, int f, const uint32_t* m, int k,
+                                                  int T, uint32_t w) {
+  double x = jb.hb[f];
+  const int base = f * k * T;
+  for (int a = 0; a < k; ++a) x += __ldg(jb.f64 + base + m[a]);
+  return decide64(x, w);
+}
+
+static __device__ __noinline__ uint32_t recompute_visible(const JobDev& jb, const uint32_t* h, int P, int n,
+                                                   uint32_t w);
+
+// ------------------------------------------------- hidden half-step
+// h^f_ij = [u < sigma(h_bias^f + sum_ab W^f_ab v_(i+a)(j+b))]  (Eq. B2, Eq. 12)
+// FP64 order (shared with the mixed path's recompute): h_bias, then kernel
+// rows a = 0..k-1.
+template <int PREC>
+__device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* v,
+                             uint32_t* h, int P, uint32_t step, int sub, unsigned& nrec) {
+  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  const int nblk = (N + 3) >> 2;
+  const int iters = (nblk + g.tpc - 1) / g.tpc;
+  const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
+  for (int it = 0; it < iters; ++it) {
+    const int q = g.r + it * g.tpc;
+    const bool act = g.active && q < nblk;
+    uint32_t m[4][kMaxk];
+    fwd_codes(v, L, N, k, T, act ? q : 0, m);
+    for (int f = 0; f < K; ++f) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + f), step, g.cid), k0, k1);
+      const int base = f * k * T;
+      uint32_t nib = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        uint32_t bit;
+        if (PREC == kFP64) {
+          double x = jb.hb[f];
+#pragma unroll
+          for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.f64[base + m[t][a]];
+          bit = decide64(x, pick(w, t));
+        } else {
+          float x = jb.hb32[f];
+#pragma unroll
+          for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.fd[base + m[t][a]];
+          bit = decide32(x, pick(w, t), jb.c0h, jb.c1);
+          if (bit == 2u) {
+            uint32_t mm[kMaxk];
+#pragma unroll
+            for (int a = 0; a < kMaxk; ++a) mm[a] = m[t][a];
+            bit = recompute_hidden(jb, f, mm, k, T, pick(w, t));
+            if (act && 4 * q + t < N) ++nrec;
+          }
+        }
+        if (act && 4 * q + t < N) nib |= bit << t;
+      }
+      store_nibble(h + f * P, q, nib, act);
+    }
+  }
+}
+
+// ------------------------------------------------- visible half-step
+// v'_ij = [u < sigma(v_bias + sum_f sum_ab W^f_ab h^f_(i-a)(j-b))]  (Eq. B3)
+// The window of hidden row i - a starting at column j - (k-1) holds, as bit
+// k-1-b, the unit h_(i-a)(j-b); the backward tables are indexed by that raw
+// window.  Order: v_bias, then kernel rows a, then filters f.
+__device__ __forceinline__ int bwd_row(int i, int a, int L) {
+  int r = i - a;
+  return r < 0 ? r + L : r;
+}
+
+template <int PREC>
+__device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* h,
+                              uint32_t* vp, int P, uint32_t step, int sub, unsigned& nrec) {
+  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  const uint32_t mk = (1u << k) - 1u;
+  const int nblk = (N + 3) >> 2;
+  const int iters = (nblk + g.tpc - 1) / g.tpc;
+  const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
+  const bool rows4 = (L & 3) == 0;
+  for (int it = 0; it < iters; ++it) {
+    const int q = g.r + it * g.tpc;
+    const bool act = g.active && q < nblk;
+    const int qq = act ? q : 0;
+    double x64[4];
+    float x32[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      x64[t] = jb.vb;
+      x32[t] = jb.vb32;
+    }
+    if (rows4) {
+      const int n0 = 4 * qq, i = n0 / L, j0 = n0 - i * L;
+      int c = j0 - (k - 1);
+      if (c < 0) c += L;
+      for (int a = 0; a < k; ++a) {
+        const int r = bwd_row(i, a, L);
+        for (int f = 0; f < K; ++f) {
+          const uint32_t win = row_window(h + f * P, L, r, c, k + 3);
+          const int base = (f * k + a) * T;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const uint32_t code = (win >> t) & mk;
+            if (PREC == kFP64) x64[t] += tb.b64[base + code];
+            else x32[t] += tb.bd[base + code];
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        int n = 4 * qq + t;
+        if (n >= N) n = 0;
+        const int i = n / L, j = n - i * L;
+        int c = j - (k - 1);
+        if (c < 0) c += L;
+        for (int a = 0; a < k; ++a) {
+          const int r = bwd_row(i, a, L);
+          for (int f = 0; f < K; ++f) {
+            const uint32_t code = row_window(h + f * P, L, r, c, k);
+            const int base = (f * k + a) * T;
+            if (PREC == kFP64) x64[t] += tb.b64[base + code];
+            else x32[t] += tb.bd[base + code];
+          }
+        }
+      }
+    }
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + K), step, g.cid), k0, k1);
+    uint32_t nib = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (act && 4 * q + t < N) {
+        uint32_t bit;
+        if (PREC == kFP64) {
+          bit = decide64(x64[t], pick(w, t));
+        } else {
+          bit = decide32(x32[t], pick(w, t), jb.c0v, jb.c1);
+          if (bit == 2u) {
+            bit = recompute_visible(jb, h, P, 4 * q + t, pick(w, t));
+            ++nrec;
+          }
+        }
+        nib |= bit << t;
+      }
+    }
+    store_nibble(vp, q, nib, act);
+  }
+}
+
+// This site's pre-activation with the FP64 tables, in the FP64 path's order.
+static __device__ __noinline__ uint32_t recompute_visible(const JobDev& jb, const uint32_t* h, int P, int n,
+                                                   uint32_t w) {
+  const int L = jb.L, K = jb.K, k = jb.k, T = 1 << k;
+  const int i = n / L, j = n - i * L;
+  int c = j - (k - 1);
+  if (c < 0) c += L;
+  double x = jb.vb;
+  for (int a = 0; a < k; ++a) {
+    const int r = bwd_row(i, a, L);
+    for (int f = 0; f < K; ++f) x += __ldg(jb.b64 + (f * k + a) * T + row_window(h + f * P, L, r, c, k));
+  }
+  return decide64(x, w);
+}
+
+// ------------------------------------------------- free energy + lattice sums
+// F(v) = -v_bias sum v - sum_{f,i,j} softplus(h_bias^f + (W^f * v)_ij)   (Eq. 13)
+// Per-thread partial sums: out[0] = sum softplus (FP64 order, or FP32 with
+// Kahan compensation), out[1] = data part of the FP32 error bound (mixed),
+// out[2] = number of ones, out[3] = number of unequal nearest-neighbour pairs
+// (Ising) or of hexagons with flux -1 (Kitaev).
+template <int PREC>
+__device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* v,
+                           double (&out)[4]) {
+  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  const int nblk = (N + 3) >> 2;
+  const int iters = (nblk + g.tpc - 1) / g.tpc;
+  double s64 = 0.0;
+  float s32 = 0.0f, c32 = 0.0f, sabs = 0.0f, ssp = 0.0f;
+  int ones = 0, pairs = 0;
+  for (int it = 0; it < iters; ++it) {
+    const int q = g.r + it * g.tpc;
+    const bool act = g.active && q < nblk;
+    if (!act) continue;
+    uint32_t m[4][kMaxk];
+    fwd_codes(v, L, N, k, T, q, m);
+    for (int f = 0; f < K; ++f) {
+      const int base = f * k * T;
+      if (PREC == kFP64) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (4 * q + t < N) {
+            double x = jb.hb[f];
+#pragma unroll
+            for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.f64[base + m[t][a]];
+            s64 += softplus64(x);
+          }
+        }
+      } else {
+        float sp[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          sp[t] = 0.0f;
+          if (4 * q + t < N) {
+            float xh = jb.hb_hi[f], xl = jb.hb_lo[f];
+#pragma unroll
+            for (int a = 0; a < kMaxk; ++a) {
+              if (a < k) {
+                xh += tb.fh[base + m[t][a]];
+                xl += tb.fl[base + m[t][a]];
+              }
+            }
+            const float x = xh + xl;
+            sp[t] = softplus32(x);
+            sabs += fabsf(x);
+          }
+        }
+        const float us = (sp[0] + sp[1]) + (sp[2] + sp[3]);
+        ssp += us;
+        const float y = us - c32;          // Kahan summation of the unit sums
+        const float tt = s32 + y;
+        c32 = (tt - s32) - y;
+        s32 = tt;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int n = 4 * q + t;
+      if (n < N) {
+        const int i = n / L, j = n - i * L;
+        const uint32_t b0 = site_bit(v, n);
+        ones += (int)b0;
+        if (jb.kind == kIsing) {
+          const uint32_t c0 = m[t][0] - 0u, c1 = (k >= 2) ? m[t][1] - (uint32_t)T : 0u;
+          const uint32_t right = (k >= 2) ? ((c0 >> 1) & 1u) : site_bit(v, i * L + (j + 1 == L ? 0 : j + 1));
+          const uint32_t down = (k >= 2) ? (c1 & 1u) : site_bit(v, (i + 1 == L ? 0 : i + 1) * L + j);
+          pairs += (int)(b0 ^ right) + (int)(b0 ^ down);
+        } else {
+          // the hexagon of cell r holds the z-bonds r and r - e1 + e2
+          const int i2 = (i == 0) ? L - 1 : i - 1, j2 = (j + 1 == L) ? 0 : j + 1;
+          pairs += (int)(b0 ^ site_bit(v, i2 * L + j2));
+        }
+      }
+    }
+  }
+  if (PREC == kFP64) {
+    out[0] = s64;
+    out[1] = 0.0;
+  } else {
+    out[0] = (double)s32;
+    // x rounding + ex2 argument: 2^-23 |x|; pairwise, Kahan and final add: 6 2^-24 sp;
+    // 1.001 covers the FP32 accumulation of these two sums themselves
+    out[1] = ((double)sabs * 0x1p-23 + (double)ssp * (6.0 * 0x1p-24)) * 1.001;
+  }
+  out[2] = (double)ones;
+  out[3] = (double)pairs;
+}
+
+// --------------------------------------------------- Kitaev log-weight
+// FP64 eigen-stage for one lattice by the whole CTA.  A = M^T M (Sec. IV,
+// M_bw = 2 J_a u_bw) is reduced to tridiagonal form by Householder
+// reflections, its eigenvalues mu_l = eps_l^2 are found by bisection with
+// Sturm counts, and log pi = sum_l log 2cosh(beta eps_l / 2).
+struct KitaevWork {
+  double* A;       // N x (N+1)
+  double* d;       // N
+  double* e;       // N
+  double* vv;      // N
+  double* pw;      // N
+  double* sc;      // 64 doubles
+};
+
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int N, double x) {
+  // sign changes of p_{-1}=1, p_0, ..., p_{N-1}; p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}
+  double pp = 1.0, p = d[0] - x;
+  bool sprev = false;                       // sign of p_{-1} (positive)
+  bool s = (p == 0.0) ? !sprev : (p < 0.0);
+  int cnt = (s != sprev);
+  sprev = s;
+  for (int i = 1; i < N; ++i) {
+    double pn = fma(-e2[i - 1], pp, (d[i] - x) * p);
+    pp = p;
+    p = pn;
+    s = (p == 0.0) ? !sprev : (p < 0.0);
+    cnt += (s != sprev);
+    sprev = s;
+    const double ap = fabs(p);
+    if (ap > 0x1p+500) {
+      p *= 0x1p-500;
+      pp *= 0x1p-500;
+    } else if (ap < 0x1p-500 && fabs(pp) < 0x1p-500) {
+      p *= 0x1p+500;
+      pp *= 0x1p+500;
+    }
+  }
+  return cnt;
+}
+
+__device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
+                               const KitaevWork& wk, double (&res)[3]) {
+  const int N = L * L, lda = N + 1, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double* A = wk.A;
+  const double tx = 2.0 * J[0], ty = 2.0 * J[1], tz = 2.0 * J[2];
+  // A = M^T M, row w accumulated in a fixed order (z, x, y bond of w, then the
+  // three whites of that black site)
+  for (int w = tid; w < N; w += nt) {
+    double* row = A + (size_t)w * lda;
+    for (int c = 0; c < N; ++c) row[c] = 0.0;
+    const int i = w / L, j = w - i * L;
+    for (int typ = 0; typ < 3; ++typ) {
+      int bi = i, bj = j;
+      if (typ == 1) bi = (i == 0) ? L - 1 : i - 1;
+      if (typ == 2) bj = (j == 0) ? L - 1 : j - 1;
+      const int b = bi * L + bj;
+      const double mz = site_bit(v, b) ? tz : -tz;
+      const double mw = (typ == 0) ? mz : (typ == 1 ? tx : ty);
+      const int wz = b;
+      const int wx = ((bi + 1 == L) ? 0 : bi + 1) * L + bj;
+      const int wy = bi * L + ((bj + 1 == L) ? 0 : bj + 1);
+      row[wz] += mw * mz;
+      row[wx] += mw * tx;
+      row[wy] += mw * ty;
+    }
+  }
+  __syncthreads();
+  // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1
+  for (int j = 0; j < N - 2; ++j) {
+    const int m = N - j - 1;
+    double s = 0.0;
+    for (int i = j + 2 + tid; i < N; i += nt) {
+      const double a = A[(size_t)i * lda + j];
+      s += a * a;
+    }
+    s = block_sum(s, wk.sc);
+    const double x0 = A[(size_t)(j + 1) * lda + j];
+    if (tid == 0) wk.d[j] = A[(size_t)j * lda + j];
+    if (s == 0.0) {
+      if (tid == 0) wk.e[j] = x0;
+      __syncthreads();
+      continue;
+    }
+    const double nrm = sqrt(x0 * x0 + s);
+    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double tau = 2.0 / (v0 * v0 + s);
+    if (tid == 0) wk.e[j] = alpha;
+    for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[(size_t)(j + 1 + l) * lda + j];
+    __syncthreads();
+    // p = tau * A22 v, one warp per row
+    for (int l = warp; l < m; l += nw) {
+      const double* row = A + (size_t)(j + 1 + l) * lda + (j + 1);
+      double acc = 0.0;
+      for (int c = lane; c < m; c += 32) acc = fma(row[c], wk.vv[c], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      if (lane == 0) wk.pw[l] = tau * acc;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int l = tid; l < m; l += nt) pv = fma(wk.pw[l], wk.vv[l], pv);
+    pv = block_sum(pv, wk.sc);
+    const double Kc = 0.5 * tau * pv;
+    for (int l = tid; l < m; l += nt) wk.pw[l] = fma(-Kc, wk.vv[l], wk.pw[l]);
+    __syncthreads();
+    // A22 -= v w^T + w v^T
+    for (int l = warp; l < m; l += nw) {
+      double* row = A + (size_t)(j + 1 + l) * lda + (j + 1);
+      const double vl = wk.vv[l], wl = wk.pw[l];
+      for (int c = lane; c < m; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    wk.d[N - 2] = A[(size_t)(N - 2) * lda + (N - 2)];
+    wk.d[N - 1] = A[(size_t)(N - 1) * lda + (N - 1)];
+    wk.e[N - 2] = A[(size_t)(N - 1) * lda + (N - 2)];
+    wk.e[N - 1] = 0.0;
+    // Gershgorin interval
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < N; ++i) {
+      const double r = fabs(wk.e[i]) + (i > 0 ? fabs(wk.e[i - 1]) : 0.0);
+      lo = fmin(lo, wk.d[i] - r);
+      hi = fmax(hi, wk.d[i] + r);
+    }
+    wk.sc[0] = lo;
+    wk.sc[1] = hi;
+  }
+  __syncthreads();
+  // squared off-diagonals for the Sturm recurrence (reuse vv)
+  for (int i = tid; i < N; i += nt) wk.vv[i] = wk.e[i] * wk.e[i];
+  const double glo = wk.sc[0], ghi = wk.sc[1];
+  __syncthreads();
+  const double tol_abs = 1e-15 * fmax(ghi - glo, 1e-300);
+  double lp = 0.0, en = 0.0, cf = 0.0;
+  for (int idx = tid; idx < N; idx += nt) {
+    double lo = glo, hi = ghi;
+    for (int itn = 0; itn < 200; ++itn) {
+      const double mid = 0.5 * (lo + hi);
+      if (hi - lo <= fmax(tol_abs, 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(wk.d, wk.vv, N, mid) > idx) hi = mid; else lo = mid;
+    }
+    const double mu = fmax(0.5 * (lo + hi), 0.0);
+    const double eps = sqrt(mu);
+    const double x = 0.5 * beta * eps;
+    const double qx = exp(-2.0 * x);
+    lp += x + log1p(qx);                                   // log 2cosh x
+    en += -0.5 * eps * (1.0 - qx) / (1.0 + qx);            // -(eps/2) tanh x
+    cf += x * x * 4.0 * qx / ((1.0 + qx) * (1.0 + qx));    // x^2 sech^2 x
+  }
+  res[0] = block_sum(lp, wk.sc);
+  res[1] = block_sum(en, wk.sc);
+  res[2] = block_sum(cf, wk.sc);
+}
+
+}  // namespace crbm

@@ -1,0 +1,20 @@
+// Host-side entry points into the kernels of crbm_kernels.cu.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace crbm {
+struct LaunchParams;
+
+// Dynamic shared memory of one CTA of the fused kernel.
+size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc);
+// Launch the fused kernel: grid = total tiles of all jobs in p.
+cudaError_t launch_step(int kind, int prec, const LaunchParams& p, int grid, size_t smem,
+                        cudaStream_t st);
+// Raise the dynamic shared-memory limit of every fused-kernel instantiation.
+cudaError_t set_smem_limits(size_t bytes);
+// Random initial lattices (init tag of the stream).
+cudaError_t launch_random_init(uint32_t* bits, int n_chains, int N, int Wd, uint64_t seed,
+                               uint64_t cid_base, cudaStream_t st);
+}  // namespace crbm
