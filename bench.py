@@ -179,6 +179,46 @@ def run_reference(args, spec):
     print(json.dumps(line), flush=True)
 
 
+def time_jobs(ctx, jobs, S, prec, steps, warmup, stream, dev, flush):
+    """Device time (ms) of `steps` batched launches, L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
+    """Proposals/s of another workload or precision (no e2e, no clocks)."""
+    from paper_2008_05401_gb300 import MIXED
+    spec = workload(name)
+    ctx = ctx_cls(dev)
+    W, hb, vb = spec["model"]
+    mid = ctx.load_model(spec["kind"], W, vb, hb)
+    jobs, base = [], 0
+    for L, n in spec["jobs"]:
+        jobs.append(ctx.new_job(mid, spec["kind"], L, spec["T"](n), spec["J"], SEED, base,
+                                wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec))
+        base += n
+    ms = time_jobs(ctx, jobs, spec["S"], prec, steps, 1, stream, dev, flush)
+    n_chains = sum(n for _, n in spec["jobs"])
+    sums = [j.observables() for j in jobs]
+    acc = sum(int(a.sum()) for _, a, _ in sums) / (n_chains * spec["S"] * (steps + 1))
+    rec = sum(int(r.sum()) for _, _, r in sums)
+    ctx.close()
+    return {"workload": spec["desc"], "precision": "mixed" if prec == MIXED else "fp64",
+            "value": n_chains * spec["S"] * steps / (ms * 1e-3), "unit": "proposals/s",
+            "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
+            "fp64_recomputes": rec}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +231,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="override chains per lattice size (profiling)")
     ap.add_argument("--Ls", default="", help="comma list restricting the lattice sizes (profiling)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the FP64-path and Kitaev lines")
     args = ap.parse_args()
     spec = workload(args.workload)
     if args.Ls:
@@ -289,6 +330,16 @@ def main():
                        "parallelism": f"chains x{world}"},
             "roofline": roofline(spec, total_ms / args.steps, clocks, K, k, sites),
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+    sums = [j.observables() for j in jobs]
+    line["config"]["acceptance"] = sum(int(a.sum()) for _, a, _ in sums) / max(1, n_chains * jobs[0].step)
+    line["config"]["fp64_recomputes_per_proposal"] = sum(int(r.sum()) for _, _, r in sums) / max(
+        1, n_chains * jobs[0].step)
+    if rank == 0 and not args.no_secondary and args.workload == "ising-batch":
+        line["secondary"] = [
+            secondary(Context, "ising-batch", FP64, 2, dev, stream, flush),
+            secondary(Context, "kitaev-small", FP64, 3, dev, stream, flush),
+            secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush)]
+        line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(spec)
     if rank == 0:

@@ -125,10 +125,11 @@ CRBM_API int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, 
 CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision,
              void* cuda_stream);
 
-/* As crbm_run for n_jobs jobs of the same model kind in ONE kernel launch
- * (chains of different L and temperature side by side).  Each job keeps its
- * own step counter and random streams, so its result equals a crbm_run of
- * that job alone.  At most 16 jobs per call; a job may appear once. */
+/* As crbm_run for n_jobs jobs in ONE kernel launch (chains of different L and
+ * temperature side by side).  The jobs must share the model kind and the
+ * filter-bank shape (K, k); their models may differ.  Each job keeps its own
+ * step counter and random streams, so its result equals a crbm_run of that
+ * job alone.  At most 16 jobs per call; a job may appear once. */
 CRBM_API int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g,
                    int correct, int precision, void* cuda_stream);
 

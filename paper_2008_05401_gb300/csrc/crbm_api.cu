@@ -23,7 +23,8 @@ struct Model {
   std::vector<double> hb;
   double* d_f64 = nullptr;   // forward FP64 row-sum table, then the backward one
   float* d_f32 = nullptr;    // fd, bd, fh, fl
-  size_t nlut = 0;
+  float4* d_q = nullptr;     // fd4, fh4, fl4 (filter-interleaved, K <= 4)
+  size_t nlut = 0, nq = 0;
   float hb32[kMaxK] = {}, hb_hi[kMaxK] = {}, hb_lo[kMaxK] = {};
   float vb32 = 0.f;
   float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f;
@@ -150,6 +151,9 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.bd = m.d_f32 + m.nlut;
   d.fh = m.d_f32 + 2 * m.nlut;
   d.fl = m.d_f32 + 3 * m.nlut;
+  d.fd4 = m.d_q;
+  d.fh4 = m.d_q + m.nq;
+  d.fl4 = m.d_q + 2 * m.nq;
   d.seed = j.seed;
   d.cid_base = j.cid_base;
   d.step0 = j.step;
@@ -179,7 +183,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
   p.mode = mode;
   p.err = ctx->d_err;
   size_t smem = 0;
-  int tiles = 0, kind = -1;
+  int tiles = 0, kind = -1, K = 0, k = 0;
   for (size_t i = 0; i < ids.size(); ++i) {
     const Job& j = ctx->jobs[ids[i]];
     const Model& m = ctx->models[j.model];
@@ -187,12 +191,16 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
     p.tile_begin[i] = tiles;
     p.job[i] = make_jobdev(ctx, j);
     tiles += j.tiles;
-    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc);
+    int KC, kC;
+    specialisation(m.K, m.k, KC, kC);
+    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, KC);
     if (b > smem) smem = b;
+    K = m.K;
+    k = m.k;
   }
   p.tile_begin[ids.size()] = tiles;
   if (tiles == 0) return CRBM_OK;
-  CK(launch_step(kind, prec, p, tiles, smem, st), "kernel launch");
+  CK(launch_step(kind, prec, K, k, p, tiles, smem, st), "kernel launch");
   return CRBM_OK;
 }
 
@@ -230,6 +238,7 @@ int crbm_destroy(crbm_ctx* ctx) {
   for (auto& m : ctx->models) {
     if (m.d_f64) cudaFree(m.d_f64);
     if (m.d_f32) cudaFree(m.d_f32);
+    if (m.d_q) cudaFree(m.d_q);
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -325,7 +334,22 @@ int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, doub
   const double lo1 = std::ldexp(1.0, -(gbits + 1));
   const double elo = (k + 2) * u24 * (k + 1) * lo1;
   m.csp = (float)(1.5 * (0.5 * ex2 + u24 + 0.69314718055994531 * lg2 + 0.7 * std::ldexp(1.0, -23)) + elo);
+  // filter-interleaved copies (entry (a*T + code)*4 + f), zero for f >= K
+  const size_t nq = (size_t)k * T;
+  std::vector<float> q4(3 * nq * 4, 0.0f);
+  if (K <= 4) {
+    for (int f = 0; f < K; ++f)
+      for (size_t e = 0; e < nq; ++e) {
+        const size_t src = (size_t)f * nq + e;
+        q4[(0 * nq + e) * 4 + f] = t32[src];
+        q4[(1 * nq + e) * 4 + f] = t32[2 * nlut + src];
+        q4[(2 * nq + e) * 4 + f] = t32[3 * nlut + src];
+      }
+  }
   m.nlut = nlut;
+  m.nq = nq;
+  CK(cudaMalloc(&m.d_q, 3 * nq * sizeof(float4)), "cudaMalloc tables");
+  CK(cudaMemcpy(m.d_q, q4.data(), 3 * nq * sizeof(float4), cudaMemcpyHostToDevice), "table copy");
   CK(cudaMalloc(&m.d_f64, 2 * nlut * sizeof(double)), "cudaMalloc tables");
   CK(cudaMalloc(&m.d_f32, 4 * nlut * sizeof(float)), "cudaMalloc tables");
   CK(cudaMemcpy(m.d_f64, fwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
@@ -438,14 +462,19 @@ int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int
   if (rc) return rc;
   if (n_jobs < 1 || n_jobs > kMaxJobs || !job_ids) return fail(ctx, CRBM_EINVAL, "n_jobs=%d outside [1,%d]", n_jobs, kMaxJobs);
   std::vector<int> ids;
-  int kind = -1;
+  int kind = -1, Kb = 0, kb = 0;
   for (int i = 0; i < n_jobs; ++i) {
     Job* j = get_job(ctx, job_ids[i]);
     if (!j) return fail(ctx, CRBM_EINVAL, "bad job id %d", job_ids[i]);
     for (int x : ids)
       if (x == job_ids[i]) return fail(ctx, CRBM_EINVAL, "job %d listed twice", x);
     if (kind >= 0 && j->kind != kind) return fail(ctx, CRBM_EINVAL, "jobs of different model kinds in one batch");
+    const Model& mj = ctx->models[j->model];
+    if (kind >= 0 && (mj.K != Kb || mj.k != kb))
+      return fail(ctx, CRBM_EINVAL, "jobs of one batch must share the filter-bank shape (K, k)");
     kind = j->kind;
+    Kb = mj.K;
+    kb = mj.k;
     if (j->step + (uint64_t)S > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
     ids.push_back(job_ids[i]);
   }

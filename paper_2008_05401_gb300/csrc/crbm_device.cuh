@@ -50,6 +50,9 @@ struct JobDev {
   const float* bd;
   const float* fh;
   const float* fl;
+  const float4* fd4;            // [k][2^k] filter-interleaved, K <= 4
+  const float4* fh4;
+  const float4* fl4;
   uint64_t seed, cid_base, step0;
   uint32_t* bits;               // [n_chains][Wd]
   const double* T;              // [n_chains]
@@ -120,15 +123,17 @@ __device__ __forceinline__ uint32_t site_bit(const uint32_t* bits, int n) {
 // sites (i_t + a, j_t + b), b = 0..k-1, as bit b) -- the offset of the
 // row-sum table entry of kernel row a for the receptive field of hidden unit
 // (i_t, j_t).  When L % 4 == 0 the 4 sites share a row and one window of
-// k + 3 bits per kernel row serves all of them.
+// k + 3 bits per kernel row serves all of them.  kC > 0 fixes k at compile time.
+template <int kC>
 __device__ __forceinline__ void fwd_codes(const uint32_t* bits, int L, int N, int k, int T, int q,
-                                          uint32_t (&m)[4][kMaxk]) {
+                                          uint32_t (&m)[4][kC ? kC : kMaxk]) {
+  constexpr int kU = kC ? kC : kMaxk;
   const uint32_t mk = (1u << k) - 1u;
   if ((L & 3) == 0) {
     const int n0 = 4 * q, i = n0 / L, j0 = n0 - i * L;
 #pragma unroll
-    for (int a = 0; a < kMaxk; ++a) {
-      if (a < k) {
+    for (int a = 0; a < kU; ++a) {
+      if (kC || a < k) {
         int r = i + a;
         if (r >= L) r -= L;
         const uint32_t win = row_window(bits, L, r, j0, k + 3);
@@ -143,8 +148,8 @@ __device__ __forceinline__ void fwd_codes(const uint32_t* bits, int L, int N, in
       if (n >= N) n = 0;
       const int i = n / L, j = n - i * L;
 #pragma unroll
-      for (int a = 0; a < kMaxk; ++a) {
-        if (a < k) {
+      for (int a = 0; a < kU; ++a) {
+        if (kC || a < k) {
           int r = i + a;
           if (r >= L) r -= L;
           m[t][a] = (uint32_t)(a * T) + row_window(bits, L, r, j, k);
@@ -272,6 +277,9 @@ __device__ __forceinline__ double block_sum(double x, double* scratch) {
 //             copies of them serve the mixed path's FP64 recomputes)
 //   fd/bd     FP32 roundings of f64/b64 (mixed-path decisions)
 //   fh/fl     hi/lo split of f64 (mixed-path free energy)
+//   fd4/fh4/fl4  the same forward tables with the filter index innermost,
+//             (a*T + code)*4 + f, for K <= 4 (zero-padded): one 16-byte load
+//             serves all filters of a site
 struct Tabs {
   const double* f64;
   const double* b64;
@@ -279,38 +287,101 @@ struct Tabs {
   const float* bd;
   const float* fh;
   const float* fl;
+  const float4* fd4;
+  const float4* fh4;
+  const float4* fl4;
   int T;
 };
+
+__device__ __forceinline__ float comp(const float4& v, int f) {
+  return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
+}
 
 // FP64 recomputes of the mixed path (rare; kept out of line so that the FP32
 // fast path keeps its registers).  Same tables (global copies), same order.
 static __device__ __noinline__ uint32_t recompute_hidden(const JobDev& jb, int f, const uint32_t* m, int k,
-                                                  int T, uint32_t w) {
+                                                         int T, uint32_t w) {
   double x = jb.hb[f];
   const int base = f * k * T;
   for (int a = 0; a < k; ++a) x += __ldg(jb.f64 + base + m[a]);
   return decide64(x, w);
 }
 
+__device__ __forceinline__ int bwd_row(int i, int a, int L) {
+  int r = i - a;
+  return r < 0 ? r + L : r;
+}
+
+// This site's visible pre-activation with the FP64 tables, in the FP64 path's order.
 static __device__ __noinline__ uint32_t recompute_visible(const JobDev& jb, const uint32_t* h, int P, int n,
-                                                   uint32_t w);
+                                                          uint32_t w) {
+  const int L = jb.L, K = jb.K, k = jb.k, T = 1 << k;
+  const int i = n / L, j = n - i * L;
+  int c = j - (k - 1);
+  if (c < 0) c += L;
+  double x = jb.vb;
+  for (int a = 0; a < k; ++a) {
+    const int r = bwd_row(i, a, L);
+    for (int f = 0; f < K; ++f) x += __ldg(jb.b64 + (f * k + a) * T + row_window(h + f * P, L, r, c, k));
+  }
+  return decide64(x, w);
+}
 
 // ------------------------------------------------- hidden half-step
 // h^f_ij = [u < sigma(h_bias^f + sum_ab W^f_ab v_(i+a)(j+b))]  (Eq. B2, Eq. 12)
 // FP64 order (shared with the mixed path's recompute): h_bias, then kernel
-// rows a = 0..k-1.
-template <int PREC>
+// rows a = 0..k-1.  KC, kC > 0 fix K and k at compile time (0: runtime).
+template <int PREC, int KC, int kC>
 __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* v,
                              uint32_t* h, int P, uint32_t step, int sub, unsigned& nrec) {
-  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  constexpr int kU = kC ? kC : kMaxk;
+  const int L = jb.L, N = jb.N, K = KC ? KC : jb.K, k = kC ? kC : jb.k, T = tb.T;
   const int nblk = (N + 3) >> 2;
   const int iters = (nblk + g.tpc - 1) / g.tpc;
   const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
   for (int it = 0; it < iters; ++it) {
     const int q = g.r + it * g.tpc;
     const bool act = g.active && q < nblk;
-    uint32_t m[4][kMaxk];
-    fwd_codes(v, L, N, k, T, act ? q : 0, m);
+    uint32_t m[4][kU];
+    fwd_codes<kC>(v, L, N, k, T, act ? q : 0, m);
+    if (PREC == kMixed && KC == 4) {
+      // all four filters per site from the filter-interleaved table
+      uint4 w[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        w[f] = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * 5 + f), step, g.cid), k0, k1);
+      uint32_t nib[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float4 x = make_float4(jb.hb32[0], jb.hb32[1], jb.hb32[2], jb.hb32[3]);
+#pragma unroll
+        for (int a = 0; a < kU; ++a) {
+          if (kC || a < k) {
+            const float4 e = tb.fd4[m[t][a]];
+            x.x += e.x;
+            x.y += e.y;
+            x.z += e.z;
+            x.w += e.w;
+          }
+        }
+        const bool site = act && 4 * q + t < N;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          uint32_t bit = decide32(comp(x, f), pick(w[f], t), jb.c0h, jb.c1);
+          if (bit == 2u) {
+            uint32_t mm[kMaxk];
+#pragma unroll
+            for (int a = 0; a < kU; ++a) mm[a] = m[t][a];
+            bit = recompute_hidden(jb, f, mm, k, T, pick(w[f], t));
+            if (site) ++nrec;
+          }
+          if (site) nib[f] |= bit << t;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) store_nibble(h + f * P, q, nib[f], act);
+      continue;
+    }
     for (int f = 0; f < K; ++f) {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + f), step, g.cid), k0, k1);
       const int base = f * k * T;
@@ -321,17 +392,17 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
         if (PREC == kFP64) {
           double x = jb.hb[f];
 #pragma unroll
-          for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.f64[base + m[t][a]];
+          for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
           bit = decide64(x, pick(w, t));
         } else {
           float x = jb.hb32[f];
 #pragma unroll
-          for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.fd[base + m[t][a]];
+          for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.fd[base + m[t][a]];
           bit = decide32(x, pick(w, t), jb.c0h, jb.c1);
           if (bit == 2u) {
             uint32_t mm[kMaxk];
 #pragma unroll
-            for (int a = 0; a < kMaxk; ++a) mm[a] = m[t][a];
+            for (int a = 0; a < kU; ++a) mm[a] = m[t][a];
             bit = recompute_hidden(jb, f, mm, k, T, pick(w, t));
             if (act && 4 * q + t < N) ++nrec;
           }
@@ -348,15 +419,12 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
 // The window of hidden row i - a starting at column j - (k-1) holds, as bit
 // k-1-b, the unit h_(i-a)(j-b); the backward tables are indexed by that raw
 // window.  Order: v_bias, then kernel rows a, then filters f.
-__device__ __forceinline__ int bwd_row(int i, int a, int L) {
-  int r = i - a;
-  return r < 0 ? r + L : r;
-}
-
-template <int PREC>
+template <int PREC, int KC, int kC>
 __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* h,
                               uint32_t* vp, int P, uint32_t step, int sub, unsigned& nrec) {
-  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  constexpr int kU = kC ? kC : kMaxk;
+  constexpr int KU = KC ? KC : kMaxK;
+  const int L = jb.L, N = jb.N, K = KC ? KC : jb.K, k = kC ? kC : jb.k, T = tb.T;
   const uint32_t mk = (1u << k) - 1u;
   const int nblk = (N + 3) >> 2;
   const int iters = (nblk + g.tpc - 1) / g.tpc;
@@ -377,16 +445,22 @@ __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, co
       const int n0 = 4 * qq, i = n0 / L, j0 = n0 - i * L;
       int c = j0 - (k - 1);
       if (c < 0) c += L;
-      for (int a = 0; a < k; ++a) {
-        const int r = bwd_row(i, a, L);
-        for (int f = 0; f < K; ++f) {
-          const uint32_t win = row_window(h + f * P, L, r, c, k + 3);
-          const int base = (f * k + a) * T;
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const uint32_t code = (win >> t) & mk;
-            if (PREC == kFP64) x64[t] += tb.b64[base + code];
-            else x32[t] += tb.bd[base + code];
+      for (int a = 0; a < kU; ++a) {
+        if (kC || a < k) {
+          const int r = bwd_row(i, a, L);
+#pragma unroll
+          for (int f = 0; f < KU; ++f) {
+            if (KC || f < K) {
+              const uint32_t win = row_window(h + f * P, L, r, c, k + 3);
+              const int base = (f * k + a) * T;
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const uint32_t code = (win >> t) & mk;
+                if (PREC == kFP64) x64[t] += tb.b64[base + code];
+                else x32[t] += tb.bd[base + code];
+              }
+            }
           }
         }
       }
@@ -431,31 +505,17 @@ __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, co
   }
 }
 
-// This site's pre-activation with the FP64 tables, in the FP64 path's order.
-static __device__ __noinline__ uint32_t recompute_visible(const JobDev& jb, const uint32_t* h, int P, int n,
-                                                   uint32_t w) {
-  const int L = jb.L, K = jb.K, k = jb.k, T = 1 << k;
-  const int i = n / L, j = n - i * L;
-  int c = j - (k - 1);
-  if (c < 0) c += L;
-  double x = jb.vb;
-  for (int a = 0; a < k; ++a) {
-    const int r = bwd_row(i, a, L);
-    for (int f = 0; f < K; ++f) x += __ldg(jb.b64 + (f * k + a) * T + row_window(h + f * P, L, r, c, k));
-  }
-  return decide64(x, w);
-}
-
 // ------------------------------------------------- free energy + lattice sums
 // F(v) = -v_bias sum v - sum_{f,i,j} softplus(h_bias^f + (W^f * v)_ij)   (Eq. 13)
 // Per-thread partial sums: out[0] = sum softplus (FP64 order, or FP32 with
 // Kahan compensation), out[1] = data part of the FP32 error bound (mixed),
 // out[2] = number of ones, out[3] = number of unequal nearest-neighbour pairs
 // (Ising) or of hexagons with flux -1 (Kitaev).
-template <int PREC>
+template <int PREC, int KC, int kC>
 __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const uint32_t* v,
                            double (&out)[4]) {
-  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = tb.T;
+  constexpr int kU = kC ? kC : kMaxk;
+  const int L = jb.L, N = jb.N, K = KC ? KC : jb.K, k = kC ? kC : jb.k, T = tb.T;
   const int nblk = (N + 3) >> 2;
   const int iters = (nblk + g.tpc - 1) / g.tpc;
   double s64 = 0.0;
@@ -465,45 +525,78 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
     const int q = g.r + it * g.tpc;
     const bool act = g.active && q < nblk;
     if (!act) continue;
-    uint32_t m[4][kMaxk];
-    fwd_codes(v, L, N, k, T, q, m);
-    for (int f = 0; f < K; ++f) {
-      const int base = f * k * T;
-      if (PREC == kFP64) {
+    uint32_t m[4][kU];
+    fwd_codes<kC>(v, L, N, k, T, q, m);
+    if (PREC == kMixed && KC == 4) {
+      float sp[4][4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (4 * q + t < N) {
-            double x = jb.hb[f];
+      for (int t = 0; t < 4; ++t) {
+        float4 xh = make_float4(jb.hb_hi[0], jb.hb_hi[1], jb.hb_hi[2], jb.hb_hi[3]);
+        float4 xl = make_float4(jb.hb_lo[0], jb.hb_lo[1], jb.hb_lo[2], jb.hb_lo[3]);
 #pragma unroll
-            for (int a = 0; a < kMaxk; ++a) if (a < k) x += tb.f64[base + m[t][a]];
-            s64 += softplus64(x);
+        for (int a = 0; a < kU; ++a) {
+          if (kC || a < k) {
+            const float4 eh = tb.fh4[m[t][a]], el = tb.fl4[m[t][a]];
+            xh.x += eh.x; xh.y += eh.y; xh.z += eh.z; xh.w += eh.w;
+            xl.x += el.x; xl.y += el.y; xl.z += el.z; xl.w += el.w;
           }
         }
-      } else {
-        float sp[4];
+        const bool site = 4 * q + t < N;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          sp[t] = 0.0f;
-          if (4 * q + t < N) {
-            float xh = jb.hb_hi[f], xl = jb.hb_lo[f];
-#pragma unroll
-            for (int a = 0; a < kMaxk; ++a) {
-              if (a < k) {
-                xh += tb.fh[base + m[t][a]];
-                xl += tb.fl[base + m[t][a]];
-              }
-            }
-            const float x = xh + xl;
-            sp[t] = softplus32(x);
-            sabs += fabsf(x);
-          }
+        for (int f = 0; f < 4; ++f) {
+          const float x = comp(xh, f) + comp(xl, f);
+          sp[t][f] = site ? softplus32(x) : 0.0f;
+          sabs += site ? fabsf(x) : 0.0f;
         }
-        const float us = (sp[0] + sp[1]) + (sp[2] + sp[3]);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float us = (sp[0][f] + sp[1][f]) + (sp[2][f] + sp[3][f]);
         ssp += us;
         const float y = us - c32;          // Kahan summation of the unit sums
         const float tt = s32 + y;
         c32 = (tt - s32) - y;
         s32 = tt;
+      }
+    } else {
+      for (int f = 0; f < K; ++f) {
+        const int base = f * k * T;
+        if (PREC == kFP64) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (4 * q + t < N) {
+              double x = jb.hb[f];
+#pragma unroll
+              for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
+              s64 += softplus64(x);
+            }
+          }
+        } else {
+          float sp[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            sp[t] = 0.0f;
+            if (4 * q + t < N) {
+              float xh = jb.hb_hi[f], xl = jb.hb_lo[f];
+#pragma unroll
+              for (int a = 0; a < kU; ++a) {
+                if (kC || a < k) {
+                  xh += tb.fh[base + m[t][a]];
+                  xl += tb.fl[base + m[t][a]];
+                }
+              }
+              const float x = xh + xl;
+              sp[t] = softplus32(x);
+              sabs += fabsf(x);
+            }
+          }
+          const float us = (sp[0] + sp[1]) + (sp[2] + sp[3]);
+          ssp += us;
+          const float y = us - c32;
+          const float tt = s32 + y;
+          c32 = (tt - s32) - y;
+          s32 = tt;
+        }
       }
     }
 #pragma unroll
@@ -511,12 +604,12 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
       const int n = 4 * q + t;
       if (n < N) {
         const int i = n / L, j = n - i * L;
-        const uint32_t b0 = site_bit(v, n);
+        const uint32_t b0 = m[t][0] & 1u;
         ones += (int)b0;
         if (jb.kind == kIsing) {
-          const uint32_t c0 = m[t][0] - 0u, c1 = (k >= 2) ? m[t][1] - (uint32_t)T : 0u;
-          const uint32_t right = (k >= 2) ? ((c0 >> 1) & 1u) : site_bit(v, i * L + (j + 1 == L ? 0 : j + 1));
-          const uint32_t down = (k >= 2) ? (c1 & 1u) : site_bit(v, (i + 1 == L ? 0 : i + 1) * L + j);
+          const uint32_t right = (k >= 2) ? ((m[t][0] >> 1) & 1u) : site_bit(v, i * L + (j + 1 == L ? 0 : j + 1));
+          const uint32_t down = (k >= 2) ? ((m[t][kU > 1 ? 1 : 0] - (uint32_t)T) & 1u)
+                                         : site_bit(v, (i + 1 == L ? 0 : i + 1) * L + j);
           pairs += (int)(b0 ^ right) + (int)(b0 ^ down);
         } else {
           // the hexagon of cell r holds the z-bonds r and r - e1 + e2

@@ -7,10 +7,13 @@
 namespace crbm {
 struct LaunchParams;
 
+// Compiled specialisation (KC, kC) serving a filter bank of K filters k x k
+// (0 = runtime values).
+void specialisation(int K, int k, int& KC, int& kC);
 // Dynamic shared memory of one CTA of the fused kernel.
-size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc);
-// Launch the fused kernel: grid = total tiles of all jobs in p.
-cudaError_t launch_step(int kind, int prec, const LaunchParams& p, int grid, size_t smem,
+size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC);
+// Launch the fused kernel: grid = total tiles of all jobs in p (one model per launch).
+cudaError_t launch_step(int kind, int prec, int K, int k, const LaunchParams& p, int grid, size_t smem,
                         cudaStream_t st);
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);

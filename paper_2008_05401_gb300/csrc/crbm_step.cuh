@@ -1,0 +1,349 @@
+// Fused CRBM proposal + Metropolis-Hastings kernel (one launch runs S
+// proposals; lattices stay in shared memory for the whole launch).
+//
+// Per proposal and chain (arXiv:2008.05401):
+//   g x [hidden half-step (Eq. B2), visible half-step (Eq. B3)]   -> v'
+//   F(v') (Eq. 13) and the lattice sums of v'
+//   log pi(v'): Ising -beta E (Eq. 14) | Kitaev sum log 2cosh(beta eps/2) (Sec. IV)
+//   log r = [log pi(v') - log pi(v)] + [F(v') - F(v)], accept iff log u < log r
+//   (Eq. B5 with the pair (pi, P_CRBM); the Gibbs kernel is reversible w.r.t.
+//   P_CRBM, App. B.1), then observables of the state after the decision.
+// Template parameters: model kind, precision, and K, k fixed at compile time
+// for the common filter banks (0 = runtime values).
+#pragma once
+#include "crbm_device.cuh"
+#include "crbm_kernels.h"
+
+namespace crbm {
+
+struct ChainSm {
+  double F, Fb, lp, E;
+  double ot[kNobs];      // observables of the current lattice
+  double os[kNobs];      // running sums
+  double Fp, Bp, lpp, Ep;
+  double otp[kNobs];
+  double beta;
+  unsigned long long acc, rec;
+  int cur, flag_rec, flag_acc, pad;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// The mixed path's FP64 free energy (rare), out of line to spare registers.
+static __device__ __noinline__ void free_energy64(const JobDev& jb, const Tabs& tb, const Grp& g,
+                                                  const uint32_t* v, double* out) {
+  double o[4];
+  free_phase<kFP64, 0, 0>(jb, tb, g, v, o);
+  for (int i = 0; i < 4; ++i) out[i] = o[i];
+}
+
+template <int KIND, int PREC, int KC, int kC>
+__global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
+  int jid = 0;
+  while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
+  const JobDev& jb = prm.job[jid];
+  const int ltile = (int)blockIdx.x - prm.tile_begin[jid];
+  const int tid = threadIdx.x;
+  const int N = jb.N, P = jb.P, K = jb.K, T = 1 << jb.k, nlut = K * jb.k * T;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sp = smem_raw;
+  Tabs tb;
+  tb.T = T;
+  tb.f64 = tb.b64 = nullptr;
+  tb.fd = tb.bd = tb.fh = tb.fl = nullptr;
+  tb.fd4 = tb.fh4 = tb.fl4 = nullptr;
+  const int nq = jb.k * T;   // entries of a filter-interleaved table
+  double* t64[2] = {nullptr, nullptr};
+  float* t32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float4* t4[3] = {nullptr, nullptr, nullptr};
+  if (PREC == kFP64) {
+    for (int i = 0; i < 2; ++i) {
+      t64[i] = (double*)sp;
+      sp += align16((size_t)nlut * 8);
+    }
+    tb.f64 = t64[0];
+    tb.b64 = t64[1];
+  } else if (KC == 4) {
+    for (int i = 0; i < 3; ++i) {
+      t4[i] = (float4*)sp;
+      sp += align16((size_t)nq * 16);
+    }
+    t32[1] = (float*)sp;
+    sp += align16((size_t)nlut * 4);
+    tb.fd4 = t4[0];
+    tb.fh4 = t4[1];
+    tb.fl4 = t4[2];
+    tb.bd = t32[1];
+  } else {
+    for (int i = 0; i < 4; ++i) {
+      t32[i] = (float*)sp;
+      sp += align16((size_t)nlut * 4);
+    }
+    tb.fd = t32[0];
+    tb.bd = t32[1];
+    tb.fh = t32[2];
+    tb.fl = t32[3];
+  }
+  ChainSm* cs = (ChainSm*)sp;
+  sp += align16(jb.nc * sizeof(ChainSm));
+  double* scratch = (double*)sp;
+  sp += align16(64 * 8);
+  KitaevWork wk;
+  if (KIND == kKitaev) {
+    wk.A = (double*)sp;
+    sp += align16((size_t)N * (N + 1) * 8);
+    wk.d = (double*)sp;
+    sp += align16((size_t)N * 8);
+    wk.e = (double*)sp;
+    sp += align16((size_t)N * 8);
+    wk.vv = (double*)sp;
+    sp += align16((size_t)N * 8);
+    wk.pw = (double*)sp;
+    sp += align16((size_t)N * 8);
+    wk.sc = (double*)sp;
+    sp += align16(64 * 8);
+  }
+  uint32_t* planes = (uint32_t*)sp;
+
+  Grp g;
+  g.tpc = kThreads / jb.nc;
+  g.gl = tid / g.tpc;
+  g.r = tid - g.gl * g.tpc;
+  g.c = ltile * jb.nc + g.gl;
+  g.active = g.c < jb.n_chains;
+  g.cid = (uint32_t)(jb.cid_base + (uint64_t)g.c);
+  uint32_t* my = planes + (size_t)g.gl * (2 + K) * P;
+  ChainSm& ch = cs[g.gl];
+
+  for (int i = tid; i < nlut; i += kThreads) {
+    if (PREC == kFP64) {
+      t64[0][i] = jb.f64[i];
+      t64[1][i] = jb.b64[i];
+    } else if (KC == 4) {
+      t32[1][i] = jb.bd[i];
+    } else {
+      t32[0][i] = jb.fd[i];
+      t32[1][i] = jb.bd[i];
+      t32[2][i] = jb.fh[i];
+      t32[3][i] = jb.fl[i];
+    }
+  }
+  if (PREC == kMixed && KC == 4) {
+    for (int i = tid; i < nq; i += kThreads) {
+      t4[0][i] = jb.fd4[i];
+      t4[1][i] = jb.fh4[i];
+      t4[2][i] = jb.fl4[i];
+    }
+  }
+  for (int i = tid; i < jb.nc * (2 + K) * P; i += kThreads) planes[i] = 0u;
+  __syncthreads();
+  if (g.r == 0) {
+    // every slot, including the unused slots of a partial last tile, starts
+    // from a defined state: the plane index `cur` addresses shared memory
+    ch.F = ch.Fb = ch.lp = ch.E = 0.0;
+    for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.os[o] = 0.0;
+    ch.beta = 1.0;
+    ch.acc = 0ull;
+    ch.rec = 0ull;
+    ch.cur = 0;
+    ch.flag_rec = 0;
+    ch.flag_acc = 0;
+  }
+  if (g.active) {
+    for (int w = g.r; w < jb.Wd; w += g.tpc) my[w] = jb.bits[(size_t)g.c * jb.Wd + w];
+    if (g.r == 0) {
+      ch.F = jb.F[g.c];
+      ch.Fb = jb.Fb[g.c];
+      ch.lp = jb.logpi[g.c];
+      ch.E = jb.Ephys[g.c];
+      for (int o = 0; o < kNobs; ++o) ch.ot[o] = jb.obs_t[(size_t)g.c * kNobs + o];
+      ch.beta = 1.0 / jb.T[g.c];
+    }
+  }
+  __syncthreads();
+  unsigned nrec = 0;
+
+  if (prm.mode == 1) {
+    // evaluate F (FP64), log pi and the observables of the current lattices
+    double fo[4];
+    free_energy64(jb, tb, g, my, fo);
+    grp_reduce<4>(fo, g, scratch);
+    double kr[3] = {0.0, 0.0, 0.0};
+    if (KIND == kKitaev) kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
+    if (g.active && g.r == 0) {
+      const double Fv = -jb.vb * fo[2] - fo[0];
+      double lp, E, ot[kNobs];
+      if (KIND == kIsing) {
+        E = -jb.J[0] * (double)(2 * N - 2 * (int)fo[3]);
+        const double M = 2.0 * fo[2] - (double)N;
+        lp = -ch.beta * E;
+        ot[0] = E; ot[1] = E * E; ot[2] = fabs(M); ot[3] = M * M;
+      } else {
+        lp = kr[0];
+        E = kr[1];
+        ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)N;
+      }
+      jb.F[g.c] = Fv;
+      jb.Fb[g.c] = 0.0;
+      jb.logpi[g.c] = lp;
+      jb.Ephys[g.c] = E;
+      for (int o = 0; o < kNobs; ++o) jb.obs_t[(size_t)g.c * kNobs + o] = ot[o];
+    }
+    return;
+  }
+
+  const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
+  for (int s = 0; s < prm.S; ++s) {
+    const uint32_t step = (uint32_t)(jb.step0 + (uint64_t)s);
+    const int cur = ch.cur;
+    uint32_t* v = my + cur * P;
+    uint32_t* vp = my + (cur ^ 1) * P;
+    uint32_t* h = my + 2 * P;
+    const uint32_t* src = v;
+    for (int sub = 0; sub < prm.g; ++sub) {
+      hidden_phase<PREC, KC, kC>(jb, tb, g, src, h, P, step, sub, nrec);
+      __syncthreads();
+      visible_phase<PREC, KC, kC>(jb, tb, g, h, vp, P, step, sub, nrec);
+      __syncthreads();
+      src = vp;
+    }
+    double fo[4];
+    free_phase<PREC, KC, kC>(jb, tb, g, vp, fo);
+    grp_reduce<4>(fo, g, scratch);
+    double kr[3] = {0.0, 0.0, 0.0};
+    if (KIND == kKitaev) kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
+    double logu = 0.0;
+    if (g.active && g.r == 0) {
+      if (KIND == kIsing) {
+        const double E = -jb.J[0] * (double)(2 * N - 2 * (int)fo[3]);
+        const double M = 2.0 * fo[2] - (double)N;
+        ch.Ep = E;
+        ch.lpp = -ch.beta * E;
+        ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
+      } else {
+        ch.Ep = kr[1];
+        ch.lpp = kr[0];
+        ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2]; ch.otp[3] = fo[3] / (double)N;
+      }
+      ch.Fp = -jb.vb * fo[2] - fo[0];
+      ch.Bp = (PREC == kMixed)
+                  ? fo[1] + (double)K * (double)N * (1.5 * 0x1p-23 + (double)jb.csp) + 1e-12 * fabs(ch.Fp)
+                  : 0.0;
+      ch.flag_rec = 0;
+      if (!prm.correct) {
+        ch.flag_acc = 1;
+      } else {
+        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+        const uint4 w = philox4x32_10(make_uint4(0u, kTagAcc, step, g.cid), k0, k1);
+        logu = log(((double)w.x + 0.5) * 0x1p-32);
+        if (PREC == kFP64) {
+          ch.flag_acc = logu < logr;
+        } else {
+          const double M = ch.Bp + ch.Fb +
+                           1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+          if (logr - logu > M) ch.flag_acc = 1;
+          else if (logu - logr > M) ch.flag_acc = 0;
+          else ch.flag_rec = 1;
+        }
+      }
+    }
+    if (PREC == kMixed) {
+      const int need = __syncthreads_or(g.active && g.r == 0 && ch.flag_rec);
+      if (need) {
+        // the FP64 path's free energies of v' (and of v when only its FP32
+        // value is known), computed by the same code and reduction order
+        // FP64 tables from global memory (the mixed kernel keeps only FP32 ones)
+        Tabs tb64g = tb;
+        tb64g.f64 = jb.f64;
+        tb64g.b64 = jb.b64;
+        Grp g2 = g;
+        g2.active = g.active && ch.flag_rec;
+        double f1[4];
+        free_energy64(jb, tb64g, g2, vp, f1);
+        grp_reduce<4>(f1, g2, scratch);
+        Grp g3 = g2;
+        g3.active = g2.active && ch.Fb != 0.0;
+        double f2[4];
+        free_energy64(jb, tb64g, g3, v, f2);
+        grp_reduce<4>(f2, g3, scratch);
+        if (g2.active && g.r == 0) {
+          ch.Fp = -jb.vb * f1[2] - f1[0];
+          ch.Bp = 0.0;
+          if (g3.active) {
+            ch.F = -jb.vb * f2[2] - f2[0];
+            ch.Fb = 0.0;
+          }
+          const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+          const uint4 w = philox4x32_10(make_uint4(0u, kTagAcc, step, g.cid), k0, k1);
+          const double lu = log(((double)w.x + 0.5) * 0x1p-32);
+          ch.flag_acc = lu < logr;
+          ch.rec += 1ull;
+        }
+      }
+    }
+    if (g.active && g.r == 0) {
+      if (ch.flag_acc) {
+        ch.cur ^= 1;
+        ch.F = ch.Fp;
+        ch.Fb = ch.Bp;
+        ch.lp = ch.lpp;
+        ch.E = ch.Ep;
+        for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
+        ch.acc += 1ull;
+      }
+      for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+    }
+    __syncthreads();
+  }
+
+  if (nrec) atomicAdd(&ch.rec, (unsigned long long)nrec);
+  __syncthreads();
+  if (g.active) {
+    const uint32_t* v = my + ch.cur * P;
+    for (int w = g.r; w < jb.Wd; w += g.tpc) jb.bits[(size_t)g.c * jb.Wd + w] = v[w];
+    if (g.r == 0) {
+      jb.F[g.c] = ch.F;
+      jb.Fb[g.c] = ch.Fb;
+      jb.logpi[g.c] = ch.lp;
+      jb.Ephys[g.c] = ch.E;
+      for (int o = 0; o < kNobs; ++o) {
+        jb.obs_t[(size_t)g.c * kNobs + o] = ch.ot[o];
+        jb.obs[(size_t)g.c * kNobs + o] += ch.os[o];
+      }
+      jb.acc[g.c] += ch.acc;
+      jb.rec[g.c] += ch.rec;
+    }
+  }
+}
+
+
+// Launch one instantiation; raise its dynamic shared-memory limit.
+template <int KIND, int PREC, int KC, int kC>
+cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  crbm_step_kernel<KIND, PREC, KC, kC><<<grid, kThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int KIND, int PREC, int KC, int kC>
+cudaError_t limit_inst(size_t bytes) {
+  return cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Variants compiled for each (kind, precision): (K, k) = (4, 5), (4, 3), runtime.
+#define CRBM_VARIANTS(KIND, PREC)                                                          \
+  cudaError_t launch_##KIND##_##PREC(int KC, int kC, const LaunchParams& p, int grid,       \
+                                     size_t smem, cudaStream_t st) {                         \
+    if (KC == 4 && kC == 5) return launch_inst<KIND, PREC, 4, 5>(p, grid, smem, st);        \
+    if (KC == 4 && kC == 3) return launch_inst<KIND, PREC, 4, 3>(p, grid, smem, st);        \
+    return launch_inst<KIND, PREC, 0, 0>(p, grid, smem, st);                                \
+  }                                                                                          \
+  cudaError_t limit_##KIND##_##PREC(size_t bytes) {                                          \
+    cudaError_t e = limit_inst<KIND, PREC, 4, 5>(bytes);                                     \
+    if (e == cudaSuccess) e = limit_inst<KIND, PREC, 4, 3>(bytes);                           \
+    if (e == cudaSuccess) e = limit_inst<KIND, PREC, 0, 0>(bytes);                           \
+    return e;                                                                                \
+  }
+
+}  // namespace crbm
