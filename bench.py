@@ -49,6 +49,12 @@ def workload(name):
         return dict(kind=1, jobs=[(6, 1024)], T=lambda n: wl.kitaev_ladder(n, 24), J=(1.0, 1.0, 1.0),
                     model=(W, hb, vb), S=2,
                     desc="Kitaev L=6 (72 sites), J=1, 1024 chains, 24 T log-spaced in [0.005,1], K=4 3x3 CRBM")
+    if name == "kitaev-batch":
+        W, hb, vb = wl.gaussian_crbm(4, 3, 0.05)
+        return dict(kind=1, jobs=[(8, 683), (10, 683), (12, 682)], T=lambda n: wl.kitaev_ladder(n, 24),
+                    J=(1.0, 1.0, 1.0), model=(W, hb, vb), S=1,
+                    desc="Kitaev L in {8,10,12} (2048 chains split by L) in one launch, 24 T log-spaced "
+                         "in [0.005,1], K=4 3x3 CRBM")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -211,12 +217,29 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
     n_chains = sum(n for _, n in spec["jobs"])
     sums = [j.observables() for j in jobs]
     acc = sum(int(a.sum()) for _, a, _ in sums) / (n_chains * spec["S"] * (steps + 1))
-    rec = sum(int(r.sum()) for _, _, r in sums)
+    rec = [sum(int(r[:, 0].sum()) for _, _, r in sums), sum(int(r[:, 1].sum()) for _, _, r in sums)]
     ctx.close()
     return {"workload": spec["desc"], "precision": "mixed" if prec == MIXED else "fp64",
             "value": n_chains * spec["S"] * steps / (ms * 1e-3), "unit": "proposals/s",
             "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
             "fp64_recomputes": rec}
+
+
+def serving_run(dev, n=60, rate=200.0):
+    """Continuous batching of a Poisson request stream (mixed Ising / Kitaev
+    jobs, 1-64 chains, 1e2-2e3 proposals each, mixed precision): p50/p99 latency
+    and aggregate proposals/s."""
+    from paper_2008_05401_gb300 import MIXED
+    from paper_2008_05401_gb300.serving import Server, synthetic_requests
+    reqs = synthetic_requests(n, rate_hz=rate, min_proposals=100, max_proposals=2000, precision=MIXED)
+    srv = Server(device=dev, hbm_budget_bytes=8 << 30, quantum=256)
+    t0 = time.perf_counter()
+    srv.run(reqs, realtime=True)
+    st = srv.stats(t_start=t0)
+    srv.close()
+    st.update({"arrivals": f"Poisson {rate:g}/s", "jobs": "Ising L in {16..256} or Kitaev L in 4..12, "
+               "1-64 chains, 1e2-2e3 proposals (log-uniform), mixed precision, HBM budget 8 GiB"})
+    return st
 
 
 def main():
@@ -332,14 +355,23 @@ def main():
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
     sums = [j.observables() for j in jobs]
     line["config"]["acceptance"] = sum(int(a.sum()) for _, a, _ in sums) / max(1, n_chains * jobs[0].step)
-    line["config"]["fp64_recomputes_per_proposal"] = sum(int(r.sum()) for _, _, r in sums) / max(
-        1, n_chains * jobs[0].step)
+    props_done = max(1, n_chains * jobs[0].step)
+    line["config"]["fp64_recomputes_per_proposal"] = {
+        "bernoulli": sum(int(r[:, 0].sum()) for _, _, r in sums) / props_done,
+        "mh": sum(int(r[:, 1].sum()) for _, _, r in sums) / props_done,
+        "mh_by_L": {str(L): int(r[:, 1].sum()) / max(1, len(r) * j.step)
+                    for (L, _), j, (_, _, r) in zip(spec["jobs"], jobs, sums)},
+        "acceptance_by_L": {str(L): int(a.sum()) / max(1, len(a) * j.step)
+                            for (L, _), j, (_, a, _) in zip(spec["jobs"], jobs, sums)}}
     if rank == 0 and not args.no_secondary and args.workload == "ising-batch":
         line["secondary"] = [
             secondary(Context, "ising-batch", FP64, 2, dev, stream, flush),
             secondary(Context, "kitaev-small", FP64, 3, dev, stream, flush),
-            secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush)]
+            secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush),
+            secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
+            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush)]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
+        line["serving"] = serving_run(dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(spec)
     if rank == 0:

@@ -126,7 +126,8 @@ CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, 
              void* cuda_stream);
 
 /* As crbm_run for n_jobs jobs in ONE kernel launch (chains of different L and
- * temperature side by side).  The jobs must share the model kind and the
+ * temperature side by side; Kitaev jobs with at most 64 cells per lattice run
+ * in CTAs of another size and form a second launch on the same stream).  The jobs must share the model kind and the
  * filter-bank shape (K, k); their models may differ.  Each job keeps its own
  * step counter and random streams, so its result equals a crbm_run of that
  * job alone.  At most 16 jobs per call; a job may appear once. */
@@ -145,8 +146,10 @@ CRBM_API int crbm_sync(crbm_ctx* ctx, int job_id);
 CRBM_API int crbm_read_energies(crbm_ctx* ctx, int job_id, double* logpi, double* F_crbm, double* E_phys);
 
 /* Copy observable sums (n_chains * CRBM_NOBS FP64, chain-major), accepted
- * proposal counts and FP64-recompute counts (n_chains int64 each; any
- * pointer may be NULL). */
+ * proposal counts (n_chains int64) and FP64-recompute counts (n_chains x 2
+ * int64: Bernoulli draws, then MH decisions, redone with the FP64 code because
+ * they fell inside the FP32 error bound; always 0 for CRBM_FP64).  Any pointer
+ * may be NULL. */
 CRBM_API int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int64_t* accepts,
                           int64_t* recomputes);
 

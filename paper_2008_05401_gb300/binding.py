@@ -145,7 +145,7 @@ def crbm_read_energies(ctx, job_id, n):
 def crbm_read_observables(ctx, job_id, n):
     sums = np.empty((n, NOBS))
     acc = np.empty(n, dtype=np.int64)
-    rec = np.empty(n, dtype=np.int64)
+    rec = np.empty((n, 2), dtype=np.int64)
     _check(ctx, load().crbm_read_observables(ctx, job_id, _ptr(sums), _ptr(acc), _ptr(rec)))
     return sums, acc, rec
 

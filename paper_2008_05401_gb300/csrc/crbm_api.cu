@@ -63,7 +63,7 @@ Layout make_layout(int L, int n) {
   y.ot = take((size_t)n * 8 * kNobs);
   y.os = take((size_t)n * 8 * kNobs);
   y.acc = take((size_t)n * 8);
-  y.rec = take((size_t)n * 8);
+  y.rec = take((size_t)n * 16);
   y.total = off;
   return y;
 }
@@ -79,7 +79,7 @@ int chains_per_tile(int kind, int L) {
   if (kind == kKitaev) return 1;
   const int nblk = (L * L + 3) / 4;
   int nc = 1;
-  while (nc < 32 && (nc * 2) * nblk <= 2 * kThreads) nc *= 2;
+  while (nc < kThreads / 8 && (nc * 2) * nblk <= 2 * kThreads) nc *= 2;
   return nc;
 }
 
@@ -92,6 +92,9 @@ struct crbm_ctx {
   std::vector<Job> jobs;
   std::string err;
   int* d_err = nullptr;
+  // non-blocking stream of the context's own copies and evaluation launches,
+  // so that job set-up never waits for other streams' work
+  cudaStream_t own = nullptr;
 };
 
 static int fail(crbm_ctx* c, int code, const char* fmt, ...) {
@@ -171,9 +174,13 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   return d;
 }
 
-// Launch the fused kernel for a set of jobs (same kind); mode 1 = evaluate.
-static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct,
-                       int prec, int mode, cudaStream_t st) {
+// Launch the fused kernel for a set of jobs (same kind and filter shape);
+// mode 1 = evaluate.  A job's CTA size depends only on its own lattice
+// (threads_for), so that its per-chain reduction order -- and hence every
+// bit of its results -- is the same alone or batched; jobs of different CTA
+// sizes go to separate launches on the same stream.
+static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec,
+                        int mode, int nt, cudaStream_t st) {
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -200,7 +207,22 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
   }
   p.tile_begin[ids.size()] = tiles;
   if (tiles == 0) return CRBM_OK;
-  CK(launch_step(kind, prec, K, k, p, tiles, smem, st), "kernel launch");
+  CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st), "kernel launch");
+  return CRBM_OK;
+}
+
+static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
+                       cudaStream_t st) {
+  for (int nt : {256, 128}) {
+    std::vector<int> part;
+    for (int id : ids) {
+      const Job& j = ctx->jobs[id];
+      if (threads_for(j.kind, j.N) == nt) part.push_back(id);
+    }
+    if (part.empty()) continue;
+    const int rc = launch_group(ctx, part, S, g, correct, prec, mode, nt, st);
+    if (rc) return rc;
+  }
   return CRBM_OK;
 }
 
@@ -217,6 +239,7 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -241,6 +264,7 @@ int crbm_destroy(crbm_ctx* ctx) {
     if (m.d_q) cudaFree(m.d_q);
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
   return CRBM_OK;
 }
@@ -367,10 +391,9 @@ size_t crbm_job_bytes(int kind, int L, int n_chains, int precision) {
 }
 
 static int evaluate(crbm_ctx* ctx, int id) {
-  Job& j = ctx->jobs[id];
-  int rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, j.stream);
+  int rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, ctx->own);
   if (rc) return rc;
-  CK(cudaStreamSynchronize(j.stream), "evaluate");
+  CK(cudaStreamSynchronize(ctx->own), "evaluate");
   return CRBM_OK;
 }
 
@@ -423,15 +446,17 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   j.stream = nullptr;
   if (n_chains > 0) {
     unsigned char* b = j.mem;
-    CK(cudaMemcpy(b + lay.T, T, (size_t)n_chains * 8, cudaMemcpyHostToDevice), "copy T");
+    cudaStream_t o = ctx->own;
+    CK(cudaMemcpyAsync(b + lay.T, T, (size_t)n_chains * 8, cudaMemcpyHostToDevice, o), "copy T");
     if (init == 1)
-      CK(cudaMemcpy(b + lay.bits, init_bits, (size_t)n_chains * j.Wd * 4, cudaMemcpyHostToDevice), "copy init_bits");
+      CK(cudaMemcpyAsync(b + lay.bits, init_bits, (size_t)n_chains * j.Wd * 4, cudaMemcpyHostToDevice, o),
+         "copy init_bits");
     else
-      CK(launch_random_init((uint32_t*)(b + lay.bits), n_chains, j.N, j.Wd, seed, chain_id_base, nullptr),
+      CK(launch_random_init((uint32_t*)(b + lay.bits), n_chains, j.N, j.Wd, seed, chain_id_base, o),
          "random init");
-    CK(cudaMemset(b + lay.os, 0, (size_t)n_chains * 8 * kNobs), "zero sums");
-    CK(cudaMemset(b + lay.acc, 0, (size_t)n_chains * 8), "zero accepts");
-    CK(cudaMemset(b + lay.rec, 0, (size_t)n_chains * 8), "zero recomputes");
+    CK(cudaMemsetAsync(b + lay.os, 0, (size_t)n_chains * 8 * kNobs, o), "zero sums");
+    CK(cudaMemsetAsync(b + lay.acc, 0, (size_t)n_chains * 8, o), "zero accepts");
+    CK(cudaMemsetAsync(b + lay.rec, 0, (size_t)n_chains * 16, o), "zero recomputes");
   }
   ctx->jobs.push_back(j);
   const int id = (int)ctx->jobs.size() - 1;
@@ -502,7 +527,8 @@ int crbm_sync(crbm_ctx* ctx, int job_id) {
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   CK(cudaStreamSynchronize(j->stream), "stream sync");
   int h = 0;
-  CK(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+  CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->own), "read error flag");
+  CK(cudaStreamSynchronize(ctx->own), "read error flag");
   if (h == kErrTimeout) return fail(ctx, CRBM_ETIMEOUT, "a device-side wait reached its iteration limit");
   if (h != 0) return fail(ctx, CRBM_EINVAL, "device reported configuration error %d", h);
   return CRBM_OK;
@@ -510,7 +536,8 @@ int crbm_sync(crbm_ctx* ctx, int job_id) {
 
 static int read_back(crbm_ctx* ctx, Job* j, void* dst, size_t off, size_t bytes) {
   if (!dst || bytes == 0) return CRBM_OK;
-  CK(cudaMemcpy(dst, j->mem + off, bytes, cudaMemcpyDeviceToHost), "device to host copy");
+  CK(cudaMemcpyAsync(dst, j->mem + off, bytes, cudaMemcpyDeviceToHost, ctx->own), "device to host copy");
+  CK(cudaStreamSynchronize(ctx->own), "device to host copy");
   return CRBM_OK;
 }
 
@@ -532,7 +559,7 @@ int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int64_t* acce
   if (rc) return rc;
   if ((rc = read_back(ctx, j, sums, j->lay.os, (size_t)j->n * 8 * kNobs))) return rc;
   if ((rc = read_back(ctx, j, accepts, j->lay.acc, (size_t)j->n * 8))) return rc;
-  return read_back(ctx, j, recomputes, j->lay.rec, (size_t)j->n * 8);
+  return read_back(ctx, j, recomputes, j->lay.rec, (size_t)j->n * 16);
 }
 
 int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step) {
@@ -553,7 +580,8 @@ int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t s
   if (rc) return rc;
   j->step = step;
   if (j->n == 0) return CRBM_OK;
-  CK(cudaMemcpy(j->mem + j->lay.bits, bits, (size_t)j->n * j->Wd * 4, cudaMemcpyHostToDevice), "copy bits");
+  CK(cudaMemcpyAsync(j->mem + j->lay.bits, bits, (size_t)j->n * j->Wd * 4, cudaMemcpyHostToDevice, ctx->own),
+     "copy bits");
   return evaluate(ctx, job_id);
 }
 

@@ -28,7 +28,15 @@ constexpr int kIsing = 0;
 constexpr int kKitaev = 1;
 constexpr int kFP64 = 0;
 constexpr int kMixed = 1;
-constexpr int kThreads = 256;
+// Threads per CTA of the fused kernel and the CTAs per SM its register budget
+// is sized for (compile-time; the defaults were chosen by measurement).
+#ifndef CRBM_THREADS
+#define CRBM_THREADS 256
+#endif
+#ifndef CRBM_MIN_BLOCKS
+#define CRBM_MIN_BLOCKS 2
+#endif
+constexpr int kThreads = CRBM_THREADS;
 constexpr unsigned kFull = 0xffffffffu;
 
 enum DevErr : int { kErrNone = 0, kErrConfig = 1, kErrTimeout = 2 };
@@ -63,7 +71,7 @@ struct JobDev {
   double* obs_t;                // [n_chains][4] observables of the current lattice
   double* obs;                  // [n_chains][4] running sums
   unsigned long long* acc;      // [n_chains]
-  unsigned long long* rec;      // [n_chains]
+  unsigned long long* rec;      // [n_chains][2] FP64 recomputes: Bernoulli draws, MH decisions
 };
 
 struct LaunchParams {
@@ -638,38 +646,162 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
 // reflections, its eigenvalues mu_l = eps_l^2 are found by bisection with
 // Sturm counts, and log pi = sum_l log 2cosh(beta eps_l / 2).
 struct KitaevWork {
-  double* A;       // N x (N+1)
+  double* A;       // N x (N+1), lower triangle used after the build
   double* d;       // N
   double* e;       // N
   double* vv;      // N
   double* pw;      // N
   double* sc;      // 64 doubles
+  float* d32;      // N   FP32 copies of the tridiagonal for eigenvalue isolation
+  float* e32;      // N   (squared off-diagonals)
 };
 
+// Number of eigenvalues below x of the symmetric tridiagonal (d, off-diagonal^2
+// = e2): sign changes of p_{-1} = 1, p_0, ..., p_{N-1} with
+// p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2} (Sturm).  A zero p_i takes the sign
+// opposite to p_{i-1}.  The pair (p_i, p_{i-1}) is rescaled by 2^-+500 when
+// it leaves [2^-500, 2^500].  Signs and exponents are read from the bit
+// patterns with integer operations: only the recurrence itself uses the FP64
+// pipe (three operations per step).
 __device__ __forceinline__ int sturm_count(const double* d, const double* e2, int N, double x) {
-  // sign changes of p_{-1}=1, p_0, ..., p_{N-1}; p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}
   double pp = 1.0, p = d[0] - x;
-  bool sprev = false;                       // sign of p_{-1} (positive)
-  bool s = (p == 0.0) ? !sprev : (p < 0.0);
-  int cnt = (s != sprev);
+  int hi = __double2hiint(p);
+  uint32_t sprev = 0u;                                           // sign of p_{-1} = +1
+  uint32_t s = ((hi & 0x7fffffff) | __double2loint(p)) == 0 ? 1u : ((uint32_t)hi >> 31);
+  int cnt = (int)(s ^ sprev);
   sprev = s;
   for (int i = 1; i < N; ++i) {
-    double pn = fma(-e2[i - 1], pp, (d[i] - x) * p);
+    const double pn = fma(-e2[i - 1], pp, (d[i] - x) * p);
     pp = p;
     p = pn;
-    s = (p == 0.0) ? !sprev : (p < 0.0);
-    cnt += (s != sprev);
+    hi = __double2hiint(p);
+    const uint32_t zero = ((hi & 0x7fffffff) | __double2loint(p)) == 0;
+    s = zero ? (sprev ^ 1u) : ((uint32_t)hi >> 31);
+    cnt += (int)(s ^ sprev);
     sprev = s;
-    const double ap = fabs(p);
-    if (ap > 0x1p+500) {
+    const int ex = (hi >> 20) & 0x7ff;                           // biased exponent of p
+    if (ex > 1023 + 500) {
       p *= 0x1p-500;
       pp *= 0x1p-500;
-    } else if (ap < 0x1p-500 && fabs(pp) < 0x1p-500) {
+    } else if (ex < 1023 - 500 && ((__double2hiint(pp) >> 20) & 0x7ff) < 1023 - 500) {
       p *= 0x1p+500;
       pp *= 0x1p+500;
     }
   }
   return cnt;
+}
+
+// FP32 Sturm count (same recurrence, rescaled by 2^-+60): used only to
+// isolate eigenvalues; every bracket it yields is checked with FP64 counts.
+__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int N, float x) {
+  float pp = 1.0f, p = d[0] - x;
+  uint32_t b = __float_as_uint(p);
+  uint32_t sprev = 0u;
+  uint32_t s = (b << 1) == 0u ? 1u : (b >> 31);
+  int cnt = (int)(s ^ sprev);
+  sprev = s;
+  for (int i = 1; i < N; ++i) {
+    const float pn = fmaf(-e2[i - 1], pp, (d[i] - x) * p);
+    pp = p;
+    p = pn;
+    b = __float_as_uint(p);
+    s = (b << 1) == 0u ? (sprev ^ 1u) : (b >> 31);
+    cnt += (int)(s ^ sprev);
+    sprev = s;
+    const int ex = (int)((b >> 23) & 0xffu);
+    if (ex > 127 + 60) {
+      p *= 0x1p-60f;
+      pp *= 0x1p-60f;
+    } else if (ex < 127 - 60 && (int)((__float_as_uint(pp) >> 23) & 0xffu) < 127 - 60) {
+      p *= 0x1p+60f;
+      pp *= 0x1p+60f;
+    }
+  }
+  return cnt;
+}
+
+// FP64 Sturm count together with p_N(x) and p_N'(x) (for a Newton step):
+// p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}', all four values of a
+// step rescaled together.  Five FP64 operations per step.
+struct SturmNewton {
+  int cnt;
+  double p, dp;
+};
+
+__device__ __forceinline__ SturmNewton sturm_newton(const double* d, const double* e2, int N, double x) {
+  double pp = 1.0, p = d[0] - x, dpp = 0.0, dp = -1.0;
+  int hi = __double2hiint(p);
+  uint32_t sprev = 0u;
+  uint32_t s = ((hi & 0x7fffffff) | __double2loint(p)) == 0 ? 1u : ((uint32_t)hi >> 31);
+  int cnt = (int)(s ^ sprev);
+  sprev = s;
+  for (int i = 1; i < N; ++i) {
+    const double dx = d[i] - x;
+    const double pn = fma(-e2[i - 1], pp, dx * p);
+    const double dpn = fma(-e2[i - 1], dpp, fma(dx, dp, -p));
+    pp = p;
+    p = pn;
+    dpp = dp;
+    dp = dpn;
+    hi = __double2hiint(p);
+    const uint32_t zero = ((hi & 0x7fffffff) | __double2loint(p)) == 0;
+    s = zero ? (sprev ^ 1u) : ((uint32_t)hi >> 31);
+    cnt += (int)(s ^ sprev);
+    sprev = s;
+    const int ex = max((hi >> 20) & 0x7ff, (__double2hiint(dp) >> 20) & 0x7ff);
+    if (ex > 1023 + 500) {
+      p *= 0x1p-500;
+      pp *= 0x1p-500;
+      dp *= 0x1p-500;
+      dpp *= 0x1p-500;
+    } else if (ex < 1023 - 500 && max((__double2hiint(pp) >> 20) & 0x7ff, (__double2hiint(dpp) >> 20) & 0x7ff) <
+                                      1023 - 500) {
+      p *= 0x1p+500;
+      pp *= 0x1p+500;
+      dp *= 0x1p+500;
+      dpp *= 0x1p+500;
+    }
+  }
+  return {cnt, p, dp};
+}
+
+// Eigenvalue idx (ascending) of the tridiagonal: FP32 bisection isolates it,
+// two FP64 Sturm counts verify the bracket (falling back to the Gershgorin
+// interval), then safeguarded Newton steps on p_N refine it in FP64; every
+// iterate updates the bracket through its Sturm count, and a step that leaves
+// the bracket is replaced by bisection.
+__device__ __forceinline__ double eigen_idx(const KitaevWork& wk, int N, int idx, double glo, double ghi) {
+  const double range = fmax(ghi - glo, 1e-300);
+  float lo32 = (float)glo, hi32 = (float)ghi;
+  const float w32 = (float)(range * 0x1p-20);
+  for (int it = 0; it < 48 && hi32 - lo32 > w32; ++it) {
+    const float mid = 0.5f * (lo32 + hi32);
+    if (!(mid > lo32 && mid < hi32)) break;
+    if (sturm_count32(wk.d32, wk.e32, N, mid) > idx) hi32 = mid; else lo32 = mid;
+  }
+  const double pad = 0x1p-14 * range;
+  double lo = fmax(glo, (double)lo32 - pad), hi = fmin(ghi, (double)hi32 + pad);
+  if (sturm_count(wk.d, wk.vv, N, lo) > idx) lo = glo;
+  if (sturm_count(wk.d, wk.vv, N, hi) <= idx) hi = ghi;
+  const double tol_abs = 1e-15 * range;
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double tol = fmax(tol_abs, 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)));
+    if (hi - lo <= tol) {
+      x = 0.5 * (lo + hi);
+      break;
+    }
+    const SturmNewton r = sturm_newton(wk.d, wk.vv, N, x);
+    if (r.cnt > idx) hi = x; else lo = x;
+    double xn = x - r.p / r.dp;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (fabs(xn - x) <= tol) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
 }
 
 __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
@@ -700,7 +832,8 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     }
   }
   __syncthreads();
-  // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1
+  // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1.
+  // Only the lower triangle of the trailing block is read and updated.
   for (int j = 0; j < N - 2; ++j) {
     const int m = N - j - 1;
     double s = 0.0;
@@ -723,11 +856,14 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     if (tid == 0) wk.e[j] = alpha;
     for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[(size_t)(j + 1 + l) * lda + j];
     __syncthreads();
-    // p = tau * A22 v, one warp per row
+    // p = tau * A22 v from the lower triangle (row part c <= l, column part c > l), one warp per row
+    double* A22 = A + (size_t)(j + 1) * lda + (j + 1);
     for (int l = warp; l < m; l += nw) {
-      const double* row = A + (size_t)(j + 1 + l) * lda + (j + 1);
       double acc = 0.0;
-      for (int c = lane; c < m; c += 32) acc = fma(row[c], wk.vv[c], acc);
+      for (int c = lane; c < m; c += 32) {
+        const int off = (c <= l) ? l * lda + c : c * lda + l;
+        acc = fma(A22[off], wk.vv[c], acc);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
       if (lane == 0) wk.pw[l] = tau * acc;
@@ -739,11 +875,11 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     const double Kc = 0.5 * tau * pv;
     for (int l = tid; l < m; l += nt) wk.pw[l] = fma(-Kc, wk.vv[l], wk.pw[l]);
     __syncthreads();
-    // A22 -= v w^T + w v^T
+    // lower triangle of A22 -= v w^T + w v^T
     for (int l = warp; l < m; l += nw) {
-      double* row = A + (size_t)(j + 1 + l) * lda + (j + 1);
+      double* row = A22 + (size_t)l * lda;
       const double vl = wk.vv[l], wl = wk.pw[l];
-      for (int c = lane; c < m; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
+      for (int c = lane; c <= l; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
     }
     __syncthreads();
   }
@@ -763,21 +899,17 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     wk.sc[1] = hi;
   }
   __syncthreads();
-  // squared off-diagonals for the Sturm recurrence (reuse vv)
-  for (int i = tid; i < N; i += nt) wk.vv[i] = wk.e[i] * wk.e[i];
+  // squared off-diagonals for the Sturm recurrence (reuse vv), FP32 copies
+  for (int i = tid; i < N; i += nt) {
+    wk.vv[i] = wk.e[i] * wk.e[i];
+    wk.d32[i] = (float)wk.d[i];
+    wk.e32[i] = (float)(wk.e[i] * wk.e[i]);
+  }
   const double glo = wk.sc[0], ghi = wk.sc[1];
   __syncthreads();
-  const double tol_abs = 1e-15 * fmax(ghi - glo, 1e-300);
   double lp = 0.0, en = 0.0, cf = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
-    double lo = glo, hi = ghi;
-    for (int itn = 0; itn < 200; ++itn) {
-      const double mid = 0.5 * (lo + hi);
-      if (hi - lo <= fmax(tol_abs, 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
-      if (mid <= lo || mid >= hi) break;
-      if (sturm_count(wk.d, wk.vv, N, mid) > idx) hi = mid; else lo = mid;
-    }
-    const double mu = fmax(0.5 * (lo + hi), 0.0);
+    const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
     const double eps = sqrt(mu);
     const double x = 0.5 * beta * eps;
     const double qx = exp(-2.0 * x);

@@ -11,7 +11,7 @@ size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC) {
              : (KC == 4 ? 3 * align16(nq * 16) + align16(nlut * 4) : 4 * align16(nlut * 4));
   b += align16(nc * sizeof(ChainSm));
   b += align16(64 * 8);
-  if (kind == kKitaev) b += align16(N * (N + 1) * 8) + 4 * align16(N * 8) + align16(64 * 8);
+  if (kind == kKitaev) b += align16(N * (N + 1) * 8) + 4 * align16(N * 8) + align16(64 * 8) + 2 * align16(N * 4);
   b += align16((size_t)nc * (2 + K) * P * 4);
   return b;
 }
@@ -36,10 +36,10 @@ __global__ void random_init_kernel(uint32_t* bits, int n_chains, int N, int Wd, 
   bits[idx] = out;
 }
 
-cudaError_t launch_kIsing_kFP64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kIsing_kMixed(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kKitaev_kFP64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kKitaev_kMixed(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t launch_kIsing_kFP64(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t launch_kIsing_kMixed(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t launch_kKitaev_kFP64(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t launch_kKitaev_kMixed(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kIsing_kFP64(size_t);
 cudaError_t limit_kIsing_kMixed(size_t);
 cudaError_t limit_kKitaev_kFP64(size_t);
@@ -54,15 +54,17 @@ void specialisation(int K, int k, int& KC, int& kC) {
   }
 }
 
-cudaError_t launch_step(int kind, int prec, int K, int k, const LaunchParams& p, int grid, size_t smem,
+int threads_for(int kind, int max_N) { return (kind == kKitaev && max_N <= 64) ? 128 : 256; }
+
+cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
                         cudaStream_t st) {
   int KC, kC;
   specialisation(K, k, KC, kC);
   if (kind == kIsing)
-    return prec == kFP64 ? launch_kIsing_kFP64(KC, kC, p, grid, smem, st)
-                         : launch_kIsing_kMixed(KC, kC, p, grid, smem, st);
-  return prec == kFP64 ? launch_kKitaev_kFP64(KC, kC, p, grid, smem, st)
-                       : launch_kKitaev_kMixed(KC, kC, p, grid, smem, st);
+    return prec == kFP64 ? launch_kIsing_kFP64(KC, kC, nt, p, grid, smem, st)
+                         : launch_kIsing_kMixed(KC, kC, nt, p, grid, smem, st);
+  return prec == kFP64 ? launch_kKitaev_kFP64(KC, kC, nt, p, grid, smem, st)
+                       : launch_kKitaev_kMixed(KC, kC, nt, p, grid, smem, st);
 }
 
 cudaError_t set_smem_limits(size_t bytes) {

@@ -12,8 +12,12 @@ struct LaunchParams;
 void specialisation(int K, int k, int& KC, int& kC);
 // Dynamic shared memory of one CTA of the fused kernel.
 size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC);
-// Launch the fused kernel: grid = total tiles of all jobs in p (one model per launch).
-cudaError_t launch_step(int kind, int prec, int K, int k, const LaunchParams& p, int grid, size_t smem,
+// Threads per CTA for a launch whose largest lattice has max_N sites: 128 for
+// Kitaev matrices up to 64 x 64 (fewer idle warps at the eigen-stage barriers),
+// else 256 (measured).
+int threads_for(int kind, int max_N);
+// Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch).
+cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
                         cudaStream_t st);
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);

@@ -23,7 +23,7 @@ struct ChainSm {
   double Fp, Bp, lpp, Ep;
   double otp[kNobs];
   double beta;
-  unsigned long long acc, rec;
+  unsigned long long acc, rec, rec_mh;
   int cur, flag_rec, flag_acc, pad;
 };
 
@@ -37,8 +37,8 @@ static __device__ __noinline__ void free_energy64(const JobDev& jb, const Tabs& 
   for (int i = 0; i < 4; ++i) out[i] = o[i];
 }
 
-template <int KIND, int PREC, int KC, int kC>
-__global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
+template <int KIND, int PREC, int KC, int kC, int NT>
+__global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN_BLOCKS) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
   int jid = 0;
   while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
   const JobDev& jb = prm.job[jid];
@@ -103,11 +103,15 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
     sp += align16((size_t)N * 8);
     wk.sc = (double*)sp;
     sp += align16(64 * 8);
+    wk.d32 = (float*)sp;
+    sp += align16((size_t)N * 4);
+    wk.e32 = (float*)sp;
+    sp += align16((size_t)N * 4);
   }
   uint32_t* planes = (uint32_t*)sp;
 
   Grp g;
-  g.tpc = kThreads / jb.nc;
+  g.tpc = NT / jb.nc;
   g.gl = tid / g.tpc;
   g.r = tid - g.gl * g.tpc;
   g.c = ltile * jb.nc + g.gl;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
   uint32_t* my = planes + (size_t)g.gl * (2 + K) * P;
   ChainSm& ch = cs[g.gl];
 
-  for (int i = tid; i < nlut; i += kThreads) {
+  for (int i = tid; i < nlut; i += NT) {
     if (PREC == kFP64) {
       t64[0][i] = jb.f64[i];
       t64[1][i] = jb.b64[i];
@@ -130,13 +134,13 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
     }
   }
   if (PREC == kMixed && KC == 4) {
-    for (int i = tid; i < nq; i += kThreads) {
+    for (int i = tid; i < nq; i += NT) {
       t4[0][i] = jb.fd4[i];
       t4[1][i] = jb.fh4[i];
       t4[2][i] = jb.fl4[i];
     }
   }
-  for (int i = tid; i < jb.nc * (2 + K) * P; i += kThreads) planes[i] = 0u;
+  for (int i = tid; i < jb.nc * (2 + K) * P; i += NT) planes[i] = 0u;
   __syncthreads();
   if (g.r == 0) {
     // every slot, including the unused slots of a partial last tile, starts
@@ -146,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
     ch.beta = 1.0;
     ch.acc = 0ull;
     ch.rec = 0ull;
+    ch.rec_mh = 0ull;
     ch.cur = 0;
     ch.flag_rec = 0;
     ch.flag_acc = 0;
@@ -157,7 +162,12 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
       ch.Fb = jb.Fb[g.c];
       ch.lp = jb.logpi[g.c];
       ch.E = jb.Ephys[g.c];
-      for (int o = 0; o < kNobs; ++o) ch.ot[o] = jb.obs_t[(size_t)g.c * kNobs + o];
+      for (int o = 0; o < kNobs; ++o) {
+        ch.ot[o] = jb.obs_t[(size_t)g.c * kNobs + o];
+        // sums continue in place: the same sequence of additions however a
+        // run is split into launches or batched with other jobs
+        ch.os[o] = jb.obs[(size_t)g.c * kNobs + o];
+      }
       ch.beta = 1.0 / jb.T[g.c];
     }
   }
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
           const uint4 w = philox4x32_10(make_uint4(0u, kTagAcc, step, g.cid), k0, k1);
           const double lu = log(((double)w.x + 0.5) * 0x1p-32);
           ch.flag_acc = lu < logr;
-          ch.rec += 1ull;
+          ch.rec_mh += 1ull;
         }
       }
     }
@@ -309,41 +319,56 @@ __global__ void __launch_bounds__(kThreads, 2) crbm_step_kernel(const __grid_con
       jb.Ephys[g.c] = ch.E;
       for (int o = 0; o < kNobs; ++o) {
         jb.obs_t[(size_t)g.c * kNobs + o] = ch.ot[o];
-        jb.obs[(size_t)g.c * kNobs + o] += ch.os[o];
+        jb.obs[(size_t)g.c * kNobs + o] = ch.os[o];
       }
       jb.acc[g.c] += ch.acc;
-      jb.rec[g.c] += ch.rec;
+      jb.rec[2 * (size_t)g.c] += ch.rec;
+      jb.rec[2 * (size_t)g.c + 1] += ch.rec_mh;
     }
   }
 }
 
 
 // Launch one instantiation; raise its dynamic shared-memory limit.
-template <int KIND, int PREC, int KC, int kC>
+template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  crbm_step_kernel<KIND, PREC, KC, kC><<<grid, kThreads, smem, st>>>(p);
+  crbm_step_kernel<KIND, PREC, KC, kC, NT><<<grid, NT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
-template <int KIND, int PREC, int KC, int kC>
+template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t limit_inst(size_t bytes) {
-  return cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC>,
+  return cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC, NT>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Variants compiled for each (kind, precision): (K, k) = (4, 5), (4, 3), runtime.
-#define CRBM_VARIANTS(KIND, PREC)                                                          \
-  cudaError_t launch_##KIND##_##PREC(int KC, int kC, const LaunchParams& p, int grid,       \
-                                     size_t smem, cudaStream_t st) {                         \
-    if (KC == 4 && kC == 5) return launch_inst<KIND, PREC, 4, 5>(p, grid, smem, st);        \
-    if (KC == 4 && kC == 3) return launch_inst<KIND, PREC, 4, 3>(p, grid, smem, st);        \
-    return launch_inst<KIND, PREC, 0, 0>(p, grid, smem, st);                                \
-  }                                                                                          \
-  cudaError_t limit_##KIND##_##PREC(size_t bytes) {                                          \
-    cudaError_t e = limit_inst<KIND, PREC, 4, 5>(bytes);                                     \
-    if (e == cudaSuccess) e = limit_inst<KIND, PREC, 4, 3>(bytes);                           \
-    if (e == cudaSuccess) e = limit_inst<KIND, PREC, 0, 0>(bytes);                           \
-    return e;                                                                                \
+template <int KIND, int PREC, int NT>
+cudaError_t launch_nt(int KC, int kC, const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (KC == 4 && kC == 5) return launch_inst<KIND, PREC, 4, 5, NT>(p, grid, smem, st);
+  if (KC == 4 && kC == 3) return launch_inst<KIND, PREC, 4, 3, NT>(p, grid, smem, st);
+  return launch_inst<KIND, PREC, 0, 0, NT>(p, grid, smem, st);
+}
+
+template <int KIND, int PREC, int NT>
+cudaError_t limit_nt(size_t bytes) {
+  cudaError_t e = limit_inst<KIND, PREC, 4, 5, NT>(bytes);
+  if (e == cudaSuccess) e = limit_inst<KIND, PREC, 4, 3, NT>(bytes);
+  if (e == cudaSuccess) e = limit_inst<KIND, PREC, 0, 0, NT>(bytes);
+  return e;
+}
+
+// Variants compiled for each (kind, precision): (K, k) = (4, 5), (4, 3), runtime;
+// CTAs of 256 threads, plus 128 threads for the Kitaev kind (small matrices).
+#define CRBM_VARIANTS(KIND, PREC)                                                            \
+  cudaError_t launch_##KIND##_##PREC(int KC, int kC, int nt, const LaunchParams& p, int grid, \
+                                     size_t smem, cudaStream_t st) {                           \
+    if (KIND == kKitaev && nt == 128) return launch_nt<KIND, PREC, 128>(KC, kC, p, grid, smem, st); \
+    return launch_nt<KIND, PREC, 256>(KC, kC, p, grid, smem, st);                             \
+  }                                                                                            \
+  cudaError_t limit_##KIND##_##PREC(size_t bytes) {                                            \
+    cudaError_t e = limit_nt<KIND, PREC, 256>(bytes);                                          \
+    if (e == cudaSuccess && KIND == kKitaev) e = limit_nt<KIND, PREC, 128>(bytes);             \
+    return e;                                                                                  \
   }
 
 }  // namespace crbm
