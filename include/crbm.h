@@ -55,7 +55,7 @@ typedef enum {
     CRBM_ENOMEM = -2,   /* job does not fit the context's HBM budget or dev_mem  */
     CRBM_ECUDA = -3,    /* a CUDA runtime call failed (message in last_error)    */
     CRBM_ETIMEOUT = -4, /* a device-side wait gave up after its iteration limit  */
-    CRBM_EBUSY = -5     /* job still referenced by an unfinished batch plan      */
+    CRBM_EBUSY = -5     /* job still referenced by a live CUDA graph             */
 } crbm_status;
 
 typedef enum { CRBM_ISING = 0, CRBM_KITAEV = 1 } crbm_model_kind;
@@ -133,6 +133,31 @@ CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, 
  * job alone.  At most 16 jobs per call; a job may appear once. */
 CRBM_API int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g,
                    int correct, int precision, void* cuda_stream);
+
+/* Capture `repeats` consecutive crbm_run_batch calls of the same jobs (S
+ * proposals each, same g / correct / precision) into a CUDA graph and
+ * instantiate it.  The jobs' step counters live in device memory, so every
+ * replay continues the chains (each replay advances every job by repeats*S
+ * proposals) and the result equals the same number of direct runs.  Work
+ * already enqueued on the jobs is waited for.  Jobs of a live graph cannot be
+ * released (CRBM_EBUSY).  *graph_id receives the id. */
+CRBM_API int crbm_graph_create(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g, int correct,
+                               int precision, int repeats, int* graph_id);
+
+/* Replay a graph on cuda_stream (asynchronous). */
+CRBM_API int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream);
+
+/* Wait for the graph's jobs and free the graph. */
+CRBM_API int crbm_graph_destroy(crbm_ctx* ctx, int graph_id);
+
+/* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
+ * lattice side L and `precision`: every admissible value is timed on a
+ * temporary job that fills the GPU (device memory allocated and freed by this
+ * call), and the fastest is used by every job of this (kind, L, K, k) created
+ * afterwards in this context.  *best_nc / *best_us_per_proposal (may be NULL)
+ * receive the choice and its time per chain-proposal in microseconds. */
+CRBM_API int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc,
+                       double* best_us_per_proposal);
 
 /* Wait for the job's last enqueued work and check the device error flag.
  * Errors: CRBM_ECUDA, CRBM_ETIMEOUT (a device wait hit its iteration cap). */

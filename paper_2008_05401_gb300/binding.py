@@ -43,6 +43,11 @@ _SIGS = {
     "crbm_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "crbm_run_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p]),
+    "crbm_graph_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.POINTER(C.c_int)]),
+    "crbm_graph_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "crbm_graph_destroy": (C.c_int, [C.c_void_p, C.c_int]),
+    "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -132,6 +137,28 @@ def crbm_run_batch(ctx, job_ids, S, g=1, correct=1, precision=FP64, stream=0):
     _check(ctx, load().crbm_run_batch(ctx, len(ids), _ptr(ids), S, g, correct, precision, C.c_void_p(stream)))
 
 
+def crbm_graph_create(ctx, job_ids, S, g=1, correct=1, precision=FP64, repeats=1) -> int:
+    ids = np.ascontiguousarray(job_ids, dtype=np.int32)
+    gid = C.c_int()
+    _check(ctx, load().crbm_graph_create(ctx, len(ids), _ptr(ids), S, g, correct, precision, repeats,
+                                         C.byref(gid)))
+    return gid.value
+
+
+def crbm_graph_launch(ctx, graph_id, stream=0):
+    _check(ctx, load().crbm_graph_launch(ctx, graph_id, C.c_void_p(stream)))
+
+
+def crbm_graph_destroy(ctx, graph_id):
+    _check(ctx, load().crbm_graph_destroy(ctx, graph_id))
+
+
+def crbm_tune(ctx, model_id, L, precision=FP64):
+    nc, us = C.c_int(), C.c_double()
+    _check(ctx, load().crbm_tune(ctx, model_id, L, precision, C.byref(nc), C.byref(us)))
+    return nc.value, us.value
+
+
 def crbm_sync(ctx, job_id):
     _check(ctx, load().crbm_sync(ctx, job_id))
 
@@ -198,6 +225,19 @@ class Job:
         self.mem = None
 
 
+class Graph:
+    def __init__(self, ctx: "Context", gid: int, jobs, steps: int):
+        self.ctx, self.id, self.jobs, self.steps = ctx, gid, list(jobs), steps
+
+    def launch(self, stream=None):
+        crbm_graph_launch(self.ctx.h, self.id, _stream_handle(stream))
+        for j in self.jobs:
+            j.step += self.steps
+
+    def destroy(self):
+        crbm_graph_destroy(self.ctx.h, self.id)
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
         return 0
@@ -229,6 +269,15 @@ class Context:
         jid = crbm_init_chains(self.h, model_id, L, T, J, seed, chain_id_base, init_bits,
                                mem.data_ptr() if len(T) else 0, mem.numel())
         return Job(self, jid, L, len(T), mem)
+
+    def tune(self, model_id, L, precision=FP64):
+        """Pick the fastest chains-per-CTA for (model, L); returns (nc, us per chain-proposal)."""
+        return crbm_tune(self.h, model_id, L, precision)
+
+    def graph(self, jobs, S, g=1, correct=True, precision=FP64, repeats=1) -> "Graph":
+        """Capture `repeats` batched runs of S proposals into a replayable CUDA graph."""
+        gid = crbm_graph_create(self.h, [j.id for j in jobs], S, g, int(correct), precision, repeats)
+        return Graph(self, gid, jobs, S * repeats)
 
     def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
         crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))

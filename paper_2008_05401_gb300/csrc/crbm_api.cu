@@ -3,6 +3,8 @@
 // filters), jobs laid out in caller-owned device memory, and kernel launches.
 #include <cmath>
 #include <cstdarg>
+#include <map>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -31,7 +33,7 @@ struct Model {
 };
 
 struct Layout {
-  size_t bits, T, F, Fb, lp, E, ot, os, acc, rec, total;
+  size_t bits, T, F, Fb, lp, E, ot, os, acc, rec, step, total;
 };
 
 struct Job {
@@ -64,7 +66,8 @@ Layout make_layout(int L, int n) {
   y.os = take((size_t)n * 8 * kNobs);
   y.acc = take((size_t)n * 8);
   y.rec = take((size_t)n * 16);
-  y.total = off;
+  y.step = take(8);
+  y.total = n > 0 ? off : 0;   // an empty job needs no device memory
   return y;
 }
 
@@ -95,6 +98,16 @@ struct crbm_ctx {
   // non-blocking stream of the context's own copies and evaluation launches,
   // so that job set-up never waits for other streams' work
   cudaStream_t own = nullptr;
+  struct Graph {
+    bool live = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> jobs;
+    uint64_t steps = 0;   // proposals per replay
+  };
+  std::vector<Graph> graphs;
+  // chains per CTA chosen by crbm_tune for (kind, L, K, k)
+  std::map<std::tuple<int, int, int, int>, int> tuned;
 };
 
 static int fail(crbm_ctx* c, int code, const char* fmt, ...) {
@@ -159,7 +172,7 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.fl4 = m.d_q + 2 * m.nq;
   d.seed = j.seed;
   d.cid_base = j.cid_base;
-  d.step0 = j.step;
+  d.step = (unsigned long long*)(j.mem + j.lay.step);
   unsigned char* b = j.mem;
   d.bits = (uint32_t*)(b + j.lay.bits);
   d.T = (const double*)(b + j.lay.T);
@@ -217,7 +230,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
-      if (threads_for(j.kind, j.N) == nt) part.push_back(id);
+      if (j.n > 0 && threads_for(j.kind, j.N) == nt) part.push_back(id);
     }
     if (part.empty()) continue;
     const int rc = launch_group(ctx, part, S, g, correct, prec, mode, nt, st);
@@ -264,6 +277,10 @@ int crbm_destroy(crbm_ctx* ctx) {
     if (m.d_q) cudaFree(m.d_q);
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
+  for (auto& gr : ctx->graphs) {
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (gr.graph) cudaGraphDestroy(gr.graph);
+  }
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
   return CRBM_OK;
@@ -431,6 +448,10 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   j.Wd = (j.N + 31) / 32;
   j.n = n_chains;
   j.nc = chains_per_tile(m.kind, L);
+  {
+    const auto it = ctx->tuned.find(std::make_tuple(m.kind, L, m.K, m.k));
+    if (it != ctx->tuned.end()) j.nc = it->second;
+  }
   j.tiles = (n_chains + j.nc - 1) / j.nc;
   if (m.kind == kIsing) {
     j.J[0] = n_chains > 0 ? J[0] : 1.0;
@@ -457,6 +478,7 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
     CK(cudaMemsetAsync(b + lay.os, 0, (size_t)n_chains * 8 * kNobs, o), "zero sums");
     CK(cudaMemsetAsync(b + lay.acc, 0, (size_t)n_chains * 8, o), "zero accepts");
     CK(cudaMemsetAsync(b + lay.rec, 0, (size_t)n_chains * 16, o), "zero recomputes");
+    CK(cudaMemsetAsync(b + lay.step, 0, 8, o), "zero step");
   }
   ctx->jobs.push_back(j);
   const int id = (int)ctx->jobs.size() - 1;
@@ -480,13 +502,9 @@ static int check_run_args(crbm_ctx* ctx, int64_t S, int g, int correct, int prec
   return CRBM_OK;
 }
 
-int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g, int correct,
-                   int precision, void* cuda_stream) {
-  if (!ctx) return CRBM_EINVAL;
-  int rc = check_run_args(ctx, S, g, correct, precision);
-  if (rc) return rc;
+static int check_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, uint64_t total_steps,
+                       std::vector<int>& ids) {
   if (n_jobs < 1 || n_jobs > kMaxJobs || !job_ids) return fail(ctx, CRBM_EINVAL, "n_jobs=%d outside [1,%d]", n_jobs, kMaxJobs);
-  std::vector<int> ids;
   int kind = -1, Kb = 0, kb = 0;
   for (int i = 0; i < n_jobs; ++i) {
     Job* j = get_job(ctx, job_ids[i]);
@@ -500,25 +518,192 @@ int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int
     kind = j->kind;
     Kb = mj.K;
     kb = mj.k;
-    if (j->step + (uint64_t)S > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
+    if (j->step + total_steps > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
     ids.push_back(job_ids[i]);
   }
-  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  return CRBM_OK;
+}
+
+// Enqueue S proposals of the jobs on st, in launches of at most 2^20 proposals.
+static int enqueue_runs(crbm_ctx* ctx, const std::vector<int>& ids, int64_t S, int g, int correct, int precision,
+                        cudaStream_t st) {
   int64_t left = S;
   while (left > 0) {
     const int chunk = (int)(left < (1 << 20) ? left : (1 << 20));
-    rc = launch_jobs(ctx, ids, chunk, g, correct, precision, 0, st);
+    const int rc = launch_jobs(ctx, ids, chunk, g, correct, precision, 0, st);
     if (rc) return rc;
-    for (int id : ids) ctx->jobs[id].step += (uint64_t)chunk;
     left -= chunk;
   }
-  for (int id : ids) ctx->jobs[id].stream = st;
+  return CRBM_OK;
+}
+
+int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g, int correct,
+                   int precision, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  int rc = check_run_args(ctx, S, g, correct, precision);
+  if (rc) return rc;
+  std::vector<int> ids;
+  if ((rc = check_batch(ctx, n_jobs, job_ids, (uint64_t)S, ids))) return rc;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if ((rc = enqueue_runs(ctx, ids, S, g, correct, precision, st))) return rc;
+  for (int id : ids) {
+    ctx->jobs[id].step += (uint64_t)S;
+    ctx->jobs[id].stream = st;
+  }
+  return CRBM_OK;
+}
+
+int crbm_graph_create(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g, int correct, int precision,
+                      int repeats, int* graph_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (!graph_id) return fail(ctx, CRBM_EINVAL, "null graph_id");
+  if (repeats < 1) return fail(ctx, CRBM_EINVAL, "repeats must be >= 1");
+  int rc = check_run_args(ctx, S, g, correct, precision);
+  if (rc) return rc;
+  std::vector<int> ids;
+  if ((rc = check_batch(ctx, n_jobs, job_ids, 0, ids))) return rc;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // the graph reads and advances the jobs' device step counters: make sure
+  // earlier work on the jobs' streams has finished before capturing
+  for (int id : ids) CK(cudaStreamSynchronize(ctx->jobs[id].stream), "stream sync");
+  crbm_ctx::Graph gr;
+  CK(cudaStreamBeginCapture(ctx->own, cudaStreamCaptureModeThreadLocal), "begin capture");
+  for (int r = 0; r < repeats && rc == CRBM_OK; ++r) rc = enqueue_runs(ctx, ids, S, g, correct, precision, ctx->own);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->own, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  if (ei != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(ctx, ei, "graph instantiate");
+  }
+  gr.live = true;
+  gr.graph = graph;
+  gr.exec = exec;
+  gr.jobs = ids;
+  gr.steps = (uint64_t)S * (uint64_t)repeats;
+  ctx->graphs.push_back(gr);
+  *graph_id = (int)ctx->graphs.size() - 1;
+  return CRBM_OK;
+}
+
+int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  if (graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id].live)
+    return fail(ctx, CRBM_EINVAL, "bad graph id %d", graph_id);
+  crbm_ctx::Graph& gr = ctx->graphs[graph_id];
+  for (int id : gr.jobs)
+    if (ctx->jobs[id].step + gr.steps > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(cudaGraphLaunch(gr.exec, st), "graph launch");
+  for (int id : gr.jobs) {
+    ctx->jobs[id].step += gr.steps;
+    ctx->jobs[id].stream = st;
+  }
+  return CRBM_OK;
+}
+
+int crbm_graph_destroy(crbm_ctx* ctx, int graph_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id].live)
+    return fail(ctx, CRBM_EINVAL, "bad graph id %d", graph_id);
+  crbm_ctx::Graph& gr = ctx->graphs[graph_id];
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  for (int id : gr.jobs) CK(cudaStreamSynchronize(ctx->jobs[id].stream), "stream sync");
+  cudaGraphExecDestroy(gr.exec);
+  cudaGraphDestroy(gr.graph);
+  gr = crbm_ctx::Graph();
   return CRBM_OK;
 }
 
 int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision, void* cuda_stream) {
   return crbm_run_batch(ctx, 1, &job_id, S, g, correct, precision, cuda_stream);
+}
+
+int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, double* best_ms) {
+  if (!ctx) return CRBM_EINVAL;
+  if (model_id < 0 || model_id >= (int)ctx->models.size() || !ctx->models[model_id].live)
+    return fail(ctx, CRBM_EINVAL, "bad model id %d", model_id);
+  const Model& m = ctx->models[model_id];
+  if (!valid_L(m.kind, L) || m.k > L) return fail(ctx, CRBM_EINVAL, "lattice side L=%d not supported", L);
+  if (precision != CRBM_FP64 && precision != CRBM_MIXED) return fail(ctx, CRBM_EINVAL, "bad precision");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int N = L * L, nblk = (N + 3) / 4;
+  std::vector<int> cand;
+  if (m.kind == kIsing) {
+    for (int nc = 1; nc <= kThreads / 8; nc *= 2)
+      if ((nc == 1 || (nc / 2) * nblk < 8 * kThreads) &&
+          smem_bytes(m.kind, precision, L, m.K, m.k, nc, m.K == 4 ? 4 : 0) <= 100 * 1024)
+        cand.push_back(nc);
+  } else {
+    cand.push_back(1);
+  }
+  // a temporary job large enough for every candidate to fill the GPU
+  const int n_chains = 4 * sms * cand.back();
+  const Layout lay = make_layout(L, n_chains);
+  unsigned char* mem = nullptr;
+  CK(cudaMalloc(&mem, lay.total), "cudaMalloc tuning job");
+  std::vector<double> T(n_chains, 2.0);
+  CK(cudaMemsetAsync(mem, 0, lay.total, ctx->own), "zero tuning job");
+  CK(cudaMemcpyAsync(mem + lay.T, T.data(), (size_t)n_chains * 8, cudaMemcpyHostToDevice, ctx->own), "copy T");
+  CK(launch_random_init((uint32_t*)(mem + lay.bits), n_chains, N, (N + 31) / 32, 12345, 0, ctx->own), "init");
+  Job j;
+  j.live = true;
+  j.model = model_id;
+  j.kind = m.kind;
+  j.L = L;
+  j.N = N;
+  j.Wd = (N + 31) / 32;
+  j.n = n_chains;
+  j.seed = 12345;
+  j.mem = mem;
+  j.bytes = lay.total;
+  j.lay = lay;
+  j.stream = ctx->own;
+  ctx->jobs.push_back(j);
+  const int id = (int)ctx->jobs.size() - 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = cand[0], rc = CRBM_OK;
+  float best_t = 1e30f;
+  for (int nc : cand) {
+    Job& jj = ctx->jobs[id];
+    jj.nc = nc;
+    jj.tiles = (n_chains + nc - 1) / nc;
+    if ((rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, ctx->own))) break;        // F, log pi of the state
+    if ((rc = launch_jobs(ctx, {id}, 2, 1, 1, precision, 0, ctx->own))) break;    // warm-up
+    cudaEventRecord(e0, ctx->own);
+    if ((rc = launch_jobs(ctx, {id}, 4, 1, 1, precision, 0, ctx->own))) break;
+    cudaEventRecord(e1, ctx->own);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)n_chains;       // per chain: candidates run different numbers of CTAs per SM
+    if (ms < best_t) {
+      best_t = ms;
+      best = nc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(ctx->own);
+  ctx->jobs[id].live = false;
+  cudaFree(mem);
+  if (rc) return rc;
+  ctx->tuned[std::make_tuple(m.kind, L, m.K, m.k)] = best;
+  if (best_nc) *best_nc = best;
+  if (best_ms) *best_ms = (double)best_t * 1e3 / 4.0;     // microseconds per chain-proposal
+  return CRBM_OK;
 }
 
 int crbm_sync(crbm_ctx* ctx, int job_id) {
@@ -582,12 +767,18 @@ int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t s
   if (j->n == 0) return CRBM_OK;
   CK(cudaMemcpyAsync(j->mem + j->lay.bits, bits, (size_t)j->n * j->Wd * 4, cudaMemcpyHostToDevice, ctx->own),
      "copy bits");
+  const unsigned long long st = step;
+  CK(cudaMemcpyAsync(j->mem + j->lay.step, &st, 8, cudaMemcpyHostToDevice, ctx->own), "copy step");
   return evaluate(ctx, job_id);
 }
 
 int crbm_release(crbm_ctx* ctx, int job_id) {
   Job* j = get_job(ctx, job_id);
   if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  for (size_t gi = 0; gi < ctx->graphs.size(); ++gi)
+    if (ctx->graphs[gi].live)
+      for (int id : ctx->graphs[gi].jobs)
+        if (id == job_id) return fail(ctx, CRBM_EBUSY, "job %d is part of live graph %zu", job_id, gi);
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   CK(cudaStreamSynchronize(j->stream), "stream sync");
   ctx->used -= j->bytes;

@@ -61,7 +61,8 @@ struct JobDev {
   const float4* fd4;            // [k][2^k] filter-interleaved, K <= 4
   const float4* fh4;
   const float4* fl4;
-  uint64_t seed, cid_base, step0;
+  uint64_t seed, cid_base;
+  unsigned long long* step;     // device-resident step counter of the job (proposals made)
   uint32_t* bits;               // [n_chains][Wd]
   const double* T;              // [n_chains]
   double* F;                    // [n_chains]

@@ -204,8 +204,11 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
   }
 
   const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
+  // the step counter lives in device memory (advanced by advance_steps after
+  // the launch), so a captured CUDA graph can be replayed
+  const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
   for (int s = 0; s < prm.S; ++s) {
-    const uint32_t step = (uint32_t)(jb.step0 + (uint64_t)s);
+    const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
     const int cur = ch.cur;
     uint32_t* v = my + cur * P;
     uint32_t* vp = my + (cur ^ 1) * P;
@@ -329,11 +332,22 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
 }
 
 
+// After a launch of S proposals: every job's device step counter += S.
+static __global__ void advance_steps_kernel(const __grid_constant__ LaunchParams p) {
+  const int i = threadIdx.x;
+  if (i < p.n_jobs) *p.job[i].step += (unsigned long long)p.S;
+}
+
 // Launch one instantiation; raise its dynamic shared-memory limit.
 template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
   crbm_step_kernel<KIND, PREC, KC, kC, NT><<<grid, NT, smem, st>>>(p);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && p.mode == 0 && p.S > 0) {
+    advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <int KIND, int PREC, int KC, int kC, int NT>

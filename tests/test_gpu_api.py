@@ -213,3 +213,62 @@ def test_run_on_a_side_stream(ctx):
     np.testing.assert_array_equal(job.state()[0], ref.state()[0])
     job.release()
     ref.release()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_cuda_graph_replay_equals_direct_runs(ctx, kind):
+    """A captured graph of 3 batched runs replayed twice continues the chains
+    exactly like 6 direct runs (device-resident step counters)."""
+    from paper_2008_05401_gb300 import KITAEV, MIXED, CrbmError
+    if kind == 0:
+        mid = _ising_model(ctx)
+        spec, J = [(16, 8, 0), (32, 3, 100)], (1.0,)
+    else:
+        W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=4)
+        mid = ctx.load_model(KITAEV, W, vb, hb)
+        spec, J = [(4, 5, 0), (10, 2, 100)], (1.0, 1.0, 1.0)
+
+    def make():
+        return [ctx.new_job(mid, kind, L, wl.ising_ladder(n, 4) if kind == 0 else wl.kitaev_ladder(n, 24), J,
+                            SEED, base, wl.pack_bits(wl.random_lattices(n, L, seed=L)), MIXED)
+                for L, n, base in spec]
+
+    graphed, direct = make(), make()
+    gr = ctx.graph(graphed, 4, precision=MIXED, repeats=3)
+    gr.launch()
+    gr.launch()
+    for _ in range(6):
+        ctx.run_batch(direct, 4, precision=MIXED)
+    with pytest.raises(CrbmError) as e:
+        graphed[0].release()
+    assert e.value.code == -5                                   # job of a live graph
+    for a, b in zip(graphed, direct):
+        sa, sb = _snapshot(a), _snapshot(b)
+        assert sa["step"] == 24
+        for key in sa:
+            np.testing.assert_array_equal(sa[key], sb[key], err_msg=key)
+    gr.destroy()
+    for j in graphed + direct:
+        j.release()
+
+
+def test_autotuned_tile_shape_keeps_parity(ctx):
+    """crbm_tune picks chains-per-CTA by timing; jobs created afterwards use it
+    and still reproduce the oracle bit for bit."""
+    from _common import decisions_are_clear, oracle_chains, run_oracle
+    from paper_2008_05401_gb300 import ISING, MIXED
+    W, hb, vb = wl.gaussian_crbm(4, 5, 0.2, seed=8)
+    mid = ctx.load_model(ISING, W, vb, hb)
+    nc, us = ctx.tune(mid, 16, MIXED)
+    assert nc in (1, 2, 4, 8, 16, 32) and us > 0
+    n, L, S = 37, 16, 6
+    T = wl.ising_ladder(n, 8)
+    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=44))
+    job = ctx.new_job(mid, ISING, L, T, (1.0,), SEED, 0, bits0, MIXED)
+    job.run(S, precision=MIXED)
+    ref = oracle_chains("ising", W, hb, vb, L, T, (1.0,), SEED, n, bits0)
+    worst = run_oracle(ref, S)
+    if decisions_are_clear(worst):
+        np.testing.assert_array_equal(job.state()[0], wl.pack_bits(ref.v))
+        np.testing.assert_array_equal(job.observables()[1], ref.accepts)
+    job.release()
