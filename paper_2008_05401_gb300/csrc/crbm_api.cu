@@ -33,7 +33,7 @@ struct Model {
 };
 
 struct Layout {
-  size_t bits, T, F, Fb, lp, E, ot, os, acc, rec, step, total;
+  size_t bits, T, F, Fb, Lb, lp, E, ot, os, acc, rec, step, total;
 };
 
 struct Job {
@@ -60,6 +60,7 @@ Layout make_layout(int L, int n) {
   y.T = take((size_t)n * 8);
   y.F = take((size_t)n * 8);
   y.Fb = take((size_t)n * 8);
+  y.Lb = take((size_t)n * 8);
   y.lp = take((size_t)n * 8);
   y.E = take((size_t)n * 8);
   y.ot = take((size_t)n * 8 * kNobs);
@@ -171,6 +172,10 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.fh4 = m.d_q + m.nq;
   d.fl4 = m.d_q + 2 * m.nq;
   d.seed = j.seed;
+  for (int r = 0; r < 10; ++r) {
+    d.rk[2 * r] = (uint32_t)j.seed + (uint32_t)r * 0x9E3779B9u;
+    d.rk[2 * r + 1] = (uint32_t)(j.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+  }
   d.cid_base = j.cid_base;
   d.step = (unsigned long long*)(j.mem + j.lay.step);
   unsigned char* b = j.mem;
@@ -178,6 +183,7 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.T = (const double*)(b + j.lay.T);
   d.F = (double*)(b + j.lay.F);
   d.Fb = (double*)(b + j.lay.Fb);
+  d.Lb = (double*)(b + j.lay.Lb);
   d.logpi = (double*)(b + j.lay.lp);
   d.Ephys = (double*)(b + j.lay.E);
   d.obs_t = (double*)(b + j.lay.ot);
@@ -367,9 +373,10 @@ int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, doub
   // decisions: |p32 - p64| <= 0.25 ex2 + 2^-24 + rcp + |u32 - u| + 0.25 dx + 2^-25 |x|,
   // dx <= (terms + 1) 2^-24 S; factor 2 of safety
   const double common = 0.25 * ex2 + u24 + rcp + std::ldexp(1.0, -25) + std::ldexp(1.0, -33);
-  m.c0h = (float)(2.0 * (common + 0.25 * (k + 1) * u24 * sh) + 1e-14);
-  m.c0v = (float)(2.0 * (common + 0.25 * ((double)K * k + 1) * u24 * sv) + 1e-14);
-  m.c1 = (float)(2.0 * std::ldexp(1.0, -25));
+  // (decide32 compares in units of 2^-32: the constants are scaled by 2^32)
+  m.c0h = (float)std::ldexp(2.0 * (common + 0.25 * (k + 1) * u24 * sh) + 1e-14, 32);
+  m.c0v = (float)std::ldexp(2.0 * (common + 0.25 * ((double)K * k + 1) * u24 * sv) + 1e-14, 32);
+  m.c1 = (float)std::ldexp(2.0 * std::ldexp(1.0, -25), 32);
   // free energy, per softplus term: 0.5 ex2 + 2^-24 (1 + e) + ln2 lg2 + 2^-23 ln2
   // (ln 2 product) + error of the FP32 sum of k + 1 lo terms; factor 1.5 of safety
   const double lo1 = std::ldexp(1.0, -(gbits + 1));

@@ -62,11 +62,13 @@ struct JobDev {
   const float4* fh4;
   const float4* fl4;
   uint64_t seed, cid_base;
+  uint32_t rk[20];              // Philox round keys (k0 + r W0, k1 + r W1), r = 0..9
   unsigned long long* step;     // device-resident step counter of the job (proposals made)
   uint32_t* bits;               // [n_chains][Wd]
   const double* T;              // [n_chains]
   double* F;                    // [n_chains]
   double* Fb;                   // [n_chains] bound on |F - F_fp64| (0: exact)
+  double* Lb;                   // [n_chains] bound on |log pi - log pi_fp64| (0: exact)
   double* logpi;                // [n_chains]
   double* Ephys;                // [n_chains]
   double* obs_t;                // [n_chains][4] observables of the current lattice
@@ -94,6 +96,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Same rounds with the ten round keys precomputed (rk[2r], rk[2r+1]): the
+// key schedule of a launch is fixed, so the kernels read it from the launch
+// parameters instead of bumping the key in every call.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
   }
   return c;
 }
@@ -204,10 +219,12 @@ __device__ __forceinline__ float sigmoid32(float x) {
 // FP32 pre-activation error, the ex2/rcp errors, the conversion of the Philox
 // word, and the FP64 path's own rounding.  Returns 0/1 when the FP64 path
 // takes the same decision, 2 when the FP64 code has to decide.
+// The comparison runs in units of 2^-32 (p 2^32 against the Philox word), so
+// c0 and c1 arrive pre-scaled by 2^32.
 __device__ __forceinline__ uint32_t decide32(float x, uint32_t w, float c0, float c1) {
-  const float d = sigmoid32(x) - __uint2float_rn(w) * 0x1p-32f;
+  const float d = fmaf(sigmoid32(x), 0x1p32f, -__uint2float_rn(w));
   const float delta = fmaf(c1, fabsf(x), c0);
-  return d > delta ? 1u : (d < -delta ? 0u : 2u);
+  return fabsf(d) > delta ? (d > 0.0f ? 1u : 0u) : 2u;
 }
 
 // log(1 + e^x) without overflow.
@@ -358,7 +375,7 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
       uint4 w[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f)
-        w[f] = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * 5 + f), step, g.cid), k0, k1);
+        w[f] = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)(sub * 5 + f), step, g.cid), jb.rk);
       uint32_t nib[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -392,7 +409,7 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
       continue;
     }
     for (int f = 0; f < K; ++f) {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + f), step, g.cid), k0, k1);
+      const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + f), step, g.cid), jb.rk);
       const int base = f * k * T;
       uint32_t nib = 0;
 #pragma unroll
@@ -458,10 +475,33 @@ __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, co
       for (int a = 0; a < kU; ++a) {
         if (kC || a < k) {
           const int r = bwd_row(i, a, L);
+          // word offsets of this window, shared by the K hidden planes
+          int o0, o1, sh;
+          const bool wide = (L & 31) == 0;
+          if (wide) {
+            const int WL = L >> 5, wi = c >> 5;
+            o0 = r * WL + wi;
+            o1 = r * WL + ((wi + 1 == WL) ? 0 : wi + 1);
+            sh = c & 31;
+          } else {
+            const int off = r * L;
+            o0 = off >> 5;
+            o1 = o0 + 1;
+            sh = off & 31;
+          }
 #pragma unroll
           for (int f = 0; f < KU; ++f) {
             if (KC || f < K) {
-              const uint32_t win = row_window(h + f * P, L, r, c, k + 3);
+              const uint32_t* pl = h + f * P;
+              uint32_t win;
+              if (wide) {
+                win = __funnelshift_r(pl[o0], pl[o1], sh);
+              } else {
+                const uint32_t row = __funnelshift_r(pl[o0], pl[o1], sh) & ((1u << L) - 1u);
+                uint64_t rr = row;
+                for (int s2 = L; s2 < 64; s2 += L) rr |= (uint64_t)row << s2;
+                win = (uint32_t)(rr >> c);
+              }
               const int base = (f * k + a) * T;
 #pragma unroll
               for (int t = 0; t < 4; ++t) {
@@ -492,7 +532,7 @@ __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, co
         }
       }
     }
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + K), step, g.cid), k0, k1);
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + K), step, g.cid), jb.rk);
     uint32_t nib = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -646,8 +686,11 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
 // M_bw = 2 J_a u_bw) is reduced to tridiagonal form by Householder
 // reflections, its eigenvalues mu_l = eps_l^2 are found by bisection with
 // Sturm counts, and log pi = sum_l log 2cosh(beta eps_l / 2).
+// Packed lower triangle of a symmetric N x N matrix: element (i, c), c <= i.
+__device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
+
 struct KitaevWork {
-  double* A;       // N x (N+1), lower triangle used after the build
+  double* A;       // packed lower triangle, N (N+1) / 2 entries
   double* d;       // N
   double* e;       // N
   double* vv;      // N
@@ -807,15 +850,15 @@ __device__ __forceinline__ double eigen_idx(const KitaevWork& wk, int N, int idx
 
 __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
                                const KitaevWork& wk, double (&res)[3]) {
-  const int N = L * L, lda = N + 1, tid = threadIdx.x, nt = blockDim.x;
+  const int N = L * L, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double* A = wk.A;
   const double tx = 2.0 * J[0], ty = 2.0 * J[1], tz = 2.0 * J[2];
   // A = M^T M, row w accumulated in a fixed order (z, x, y bond of w, then the
   // three whites of that black site)
   for (int w = tid; w < N; w += nt) {
-    double* row = A + (size_t)w * lda;
-    for (int c = 0; c < N; ++c) row[c] = 0.0;
+    double* row = A + tri(w, 0);                    // lower-triangle row w: columns 0..w
+    for (int c = 0; c <= w; ++c) row[c] = 0.0;
     const int i = w / L, j = w - i * L;
     for (int typ = 0; typ < 3; ++typ) {
       int bi = i, bj = j;
@@ -827,9 +870,9 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       const int wz = b;
       const int wx = ((bi + 1 == L) ? 0 : bi + 1) * L + bj;
       const int wy = bi * L + ((bj + 1 == L) ? 0 : bj + 1);
-      row[wz] += mw * mz;
-      row[wx] += mw * tx;
-      row[wy] += mw * ty;
+      if (wz <= w) row[wz] += mw * mz;
+      if (wx <= w) row[wx] += mw * tx;
+      if (wy <= w) row[wy] += mw * ty;
     }
   }
   __syncthreads();
@@ -839,12 +882,12 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     const int m = N - j - 1;
     double s = 0.0;
     for (int i = j + 2 + tid; i < N; i += nt) {
-      const double a = A[(size_t)i * lda + j];
+      const double a = A[tri(i, j)];
       s += a * a;
     }
     s = block_sum(s, wk.sc);
-    const double x0 = A[(size_t)(j + 1) * lda + j];
-    if (tid == 0) wk.d[j] = A[(size_t)j * lda + j];
+    const double x0 = A[tri(j + 1, j)];
+    if (tid == 0) wk.d[j] = A[tri(j, j)];
     if (s == 0.0) {
       if (tid == 0) wk.e[j] = x0;
       __syncthreads();
@@ -855,15 +898,14 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     const double v0 = x0 - alpha;
     const double tau = 2.0 / (v0 * v0 + s);
     if (tid == 0) wk.e[j] = alpha;
-    for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[(size_t)(j + 1 + l) * lda + j];
+    for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
     __syncthreads();
     // p = tau * A22 v from the lower triangle (row part c <= l, column part c > l), one warp per row
-    double* A22 = A + (size_t)(j + 1) * lda + (j + 1);
     for (int l = warp; l < m; l += nw) {
       double acc = 0.0;
       for (int c = lane; c < m; c += 32) {
-        const int off = (c <= l) ? l * lda + c : c * lda + l;
-        acc = fma(A22[off], wk.vv[c], acc);
+        const int off = (c <= l) ? tri(j + 1 + l, j + 1 + c) : tri(j + 1 + c, j + 1 + l);
+        acc = fma(A[off], wk.vv[c], acc);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
@@ -878,16 +920,16 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     __syncthreads();
     // lower triangle of A22 -= v w^T + w v^T
     for (int l = warp; l < m; l += nw) {
-      double* row = A22 + (size_t)l * lda;
+      double* row = A + tri(j + 1 + l, j + 1);
       const double vl = wk.vv[l], wl = wk.pw[l];
       for (int c = lane; c <= l; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
     }
     __syncthreads();
   }
   if (tid == 0) {
-    wk.d[N - 2] = A[(size_t)(N - 2) * lda + (N - 2)];
-    wk.d[N - 1] = A[(size_t)(N - 1) * lda + (N - 1)];
-    wk.e[N - 2] = A[(size_t)(N - 1) * lda + (N - 2)];
+    wk.d[N - 2] = A[tri(N - 2, N - 2)];
+    wk.d[N - 1] = A[tri(N - 1, N - 1)];
+    wk.e[N - 2] = A[tri(N - 1, N - 2)];
     wk.e[N - 1] = 0.0;
     // Gershgorin interval
     double lo = 1e300, hi = -1e300;

@@ -12,6 +12,7 @@
 // for the common filter banks (0 = runtime values).
 #pragma once
 #include "crbm_device.cuh"
+#include "crbm_df64.cuh"
 #include "crbm_kernels.h"
 
 namespace crbm {
@@ -21,6 +22,7 @@ struct ChainSm {
   double ot[kNobs];      // observables of the current lattice
   double os[kNobs];      // running sums
   double Fp, Bp, lpp, Ep;
+  double lpb, lppb;      // bounds on |log pi - FP64 path's log pi| (current, proposed)
   double otp[kNobs];
   double beta;
   unsigned long long acc, rec, rec_mh;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
   KitaevWork wk;
   if (KIND == kKitaev) {
     wk.A = (double*)sp;
-    sp += align16((size_t)N * (N + 1) * 8);
+    sp += align16((size_t)N * (N + 1) / 2 * 8);
     wk.d = (double*)sp;
     sp += align16((size_t)N * 8);
     wk.e = (double*)sp;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     // every slot, including the unused slots of a partial last tile, starts
     // from a defined state: the plane index `cur` addresses shared memory
     ch.F = ch.Fb = ch.lp = ch.E = 0.0;
+    ch.lpb = ch.lppb = 0.0;
     for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.os[o] = 0.0;
     ch.beta = 1.0;
     ch.acc = 0ull;
@@ -160,6 +163,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     if (g.r == 0) {
       ch.F = jb.F[g.c];
       ch.Fb = jb.Fb[g.c];
+      ch.lpb = jb.Lb[g.c];
       ch.lp = jb.logpi[g.c];
       ch.E = jb.Ephys[g.c];
       for (int o = 0; o < kNobs; ++o) {
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
       }
       jb.F[g.c] = Fv;
       jb.Fb[g.c] = 0.0;
+      jb.Lb[g.c] = 0.0;
       jb.logpi[g.c] = lp;
       jb.Ephys[g.c] = E;
       for (int o = 0; o < kNobs; ++o) jb.obs_t[(size_t)g.c * kNobs + o] = ot[o];
@@ -224,8 +229,18 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     double fo[4];
     free_phase<PREC, KC, kC>(jb, tb, g, vp, fo);
     grp_reduce<4>(fo, g, scratch);
-    double kr[3] = {0.0, 0.0, 0.0};
-    if (KIND == kKitaev) kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
+    double kr[4] = {0.0, 0.0, 0.0, 0.0};
+    if (KIND == kKitaev) {
+      if (PREC == kMixed) {
+        kitaev_logpi_df(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
+      } else {
+        double k3[3];
+        kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3);
+        kr[0] = k3[0];
+        kr[1] = k3[1];
+        kr[2] = k3[2];
+      }
+    }
     double logu = 0.0;
     if (g.active && g.r == 0) {
       if (KIND == kIsing) {
@@ -239,6 +254,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         ch.lpp = kr[0];
         ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2]; ch.otp[3] = fo[3] / (double)N;
       }
+      ch.lppb = kr[3];
       ch.Fp = -jb.vb * fo[2] - fo[0];
       ch.Bp = (PREC == kMixed)
                   ? fo[1] + (double)K * (double)N * (1.5 * 0x1p-23 + (double)jb.csp) + 1e-12 * fabs(ch.Fp)
@@ -248,12 +264,12 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         ch.flag_acc = 1;
       } else {
         const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-        const uint4 w = philox4x32_10(make_uint4(0u, kTagAcc, step, g.cid), k0, k1);
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g.cid), jb.rk);
         logu = log(((double)w.x + 0.5) * 0x1p-32);
         if (PREC == kFP64) {
           ch.flag_acc = logu < logr;
         } else {
-          const double M = ch.Bp + ch.Fb +
+          const double M = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
                            1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
           if (logr - logu > M) ch.flag_acc = 1;
           else if (logu - logr > M) ch.flag_acc = 0;
@@ -280,6 +296,14 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         double f2[4];
         free_energy64(jb, tb64g, g3, v, f2);
         grp_reduce<4>(f2, g3, scratch);
+        // Kitaev: the FP64 eigen-stage of v' (and of v when its log-weight
+        // came from the df64 stage); one chain per CTA, so this is CTA-uniform
+        double k1v[3] = {0.0, 0.0, 0.0}, k0v[3] = {0.0, 0.0, 0.0};
+        const bool redo_v = ch.lpb != 0.0;
+        if (KIND == kKitaev) {
+          kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v);
+          if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v);
+        }
         if (g2.active && g.r == 0) {
           ch.Fp = -jb.vb * f1[2] - f1[0];
           ch.Bp = 0.0;
@@ -287,8 +311,18 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
             ch.F = -jb.vb * f2[2] - f2[0];
             ch.Fb = 0.0;
           }
+          if (KIND == kKitaev) {
+            ch.lpp = k1v[0];
+            ch.lppb = 0.0;
+            ch.Ep = k1v[1];
+            ch.otp[0] = k1v[1]; ch.otp[1] = k1v[1] * k1v[1]; ch.otp[2] = k1v[2];
+            if (redo_v) {
+              ch.lp = k0v[0];
+              ch.lpb = 0.0;
+            }
+          }
           const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-          const uint4 w = philox4x32_10(make_uint4(0u, kTagAcc, step, g.cid), k0, k1);
+          const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g.cid), jb.rk);
           const double lu = log(((double)w.x + 0.5) * 0x1p-32);
           ch.flag_acc = lu < logr;
           ch.rec_mh += 1ull;
@@ -301,6 +335,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         ch.F = ch.Fp;
         ch.Fb = ch.Bp;
         ch.lp = ch.lpp;
+        ch.lpb = ch.lppb;
         ch.E = ch.Ep;
         for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
         ch.acc += 1ull;
@@ -318,6 +353,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     if (g.r == 0) {
       jb.F[g.c] = ch.F;
       jb.Fb[g.c] = ch.Fb;
+      jb.Lb[g.c] = ch.lpb;
       jb.logpi[g.c] = ch.lp;
       jb.Ephys[g.c] = ch.E;
       for (int o = 0; o < kNobs; ++o) {

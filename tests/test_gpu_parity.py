@@ -146,3 +146,31 @@ def test_analytic_crbm_accepts_everything(ctx):
         _, acc, _ = job.observables()
         assert np.all(acc == 10)
         job.release()
+
+
+@pytest.mark.parametrize("L", [6, 10, 12])
+def test_kitaev_mixed_df64_stage_matches_fp64(ctx, L):
+    """The mixed path's df64 eigen-stage: lattices and acceptances identical to
+    the FP64 path over the whole temperature ladder (down to T = 0.005), and
+    log-weights far inside the certified bound (~1e-13 relative)."""
+    from paper_2008_05401_gb300 import FP64, KITAEV, MIXED
+    W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=L + 99)
+    n, S = 24, 4
+    T = wl.kitaev_ladder(n, 24)
+    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=L + 5))
+    mid = ctx.load_model(KITAEV, W, vb, hb)
+    a = ctx.new_job(mid, KITAEV, L, T, (1.0, 1.0, 1.0), SEED, 0, bits0, FP64)
+    b = ctx.new_job(mid, KITAEV, L, T, (1.0, 1.0, 1.0), SEED, 0, bits0, MIXED)
+    a.run(S, precision=FP64)
+    b.run(S, precision=MIXED)
+    np.testing.assert_array_equal(a.state()[0], b.state()[0])
+    _, acc_a, _ = a.observables()
+    _, acc_b, rec_b = b.observables()
+    np.testing.assert_array_equal(acc_a, acc_b)
+    lp_a, _, E_a = a.energies()
+    lp_b, _, E_b = b.energies()
+    np.testing.assert_allclose(lp_b, lp_a, rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(E_b, E_a, rtol=1e-9, atol=1e-9)
+    assert rec_b[:, 1].sum() <= n * S // 2          # MH recomputes stay the exception
+    a.release()
+    b.release()
