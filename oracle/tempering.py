@@ -13,7 +13,7 @@ x_i (target pi_i) and an RBM chain y_i (target P_CRBM ~ e^{-F}).  One cycle:
     pairing (0,1), (2,3), ... on even cycles and (1,2), (3,4), ... on odd ones;
  4. the observables of the physical chains are accumulated.
 Uniforms: acceptance of step 2 from tag TAG_SWAP of the physical chain (step =
-cycle); of step 3 from tag TAG_TEMP of the lower chain of the pair.  The
+cycle counter = the physical chains' step); of step 3 from tag TAG_TEMP of the lower chain of the pair.  The
 oracle evaluates the log-weight of a state at another temperature afresh; it
 depends on the state only through its single-fermion energies eps (Kitaev) or
 its energy E (Ising), so a fast path may reuse those.
@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import chain, kitaev, philox
+from . import chain, crbm, philox
 
 TAG_SWAP = 0xFFFFFFFD
 TAG_TEMP = 0xFFFFFFFC
@@ -33,16 +33,25 @@ def _log_weight_at(model, v, beta, J):
     return chain.target(model, v, beta, J)[0]
 
 
-def cycle(phys: chain.Chains, rbm: chain.Chains, k: int, c: int):
-    """One PT-exchange-correction cycle; mutates both chain sets.  Returns the
-    swap and temperature-exchange decisions for diagnostics."""
+def cycle(phys: chain.Chains, rbm: chain.Chains, k: int):
+    """One PT-exchange-correction cycle; mutates both chain sets.  The cycle
+    counter is the physical chains' step counter.  Returns the swap and
+    temperature-exchange decisions and how close each came to its threshold."""
     n = len(phys.chain_ids)
-    # 1. RBM chains: k Gibbs steps from their own states (no correction)
-    chain.step(rbm, g=k, correct=False)
+    c = int(phys.step)
+    # 1. RBM chains: k Gibbs steps from their own states, then the FP64 values
+    #    the exchange needs (no correction, no observables of their own)
+    y, bmargin = chain.propose(rbm, k)
+    rbm.v = y
+    rbm.F = crbm.free_energy(y, rbm.W, rbm.hb, rbm.vb)
+    rbm.logpi, rbm.E_phys, rbm.obs_terms = chain.target(rbm.model, y, rbm.beta, rbm.J)
+    rbm.step += 1
     # 2. physical <-> RBM exchange at every temperature
     log_a = (rbm.logpi - phys.logpi) + (rbm.F - phys.F)
     u = philox.uniforms(phys.seed, phys.chain_ids, c, TAG_SWAP, 1)[:, 0]
     swap = np.log(u) < log_a
+    swap_margin = np.abs(np.log(u) - log_a) / (
+        np.abs(rbm.logpi) + np.abs(phys.logpi) + np.abs(rbm.F) + np.abs(phys.F) + 1.0)
     for name in ("v", "F", "logpi", "E_phys", "obs_terms"):
         a, b = getattr(phys, name), getattr(rbm, name)
         m = swap.reshape((-1,) + (1,) * (a.ndim - 1))
@@ -53,6 +62,7 @@ def cycle(phys: chain.Chains, rbm: chain.Chains, k: int, c: int):
     i = np.arange(c % 2, n - 1, 2)
     j = i + 1
     temp = np.zeros(n, dtype=bool)
+    temp_margin = np.full(n, np.inf)
     if len(i):
         beta = phys.beta
         lp_ij = _log_weight_at(phys.model, phys.v[j], beta[i], phys.J)   # log pi_i(x_j)
@@ -60,6 +70,8 @@ def cycle(phys: chain.Chains, rbm: chain.Chains, k: int, c: int):
         log_b = lp_ij + lp_ji - phys.logpi[i] - phys.logpi[j]
         ub = philox.uniforms(phys.seed, phys.chain_ids[i], c, TAG_TEMP, 1)[:, 0]
         acc = np.log(ub) < log_b
+        temp_margin[i] = np.abs(np.log(ub) - log_b) / (
+            np.abs(lp_ij) + np.abs(lp_ji) + np.abs(phys.logpi[i]) + np.abs(phys.logpi[j]) + 1.0)
         temp[i[acc]] = True
         ii, jj = i[acc], j[acc]
         v_i, v_j = phys.v[ii].copy(), phys.v[jj].copy()
@@ -75,10 +87,14 @@ def cycle(phys: chain.Chains, rbm: chain.Chains, k: int, c: int):
     phys.obs += phys.obs_terms
     phys.accepts += swap
     phys.step += 1
-    return {"swap": swap, "temp": temp}
+    return {"swap": swap, "temp": temp, "bernoulli_margin": bmargin,
+            "swap_margin": swap_margin, "temp_margin": temp_margin}
 
 
-def run(phys, rbm, k, cycles, c0=0):
-    for c in range(c0, c0 + cycles):
-        cycle(phys, rbm, k, c)
+def run(phys, rbm, k, cycles, record=None):
+    """``cycles`` PT cycles; ``record`` (optional) sees the diagnostics of each."""
+    for _ in range(cycles):
+        d = cycle(phys, rbm, k)
+        if record is not None:
+            record(d)
     return phys, rbm
