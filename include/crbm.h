@@ -97,7 +97,8 @@ CRBM_API int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double
                     double v_bias, const double* h_bias, int* model_id);
 
 /* Bytes of caller-owned device memory one job needs: packed lattices, FP64
- * temperatures and energies, observable sums and counters, 256-byte aligned.
+ * temperatures and energies, observable sums and counters (and, for the
+ * Kitaev kind, the L*L single-fermion energies of each lattice), 256-byte aligned.
  * Returns 0 for arguments out of range. */
 CRBM_API size_t crbm_job_bytes(int kind, int L, int n_chains, int precision);
 
@@ -149,6 +150,37 @@ CRBM_API int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream);
 
 /* Wait for the graph's jobs and free the graph. */
 CRBM_API int crbm_graph_destroy(crbm_ctx* ctx, int graph_id);
+
+/* Parallel-tempering exchange correction (App. B.2, Fig. 8b), `cycles`
+ * cycles enqueued on cuda_stream.  phys_job holds the physical chains x_i
+ * (target pi_i at temperature T_i; the temperature belongs to the slot i),
+ * rbm_job the RBM chains y_i; both jobs must use the same model and have the
+ * same L, couplings and temperatures, chain by chain.  One cycle:
+ *   1. every RBM chain makes one proposal of g Gibbs steps without
+ *      correction (Eq. B4); F, log pi_i, E and the observables of the new
+ *      lattice are evaluated in FP64 (precision selects the arithmetic of the
+ *      Gibbs steps only; CRBM_MIXED takes the FP64 path's Bernoulli draws);
+ *   2. x_i and y_i are exchanged with probability min(1, a),
+ *      log a = [log pi_i(y) - log pi_i(x)] + [F(y) - F(x)] (Eq. B5 with the
+ *      pair (pi_i, P_CRBM)), uniform from tag 0xFFFFFFFD of chain i of
+ *      phys_job at step = the cycle counter (phys_job's step counter);
+ *   3. neighbouring physical chains (i, i+1), i even on even cycles and odd
+ *      on odd ones, exchange lattices with probability min(1, b),
+ *      log b = log pi_i(x_{i+1}) + log pi_{i+1}(x_i) - log pi_i(x_i)
+ *              - log pi_{i+1}(x_{i+1}),
+ *      uniform from tag 0xFFFFFFFC of chain i; the Kitaev weight at another
+ *      temperature comes from the cached spectrum of the lattice;
+ *   4. every physical chain adds its observables to its sums; its accept
+ *      count counts the exchanges of step 2.
+ * Both step counters advance by `cycles`.  The RBM job's sums and accept
+ * counts are left unchanged.  If proposals (crbm_run and the like) ran on
+ * phys_job since its last evaluation, its chains are first re-evaluated in
+ * FP64 (synchronously).  Work enqueued earlier on either job must be ordered
+ * before cuda_stream by the caller.
+ * Errors: CRBM_EINVAL (mismatched jobs, g, precision, step counter past
+ * 2^32), CRBM_ECUDA. */
+CRBM_API int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g, int precision,
+                         void* cuda_stream);
 
 /* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
  * lattice side L and `precision`: every admissible value is timed on a

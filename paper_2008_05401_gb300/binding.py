@@ -47,6 +47,7 @@ _SIGS = {
                                     C.c_int, C.POINTER(C.c_int)]),
     "crbm_graph_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "crbm_graph_destroy": (C.c_int, [C.c_void_p, C.c_int]),
+    "crbm_pt_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -151,6 +152,10 @@ def crbm_graph_launch(ctx, graph_id, stream=0):
 
 def crbm_graph_destroy(ctx, graph_id):
     _check(ctx, load().crbm_graph_destroy(ctx, graph_id))
+
+
+def crbm_pt_run(ctx, phys_job, rbm_job, cycles, g=1, precision=FP64, stream=0):
+    _check(ctx, load().crbm_pt_run(ctx, phys_job, rbm_job, cycles, g, precision, C.c_void_p(stream)))
 
 
 def crbm_tune(ctx, model_id, L, precision=FP64):
@@ -278,6 +283,13 @@ class Context:
         """Capture `repeats` batched runs of S proposals into a replayable CUDA graph."""
         gid = crbm_graph_create(self.h, [j.id for j in jobs], S, g, int(correct), precision, repeats)
         return Graph(self, gid, jobs, S * repeats)
+
+    def pt_run(self, phys: Job, rbm: Job, cycles, g=1, precision=FP64, stream=None):
+        """Parallel-tempering exchange correction: `cycles` cycles of RBM
+        proposals, physical <-> RBM swaps and neighbour temperature exchanges."""
+        crbm_pt_run(self.h, phys.id, rbm.id, cycles, g, precision, _stream_handle(stream))
+        phys.step += cycles
+        rbm.step += cycles
 
     def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
         crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))

@@ -33,7 +33,7 @@ struct Model {
 };
 
 struct Layout {
-  size_t bits, T, F, Fb, Lb, lp, E, ot, os, acc, rec, step, total;
+  size_t bits, T, F, Fb, Lb, lp, E, ot, os, acc, rec, step, eps, total;
 };
 
 struct Job {
@@ -45,9 +45,14 @@ struct Job {
   size_t bytes = 0;
   Layout lay{};
   cudaStream_t stream = nullptr;
+  std::vector<double> T;   // host copy of the temperatures
+  // F and log pi of every chain are FP64 values (bounds 0) and, for the
+  // Kitaev kind, eps holds the spectra of the current lattices: true after an
+  // evaluation or a tempering cycle, false after proposals (mode 0)
+  bool exact = false;
 };
 
-Layout make_layout(int L, int n) {
+Layout make_layout(int kind, int L, int n) {
   Layout y{};
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -68,6 +73,7 @@ Layout make_layout(int L, int n) {
   y.acc = take((size_t)n * 8);
   y.rec = take((size_t)n * 16);
   y.step = take(8);
+  y.eps = take(kind == kKitaev ? (size_t)n * L * L * 8 : 0);
   y.total = n > 0 ? off : 0;   // an empty job needs no device memory
   return y;
 }
@@ -190,6 +196,7 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.obs = (double*)(b + j.lay.os);
   d.acc = (unsigned long long*)(b + j.lay.acc);
   d.rec = (unsigned long long*)(b + j.lay.rec);
+  d.eps = (double*)(b + j.lay.eps);
   return d;
 }
 
@@ -411,13 +418,14 @@ int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, doub
 
 size_t crbm_job_bytes(int kind, int L, int n_chains, int precision) {
   if (!valid_L(kind, L) || n_chains < 0 || (precision != CRBM_FP64 && precision != CRBM_MIXED)) return 0;
-  return make_layout(L, n_chains).total;
+  return make_layout(kind, L, n_chains).total;
 }
 
 static int evaluate(crbm_ctx* ctx, int id) {
   int rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, ctx->own);
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->own), "evaluate");
+  ctx->jobs[id].exact = true;
   return CRBM_OK;
 }
 
@@ -438,7 +446,7 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   if (init == 1 && n_chains > 0 && !init_bits) return fail(ctx, CRBM_EINVAL, "null init_bits");
   for (int c = 0; c < n_chains; ++c)
     if (!(T[c] > 0.0) || !std::isfinite(T[c])) return fail(ctx, CRBM_EINVAL, "temperature of chain %d not > 0", c);
-  const Layout lay = make_layout(L, n_chains);
+  const Layout lay = make_layout(m.kind, L, n_chains);
   if (n_chains > 0 && (!dev_mem || dev_bytes < lay.total))
     return fail(ctx, CRBM_ENOMEM, "dev_mem holds %zu bytes, job needs %zu", dev_bytes, lay.total);
   if (((uintptr_t)dev_mem & 255) != 0) return fail(ctx, CRBM_EINVAL, "dev_mem must be 256-byte aligned");
@@ -472,6 +480,7 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   j.bytes = lay.total;
   j.lay = lay;
   j.stream = nullptr;
+  if (n_chains > 0) j.T.assign(T, T + n_chains);
   if (n_chains > 0) {
     unsigned char* b = j.mem;
     cudaStream_t o = ctx->own;
@@ -557,6 +566,7 @@ int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int
   for (int id : ids) {
     ctx->jobs[id].step += (uint64_t)S;
     ctx->jobs[id].stream = st;
+    if (S > 0) ctx->jobs[id].exact = false;
   }
   return CRBM_OK;
 }
@@ -613,6 +623,7 @@ int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream) {
   for (int id : gr.jobs) {
     ctx->jobs[id].step += gr.steps;
     ctx->jobs[id].stream = st;
+    if (gr.steps > 0) ctx->jobs[id].exact = false;
   }
   return CRBM_OK;
 }
@@ -627,6 +638,43 @@ int crbm_graph_destroy(crbm_ctx* ctx, int graph_id) {
   cudaGraphExecDestroy(gr.exec);
   cudaGraphDestroy(gr.graph);
   gr = crbm_ctx::Graph();
+  return CRBM_OK;
+}
+
+int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g, int precision,
+                void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  int rc = check_run_args(ctx, cycles, g, 0, precision);
+  if (rc) return rc;
+  Job* x = get_job(ctx, phys_job);
+  Job* y = get_job(ctx, rbm_job);
+  if (!x || !y) return fail(ctx, CRBM_EINVAL, "bad job id");
+  if (x == y) return fail(ctx, CRBM_EINVAL, "the physical and the RBM job must differ");
+  if (x->model != y->model) return fail(ctx, CRBM_EINVAL, "both jobs must use the same model");
+  if (x->L != y->L || x->n != y->n) return fail(ctx, CRBM_EINVAL, "both jobs need the same L and number of chains");
+  for (int i = 0; i < 3; ++i)
+    if (x->J[i] != y->J[i]) return fail(ctx, CRBM_EINVAL, "both jobs need the same couplings J");
+  if (x->T != y->T) return fail(ctx, CRBM_EINVAL, "both jobs need the same temperatures, chain by chain");
+  for (const Job* j : {x, y})
+    if (j->step + (uint64_t)cycles > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (cycles == 0 || x->n == 0) return CRBM_OK;
+  // the exchange needs FP64 F and log pi (and Kitaev spectra) of the physical chains
+  if (!x->exact) {
+    if ((rc = crbm_sync(ctx, phys_job))) return rc;
+    if ((rc = evaluate(ctx, phys_job))) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const JobDev xd = make_jobdev(ctx, *x), yd = make_jobdev(ctx, *y);
+  for (int64_t c = 0; c < cycles; ++c) {
+    if ((rc = launch_jobs(ctx, {rbm_job}, 1, g, 0, precision, 2, st))) return rc;
+    CK(launch_pt_exchange(xd, yd, st), "exchange launch");
+  }
+  for (Job* j : {x, y}) {
+    j->step += (uint64_t)cycles;
+    j->stream = st;
+    j->exact = true;
+  }
   return CRBM_OK;
 }
 
@@ -656,7 +704,7 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
   }
   // a temporary job large enough for every candidate to fill the GPU
   const int n_chains = 4 * sms * cand.back();
-  const Layout lay = make_layout(L, n_chains);
+  const Layout lay = make_layout(m.kind, L, n_chains);
   unsigned char* mem = nullptr;
   CK(cudaMalloc(&mem, lay.total), "cudaMalloc tuning job");
   std::vector<double> T(n_chains, 2.0);

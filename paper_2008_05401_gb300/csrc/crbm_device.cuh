@@ -24,6 +24,8 @@ constexpr int kMaxJobs = 16;
 constexpr int kNobs = 4;
 constexpr uint32_t kTagAcc = 0xFFFFFFFEu;
 constexpr uint32_t kTagInit = 0xFFFFFFFFu;
+constexpr uint32_t kTagSwap = 0xFFFFFFFDu;   // tempering: physical <-> RBM exchange
+constexpr uint32_t kTagTemp = 0xFFFFFFFCu;   // tempering: neighbour temperature exchange
 constexpr int kIsing = 0;
 constexpr int kKitaev = 1;
 constexpr int kFP64 = 0;
@@ -75,10 +77,14 @@ struct JobDev {
   double* obs;                  // [n_chains][4] running sums
   unsigned long long* acc;      // [n_chains]
   unsigned long long* rec;      // [n_chains][2] FP64 recomputes: Bernoulli draws, MH decisions
+  double* eps;                  // [n_chains][N] Kitaev: single-fermion energies of the current
+                                // lattice, ascending (written by modes 1 and 2 only)
 };
 
 struct LaunchParams {
-  int n_jobs, S, g, correct, mode;   // mode 0: S proposals; 1: evaluate current state
+  // mode 0: S proposals; 1: evaluate the current state; 2: one uncorrected
+  // proposal and the FP64 evaluation of the new state (tempering RBM chains)
+  int n_jobs, S, g, correct, mode;
   int tile_begin[kMaxJobs + 1];
   int* err;
   JobDev job[kMaxJobs];
@@ -848,8 +854,19 @@ __device__ __forceinline__ double eigen_idx(const KitaevWork& wk, int N, int idx
   return x;
 }
 
+// One single-fermion level's share of log pi, e and c_f (Sec. IV):
+// log 2cosh x, -(eps/2) tanh x and x^2 sech^2 x with x = beta eps / 2.
+__device__ __forceinline__ void thermal_add(double eps, double beta, double& lp, double& en, double& cf) {
+  const double x = 0.5 * beta * eps;
+  const double qx = exp(-2.0 * x);
+  lp += x + log1p(qx);
+  en += -0.5 * eps * (1.0 - qx) / (1.0 + qx);
+  cf += x * x * 4.0 * qx / ((1.0 + qx) * (1.0 + qx));
+}
+
+// eps_out (optional, device memory): the N energies eps, ascending.
 __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
-                               const KitaevWork& wk, double (&res)[3]) {
+                               const KitaevWork& wk, double (&res)[3], double* eps_out = nullptr) {
   const int N = L * L, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double* A = wk.A;
@@ -954,11 +971,8 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
   for (int idx = tid; idx < N; idx += nt) {
     const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
     const double eps = sqrt(mu);
-    const double x = 0.5 * beta * eps;
-    const double qx = exp(-2.0 * x);
-    lp += x + log1p(qx);                                   // log 2cosh x
-    en += -0.5 * eps * (1.0 - qx) / (1.0 + qx);            // -(eps/2) tanh x
-    cf += x * x * 4.0 * qx / ((1.0 + qx) * (1.0 + qx));    // x^2 sech^2 x
+    if (eps_out) eps_out[idx] = eps;
+    thermal_add(eps, beta, lp, en, cf);
   }
   res[0] = block_sum(lp, wk.sc);
   res[1] = block_sum(en, wk.sc);

@@ -190,12 +190,7 @@ __device__ inline void kitaev_logpi_df(const uint32_t* v, int L, const double* J
   double lp = 0.0, en = 0.0, cf = 0.0, bd = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
     const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
-    const double eps = sqrt(mu);
-    const double x = 0.5 * beta * eps;
-    const double qx = exp(-2.0 * x);
-    lp += x + log1p(qx);
-    en += -0.5 * eps * (1.0 - qx) / (1.0 + qx);
-    cf += x * x * 4.0 * qx / ((1.0 + qx) * (1.0 + qx));
+    thermal_add(sqrt(mu), beta, lp, en, cf);
     const double mlo = fmax(mu - dmu, 0.0);
     const double slope = (mlo > 0.0) ? fmin(0.125 * beta * beta, 0.25 * beta / sqrt(mlo)) : 0.125 * beta * beta;
     bd += slope * dmu;

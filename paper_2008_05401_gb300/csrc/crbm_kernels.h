@@ -6,6 +6,7 @@
 
 namespace crbm {
 struct LaunchParams;
+struct JobDev;
 
 // Compiled specialisation (KC, kC) serving a filter bank of K filters k x k
 // (0 = runtime values).
@@ -24,4 +25,7 @@ cudaError_t set_smem_limits(size_t bytes);
 // Random initial lattices (init tag of the stream).
 cudaError_t launch_random_init(uint32_t* bits, int n_chains, int N, int Wd, uint64_t seed,
                                uint64_t cid_base, cudaStream_t st);
+// Exchange step of one tempering cycle (crbm_tempering.cu): physical job x,
+// RBM job y; advances x's step counter by one.
+cudaError_t launch_pt_exchange(const JobDev& x, const JobDev& y, cudaStream_t st);
 }  // namespace crbm

@@ -39,6 +39,32 @@ static __device__ __noinline__ void free_energy64(const JobDev& jb, const Tabs& 
   for (int i = 0; i < 4; ++i) out[i] = o[i];
 }
 
+// FP64 free energy, log pi, E and observables of chain c's lattice from the
+// group sums fo (Eq. 13 sums, magnetisation count, bond/vison count) and, for
+// the Kitaev kind, kr = (log pi, e, c_f) of its spectrum.
+template <int KIND>
+__device__ inline void store_evaluation(const JobDev& jb, int c, double beta, const double* fo, const double* kr) {
+  const int N = jb.N;
+  const double Fv = -jb.vb * fo[2] - fo[0];
+  double lp, E, ot[kNobs];
+  if (KIND == kIsing) {
+    E = -jb.J[0] * (double)(2 * N - 2 * (int)fo[3]);
+    const double M = 2.0 * fo[2] - (double)N;
+    lp = -beta * E;
+    ot[0] = E; ot[1] = E * E; ot[2] = fabs(M); ot[3] = M * M;
+  } else {
+    lp = kr[0];
+    E = kr[1];
+    ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)N;
+  }
+  jb.F[c] = Fv;
+  jb.Fb[c] = 0.0;
+  jb.Lb[c] = 0.0;
+  jb.logpi[c] = lp;
+  jb.Ephys[c] = E;
+  for (int o = 0; o < kNobs; ++o) jb.obs_t[(size_t)c * kNobs + o] = ot[o];
+}
+
 template <int KIND, int PREC, int KC, int kC, int NT>
 __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN_BLOCKS) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
   int jid = 0;
@@ -184,26 +210,45 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     free_energy64(jb, tb, g, my, fo);
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
-    if (KIND == kKitaev) kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
-    if (g.active && g.r == 0) {
-      const double Fv = -jb.vb * fo[2] - fo[0];
-      double lp, E, ot[kNobs];
-      if (KIND == kIsing) {
-        E = -jb.J[0] * (double)(2 * N - 2 * (int)fo[3]);
-        const double M = 2.0 * fo[2] - (double)N;
-        lp = -ch.beta * E;
-        ot[0] = E; ot[1] = E * E; ot[2] = fabs(M); ot[3] = M * M;
-      } else {
-        lp = kr[0];
-        E = kr[1];
-        ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)N;
+    if (KIND == kKitaev)
+      kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+                     g.active ? jb.eps + (size_t)g.c * N : nullptr);
+    if (g.active && g.r == 0) store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
+    return;
+  }
+
+  if (prm.mode == 2) {
+    // tempering RBM chains: g Gibbs steps without correction (Eq. B4), then
+    // the FP64 values of the new lattice that the exchange step needs
+    const uint32_t step = (uint32_t)*(volatile unsigned long long*)jb.step;
+    uint32_t* vp = my + P;
+    uint32_t* h = my + 2 * P;
+    const uint32_t* src = my;
+    for (int sub = 0; sub < prm.g; ++sub) {
+      hidden_phase<PREC, KC, kC>(jb, tb, g, src, h, P, step, sub, nrec);
+      __syncthreads();
+      visible_phase<PREC, KC, kC>(jb, tb, g, h, vp, P, step, sub, nrec);
+      __syncthreads();
+      src = vp;
+    }
+    Tabs tb64 = tb;
+    tb64.f64 = jb.f64;       // FP64 tables from global memory (the mixed kernel
+    tb64.b64 = jb.b64;       // keeps only FP32 ones in shared memory)
+    double fo[4];
+    free_energy64(jb, tb64, g, vp, fo);
+    grp_reduce<4>(fo, g, scratch);
+    double kr[3] = {0.0, 0.0, 0.0};
+    if (KIND == kKitaev)
+      kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+                     g.active ? jb.eps + (size_t)g.c * N : nullptr);
+    if (nrec) atomicAdd(&ch.rec, (unsigned long long)nrec);
+    __syncthreads();
+    if (g.active) {
+      for (int w = g.r; w < jb.Wd; w += g.tpc) jb.bits[(size_t)g.c * jb.Wd + w] = vp[w];
+      if (g.r == 0) {
+        store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
+        jb.rec[2 * (size_t)g.c] += ch.rec;
       }
-      jb.F[g.c] = Fv;
-      jb.Fb[g.c] = 0.0;
-      jb.Lb[g.c] = 0.0;
-      jb.logpi[g.c] = lp;
-      jb.Ephys[g.c] = E;
-      for (int o = 0; o < kNobs; ++o) jb.obs_t[(size_t)g.c * kNobs + o] = ot[o];
     }
     return;
   }
@@ -379,7 +424,7 @@ template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
   crbm_step_kernel<KIND, PREC, KC, kC, NT><<<grid, NT, smem, st>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && p.mode == 0 && p.S > 0) {
+  if (e == cudaSuccess && p.mode != 1 && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
     e = cudaGetLastError();
   }

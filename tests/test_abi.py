@@ -42,6 +42,8 @@ def test_host_only_calls_without_gpu():
     assert binding.crbm_job_bytes(0, 100, 4, 0) == 0          # L=100 unsupported for Ising
     assert binding.crbm_job_bytes(1, 13, 4, 0) == 0           # Kitaev L <= 12
     assert binding.crbm_job_bytes(0, 16, 0, 0) == 0           # empty job
+    # Kitaev jobs also hold the spectrum of every lattice (L*L FP64 values)
+    assert binding.crbm_job_bytes(1, 12, 10, 0) >= binding.crbm_job_bytes(0, 12, 10, 0) + 10 * 144 * 8
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         with pytest.raises(binding.CrbmError):
