@@ -225,6 +225,42 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
             "fp64_recomputes": rec}
 
 
+def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush):
+    """Parallel-tempering exchange correction (App. B.2) on a workload's first
+    lattice size: the workload's chains are the physical ladder, as many RBM
+    chains run beside them.  value = chain-cycles/s (one RBM proposal, one
+    swap decision and one temperature-exchange decision per pair and cycle)."""
+    import torch
+    from paper_2008_05401_gb300 import MIXED
+    spec = workload(name)
+    L, n = spec["jobs"][0]
+    ctx = ctx_cls(dev)
+    W, hb, vb = spec["model"]
+    mid = ctx.load_model(spec["kind"], W, vb, hb)
+    T = spec["T"](n)
+    x = ctx.new_job(mid, spec["kind"], L, T, spec["J"], SEED, 0,
+                    wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec)
+    y = ctx.new_job(mid, spec["kind"], L, T, spec["J"], SEED + 1, n,
+                    wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L + 1)), prec)
+    ctx.pt_run(x, y, 2, precision=prec, stream=stream)
+    torch.cuda.synchronize(dev)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.pt_run(x, y, cycles, precision=prec, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    _, acc, _ = x.observables()
+    ctx.close()
+    model = "2D Ising" if spec["kind"] == 0 else "Kitaev"
+    return {"workload": f"parallel tempering, {model} L={L}, {n} physical + {n} RBM chains, one proposal "
+                        f"(g=1) per RBM chain and cycle, the workload's T ladder",
+            "precision": "mixed" if prec == MIXED else "fp64", "value": n * cycles / (ms * 1e-3),
+            "unit": "chain-cycles/s", "ms_per_cycle": ms / cycles, "cycles": cycles,
+            "swap_rate": float(acc.sum()) / (n * (cycles + 2))}
+
+
 def serving_run(dev, n=60, rate=200.0):
     """Continuous batching of a Poisson request stream (mixed Ising / Kitaev
     jobs, 1-64 chains, 1e2-2e3 proposals each, mixed precision): p50/p99 latency
@@ -369,7 +405,9 @@ def main():
             secondary(Context, "kitaev-small", FP64, 3, dev, stream, flush),
             secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush),
             secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
-            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush)]
+            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush),
+            tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush),
+            tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush)]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
     if rank == 0 and not args.no_cpu_baseline:
