@@ -26,4 +26,13 @@ Modules and what pins each (pins are tests under ``tests/test_oracle_*.py``):
   (Eq. B5 read with (pi, P_CRBM) as the two distributions).  Pinned by exact
   stationary distributions (Ising L=4, Kitaev L=2) and by acceptance == 1 for
   the analytic Ising CRBM.
+* ``tempering``  Parallel-tempering exchange correction (App. B.2, Fig. 8b).
+  Pinned by exact stationarity at every temperature of a ladder (Ising L=4)
+  and by planted mistakes that break it.
+* ``metropolis`` Local-update Metropolis baselines (Sec. III, Sec. IV):
+  checkerboard single-spin flips (Ising), sequential single-eta flips (Kitaev),
+  optionally with temperature exchange.  Pinned by exact stationarity and a
+  deterministic zero-temperature sweep.
+* ``autocorr``   Integrated autocorrelation time (Sokal's windowed
+  estimator).  Pinned by the AR(1) closed form and exact small cases.
 """

@@ -33,32 +33,12 @@ def _log_weight_at(model, v, beta, J):
     return chain.target(model, v, beta, J)[0]
 
 
-def cycle(phys: chain.Chains, rbm: chain.Chains, k: int):
-    """One PT-exchange-correction cycle; mutates both chain sets.  The cycle
-    counter is the physical chains' step counter.  Returns the swap and
-    temperature-exchange decisions and how close each came to its threshold."""
+def exchange_temperatures(phys: chain.Chains, c: int):
+    """Neighbouring chains (i, i+1), i = c % 2, c % 2 + 2, ... exchange their
+    lattices with the Eq. (B5) probability for the pair (pi_i, pi_{i+1});
+    uniform from tag TAG_TEMP of chain i at step c.  Returns the per-chain
+    decision (set at the lower chain of an accepted pair) and margin."""
     n = len(phys.chain_ids)
-    c = int(phys.step)
-    # 1. RBM chains: k Gibbs steps from their own states, then the FP64 values
-    #    the exchange needs (no correction, no observables of their own)
-    y, bmargin = chain.propose(rbm, k)
-    rbm.v = y
-    rbm.F = crbm.free_energy(y, rbm.W, rbm.hb, rbm.vb)
-    rbm.logpi, rbm.E_phys, rbm.obs_terms = chain.target(rbm.model, y, rbm.beta, rbm.J)
-    rbm.step += 1
-    # 2. physical <-> RBM exchange at every temperature
-    log_a = (rbm.logpi - phys.logpi) + (rbm.F - phys.F)
-    u = philox.uniforms(phys.seed, phys.chain_ids, c, TAG_SWAP, 1)[:, 0]
-    swap = np.log(u) < log_a
-    swap_margin = np.abs(np.log(u) - log_a) / (
-        np.abs(rbm.logpi) + np.abs(phys.logpi) + np.abs(rbm.F) + np.abs(phys.F) + 1.0)
-    for name in ("v", "F", "logpi", "E_phys", "obs_terms"):
-        a, b = getattr(phys, name), getattr(rbm, name)
-        m = swap.reshape((-1,) + (1,) * (a.ndim - 1))
-        a_new, b_new = np.where(m, b, a), np.where(m, a, b)
-        setattr(phys, name, a_new)
-        setattr(rbm, name, b_new)
-    # 3. temperature exchange between neighbours
     i = np.arange(c % 2, n - 1, 2)
     j = i + 1
     temp = np.zeros(n, dtype=bool)
@@ -83,6 +63,35 @@ def cycle(phys: chain.Chains, rbm: chain.Chains, k: int):
             if len(idx):
                 lp, E, ot = chain.target(phys.model, phys.v[idx], phys.beta[idx], phys.J)
                 phys.logpi[idx], phys.E_phys[idx], phys.obs_terms[idx] = lp, E, ot
+    return temp, temp_margin
+
+
+def cycle(phys: chain.Chains, rbm: chain.Chains, k: int):
+    """One PT-exchange-correction cycle; mutates both chain sets.  The cycle
+    counter is the physical chains' step counter.  Returns the swap and
+    temperature-exchange decisions and how close each came to its threshold."""
+    c = int(phys.step)
+    # 1. RBM chains: k Gibbs steps from their own states, then the FP64 values
+    #    the exchange needs (no correction, no observables of their own)
+    y, bmargin = chain.propose(rbm, k)
+    rbm.v = y
+    rbm.F = crbm.free_energy(y, rbm.W, rbm.hb, rbm.vb)
+    rbm.logpi, rbm.E_phys, rbm.obs_terms = chain.target(rbm.model, y, rbm.beta, rbm.J)
+    rbm.step += 1
+    # 2. physical <-> RBM exchange at every temperature
+    log_a = (rbm.logpi - phys.logpi) + (rbm.F - phys.F)
+    u = philox.uniforms(phys.seed, phys.chain_ids, c, TAG_SWAP, 1)[:, 0]
+    swap = np.log(u) < log_a
+    swap_margin = np.abs(np.log(u) - log_a) / (
+        np.abs(rbm.logpi) + np.abs(phys.logpi) + np.abs(rbm.F) + np.abs(phys.F) + 1.0)
+    for name in ("v", "F", "logpi", "E_phys", "obs_terms"):
+        a, b = getattr(phys, name), getattr(rbm, name)
+        m = swap.reshape((-1,) + (1,) * (a.ndim - 1))
+        a_new, b_new = np.where(m, b, a), np.where(m, a, b)
+        setattr(phys, name, a_new)
+        setattr(rbm, name, b_new)
+    # 3. temperature exchange between neighbours
+    temp, temp_margin = exchange_temperatures(phys, c)
     # 4. observables of the physical chains
     phys.obs += phys.obs_terms
     phys.accepts += swap
