@@ -182,6 +182,54 @@ CRBM_API int crbm_graph_destroy(crbm_ctx* ctx, int graph_id);
 CRBM_API int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g, int precision,
                          void* cuda_stream);
 
+/* Local-update Metropolis sweeps, the paper's baseline sampler (Sec. III:
+ * single spin flips for the Ising model; Sec. IV: single gauge-field flips
+ * for the Kitaev model, with parallel tempering), `sweeps` sweeps of every
+ * chain enqueued on cuda_stream.  One sweep at step t:
+ *   Ising (L even): checkerboard order, sites with (i+j) even then odd; site
+ *     (i,j) flips iff u < exp(-beta dE), dE = 2 J s_ij (sum of its 4
+ *     neighbours), in FP64 (precision is ignored);
+ *   Kitaev: sites n = 0..N-1 in order; eta_n flips iff
+ *     log u < log pi(eta with eta_n flipped) - log pi(eta), one eigen-stage
+ *     per proposal (CRBM_MIXED: the df64 stage with its certified bound and
+ *     FP64 recompute, so decisions equal the FP64 path's);
+ *   u of site n: word n%4 of Philox block n/4, tag 0xFFFFFFFB, step t.
+ * exchange = 1 follows every sweep by the neighbour temperature exchange of
+ * crbm_pt_run (step 3 there, cycle counter t; Kitaev sweeps then use the
+ * FP64 stage).  After each sweep (and exchange) the observables of the
+ * lattice are added to the sums; the accept count counts accepted flips; F
+ * and log pi of the final lattices are FP64.  The step counter advances by
+ * `sweeps`.  If proposals ran on the job since its last evaluation and
+ * exchange = 1, the chains are first re-evaluated in FP64 (synchronously).
+ * Errors: CRBM_EINVAL (odd Ising L, bad arguments, step counter past 2^32),
+ * CRBM_ECUDA. */
+CRBM_API int crbm_local_run(crbm_ctx* ctx, int job_id, int64_t sweeps, int exchange, int precision,
+                            void* cuda_stream);
+
+/* Record E_phys of every chain after each later step t of the job (proposal,
+ * sweep or tempering cycle; after the exchanges) into dev_trace, a
+ * caller-owned device array of capacity_steps * n_chains FP64 values,
+ * time-major: row t - t0 (t0 = the job's step counter at this call), column
+ * = chain.  Steps past the capacity are not recorded.  dev_trace = NULL stops
+ * recording.  The buffer must stay allocated while recording; CUDA graphs
+ * keep the setting they were captured with.  No counterpart in the paper:
+ * the input of crbm_autocorr.  Errors: CRBM_EINVAL. */
+CRBM_API int crbm_set_trace(crbm_ctx* ctx, int job_id, double* dev_trace, int64_t capacity_steps);
+
+/* Integrated autocorrelation time of each of n_series series stored
+ * time-major in device memory (dev_series[t * n_series + j], t < length),
+ * for the paper's comparison of samplers by the autocorrelation of the
+ * energy (Sec. III, Sec. IV).  Windowed estimator with Sokal's automatic
+ * window: m = mean, G(t) = (1/n) sum_{s<n-t} (x_s - m)(x_{s+t} - m),
+ * tau(W) = 1/2 + sum_{t=1..W} G(t)/G(0), W = first W >= 1 with W >= c tau(W)
+ * (W <= length-1; a constant series gives tau = 1/2, W = 0).  tau[n_series]
+ * (FP64) and window[n_series] (int64) are host arrays.  Runs on cuda_stream
+ * after the work already there, allocates its small result buffers on it
+ * (stream-ordered) and returns when the results are on the host.
+ * Errors: CRBM_EINVAL (null pointers, c <= 0), CRBM_ECUDA. */
+CRBM_API int crbm_autocorr(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length, double c,
+                           double* tau, int64_t* window, void* cuda_stream);
+
 /* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
  * lattice side L and `precision`: every admissible value is timed on a
  * temporary job that fills the GPU (device memory allocated and freed by this

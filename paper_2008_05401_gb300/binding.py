@@ -48,6 +48,10 @@ _SIGS = {
     "crbm_graph_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "crbm_graph_destroy": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_pt_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "crbm_local_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "crbm_set_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "crbm_autocorr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -158,6 +162,22 @@ def crbm_pt_run(ctx, phys_job, rbm_job, cycles, g=1, precision=FP64, stream=0):
     _check(ctx, load().crbm_pt_run(ctx, phys_job, rbm_job, cycles, g, precision, C.c_void_p(stream)))
 
 
+def crbm_local_run(ctx, job_id, sweeps, exchange=0, precision=FP64, stream=0):
+    _check(ctx, load().crbm_local_run(ctx, job_id, sweeps, exchange, precision, C.c_void_p(stream)))
+
+
+def crbm_set_trace(ctx, job_id, dev_ptr, capacity_steps):
+    _check(ctx, load().crbm_set_trace(ctx, job_id, C.c_void_p(dev_ptr), capacity_steps))
+
+
+def crbm_autocorr(ctx, dev_ptr, n_series, length, c=5.0, stream=0):
+    tau = np.empty(n_series)
+    win = np.empty(n_series, dtype=np.int64)
+    _check(ctx, load().crbm_autocorr(ctx, C.c_void_p(dev_ptr), n_series, length, c, _ptr(tau), _ptr(win),
+                                     C.c_void_p(stream)))
+    return tau, win
+
+
 def crbm_tune(ctx, model_id, L, precision=FP64):
     nc, us = C.c_int(), C.c_double()
     _check(ctx, load().crbm_tune(ctx, model_id, L, precision, C.byref(nc), C.byref(us)))
@@ -225,6 +245,25 @@ class Job:
         crbm_write_state(self.ctx.h, self.id, bits, step)
         self.step = step
 
+    def local_run(self, sweeps, exchange=False, precision=FP64, stream=None):
+        """Local-update Metropolis sweeps (optionally with temperature exchange)."""
+        crbm_local_run(self.ctx.h, self.id, sweeps, int(exchange), precision, _stream_handle(stream))
+        self.step += sweeps
+        return self
+
+    def set_trace(self, steps):
+        """Record E_phys of every chain for the next `steps` steps; returns the
+        (steps, n) float64 torch tensor that receives it (None: stop)."""
+        import torch
+        if steps is None:
+            crbm_set_trace(self.ctx.h, self.id, 0, 0)
+            self.trace = None
+            return None
+        self.trace = torch.full((steps, self.n), float("nan"), dtype=torch.float64,
+                                device=f"cuda:{self.ctx.device}")
+        crbm_set_trace(self.ctx.h, self.id, self.trace.data_ptr(), steps)
+        return self.trace
+
     def release(self):
         crbm_release(self.ctx.h, self.id)
         self.mem = None
@@ -290,6 +329,12 @@ class Context:
         crbm_pt_run(self.h, phys.id, rbm.id, cycles, g, precision, _stream_handle(stream))
         phys.step += cycles
         rbm.step += cycles
+
+    def autocorr(self, series, c=5.0, stream=None):
+        """tau_int and window of every column of a (length, n) float64 CUDA tensor."""
+        series = series.contiguous()
+        return crbm_autocorr(self.h, series.data_ptr(), series.shape[1], series.shape[0], c,
+                             _stream_handle(stream))
 
     def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
         crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))

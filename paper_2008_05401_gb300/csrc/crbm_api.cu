@@ -50,6 +50,10 @@ struct Job {
   // Kitaev kind, eps holds the spectra of the current lattices: true after an
   // evaluation or a tempering cycle, false after proposals (mode 0)
   bool exact = false;
+  // optional E_phys trace in caller-owned device memory (crbm_set_trace)
+  double* trace = nullptr;
+  uint64_t trace_base = 0;
+  int64_t trace_cap = 0;
 };
 
 Layout make_layout(int kind, int L, int n) {
@@ -197,6 +201,9 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.acc = (unsigned long long*)(b + j.lay.acc);
   d.rec = (unsigned long long*)(b + j.lay.rec);
   d.eps = (double*)(b + j.lay.eps);
+  d.trace = j.trace;
+  d.trace_base = j.trace_base;
+  d.trace_cap = j.trace_cap;
   return d;
 }
 
@@ -668,13 +675,87 @@ int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g,
   const JobDev xd = make_jobdev(ctx, *x), yd = make_jobdev(ctx, *y);
   for (int64_t c = 0; c < cycles; ++c) {
     if ((rc = launch_jobs(ctx, {rbm_job}, 1, g, 0, precision, 2, st))) return rc;
-    CK(launch_pt_exchange(xd, yd, st), "exchange launch");
+    CK(launch_pt_exchange(xd, &yd, 0, true, st), "exchange launch");
   }
   for (Job* j : {x, y}) {
     j->step += (uint64_t)cycles;
     j->stream = st;
     j->exact = true;
   }
+  return CRBM_OK;
+}
+
+int crbm_local_run(crbm_ctx* ctx, int job_id, int64_t sweeps, int exchange, int precision, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  int rc = check_run_args(ctx, sweeps, 1, 1, precision);
+  if (rc) return rc;
+  if (exchange != 0 && exchange != 1) return fail(ctx, CRBM_EINVAL, "exchange must be 0 or 1");
+  Job* j = get_job(ctx, job_id);
+  if (!j) return fail(ctx, CRBM_EINVAL, "bad job id %d", job_id);
+  if (j->kind == kIsing && j->L % 2) return fail(ctx, CRBM_EINVAL, "checkerboard sweeps need an even L (L=%d)", j->L);
+  if (j->step + (uint64_t)sweeps > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (sweeps == 0 || j->n == 0) return CRBM_OK;
+  // the temperature exchange needs FP64 log pi (and Kitaev spectra) of every chain
+  if (exchange && !j->exact) {
+    if ((rc = crbm_sync(ctx, job_id))) return rc;
+    if ((rc = evaluate(ctx, job_id))) return rc;
+  }
+  // Ising sweeps have no precision choice (integer counts, FP64 thresholds);
+  // with the exchange the Kitaev spectra must come from the FP64 stage
+  const int prec = (j->kind == kIsing || exchange) ? (int)kFP64 : precision;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!exchange) {
+    int64_t left = sweeps;
+    while (left > 0) {
+      const int chunk = (int)(left < (1 << 20) ? left : (1 << 20));
+      if ((rc = launch_jobs(ctx, {job_id}, chunk, 1, 1, prec, 3, st))) return rc;
+      left -= chunk;
+    }
+  } else {
+    const JobDev xd = make_jobdev(ctx, *j);
+    for (int64_t c = 0; c < sweeps; ++c) {
+      if ((rc = launch_jobs(ctx, {job_id}, 1, 1, 0, prec, 3, st))) return rc;
+      CK(launch_pt_exchange(xd, nullptr, -1, false, st), "exchange launch");
+    }
+  }
+  j->step += (uint64_t)sweeps;
+  j->stream = st;
+  j->exact = (prec == kFP64);
+  return CRBM_OK;
+}
+
+int crbm_set_trace(crbm_ctx* ctx, int job_id, double* dev_trace, int64_t capacity_steps) {
+  Job* j = get_job(ctx, job_id);
+  if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
+  if (dev_trace && capacity_steps < 1) return fail(ctx, CRBM_EINVAL, "capacity_steps must be >= 1");
+  if (((uintptr_t)dev_trace & 7) != 0) return fail(ctx, CRBM_EINVAL, "dev_trace must be 8-byte aligned");
+  j->trace = dev_trace;
+  j->trace_base = j->step;
+  j->trace_cap = dev_trace ? capacity_steps : 0;
+  return CRBM_OK;
+}
+
+int crbm_autocorr(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length, double c,
+                  double* tau, int64_t* window, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  if (n_series < 0 || length < 0) return fail(ctx, CRBM_EINVAL, "negative size");
+  if (!(c > 0.0)) return fail(ctx, CRBM_EINVAL, "window constant c must be > 0");
+  if (n_series == 0) return CRBM_OK;
+  if (!dev_series || !tau || !window) return fail(ctx, CRBM_EINVAL, "null pointer");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* d_tau = nullptr;
+  long long* d_w = nullptr;
+  CK(cudaMallocAsync(&d_tau, (size_t)n_series * 8, st), "cudaMallocAsync");
+  CK(cudaMallocAsync(&d_w, (size_t)n_series * 8, st), "cudaMallocAsync");
+  cudaError_t e = launch_tau(dev_series, n_series, (long long)length, c, d_tau, d_w, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tau, d_tau, (size_t)n_series * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(window, d_w, (size_t)n_series * 8, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_tau, st);
+  cudaFreeAsync(d_w, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autocorrelation");
   return CRBM_OK;
 }
 

@@ -26,6 +26,7 @@ constexpr uint32_t kTagAcc = 0xFFFFFFFEu;
 constexpr uint32_t kTagInit = 0xFFFFFFFFu;
 constexpr uint32_t kTagSwap = 0xFFFFFFFDu;   // tempering: physical <-> RBM exchange
 constexpr uint32_t kTagTemp = 0xFFFFFFFCu;   // tempering: neighbour temperature exchange
+constexpr uint32_t kTagLocal = 0xFFFFFFFBu;  // local-update Metropolis sweeps
 constexpr int kIsing = 0;
 constexpr int kKitaev = 1;
 constexpr int kFP64 = 0;
@@ -79,11 +80,23 @@ struct JobDev {
   unsigned long long* rec;      // [n_chains][2] FP64 recomputes: Bernoulli draws, MH decisions
   double* eps;                  // [n_chains][N] Kitaev: single-fermion energies of the current
                                 // lattice, ascending (written by modes 1 and 2 only)
+  double* trace;                // optional [trace_cap][n_chains]: E_phys after step t at row
+  unsigned long long trace_base;  // t - trace_base, for 0 <= t - trace_base < trace_cap
+  long long trace_cap;
 };
+
+// E_phys of chain c after step t into the job's trace, if one is set and t is inside it.
+__device__ __forceinline__ void trace_store(const JobDev& jb, int c, unsigned long long t, double E) {
+  if (jb.trace == nullptr) return;
+  const long long r = (long long)(t - jb.trace_base);
+  if (t >= jb.trace_base && r < jb.trace_cap) jb.trace[r * jb.n_chains + c] = E;
+}
 
 struct LaunchParams {
   // mode 0: S proposals; 1: evaluate the current state; 2: one uncorrected
-  // proposal and the FP64 evaluation of the new state (tempering RBM chains)
+  // proposal and the FP64 evaluation of the new state (tempering RBM chains);
+  // 3: S local-update Metropolis sweeps, where correct = 1 adds each sweep's
+  // observables to the sums (0: the exchange kernel that follows does)
   int n_jobs, S, g, correct, mode;
   int tile_begin[kMaxJobs + 1];
   int* err;

@@ -11,7 +11,8 @@ size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC) {
              : (KC == 4 ? 3 * align16(nq * 16) + align16(nlut * 4) : 4 * align16(nlut * 4));
   b += align16(nc * sizeof(ChainSm));
   b += align16(64 * 8);
-  if (kind == kKitaev) b += align16(N * (N + 1) / 2 * 8) + 4 * align16(N * 8) + align16(64 * 8) + 2 * align16(N * 4);
+  if (kind == kKitaev)
+    b += align16(N * (N + 1) / 2 * 8) + 4 * align16(N * 8) + align16(64 * 8) + 2 * align16(N * 4) + align16(N * 8);
   b += align16((size_t)nc * (2 + K) * P * 4);
   return b;
 }

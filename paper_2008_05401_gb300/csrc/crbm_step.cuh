@@ -13,6 +13,7 @@
 #pragma once
 #include "crbm_device.cuh"
 #include "crbm_df64.cuh"
+#include "crbm_local.cuh"
 #include "crbm_kernels.h"
 
 namespace crbm {
@@ -25,6 +26,7 @@ struct ChainSm {
   double lpb, lppb;      // bounds on |log pi - FP64 path's log pi| (current, proposed)
   double otp[kNobs];
   double beta;
+  double thr[5];         // local Ising sweeps: e^{-beta dE} 2^32 for 0..4 unequal neighbours
   unsigned long long acc, rec, rec_mh;
   int cur, flag_rec, flag_acc, pad;
 };
@@ -135,6 +137,11 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     sp += align16((size_t)N * 4);
     wk.e32 = (float*)sp;
     sp += align16((size_t)N * 4);
+  }
+  double* eps_st = nullptr;     // Kitaev local sweeps: spectrum of the proposed lattice
+  if (KIND == kKitaev) {
+    eps_st = (double*)sp;
+    sp += align16((size_t)N * 8);
   }
   uint32_t* planes = (uint32_t*)sp;
 
@@ -248,6 +255,151 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
       if (g.r == 0) {
         store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
         jb.rec[2 * (size_t)g.c] += ch.rec;
+      }
+    }
+    return;
+  }
+
+  if (prm.mode == 3) {
+    // local-update Metropolis sweeps (Sec. III, Sec. IV baselines)
+    const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
+    if (KIND == kIsing && g.active && g.r == 0) {
+      for (int u = 0; u < 5; ++u) {
+        const double dE = (2.0 * jb.J[0]) * (double)(4 - 2 * u);
+        ch.thr[u] = exp(-ch.beta * dE) * 0x1p32;
+      }
+    }
+    __syncthreads();
+    unsigned nacc = 0;
+    for (int s = 0; s < prm.S; ++s) {
+      const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
+      if (KIND == kIsing) {
+        uint32_t* v = my + ch.cur * P;
+        nacc += ising_colour(jb, g, v, step, 0, ch.thr);
+        __syncthreads();
+        nacc += ising_colour(jb, g, v, step, 1, ch.thr);
+        __syncthreads();
+      } else {
+        // one chain per CTA: every branch below is CTA-uniform
+        for (int n = 0; n < N; ++n) {
+          const uint32_t* v = my + ch.cur * P;
+          uint32_t* vp = my + (ch.cur ^ 1) * P;
+          for (int w = tid; w < jb.Wd; w += NT) vp[w] = v[w] ^ ((w == (n >> 5)) ? (1u << (n & 31)) : 0u);
+          __syncthreads();
+          double kr[4] = {0.0, 0.0, 0.0, 0.0};
+          if (PREC == kMixed) {
+            kitaev_logpi_df(vp, jb.L, jb.J, ch.beta, wk, kr);
+          } else {
+            double k3[3];
+            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k3, eps_st);
+            kr[0] = k3[0];
+            kr[1] = k3[1];
+            kr[2] = k3[2];
+          }
+          if (tid == 0) {
+            const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n >> 2), kTagLocal, step, g.cid), jb.rk);
+            const double logu = log(((double)pick(w, n & 3) + 0.5) * 0x1p-32);
+            const double logr = kr[0] - ch.lp;
+            ch.lpp = kr[0];
+            ch.lppb = kr[3];
+            ch.Ep = kr[1];
+            ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2];
+            ch.flag_rec = 0;
+            if (PREC == kFP64) {
+              ch.flag_acc = logu < logr;
+            } else {
+              const double M = ch.lppb + ch.lpb + 1e-12 * (fabs(ch.lpp) + fabs(ch.lp)) + 1e-300;
+              if (logr - logu > M) ch.flag_acc = 1;
+              else if (logu - logr > M) ch.flag_acc = 0;
+              else ch.flag_rec = 1;
+            }
+          }
+          __syncthreads();
+          if (PREC == kMixed && ch.flag_rec) {
+            // the FP64 eigen-stage of the proposal (and of the current lattice
+            // when its log-weight came from the df64 stage)
+            double k1v[3], k0v[3] = {0.0, 0.0, 0.0};
+            const bool redo_v = ch.lpb != 0.0;
+            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st);
+            if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v);
+            if (tid == 0) {
+              ch.lpp = k1v[0];
+              ch.lppb = 0.0;
+              ch.Ep = k1v[1];
+              ch.otp[0] = k1v[1]; ch.otp[1] = k1v[1] * k1v[1]; ch.otp[2] = k1v[2];
+              if (redo_v) {
+                ch.lp = k0v[0];
+                ch.lpb = 0.0;
+              }
+              const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n >> 2), kTagLocal, step, g.cid), jb.rk);
+              const double logu = log(((double)pick(w, n & 3) + 0.5) * 0x1p-32);
+              ch.flag_acc = logu < ch.lpp - ch.lp;
+              ch.rec_mh += 1ull;
+            }
+            __syncthreads();
+          }
+          if (ch.flag_acc) {
+            // the spectrum cache follows the lattice when the proposal's came from the FP64 stage
+            if (PREC == kFP64 || ch.flag_rec)
+              for (int l = tid; l < N; l += NT) jb.eps[(size_t)g.c * N + l] = eps_st[l];
+            __syncthreads();
+            if (tid == 0) {
+              ch.cur ^= 1;
+              ch.lp = ch.lpp;
+              ch.lpb = ch.lppb;
+              ch.E = ch.Ep;
+              for (int o = 0; o < 3; ++o) ch.ot[o] = ch.otp[o];
+              ch.acc += 1ull;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      // observables of the lattice after the sweep
+      double cn[2];
+      lattice_counts(jb, g, my + ch.cur * P, cn);
+      grp_reduce<2>(cn, g, scratch);
+      if (g.active && g.r == 0) {
+        if (KIND == kIsing) {
+          const double E = -jb.J[0] * (double)(2 * N - 2 * (int)cn[1]);
+          const double M = 2.0 * cn[0] - (double)N;
+          ch.E = E;
+          ch.lp = -ch.beta * E;
+          ch.ot[0] = E; ch.ot[1] = E * E; ch.ot[2] = fabs(M); ch.ot[3] = M * M;
+        } else {
+          ch.ot[3] = cn[1] / (double)N;
+        }
+        if (prm.correct) {
+          for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+          trace_store(jb, g.c, step0 + (uint64_t)s, ch.E);
+        }
+      }
+      __syncthreads();
+    }
+    if (nacc) atomicAdd(&ch.acc, (unsigned long long)nacc);
+    __syncthreads();
+    // FP64 free energy of the final lattices, then everything back to the job
+    Tabs tb64 = tb;
+    tb64.f64 = jb.f64;
+    tb64.b64 = jb.b64;
+    double fo[4];
+    free_energy64(jb, tb64, g, my + ch.cur * P, fo);
+    grp_reduce<4>(fo, g, scratch);
+    if (g.active) {
+      const uint32_t* v = my + ch.cur * P;
+      for (int w = g.r; w < jb.Wd; w += g.tpc) jb.bits[(size_t)g.c * jb.Wd + w] = v[w];
+      if (g.r == 0) {
+        jb.F[g.c] = -jb.vb * fo[2] - fo[0];
+        jb.Fb[g.c] = 0.0;
+        jb.Lb[g.c] = ch.lpb;
+        jb.logpi[g.c] = ch.lp;
+        jb.Ephys[g.c] = ch.E;
+        for (int o = 0; o < kNobs; ++o) {
+          jb.obs_t[(size_t)g.c * kNobs + o] = ch.ot[o];
+          jb.obs[(size_t)g.c * kNobs + o] = ch.os[o];
+        }
+        jb.acc[g.c] += ch.acc;
+        jb.rec[2 * (size_t)g.c + 1] += ch.rec_mh;
       }
     }
     return;
@@ -386,6 +538,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         ch.acc += 1ull;
       }
       for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+      trace_store(jb, g.c, step0 + (uint64_t)s, ch.E);
     }
     __syncthreads();
   }

@@ -26,8 +26,10 @@ namespace crbm {
 namespace {
 
 struct PtParams {
-  JobDev x;   // physical chains
-  JobDev y;   // RBM chains (same model, L, chains and temperatures)
+  JobDev x;          // physical chains
+  JobDev y;          // RBM chains (same model, L, chains and temperatures); unused without swap
+  int swap;          // 1: physical <-> RBM exchange first (tempering correction); 0: temperatures only
+  int step_offset;   // cycle counter = x's step counter + step_offset
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -102,13 +104,14 @@ __global__ void __launch_bounds__(128) pt_exchange_kernel(const __grid_constant_
   const JobDev& y = p.y;
   const int lane = threadIdx.x & 31;
   const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const uint32_t cycle = (uint32_t)*x.step;
+  const unsigned long long cyc = *x.step + (long long)p.step_offset;
+  const uint32_t cycle = (uint32_t)cyc;
   const int par = (int)(cycle & 1u);
   const int n = x.n_chains;
   const int lo = max(2 * u - par, 0), hi = min(2 * u + 2 - par, n);
   if (lo >= hi) return;
   // 1. physical <-> RBM exchange at every temperature of the unit
-  for (int i = lo; i < hi; ++i) {
+  for (int i = lo; i < hi && p.swap; ++i) {
     int sw = 0;
     if (lane == 0) {
       const double log_a = (y.logpi[i] - x.logpi[i]) + (y.F[i] - x.F[i]);
@@ -156,22 +159,25 @@ __global__ void __launch_bounds__(128) pt_exchange_kernel(const __grid_constant_
     const size_t e = (size_t)lo * kNobs + lane;
     x.obs[e] += x.obs_t[e];
   }
+  if (lane < hi - lo) trace_store(x, lo + lane, cyc, x.Ephys[lo + lane]);
 }
 
 __global__ void pt_advance_kernel(unsigned long long* step) { *step += 1ull; }
 
 }  // namespace
 
-cudaError_t launch_pt_exchange(const JobDev& x, const JobDev& y, cudaStream_t st) {
+cudaError_t launch_pt_exchange(const JobDev& x, const JobDev* y, int step_offset, bool advance, cudaStream_t st) {
   if (x.n_chains == 0) return cudaSuccess;
   PtParams p;
   p.x = x;
-  p.y = y;
+  p.y = y ? *y : x;
+  p.swap = y ? 1 : 0;
+  p.step_offset = step_offset;
   const int units = (x.n_chains + 2) / 2;     // most units over both parities
   const int warps = 4;
   pt_exchange_kernel<<<(units + warps - 1) / warps, 32 * warps, 0, st>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !advance) return e;
   pt_advance_kernel<<<1, 1, 0, st>>>(x.step);
   return cudaGetLastError();
 }
