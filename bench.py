@@ -261,6 +261,46 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush):
             "swap_rate": float(acc.sum()) / (n * (cycles + 2))}
 
 
+def tau_run(ctx_cls, L, n, T, steps, dev, stream, warm=200):
+    """The paper's sampler comparison (Sec. III): integrated autocorrelation
+    time of the energy for CRBM proposals (the batch workload's CD-1 filters,
+    mixed precision, MH-corrected) and for checkerboard single-spin Metropolis
+    sweeps, from E traces of `steps` steps of n chains at one temperature;
+    tau from crbm_autocorr (mean over chains), time per step from CUDA events."""
+    import torch
+    from paper_2008_05401_gb300 import FP64, ISING, MIXED
+    W, hb, vb = _ising_batch_model()
+    ctx = ctx_cls(dev)
+    mid = ctx.load_model(ISING, W, vb, hb)
+    out = {"workload": f"2D Ising L={L}, {n} chains, T={T}, E traces of {steps} steps after {warm} of warm-up"}
+    for name, prec in (("crbm", MIXED), ("metropolis", FP64)):
+        job = ctx.new_job(mid, ISING, L, np.full(n, T), (1.0,), SEED, 0,
+                          wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec)
+        step = (lambda k: job.run(k, precision=MIXED, stream=stream)) if name == "crbm" else \
+            (lambda k: job.local_run(k, stream=stream))
+        step(warm)
+        torch.cuda.synchronize(dev)
+        buf = job.set_trace(steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        tau, win = ctx.autocorr(buf, stream=stream)
+        _, acc, _ = job.observables()
+        t = float(np.mean(tau))
+        out[name] = {"tau_E_steps": t, "tau_E_median": float(np.median(tau)), "window_median": int(np.median(win)),
+                     "ms_per_step": ms, "independent_samples_per_s": n / (2.0 * t * ms * 1e-3),
+                     "acceptance": float(acc.sum()) / (n * (steps + warm) * (1 if name == "crbm" else L * L))}
+        job.set_trace(None)
+        job.release()
+    ctx.close()
+    out["crbm_over_metropolis_independent_samples"] = (out["crbm"]["independent_samples_per_s"]
+                                                       / out["metropolis"]["independent_samples_per_s"])
+    return out
+
+
 def serving_run(dev, n=60, rate=200.0):
     """Continuous batching of a Poisson request stream (mixed Ising / Kitaev
     jobs, 1-64 chains, 1e2-2e3 proposals each, mixed precision): p50/p99 latency
@@ -410,6 +450,8 @@ def main():
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush)]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
+        line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream),
+                       tau_run(Context, 64, 512, 2.269, 2000, dev, stream)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(spec)
     if rank == 0:
