@@ -230,6 +230,27 @@ CRBM_API int crbm_set_trace(crbm_ctx* ctx, int job_id, double* dev_trace, int64_
 CRBM_API int crbm_autocorr(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length, double c,
                            double* tau, int64_t* window, void* cuda_stream);
 
+/* Largest n_series crbm_autocorr_noalloc accepts. */
+#define CRBM_AUTOCORR_NOALLOC_MAX_SERIES 16384
+
+/* crbm_autocorr without any device allocation, for callers that must not
+ * allocate device memory during the call (a serving loop that has handed its
+ * whole HBM budget to jobs, where an allocation could fail or make the
+ * allocator trim).  The paper has no counterpart: same estimator and results
+ * as crbm_autocorr, but the per-series results pass through a fixed device
+ * array of CRBM_AUTOCORR_NOALLOC_MAX_SERIES x 16 bytes (256 KiB) in the
+ * library, shared by every call on a device.  Nothing in that array has to
+ * start at zero: each call's kernel writes every entry it copies back.
+ * The first call on a device looks the array up (cudaGetSymbolAddress) and
+ * must not happen while a stream capture is in progress on that device.
+ * Calls on one device must not overlap in time (two host threads, or a call
+ * on one stream while another is still running): they would race on the
+ * array.  Returns when tau and window are on the host.
+ * Errors: CRBM_EINVAL (n_series > CRBM_AUTOCORR_NOALLOC_MAX_SERIES, null
+ * pointers, c <= 0), CRBM_ECUDA. */
+CRBM_API int crbm_autocorr_noalloc(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length,
+                                   double c, double* tau, int64_t* window, void* cuda_stream);
+
 /* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
  * lattice side L and `precision`: every admissible value is timed on a
  * temporary job that fills the GPU (device memory allocated and freed by this

@@ -52,6 +52,8 @@ _SIGS = {
     "crbm_set_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "crbm_autocorr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "crbm_autocorr_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -175,6 +177,14 @@ def crbm_autocorr(ctx, dev_ptr, n_series, length, c=5.0, stream=0):
     win = np.empty(n_series, dtype=np.int64)
     _check(ctx, load().crbm_autocorr(ctx, C.c_void_p(dev_ptr), n_series, length, c, _ptr(tau), _ptr(win),
                                      C.c_void_p(stream)))
+    return tau, win
+
+
+def crbm_autocorr_noalloc(ctx, dev_ptr, n_series, length, c=5.0, stream=0):
+    tau = np.empty(n_series)
+    win = np.empty(n_series, dtype=np.int64)
+    _check(ctx, load().crbm_autocorr_noalloc(ctx, C.c_void_p(dev_ptr), n_series, length, c, _ptr(tau),
+                                             _ptr(win), C.c_void_p(stream)))
     return tau, win
 
 

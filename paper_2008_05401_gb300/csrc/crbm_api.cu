@@ -759,6 +759,26 @@ int crbm_autocorr(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t
   return CRBM_OK;
 }
 
+// For callers that must not allocate device memory during the call (for
+// instance a serving loop that has handed its whole HBM budget to jobs, where
+// an allocation could fail or force the allocator to trim): the results pass
+// through a fixed 256 KiB device array instead of stream-ordered buffers.
+int crbm_autocorr_noalloc(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length, double c,
+                          double* tau, int64_t* window, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  if (n_series < 0 || length < 0) return fail(ctx, CRBM_EINVAL, "negative size");
+  if (n_series > CRBM_AUTOCORR_NOALLOC_MAX_SERIES)
+    return fail(ctx, CRBM_EINVAL, "n_series=%d exceeds the no-allocation limit %d", n_series,
+                CRBM_AUTOCORR_NOALLOC_MAX_SERIES);
+  if (!(c > 0.0)) return fail(ctx, CRBM_EINVAL, "window constant c must be > 0");
+  if (n_series == 0) return CRBM_OK;
+  if (!dev_series || !tau || !window) return fail(ctx, CRBM_EINVAL, "null pointer");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(launch_tau_noalloc(dev_series, n_series, (long long)length, c, tau, window, (cudaStream_t)cuda_stream),
+     "autocorrelation (no allocation)");
+  return CRBM_OK;
+}
+
 int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision, void* cuda_stream) {
   return crbm_run_batch(ctx, 1, &job_id, S, g, correct, precision, cuda_stream);
 }

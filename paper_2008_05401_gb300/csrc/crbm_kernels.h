@@ -33,4 +33,9 @@ cudaError_t launch_pt_exchange(const JobDev& x, const JobDev* y, int step_offset
 // [n][n_series] device array (crbm_analysis.cu); tau and w are device arrays.
 cudaError_t launch_tau(const double* x, int n_series, long long n, double c, double* tau, long long* w,
                        cudaStream_t st);
+// The same into a fixed device scratch array (no device allocation), results
+// copied to the host arrays; returns after the copies.  n_series must not
+// exceed CRBM_AUTOCORR_NOALLOC_MAX_SERIES.
+cudaError_t launch_tau_noalloc(const double* x, int n_series, long long n, double c, double* tau_host,
+                               int64_t* w_host, cudaStream_t st);
 }  // namespace crbm
