@@ -79,3 +79,24 @@ def unpack_bits(words: np.ndarray, L: int) -> np.ndarray:
 def random_lattices(n_chains: int, L: int, seed: int = BASE_SEED) -> np.ndarray:
     """Bernoulli(1/2) initial lattices, (C, L, L) uint8."""
     return rng(seed).integers(0, 2, size=(n_chains, L, L), dtype=np.uint8)
+
+
+def init_train_params(K: int, k: int, seed: int = BASE_SEED):
+    """Initial CRBM parameters of the trainer (Algorithm 1): W ~ N(0, sigma)
+    with sigma = 2 / (K k^2) read as a standard deviation, v_bias = 0,
+    h_bias = 0.  Returned as the flat FP64 vector [W (K*k*k), v_bias, h_bias (K)]."""
+    g = rng(seed)
+    W = g.normal(0.0, 2.0 / (K * k * k), size=K * k * k)
+    return np.concatenate([W, [0.0], np.zeros(K)])
+
+
+def split_params(theta, K: int, k: int):
+    """[W, v_bias, h_bias] flat vector -> (W (K, k, k), h_bias (K,), v_bias)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    return theta[:K * k * k].reshape(K, k, k), theta[K * k * k + 1:].copy(), float(theta[K * k * k])
+
+
+def epoch_order(n: int, seed: int, epoch: int) -> np.ndarray:
+    """Order in which one training epoch visits its n samples (a seeded
+    permutation; minibatches are consecutive runs of it)."""
+    return rng(seed * 1000003 + epoch).permutation(n).astype(np.int32)

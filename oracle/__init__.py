@@ -33,6 +33,10 @@ Modules and what pins each (pins are tests under ``tests/test_oracle_*.py``):
   checkerboard single-spin flips (Ising), sequential single-eta flips (Kitaev),
   optionally with temperature exchange.  Pinned by exact stationarity and a
   deterministic zero-temperature sweep.
+* ``train``      The paper's trainer: energy-matching loss with the optimal
+  constant C, its gradient, ADAM, epochs of minibatches and the outer loop of
+  Algorithm 1.  Pinned by finite differences, the zero loss of the analytic
+  CRBM of App. C, closed-form ADAM properties and the L = 3 Ising protocol.
 * ``autocorr``   Integrated autocorrelation time (Sokal's windowed
   estimator).  Pinned by the AR(1) closed form and exact small cases.
 """
