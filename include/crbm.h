@@ -96,6 +96,14 @@ CRBM_API const char* crbm_last_error(const crbm_ctx* ctx);
 CRBM_API int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W,
                     double v_bias, const double* h_bias, int* model_id);
 
+/* Replace the parameters of model `model_id` (same K, k; same layout as
+ * crbm_load_model), for instance after a training epoch.  Waits until the
+ * device is idle, then rewrites the model's tables; its jobs use the new
+ * parameters from their next launch on.  Their stored F (and the exactness
+ * the tempering and exchange calls rely on) refer to the old parameters until
+ * the next proposal or evaluation.  Errors: CRBM_EINVAL, CRBM_ECUDA. */
+CRBM_API int crbm_update_model(crbm_ctx* ctx, int model_id, const double* W, double v_bias, const double* h_bias);
+
 /* Bytes of caller-owned device memory one job needs: packed lattices, FP64
  * temperatures and energies, observable sums and counters (and, for the
  * Kitaev kind, the L*L single-fermion energies of each lattice), 256-byte aligned.
@@ -250,6 +258,45 @@ CRBM_API int crbm_autocorr(crbm_ctx* ctx, const double* dev_series, int n_series
  * pointers, c <= 0), CRBM_ECUDA. */
 CRBM_API int crbm_autocorr_noalloc(crbm_ctx* ctx, const double* dev_series, int n_series, int64_t length,
                                    double c, double* tau, int64_t* window, void* cuda_stream);
+
+/* One training problem of crbm_train_epochs: the paper trains one CRBM per
+ * temperature (Sec. IV), so many problems run side by side.  All pointers
+ * are device memory owned by the caller. */
+typedef struct {
+    int K, k;                 /* filter bank shape: 1 <= K <= 8, 1 <= k <= min(7, L) */
+    int L;                    /* lattice side of the samples, 2 <= L <= 32 */
+    int n_samples;            /* samples of the epoch */
+    const uint32_t* samples;  /* [n_samples][ceil(L*L/32)] packed lattices (layout of crbm_init_chains) */
+    const double* targets;    /* [n_samples] t_i = beta E_phys(x_i) (Kitaev: -log pi(x_i)) */
+    const int32_t* order;     /* [n_samples] visiting order of the epoch (indices into samples) */
+    double* theta;            /* [K*k*k + 1 + K] parameters [W (row-major W[f][a][b]), v_bias, h_bias]; updated */
+    double* adam_m;           /* [K*k*k + 1 + K] ADAM first moments; updated */
+    double* adam_v;           /* [K*k*k + 1 + K] ADAM second moments; updated */
+    int64_t* adam_t;          /* [1] ADAM steps taken so far; updated */
+    double* losses;           /* [ceil(n_samples / batch)] loss of each minibatch, or NULL */
+} crbm_train_problem;
+
+/* Largest number of problems one kernel launch of crbm_train_epochs takes
+ * (more are split over several launches). */
+#define CRBM_TRAIN_MAX_PROBLEMS 64
+
+/* One epoch of the paper's trainer (Sec. II, App. A, Algorithm 1) for each
+ * of n_problems problems (host array of descriptors), enqueued on
+ * cuda_stream.  The epoch visits order[0..n_samples-1] in consecutive
+ * minibatches of `batch` samples (the last one holds the remainder); per
+ * minibatch, in FP64:
+ *   diff_i = t_i - F(x_i) (F of Eq. 13), C = mean_i diff_i,
+ *   loss = mean_i (diff_i - C)^2,
+ *   g = d loss / d theta = -(2/M) sum_i (diff_i - C) dF(x_i)/d theta,
+ * then one ADAM step (Kingma & Ba): m <- b1 m + (1-b1) g,
+ * v <- b2 v + (1-b2) g^2, t <- t+1,
+ * theta <- theta - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * The paper uses lr = 1e-3 and batch 20 (App. D); b1 = 0.9, b2 = 0.999,
+ * eps = 1e-8 are ADAM's published defaults (the paper names none).
+ * Errors: CRBM_EINVAL (shapes out of range, null pointers, batch outside
+ * [1, 64]), CRBM_ECUDA. */
+CRBM_API int crbm_train_epochs(crbm_ctx* ctx, int n_problems, const crbm_train_problem* problems, int batch,
+                               double lr, double b1, double b2, double eps, void* cuda_stream);
 
 /* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
  * lattice side L and `precision`: every admissible value is timed on a

@@ -30,6 +30,14 @@ class CrbmError(RuntimeError):
         self.code = code
 
 
+class TrainProblem(C.Structure):
+    """crbm_train_problem (include/crbm.h): device pointers and sizes of one training problem."""
+    _fields_ = [("K", C.c_int), ("k", C.c_int), ("L", C.c_int), ("n_samples", C.c_int),
+                ("samples", C.c_void_p), ("targets", C.c_void_p), ("order", C.c_void_p),
+                ("theta", C.c_void_p), ("adam_m", C.c_void_p), ("adam_v", C.c_void_p),
+                ("adam_t", C.c_void_p), ("losses", C.c_void_p)]
+
+
 _SIGS = {
     "crbm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]),
     "crbm_destroy": (C.c_int, [C.c_void_p]),
@@ -54,6 +62,9 @@ _SIGS = {
                                 C.c_void_p, C.c_void_p]),
     "crbm_autocorr_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
+    "crbm_train_epochs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, C.c_void_p]),
+    "crbm_update_model": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -186,6 +197,18 @@ def crbm_autocorr_noalloc(ctx, dev_ptr, n_series, length, c=5.0, stream=0):
     _check(ctx, load().crbm_autocorr_noalloc(ctx, C.c_void_p(dev_ptr), n_series, length, c, _ptr(tau),
                                              _ptr(win), C.c_void_p(stream)))
     return tau, win
+
+
+def crbm_train_epochs(ctx, problems, batch=20, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=0):
+    arr = (TrainProblem * max(len(problems), 1))(*problems)
+    _check(ctx, load().crbm_train_epochs(ctx, len(problems), C.cast(arr, C.c_void_p), batch, lr, b1, b2, eps,
+                                         C.c_void_p(stream)))
+
+
+def crbm_update_model(ctx, model_id, W, v_bias, h_bias):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    hb = np.ascontiguousarray(h_bias, dtype=np.float64)
+    _check(ctx, load().crbm_update_model(ctx, model_id, _ptr(W), float(v_bias), _ptr(hb)))
 
 
 def crbm_tune(ctx, model_id, L, precision=FP64):
@@ -323,6 +346,10 @@ class Context:
         jid = crbm_init_chains(self.h, model_id, L, T, J, seed, chain_id_base, init_bits,
                                mem.data_ptr() if len(T) else 0, mem.numel())
         return Job(self, jid, L, len(T), mem)
+
+    def update_model(self, model_id, W, v_bias, h_bias):
+        """New parameters for an existing model (same K, k)."""
+        crbm_update_model(self.h, model_id, W, v_bias, h_bias)
 
     def tune(self, model_id, L, precision=FP64):
         """Pick the fastest chains-per-CTA for (model, L); returns (nc, us per chain-proposal)."""

@@ -308,17 +308,10 @@ int crbm_destroy(crbm_ctx* ctx) {
 
 const char* crbm_last_error(const crbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, double v_bias,
-                    const double* h_bias, int* model_id) {
-  if (!ctx) return CRBM_EINVAL;
-  if (kind != kIsing && kind != kKitaev) return fail(ctx, CRBM_EINVAL, "unknown model kind %d", kind);
-  if (K < 1 || K > kMaxK) return fail(ctx, CRBM_EINVAL, "K=%d outside [1,%d]", K, kMaxK);
-  if (k < 1 || k > kMaxk) return fail(ctx, CRBM_EINVAL, "k=%d outside [1,%d]", k, kMaxk);
-  if (!W || !h_bias || !model_id) return fail(ctx, CRBM_EINVAL, "null pointer");
-  for (int i = 0; i < K * k * k; ++i)
-    if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
-  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  Model m;
+// Host tables and error constants of a model from its parameters, copied to
+// the device (into new buffers when alloc, else into the model's own).
+static int build_model(crbm_ctx* ctx, Model& m, int kind, int K, int k, const double* W, double v_bias,
+                       const double* h_bias, bool alloc) {
   m.kind = kind;
   m.K = K;
   m.k = k;
@@ -410,16 +403,52 @@ int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, doub
   }
   m.nlut = nlut;
   m.nq = nq;
-  CK(cudaMalloc(&m.d_q, 3 * nq * sizeof(float4)), "cudaMalloc tables");
+  if (alloc) CK(cudaMalloc(&m.d_q, 3 * nq * sizeof(float4)), "cudaMalloc tables");
   CK(cudaMemcpy(m.d_q, q4.data(), 3 * nq * sizeof(float4), cudaMemcpyHostToDevice), "table copy");
-  CK(cudaMalloc(&m.d_f64, 2 * nlut * sizeof(double)), "cudaMalloc tables");
-  CK(cudaMalloc(&m.d_f32, 4 * nlut * sizeof(float)), "cudaMalloc tables");
+  if (alloc) {
+    CK(cudaMalloc(&m.d_f64, 2 * nlut * sizeof(double)), "cudaMalloc tables");
+    CK(cudaMalloc(&m.d_f32, 4 * nlut * sizeof(float)), "cudaMalloc tables");
+  }
   CK(cudaMemcpy(m.d_f64, fwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
   CK(cudaMemcpy(m.d_f64 + nlut, bwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
   CK(cudaMemcpy(m.d_f32, t32.data(), 4 * nlut * sizeof(float), cudaMemcpyHostToDevice), "table copy");
+  return CRBM_OK;
+}
+
+int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, double v_bias,
+                    const double* h_bias, int* model_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (kind != kIsing && kind != kKitaev) return fail(ctx, CRBM_EINVAL, "unknown model kind %d", kind);
+  if (K < 1 || K > kMaxK) return fail(ctx, CRBM_EINVAL, "K=%d outside [1,%d]", K, kMaxK);
+  if (k < 1 || k > kMaxk) return fail(ctx, CRBM_EINVAL, "k=%d outside [1,%d]", k, kMaxk);
+  if (!W || !h_bias || !model_id) return fail(ctx, CRBM_EINVAL, "null pointer");
+  for (int i = 0; i < K * k * k; ++i)
+    if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Model m;
+  const int rc = build_model(ctx, m, kind, K, k, W, v_bias, h_bias, true);
+  if (rc) return rc;
   m.live = true;
   ctx->models.push_back(m);
   *model_id = (int)ctx->models.size() - 1;
+  return CRBM_OK;
+}
+
+int crbm_update_model(crbm_ctx* ctx, int model_id, const double* W, double v_bias, const double* h_bias) {
+  if (!ctx) return CRBM_EINVAL;
+  if (model_id < 0 || model_id >= (int)ctx->models.size() || !ctx->models[model_id].live)
+    return fail(ctx, CRBM_EINVAL, "bad model id %d", model_id);
+  Model& m = ctx->models[model_id];
+  if (!W || !h_bias) return fail(ctx, CRBM_EINVAL, "null pointer");
+  for (int i = 0; i < m.K * m.k * m.k; ++i)
+    if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // the tables are read by every launch of the model's jobs: wait until none runs
+  CK(cudaDeviceSynchronize(), "device synchronize");
+  const int rc = build_model(ctx, m, m.kind, m.K, m.k, W, v_bias, h_bias, false);
+  if (rc) return rc;
+  for (auto& j : ctx->jobs)
+    if (j.live && j.model == model_id) j.exact = false;
   return CRBM_OK;
 }
 
@@ -778,6 +807,36 @@ int crbm_autocorr_noalloc(crbm_ctx* ctx, const double* dev_series, int n_series,
      "autocorrelation (no allocation)");
   return CRBM_OK;
 }
+
+int crbm_train_epochs(crbm_ctx* ctx, int n_problems, const crbm_train_problem* problems, int batch, double lr,
+                      double b1, double b2, double eps, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  if (n_problems < 0 || (n_problems > 0 && !problems)) return fail(ctx, CRBM_EINVAL, "bad problem list");
+  if (batch < 1 || batch > 64) return fail(ctx, CRBM_EINVAL, "batch=%d outside [1,64]", batch);
+  if (!(lr >= 0.0) || !(b1 >= 0.0 && b1 < 1.0) || !(b2 >= 0.0 && b2 < 1.0) || !(eps > 0.0))
+    return fail(ctx, CRBM_EINVAL, "bad ADAM hyper-parameters");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  for (int i = 0; i < n_problems; ++i) {
+    const crbm_train_problem& q = problems[i];
+    if (q.L < 2 || q.L > 32) return fail(ctx, CRBM_EINVAL, "problem %d: L=%d outside [2,32]", i, q.L);
+    if (q.K < 1 || q.K > kMaxK || q.k < 1 || q.k > kMaxk || q.k > q.L)
+      return fail(ctx, CRBM_EINVAL, "problem %d: filter shape (%d,%d) out of range", i, q.K, q.k);
+    if (q.n_samples < 0) return fail(ctx, CRBM_EINVAL, "problem %d: n_samples < 0", i);
+    if (!q.theta || !q.adam_m || !q.adam_v || !q.adam_t || (q.n_samples > 0 && (!q.samples || !q.targets || !q.order)))
+      return fail(ctx, CRBM_EINVAL, "problem %d: null pointer", i);
+    if (train_smem_bytes(q, batch) > (size_t)optin)
+      return fail(ctx, CRBM_EINVAL, "problem %d needs %zu bytes of shared memory", i, train_smem_bytes(q, batch));
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (int i0 = 0; i0 < n_problems; i0 += CRBM_TRAIN_MAX_PROBLEMS) {
+    const int n = n_problems - i0 < CRBM_TRAIN_MAX_PROBLEMS ? n_problems - i0 : CRBM_TRAIN_MAX_PROBLEMS;
+    CK(launch_train(problems + i0, n, batch, lr, b1, b2, eps, st), "trainer launch");
+  }
+  return CRBM_OK;
+}
+
 
 int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision, void* cuda_stream) {
   return crbm_run_batch(ctx, 1, &job_id, S, g, correct, precision, cuda_stream);

@@ -38,4 +38,12 @@ cudaError_t launch_tau(const double* x, int n_series, long long n, double c, dou
 // exceed CRBM_AUTOCORR_NOALLOC_MAX_SERIES.
 cudaError_t launch_tau_noalloc(const double* x, int n_series, long long n, double c, double* tau_host,
                                int64_t* w_host, cudaStream_t st);
+// Trainer (crbm_train.cu): one epoch of each of n <= CRBM_TRAIN_MAX_PROBLEMS
+// problems (crbm_train_problem is declared in crbm.h).
+}  // namespace crbm
+#include "crbm.h"
+namespace crbm {
+size_t train_smem_bytes(const crbm_train_problem& q, int batch);
+cudaError_t launch_train(const crbm_train_problem* pr, int n, int batch, double lr, double b1, double b2,
+                         double eps, cudaStream_t st);
 }  // namespace crbm
