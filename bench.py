@@ -301,6 +301,44 @@ def tau_run(ctx_cls, L, n, T, steps, dev, stream, warm=200):
     return out
 
 
+def train_run(ctx_cls, dev, stream, n_problems=24, L=8, K=2, k=5, n=10_000, batch=20):
+    """The paper's trainer (Algorithm 1's epoch, App. D sizes): one CRBM of
+    K x k x k filters per temperature, n samples of L x L each, minibatches of
+    `batch`, ADAM; one epoch of all problems is one launch.  value = sample
+    gradients/s; flops counted as a direct forward and weight-gradient
+    convolution, 4 K k^2 L^2 per sample."""
+    import torch
+    from paper_2008_05401_gb300 import FP64, ISING, trainer
+    ctx = ctx_cls(dev)
+    mid = ctx.load_model(ISING, np.zeros((K, k, k)), 0.0, np.zeros(K))
+    probs, xs, ts, os_ = [], [], [], []
+    for i in range(n_problems):
+        bits = wl.pack_bits(wl.random_lattices(n, L, seed=SEED + i))
+        job = ctx.new_job(mid, ISING, L, np.full(n, 1.5 + i * 0.05), (1.0,), SEED, 0, bits, FP64)
+        lp, _, _ = job.energies()
+        job.release()
+        xs.append(torch.tensor(bits.view(np.int32), device=f"cuda:{dev}"))
+        ts.append(torch.tensor(-lp, device=f"cuda:{dev}"))
+        os_.append(torch.tensor(wl.epoch_order(n, SEED, i), device=f"cuda:{dev}"))
+        probs.append(trainer.Problem.new(ctx, K, k, L, wl.init_train_params(K, k, seed=SEED + i)))
+    trainer.train_epochs(ctx, probs, xs, ts, os_, batch, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = trainer.train_epochs(ctx, probs, xs, ts, os_, batch, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    flops = 4.0 * K * k * k * L * L * n * n_problems
+    return {"workload": f"trainer epoch: {n_problems} problems (one per temperature), K={K} {k}x{k} filters, "
+                        f"L={L}, {n} samples each, minibatch {batch}, ADAM, FP64",
+            "value": n * n_problems / (ms * 1e-3), "unit": "sample-gradients/s", "ms_per_epoch": ms,
+            "adam_steps_per_s": n_problems * ((n + batch - 1) // batch) / (ms * 1e-3),
+            "fp64_gflops_direct_conv_equiv": flops / (ms * 1e-3) / 1e9,
+            "mean_loss_epoch2": float(np.mean([float(x.mean()) for x in losses]))}
+
+
 def serving_run(dev, n=60, rate=200.0):
     """Continuous batching of a Poisson request stream (mixed Ising / Kitaev
     jobs, 1-64 chains, 1e2-2e3 proposals each, mixed precision): p50/p99 latency
@@ -450,6 +488,7 @@ def main():
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush)]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
+        line["train"] = train_run(Context, dev, stream)
         line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream),
                        tau_run(Context, 64, 512, 2.269, 2000, dev, stream)]
     if rank == 0 and not args.no_cpu_baseline:
