@@ -225,7 +225,24 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
             "fp64_recomputes": rec}
 
 
-def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush):
+def _oracle_rate(fn, budget_s):
+    """Calls of fn() per second over about budget_s seconds (at least one call), one BLAS thread."""
+    try:
+        from threadpoolctl import threadpool_limits
+        lim = threadpool_limits(1)
+    except Exception:  # noqa: BLE001
+        lim = None
+    t0, n = time.perf_counter(), 0
+    while n == 0 or time.perf_counter() - t0 < budget_s:
+        fn()
+        n += 1
+    dt = time.perf_counter() - t0
+    if lim is not None and hasattr(lim, "unregister"):
+        lim.unregister()
+    return n / dt, n, dt
+
+
+def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0, clocks=None):
     """Parallel-tempering exchange correction (App. B.2) on a workload's first
     lattice size: the workload's chains are the physical ladder, as many RBM
     chains run beside them.  value = chain-cycles/s (one RBM proposal, one
@@ -254,14 +271,27 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush):
     _, acc, _ = x.observables()
     ctx.close()
     model = "2D Ising" if spec["kind"] == 0 else "Kitaev"
-    return {"workload": f"parallel tempering, {model} L={L}, {n} physical + {n} RBM chains, one proposal "
-                        f"(g=1) per RBM chain and cycle, the workload's T ladder",
-            "precision": "mixed" if prec == MIXED else "fp64", "value": n * cycles / (ms * 1e-3),
-            "unit": "chain-cycles/s", "ms_per_cycle": ms / cycles, "cycles": cycles,
-            "swap_rate": float(acc.sum()) / (n * (cycles + 2))}
+    out = {"workload": f"parallel tempering, {model} L={L}, {n} physical + {n} RBM chains, one proposal "
+                       f"(g=1) per RBM chain and cycle, the workload's T ladder",
+           "precision": "mixed" if prec == MIXED else "fp64", "value": n * cycles / (ms * 1e-3),
+           "unit": "chain-cycles/s", "ms_per_cycle": ms / cycles, "cycles": cycles,
+           "swap_rate": float(acc.sum()) / (n * (cycles + 2))}
+    if spec["kind"] == 0:
+        # the RBM proposal (mode-2 kernel) dominates: the headline's conv-flop count per site
+        K, k = W.shape[0], W.shape[1]
+        out["roofline"] = roofline(None, ms / cycles, clocks or {}, K, k, n * L * L)
+    if oracle_s > 0:
+        from oracle import chain, tempering
+        nc = 32
+        px = chain.make_chains(spec["kind"], W, hb, vb, L, T[:nc], spec["J"], SEED, np.arange(nc))
+        py = chain.make_chains(spec["kind"], W, hb, vb, L, T[:nc], spec["J"], SEED + 1, np.arange(nc, 2 * nc))
+        rate, c, dt = _oracle_rate(lambda: tempering.cycle(px, py, 1), oracle_s)
+        out["cpu_baseline"] = {"value": rate * nc, "unit": "chain-cycles/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{nc} + {nc} chains x {c} cycles in {dt:.1f}s"}
+    return out
 
 
-def tau_run(ctx_cls, L, n, T, steps, dev, stream, warm=200):
+def tau_run(ctx_cls, L, n, T, steps, dev, stream, warm=200, oracle_s=2.0):
     """The paper's sampler comparison (Sec. III): integrated autocorrelation
     time of the energy for CRBM proposals (the batch workload's CD-1 filters,
     mixed precision, MH-corrected) and for checkerboard single-spin Metropolis
@@ -298,10 +328,18 @@ def tau_run(ctx_cls, L, n, T, steps, dev, stream, warm=200):
     ctx.close()
     out["crbm_over_metropolis_independent_samples"] = (out["crbm"]["independent_samples_per_s"]
                                                        / out["metropolis"]["independent_samples_per_s"])
+    out["metropolis"]["chain_sweeps_per_s"] = n / (out["metropolis"]["ms_per_step"] * 1e-3)
+    if oracle_s > 0:
+        from oracle import chain, metropolis
+        nc = 64
+        och = chain.make_chains(chain.ISING, W, hb, vb, L, np.full(nc, T), (1.0,), SEED, np.arange(nc))
+        rate, c, dt = _oracle_rate(lambda: metropolis.sweep(och), oracle_s)
+        out["metropolis"]["cpu_baseline"] = {"value": rate * nc, "unit": "chain-sweeps/s", "cores": 1,
+                                             "kind": "oracle", "sample": f"{nc} chains x {c} sweeps in {dt:.1f}s"}
     return out
 
 
-def train_run(ctx_cls, dev, stream, n_problems=24, L=8, K=2, k=5, n=10_000, batch=20):
+def train_run(ctx_cls, dev, stream, n_problems=24, L=8, K=2, k=5, n=10_000, batch=20, oracle_s=2.0):
     """The paper's trainer (Algorithm 1's epoch, App. D sizes): one CRBM of
     K x k x k filters per temperature, n samples of L x L each, minibatches of
     `batch`, ADAM; one epoch of all problems is one launch.  value = sample
@@ -331,12 +369,26 @@ def train_run(ctx_cls, dev, stream, n_problems=24, L=8, K=2, k=5, n=10_000, batc
     ms = e0.elapsed_time(e1)
     ctx.close()
     flops = 4.0 * K * k * k * L * L * n * n_problems
-    return {"workload": f"trainer epoch: {n_problems} problems (one per temperature), K={K} {k}x{k} filters, "
-                        f"L={L}, {n} samples each, minibatch {batch}, ADAM, FP64",
-            "value": n * n_problems / (ms * 1e-3), "unit": "sample-gradients/s", "ms_per_epoch": ms,
-            "adam_steps_per_s": n_problems * ((n + batch - 1) // batch) / (ms * 1e-3),
-            "fp64_gflops_direct_conv_equiv": flops / (ms * 1e-3) / 1e9,
-            "mean_loss_epoch2": float(np.mean([float(x.mean()) for x in losses]))}
+    achieved = flops / (ms * 1e-3) / 1e12
+    out = {"workload": f"trainer epoch: {n_problems} problems (one per temperature), K={K} {k}x{k} filters, "
+                       f"L={L}, {n} samples each, minibatch {batch}, ADAM, FP64",
+           "value": n * n_problems / (ms * 1e-3), "unit": "sample-gradients/s", "ms_per_epoch": ms,
+           "adam_steps_per_s": n_problems * ((n + batch - 1) // batch) / (ms * 1e-3),
+           "mean_loss_epoch2": float(np.mean([float(x.mean()) for x in losses])),
+           "roofline": {"bound": "fp64", "achieved": round(achieved, 4), "peak": 1.25, "unit": "TFLOP/s",
+                        "frac": round(achieved / 1.25, 4), "traffic": None,
+                        "peak_source": "nominal GB300 FP64 (no measured FP64 peak); flops = direct forward + "
+                                       "weight-gradient convolutions, 4 K k^2 L^2 per sample"}}
+    if oracle_s > 0:
+        from oracle import train
+        v = wl.random_lattices(2000, L, seed=SEED)
+        tt = np.random.default_rng(1).normal(size=2000)
+        st = train.Adam.zeros(K * k * k + 1 + K)
+        th = wl.init_train_params(K, k)
+        rate, c, dt = _oracle_rate(lambda: train.epoch(th, st, v, tt, np.arange(2000), K, k, M=batch), oracle_s)
+        out["cpu_baseline"] = {"value": rate * 2000, "unit": "sample-gradients/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{c} epochs of 2000 samples in {dt:.1f}s"}
+    return out
 
 
 def serving_run(dev, n=60, rate=200.0):
@@ -484,13 +536,16 @@ def main():
             secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush),
             secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
             secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush),
-            tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush),
-            tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush)]
+            tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush, clocks=clocks,
+                          oracle_s=0.0 if args.no_cpu_baseline else 3.0),
+            tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
+                          oracle_s=0.0 if args.no_cpu_baseline else 2.0)]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
-        line["train"] = train_run(Context, dev, stream)
-        line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream),
-                       tau_run(Context, 64, 512, 2.269, 2000, dev, stream)]
+        ob = 0.0 if args.no_cpu_baseline else 2.0
+        line["train"] = train_run(Context, dev, stream, oracle_s=ob)
+        line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream, oracle_s=ob),
+                       tau_run(Context, 64, 512, 2.269, 2000, dev, stream, oracle_s=ob)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(spec)
     if rank == 0:

@@ -323,6 +323,11 @@ __device__ __forceinline__ double block_sum(double x, double* scratch) {
 //   fd/bd     FP32 roundings of f64/b64 (mixed-path decisions)
 //   fh/fl     hi/lo split of f64 (mixed-path free energy)
 //   fd4/fh4/fl4  the same forward tables with the filter index innermost,
+//             in shared memory replicated 8 times, entry e of copy c at
+//             float4 index 8 e + c; thread t reads copy t % 8 (the pointer
+//             below already includes + t % 8, so entry e is at [e << 3]):
+//             the 8 threads of a quarter-warp hit 8 distinct bank groups
+//             whatever their codes, so a 16-byte table load never conflicts;
 //             (a*T + code)*4 + f, for K <= 4 (zero-padded): one 16-byte load
 //             serves all filters of a site
 struct Tabs {
@@ -402,7 +407,7 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
 #pragma unroll
         for (int a = 0; a < kU; ++a) {
           if (kC || a < k) {
-            const float4 e = tb.fd4[m[t][a]];
+            const float4 e = tb.fd4[m[t][a] << 3];
             x.x += e.x;
             x.y += e.y;
             x.z += e.z;
@@ -604,7 +609,7 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
 #pragma unroll
         for (int a = 0; a < kU; ++a) {
           if (kC || a < k) {
-            const float4 eh = tb.fh4[m[t][a]], el = tb.fl4[m[t][a]];
+            const float4 eh = tb.fh4[m[t][a] << 3], el = tb.fl4[m[t][a] << 3];
             xh.x += eh.x; xh.y += eh.y; xh.z += eh.z; xh.w += eh.w;
             xl.x += el.x; xl.y += el.y; xl.z += el.z; xl.w += el.w;
           }

@@ -8,7 +8,7 @@ size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC) {
   const size_t N = (size_t)L * L, P = (N + 31) / 32 + 1, nlut = (size_t)K * k * ((size_t)1 << k);
   const size_t nq = (size_t)k << k;
   size_t b = (prec == kFP64) ? 2 * align16(nlut * 8)
-             : (KC == 4 ? 3 * align16(nq * 16) + align16(nlut * 4) : 4 * align16(nlut * 4));
+             : (KC == 4 ? 3 * align16(nq * 16 * 8) + align16(nlut * 4) : 4 * align16(nlut * 4));
   b += align16(nc * sizeof(ChainSm));
   b += align16(64 * 8);
   if (kind == kKitaev)

@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
   } else if (KC == 4) {
     for (int i = 0; i < 3; ++i) {
       t4[i] = (float4*)sp;
-      sp += align16((size_t)nq * 16);
+      sp += align16((size_t)nq * 16 * 8);      // 8 bank-interleaved copies
     }
     t32[1] = (float*)sp;
     sp += align16((size_t)nlut * 4);
-    tb.fd4 = t4[0];
-    tb.fh4 = t4[1];
-    tb.fl4 = t4[2];
+    tb.fd4 = t4[0] + (threadIdx.x & 7);
+    tb.fh4 = t4[1] + (threadIdx.x & 7);
+    tb.fl4 = t4[2] + (threadIdx.x & 7);
     tb.bd = t32[1];
   } else {
     for (int i = 0; i < 4; ++i) {
@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     }
   }
   if (PREC == kMixed && KC == 4) {
-    for (int i = tid; i < nq; i += NT) {
-      t4[0][i] = jb.fd4[i];
-      t4[1][i] = jb.fh4[i];
-      t4[2][i] = jb.fl4[i];
+    for (int i = tid; i < nq * 8; i += NT) {
+      t4[0][i] = jb.fd4[i >> 3];
+      t4[1][i] = jb.fh4[i >> 3];
+      t4[2][i] = jb.fl4[i >> 3];
     }
   }
   for (int i = tid; i < jb.nc * (2 + K) * P; i += NT) planes[i] = 0u;
