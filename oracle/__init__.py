@@ -26,6 +26,11 @@ Modules and what pins each (pins are tests under ``tests/test_oracle_*.py``):
   (Eq. B5 read with (pi, P_CRBM) as the two distributions).  Pinned by exact
   stationary distributions (Ising L=4, Kitaev L=2) and by acceptance == 1 for
   the analytic Ising CRBM.
+* ``lcrbm``      Locally connected CRBM with unshared edge kernels for the
+  open-boundary Kitaev model (Sec. IV); ``kitaev`` takes ``open_cols`` for the
+  lattice open along j.  Pinned by brute-force marginalisation, conditionals
+  read off the joint energy, the 1x1-kernel reduction to the CRBM, closed-form
+  open spectra, the sum rule and exact stationarity of the chain.
 * ``tempering``  Parallel-tempering exchange correction (App. B.2, Fig. 8b).
   Pinned by exact stationarity at every temperature of a ladder (Ising L=4)
   and by planted mistakes that break it.

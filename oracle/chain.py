@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import crbm, ising, kitaev, philox
+from . import crbm, ising, kitaev, lcrbm, philox
 
 ISING = 0
 KITAEV = 1
@@ -54,14 +54,38 @@ class Chains:
     obs_terms: np.ndarray = None  # (C, NOBS) observables of the current lattices
     accepts: np.ndarray = None    # (C,)
     extras: dict = field(default_factory=dict)
+    edge: int = 0                 # > 0: LCRBM with `edge` unshared kernels per side, open columns
 
     @property
     def beta(self):
         return 1.0 / self.T
 
     @property
+    def open_cols(self):
+        return self.edge > 0
+
+    # the model's free energy and conditionals: periodic CRBM or, with edge > 0, LCRBM
+    def free(self, v):
+        if self.edge:
+            return lcrbm.free_energy(v, self.W, self.hb, self.vb, self.edge)
+        return crbm.free_energy(v, self.W, self.hb, self.vb)
+
+    def hpre(self, v):
+        if self.edge:
+            return lcrbm.hidden_preact(v, self.W, self.hb, self.edge)
+        return crbm.hidden_preact(v, self.W, self.hb)
+
+    def vpre(self, h):
+        if self.edge:
+            return lcrbm.visible_preact(h, self.W, self.vb, self.edge)
+        return crbm.visible_preact(h, self.W, self.vb)
+
+    def targ(self, v, beta=None):
+        return target(self.model, v, self.beta if beta is None else beta, self.J, self.open_cols)
+
+    @property
     def K(self):
-        return self.W.shape[0]
+        return self.W.shape[-3]
 
 
 def random_init(seed: int, chain_ids, L: int) -> np.ndarray:
@@ -70,28 +94,29 @@ def random_init(seed: int, chain_ids, L: int) -> np.ndarray:
     return (w < np.uint32(2 ** 31)).astype(np.uint8).reshape(len(chain_ids), L, L)
 
 
-def target(model: int, v, beta, J):
-    """(log pi, E_phys, obs-terms) of each chain's lattice."""
+def target(model: int, v, beta, J, open_cols=False):
+    """(log pi, E_phys, obs-terms) of each chain's lattice (open_cols: the
+    Kitaev lattice is open along j, see ``kitaev.hopping_matrix``)."""
     if model == ISING:
         E = ising.energy(v, J[0])
         M = ising.magnetisation(v)
         return -beta * E, E, np.stack([E, E * E, np.abs(M), M * M], axis=1)
-    eps = kitaev.energies(v, J)
+    eps = kitaev.energies(v, J, open_cols)
     lp = kitaev.log_weight_from_eps(eps, beta)
     e, cf = kitaev.thermal_terms(eps, beta)
-    return lp, e, np.stack([e, e * e, cf, kitaev.vison_density(v)], axis=1)
+    return lp, e, np.stack([e, e * e, cf, kitaev.vison_density(v, open_cols)], axis=1)
 
 
-def make_chains(model, W, hb, vb, L, T, J, seed, chain_ids, v0=None) -> Chains:
+def make_chains(model, W, hb, vb, L, T, J, seed, chain_ids, v0=None, edge=0) -> Chains:
     chain_ids = np.asarray(chain_ids, dtype=np.uint64)
     T = np.broadcast_to(np.asarray(T, dtype=np.float64), (len(chain_ids),)).copy()
     if v0 is None:
         v0 = random_init(seed, chain_ids, L)
     ch = Chains(model, np.asarray(W, dtype=np.float64), np.asarray(hb, dtype=np.float64),
                 float(vb), L, T, tuple(float(x) for x in J), seed, chain_ids,
-                np.asarray(v0, dtype=np.uint8).copy())
-    ch.F = crbm.free_energy(ch.v, ch.W, ch.hb, ch.vb)
-    ch.logpi, ch.E_phys, ch.obs_terms = target(model, ch.v, ch.beta, ch.J)
+                np.asarray(v0, dtype=np.uint8).copy(), edge=int(edge))
+    ch.F = ch.free(ch.v)
+    ch.logpi, ch.E_phys, ch.obs_terms = ch.targ(ch.v)
     ch.obs = np.zeros((len(chain_ids), NOBS))
     ch.accepts = np.zeros(len(chain_ids), dtype=np.int64)
     return ch
@@ -111,9 +136,9 @@ def propose(ch: Chains, g: int = 1):
         u_h = np.stack([philox.uniforms(ch.seed, ch.chain_ids, ch.step, philox.hidden_tag(s, K, kk), N)
                         for kk in range(K)], axis=1).reshape(C, K, L, L)
         u_v = philox.uniforms(ch.seed, ch.chain_ids, ch.step, philox.visible_tag(s, K), N).reshape(C, L, L)
-        p_h = crbm.sigmoid(crbm.hidden_preact(v, ch.W, ch.hb))
+        p_h = crbm.sigmoid(ch.hpre(v))
         h = (u_h < p_h).astype(np.uint8)
-        p_v = crbm.sigmoid(crbm.visible_preact(h, ch.W, ch.vb))
+        p_v = crbm.sigmoid(ch.vpre(h))
         v = (u_v < p_v).astype(np.uint8)
         margin = np.minimum(margin, np.abs(u_h - p_h).reshape(C, -1).min(axis=1))
         margin = np.minimum(margin, np.abs(u_v - p_v).reshape(C, -1).min(axis=1))
@@ -127,8 +152,8 @@ def step(ch: Chains, g: int = 1, correct: bool = True):
     bernoulli_margin and the MH margin |log u - log r|.
     """
     v_new, bmargin = propose(ch, g)
-    F_new = crbm.free_energy(v_new, ch.W, ch.hb, ch.vb)
-    lp_new, E_new, obs_new = target(ch.model, v_new, ch.beta, ch.J)
+    F_new = ch.free(v_new)
+    lp_new, E_new, obs_new = ch.targ(v_new)
     log_r = (lp_new - ch.logpi) + (F_new - ch.F)
     scale = np.abs(lp_new) + np.abs(ch.logpi) + np.abs(F_new) + np.abs(ch.F) + 1.0
     u_acc = philox.uniforms(ch.seed, ch.chain_ids, ch.step, philox.TAG_ACC, 1)[:, 0]

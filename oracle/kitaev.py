@@ -20,9 +20,12 @@ from __future__ import annotations
 import numpy as np
 
 
-def hopping_matrix(v, J):
+def hopping_matrix(v, J, open_cols=False):
     """M(eta) per chain: (C, N, N) FP64 with M[b(r), w(r)] = 2 Jz eta_r,
-    M[b(r), w(r+e1)] = 2 Jx, M[b(r), w(r+e2)] = 2 Jy (entries add if bonds coincide)."""
+    M[b(r), w(r+e1)] = 2 Jx, M[b(r), w(r+e2)] = 2 Jy (entries add if bonds coincide).
+    open_cols: the lattice is open along j -- the y-bonds from column L-1 to
+    column 0 are absent (a cylinder, periodic along i; the reading of the
+    paper's open boundary conditions, Sec. IV)."""
     v = np.asarray(v)
     C, L, _ = v.shape
     N = L * L
@@ -34,13 +37,14 @@ def hopping_matrix(v, J):
             b = i * L + j
             M[:, b, b] += 2.0 * Jz * eta[:, i, j]
             M[:, b, ((i + 1) % L) * L + j] += 2.0 * Jx
-            M[:, b, i * L + (j + 1) % L] += 2.0 * Jy
+            if not (open_cols and j == L - 1):
+                M[:, b, i * L + (j + 1) % L] += 2.0 * Jy
     return M
 
 
-def energies(v, J):
+def energies(v, J, open_cols=False):
     """Single-fermion energies eps_l >= 0 (singular values of M, LAPACK), (C, N)."""
-    return np.linalg.svd(hopping_matrix(v, J), compute_uv=False)
+    return np.linalg.svd(hopping_matrix(v, J, open_cols), compute_uv=False)
 
 
 def log2cosh(x):
@@ -55,8 +59,8 @@ def log_weight_from_eps(eps, beta):
     return log2cosh(beta * eps / 2.0).sum(axis=1)
 
 
-def log_weight(v, beta, J):
-    return log_weight_from_eps(energies(v, J), beta)
+def log_weight(v, beta, J, open_cols=False):
+    return log_weight_from_eps(energies(v, J, open_cols), beta)
 
 
 def thermal_terms(eps, beta):
@@ -74,13 +78,18 @@ def thermal_terms(eps, beta):
     return e, cf
 
 
-def vison_density(v):
+def vison_density(v, open_cols=False):
     """Fraction of hexagons with flux -1: the hexagon of cell r carries the two
-    z-bonds r and r - e1 + e2, so its flux is eta_r * eta_{r-e1+e2}."""
+    z-bonds r and r - e1 + e2, so its flux is eta_r * eta_{r-e1+e2}.  With
+    open columns the hexagons of column L-1 (which would cross the cut) do not
+    exist: L (L-1) hexagons."""
     v = np.asarray(v).astype(np.int64)
     other = np.roll(np.roll(v, 1, axis=1), -1, axis=2)   # v[(i-1) % L, (j+1) % L]
     L = v.shape[1]
-    return (v != other).sum(axis=(1, 2)) / float(L * L)
+    diff = v != other
+    if open_cols:
+        return diff[:, :, :L - 1].sum(axis=(1, 2)) / float(L * (L - 1))
+    return diff.sum(axis=(1, 2)) / float(L * L)
 
 
 def bloch_energies(L: int, J, eta: float = 1.0):
@@ -92,9 +101,9 @@ def bloch_energies(L: int, J, eta: float = 1.0):
     return np.sort((2.0 * np.abs(Jz * eta + Jx * np.exp(1j * k1) + Jy * np.exp(1j * k2))).ravel())
 
 
-def majorana_spectrum(v, J):
+def majorana_spectrum(v, J, open_cols=False):
     """Eigenvalues of the 2N x 2N Hermitian iA (A_bw = -2 J u_bw, A_wb = -A_bw)."""
-    M = hopping_matrix(v, J)
+    M = hopping_matrix(v, J, open_cols)
     C, N, _ = M.shape
     A = np.zeros((C, 2 * N, 2 * N))
     A[:, :N, N:] = -M

@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import chain, crbm, kitaev, philox, tempering
+from . import chain, kitaev, philox, tempering
 
 TAG_LOCAL = 0xFFFFFFFB
 
@@ -73,7 +73,7 @@ def kitaev_sweep(ch: chain.Chains):
     for n in range(N):
         w = v.copy()
         w[:, n] ^= 1
-        lp_new = kitaev.log_weight(w.reshape(C, L, L), ch.beta, ch.J)
+        lp_new = kitaev.log_weight(w.reshape(C, L, L), ch.beta, ch.J, ch.open_cols)
         log_r = lp_new - lp
         log_u = np.log(u[:, n])
         acc = log_u < log_r
@@ -92,8 +92,8 @@ def sweep(ch: chain.Chains, exchange: bool = False):
         flips, margin = ising_sweep(ch)
     else:
         flips, margin = kitaev_sweep(ch)
-    ch.F = crbm.free_energy(ch.v, ch.W, ch.hb, ch.vb)
-    ch.logpi, ch.E_phys, ch.obs_terms = chain.target(ch.model, ch.v, ch.beta, ch.J)
+    ch.F = ch.free(ch.v)
+    ch.logpi, ch.E_phys, ch.obs_terms = ch.targ(ch.v)
     temp = np.zeros(len(ch.chain_ids), dtype=bool)
     temp_margin = np.full(len(ch.chain_ids), np.inf)
     if exchange:

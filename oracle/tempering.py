@@ -22,15 +22,15 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import chain, crbm, philox
+from . import chain, philox
 
 TAG_SWAP = 0xFFFFFFFD
 TAG_TEMP = 0xFFFFFFFC
 
 
-def _log_weight_at(model, v, beta, J):
-    """log pi_beta of lattices v (one beta per lattice)."""
-    return chain.target(model, v, beta, J)[0]
+def _log_weight_at(ch, v, beta):
+    """log pi_beta of lattices v (one beta per lattice) under ch's physics."""
+    return ch.targ(v, beta)[0]
 
 
 def exchange_temperatures(phys: chain.Chains, c: int):
@@ -45,8 +45,8 @@ def exchange_temperatures(phys: chain.Chains, c: int):
     temp_margin = np.full(n, np.inf)
     if len(i):
         beta = phys.beta
-        lp_ij = _log_weight_at(phys.model, phys.v[j], beta[i], phys.J)   # log pi_i(x_j)
-        lp_ji = _log_weight_at(phys.model, phys.v[i], beta[j], phys.J)   # log pi_j(x_i)
+        lp_ij = _log_weight_at(phys, phys.v[j], beta[i])   # log pi_i(x_j)
+        lp_ji = _log_weight_at(phys, phys.v[i], beta[j])   # log pi_j(x_i)
         log_b = lp_ij + lp_ji - phys.logpi[i] - phys.logpi[j]
         ub = philox.uniforms(phys.seed, phys.chain_ids[i], c, TAG_TEMP, 1)[:, 0]
         acc = np.log(ub) < log_b
@@ -61,7 +61,7 @@ def exchange_temperatures(phys: chain.Chains, c: int):
         # log pi, E and observables of the moved states at their new temperatures
         for idx in (ii, jj):
             if len(idx):
-                lp, E, ot = chain.target(phys.model, phys.v[idx], phys.beta[idx], phys.J)
+                lp, E, ot = phys.targ(phys.v[idx], phys.beta[idx])
                 phys.logpi[idx], phys.E_phys[idx], phys.obs_terms[idx] = lp, E, ot
     return temp, temp_margin
 
@@ -75,8 +75,8 @@ def cycle(phys: chain.Chains, rbm: chain.Chains, k: int):
     #    the exchange needs (no correction, no observables of their own)
     y, bmargin = chain.propose(rbm, k)
     rbm.v = y
-    rbm.F = crbm.free_energy(y, rbm.W, rbm.hb, rbm.vb)
-    rbm.logpi, rbm.E_phys, rbm.obs_terms = chain.target(rbm.model, y, rbm.beta, rbm.J)
+    rbm.F = rbm.free(y)
+    rbm.logpi, rbm.E_phys, rbm.obs_terms = rbm.targ(y)
     rbm.step += 1
     # 2. physical <-> RBM exchange at every temperature
     log_a = (rbm.logpi - phys.logpi) + (rbm.F - phys.F)

@@ -8,8 +8,6 @@ enumerated exactly).  Two planted mistakes -- the swap without its F term, and
 temperature exchanges accepted unconditionally -- each fail the same test by
 thousands of chi^2 units.
 """
-from types import SimpleNamespace
-
 import numpy as np
 import pytest
 
@@ -63,22 +61,13 @@ def test_pt_cycles_keep_every_temperature_exact(k):
 
 def test_planted_swap_without_F_term_fails(monkeypatch):
     # the F(y) - F(x) term replaced by zero: log a = log pi(y) - log pi(x)
-    monkeypatch.setattr(tempering, "crbm", SimpleNamespace(free_energy=lambda v, *a: np.zeros(len(v))))
-    monkeypatch.setattr(chain, "make_chains", _zero_F(chain.make_chains))
+    monkeypatch.setattr(chain.Chains, "free", lambda self, v: np.zeros(len(v)))
     res, _, _ = _pt_chi2(1)
     assert sum(chi2 for chi2, _, _ in res) > 1000
 
 
-def _zero_F(make):
-    def wrapped(*a, **kw):
-        ch = make(*a, **kw)
-        ch.F = np.zeros_like(ch.F)
-        return ch
-    return wrapped
-
-
 def test_planted_unconditional_temperature_exchange_fails(monkeypatch):
-    monkeypatch.setattr(tempering, "_log_weight_at", lambda m, v, b, J: np.full(len(v), 1e300))
+    monkeypatch.setattr(tempering, "_log_weight_at", lambda ch, v, b: np.full(len(v), 1e300))
     res, _, _ = _pt_chi2(1)
     assert sum(chi2 for chi2, _, _ in res) > 1000
 
