@@ -96,6 +96,25 @@ CRBM_API const char* crbm_last_error(const crbm_ctx* ctx);
 CRBM_API int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W,
                     double v_bias, const double* h_bias, int* model_id);
 
+/* Load a locally connected CRBM (LCRBM) for the Kitaev model with open
+ * boundaries (Sec. IV, open boundary conditions).  Reading: the lattice is
+ * open along the column direction j (the y-bonds from column L-1 to column 0
+ * are absent; rows stay periodic) and so are the LCRBM's windows (a column
+ * past L-1 contributes nothing); the hidden units of the `edge` left columns
+ * and of the `edge` right columns each have their own K kernels, all other
+ * columns share the bulk kernels (the paper uses edge = 3).  W holds
+ * (2 edge + 1) x K x k x k FP64 values, class-major: classes 0..edge-1 are the
+ * left columns j = 0..edge-1, classes edge..2 edge-1 the right columns
+ * j = L-edge..L-1, class 2 edge the bulk; then W[c][f][a][b] couples hidden
+ * unit (f, i, j) of class c to visible unit ((i+a) mod L, j+b).  Hidden biases
+ * (K) and the visible bias are shared.  Jobs of this model simulate the
+ * open-boundary Kitaev model (vison density over the L (L-1) hexagons that do
+ * not cross the cut) and run in CRBM_FP64 only.
+ * Errors: CRBM_EINVAL (kind not Kitaev, edge outside [1, 6],
+ * (2 edge + 1) K k 2^k > 4096), CRBM_ECUDA. */
+CRBM_API int crbm_load_lcrbm(crbm_ctx* ctx, int kind, int K, int k, int edge, const double* W, double v_bias,
+                             const double* h_bias, int* model_id);
+
 /* Replace the parameters of model `model_id` (same K, k; same layout as
  * crbm_load_model), for instance after a training epoch.  Waits until the
  * device is idle, then rewrites the model's tables; its jobs use the new
@@ -120,6 +139,7 @@ CRBM_API size_t crbm_job_bytes(int kind, int L, int n_chains, int precision);
  *   dev_mem       caller-owned device buffer of dev_bytes >= crbm_job_bytes().
  * Evaluates F, log pi and the observables of the initial lattices in FP64 and
  * resets the sums.  The call returns after the work is complete.
+ * With an LCRBM model L must be at least 2 edge.
  * Errors: CRBM_EINVAL, CRBM_ENOMEM (dev_bytes too small or budget exceeded),
  * CRBM_ECUDA. */
 CRBM_API int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const double* T,

@@ -44,6 +44,8 @@ _SIGS = {
     "crbm_last_error": (C.c_char_p, [C.c_void_p]),
     "crbm_load_model": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double,
                                   C.c_void_p, C.POINTER(C.c_int)]),
+    "crbm_load_lcrbm": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                                  C.c_void_p, C.POINTER(C.c_int)]),
     "crbm_job_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
     "crbm_init_chains": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -128,6 +130,17 @@ def crbm_load_model(ctx, kind, W, v_bias, h_bias) -> int:
     K, k, _ = W.shape
     mid = C.c_int()
     _check(ctx, load().crbm_load_model(ctx, kind, K, k, _ptr(W), float(v_bias), _ptr(hb), C.byref(mid)))
+    return mid.value
+
+
+def crbm_load_lcrbm(ctx, kind, W, v_bias, h_bias) -> int:
+    """W: (2 edge + 1, K, k, k) class kernels (left edge, right edge, bulk)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    hb = np.ascontiguousarray(h_bias, dtype=np.float64)
+    ncls, K, k, _ = W.shape
+    mid = C.c_int()
+    _check(ctx, load().crbm_load_lcrbm(ctx, kind, K, k, (ncls - 1) // 2, _ptr(W), float(v_bias), _ptr(hb),
+                                       C.byref(mid)))
     return mid.value
 
 
@@ -335,6 +348,10 @@ class Context:
 
     def load_model(self, kind, W, v_bias, h_bias) -> int:
         return crbm_load_model(self.h, kind, W, v_bias, h_bias)
+
+    def load_lcrbm(self, kind, W, v_bias, h_bias) -> int:
+        """Locally connected CRBM for the open-boundary Kitaev model; W (2 edge + 1, K, k, k)."""
+        return crbm_load_lcrbm(self.h, kind, W, v_bias, h_bias)
 
     def new_job(self, model_id, kind, L, T, J, seed, chain_id_base=0, init_bits=None, precision=FP64,
                 mem=None) -> Job:

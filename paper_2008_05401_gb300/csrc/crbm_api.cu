@@ -1,6 +1,7 @@
 // C ABI of the CRBM-aided Monte Carlo library (declarations and contracts in
 // include/crbm.h).  Host side: contexts, models (row-sum tables of the CRBM
 // filters), jobs laid out in caller-owned device memory, and kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -21,6 +22,7 @@ namespace {
 struct Model {
   bool live = false;
   int kind = 0, K = 0, k = 0;
+  int edge = 0, ncls = 1;    // LCRBM: edge unshared kernels per side, 2 edge + 1 classes (FP64 tables only)
   double vb = 0.0;
   std::vector<double> hb;
   double* d_f64 = nullptr;   // forward FP64 row-sum table, then the backward one
@@ -160,6 +162,9 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.n_chains = j.n;
   d.nc = j.nc;
   d.vb = m.vb;
+  d.lc_edge = m.edge;
+  d.ncls = m.ncls;
+  d.nhex = m.edge ? j.L * (j.L - 1) : j.N;
   for (int f = 0; f < m.K; ++f) {
     d.hb[f] = m.hb[f];
     d.hb32[f] = m.hb32[f];
@@ -174,13 +179,17 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.csp = m.csp;
   d.f64 = m.d_f64;
   d.b64 = m.d_f64 + m.nlut;
-  d.fd = m.d_f32;
-  d.bd = m.d_f32 + m.nlut;
-  d.fh = m.d_f32 + 2 * m.nlut;
-  d.fl = m.d_f32 + 3 * m.nlut;
-  d.fd4 = m.d_q;
-  d.fh4 = m.d_q + m.nq;
-  d.fl4 = m.d_q + 2 * m.nq;
+  if (m.d_f32) {                 // an LCRBM has FP64 tables only
+    d.fd = m.d_f32;
+    d.bd = m.d_f32 + m.nlut;
+    d.fh = m.d_f32 + 2 * m.nlut;
+    d.fl = m.d_f32 + 3 * m.nlut;
+  }
+  if (m.d_q) {
+    d.fd4 = m.d_q;
+    d.fh4 = m.d_q + m.nq;
+    d.fl4 = m.d_q + 2 * m.nq;
+  }
   d.seed = j.seed;
   for (int r = 0; r < 10; ++r) {
     d.rk[2 * r] = (uint32_t)j.seed + (uint32_t)r * 0x9E3779B9u;
@@ -224,6 +233,7 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
   p.err = ctx->d_err;
   size_t smem = 0;
   int tiles = 0, kind = -1, K = 0, k = 0;
+  bool generic = false;
   for (size_t i = 0; i < ids.size(); ++i) {
     const Job& j = ctx->jobs[ids[i]];
     const Model& m = ctx->models[j.model];
@@ -231,16 +241,30 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
     p.tile_begin[i] = tiles;
     p.job[i] = make_jobdev(ctx, j);
     tiles += j.tiles;
+    if (m.edge && prec != kFP64) return fail(ctx, CRBM_EINVAL, "LCRBM models run in CRBM_FP64 only");
     int KC, kC;
     specialisation(m.K, m.k, KC, kC);
-    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, KC);
+    if (m.edge) {
+      KC = kC = 0;                // the class tables are read by the runtime-shape code
+      generic = true;
+    }
+    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, KC, m.ncls);
     if (b > smem) smem = b;
     K = m.K;
     k = m.k;
   }
   p.tile_begin[ids.size()] = tiles;
   if (tiles == 0) return CRBM_OK;
-  CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st), "kernel launch");
+  if (generic) {
+    // every job of the launch runs the runtime-shape variant: size its shared memory so
+    smem = 0;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      const Job& j = ctx->jobs[ids[i]];
+      const Model& m = ctx->models[j.model];
+      smem = std::max(smem, smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, 0, m.ncls));
+    }
+  }
+  CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st, generic), "kernel launch");
   return CRBM_OK;
 }
 
@@ -434,11 +458,65 @@ int crbm_load_model(crbm_ctx* ctx, int kind, int K, int k, const double* W, doub
   return CRBM_OK;
 }
 
+int crbm_load_lcrbm(crbm_ctx* ctx, int kind, int K, int k, int edge, const double* W, double v_bias,
+                    const double* h_bias, int* model_id) {
+  if (!ctx) return CRBM_EINVAL;
+  if (kind != kKitaev) return fail(ctx, CRBM_EINVAL, "the LCRBM serves the open-boundary Kitaev model only");
+  if (K < 1 || K > kMaxK) return fail(ctx, CRBM_EINVAL, "K=%d outside [1,%d]", K, kMaxK);
+  if (k < 1 || k > kMaxk) return fail(ctx, CRBM_EINVAL, "k=%d outside [1,%d]", k, kMaxk);
+  if (edge < 1 || edge > 6) return fail(ctx, CRBM_EINVAL, "edge=%d outside [1,6]", edge);
+  if (!W || !h_bias || !model_id) return fail(ctx, CRBM_EINVAL, "null pointer");
+  const int ncls = 2 * edge + 1, T = 1 << k;
+  const size_t per = (size_t)K * k * T, nlut = (size_t)ncls * per;
+  if (nlut > 4096)
+    return fail(ctx, CRBM_EINVAL, "(2 edge + 1) K k 2^k = %zu exceeds 4096 table entries", nlut);
+  for (int i = 0; i < ncls * K * k * k; ++i)
+    if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // per class c the tables of the periodic CRBM: fwd[((c K + f) k + a) 2^k + code]
+  // sums W[c][f][a][b] over the set bits b of code in increasing b; bwd is
+  // indexed by the raw (reversed) window
+  std::vector<double> fwd(nlut), bwd(nlut);
+  for (int c = 0; c < ncls; ++c)
+    for (int f = 0; f < K; ++f)
+      for (int a = 0; a < k; ++a)
+        for (int code = 0; code < T; ++code) {
+          double acc = 0.0;
+          for (int b = 0; b < k; ++b)
+            if ((code >> b) & 1) acc += W[(((size_t)c * K + f) * k + a) * k + b];
+          fwd[(((size_t)c * K + f) * k + a) * T + code] = acc;
+        }
+  for (size_t e = 0; e < nlut; ++e) {
+    const int w = (int)(e % T);
+    int rev = 0;
+    for (int b = 0; b < k; ++b)
+      if ((w >> b) & 1) rev |= 1 << (k - 1 - b);
+    bwd[e] = fwd[e - w + rev];
+  }
+  Model m;
+  m.kind = kind;
+  m.K = K;
+  m.k = k;
+  m.edge = edge;
+  m.ncls = ncls;
+  m.vb = v_bias;
+  m.hb.assign(h_bias, h_bias + K);
+  m.nlut = nlut;
+  CK(cudaMalloc(&m.d_f64, 2 * nlut * sizeof(double)), "cudaMalloc tables");
+  CK(cudaMemcpy(m.d_f64, fwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
+  CK(cudaMemcpy(m.d_f64 + nlut, bwd.data(), nlut * sizeof(double), cudaMemcpyHostToDevice), "table copy");
+  m.live = true;
+  ctx->models.push_back(m);
+  *model_id = (int)ctx->models.size() - 1;
+  return CRBM_OK;
+}
+
 int crbm_update_model(crbm_ctx* ctx, int model_id, const double* W, double v_bias, const double* h_bias) {
   if (!ctx) return CRBM_EINVAL;
   if (model_id < 0 || model_id >= (int)ctx->models.size() || !ctx->models[model_id].live)
     return fail(ctx, CRBM_EINVAL, "bad model id %d", model_id);
   Model& m = ctx->models[model_id];
+  if (m.edge) return fail(ctx, CRBM_EINVAL, "model %d is an LCRBM: load a new one instead", model_id);
   if (!W || !h_bias) return fail(ctx, CRBM_EINVAL, "null pointer");
   for (int i = 0; i < m.K * m.k * m.k; ++i)
     if (!std::isfinite(W[i])) return fail(ctx, CRBM_EINVAL, "non-finite weight");
@@ -475,6 +553,8 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   const Model& m = ctx->models[model_id];
   if (!valid_L(m.kind, L)) return fail(ctx, CRBM_EINVAL, "lattice side L=%d not supported", L);
   if (m.k > L) return fail(ctx, CRBM_EINVAL, "kernel side k=%d exceeds L=%d", m.k, L);
+  if (m.edge && L < 2 * m.edge)
+    return fail(ctx, CRBM_EINVAL, "L=%d has fewer than the 2 x %d edge columns of the LCRBM", L, m.edge);
   if (n_chains < 0) return fail(ctx, CRBM_EINVAL, "n_chains < 0");
   if (chain_id_base + (uint64_t)n_chains > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "chain ids must stay below 2^32");
   if (n_chains > 0 && (!T || !J)) return fail(ctx, CRBM_EINVAL, "null T or J");
@@ -847,6 +927,7 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
   if (model_id < 0 || model_id >= (int)ctx->models.size() || !ctx->models[model_id].live)
     return fail(ctx, CRBM_EINVAL, "bad model id %d", model_id);
   const Model& m = ctx->models[model_id];
+  if (m.edge) return fail(ctx, CRBM_EINVAL, "model %d is an LCRBM: nothing to tune", model_id);
   if (!valid_L(m.kind, L) || m.k > L) return fail(ctx, CRBM_EINVAL, "lattice side L=%d not supported", L);
   if (precision != CRBM_FP64 && precision != CRBM_MIXED) return fail(ctx, CRBM_EINVAL, "bad precision");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");

@@ -48,7 +48,9 @@ enum DevErr : int { kErrNone = 0, kErrConfig = 1, kErrTimeout = 2 };
 // parameters.  Pointers into the job's caller-owned device memory.
 struct JobDev {
   int kind, L, N, Wd, P, K, k, n_chains, nc;
-  int pad0;
+  int lc_edge;                  // > 0: LCRBM with lc_edge unshared kernels per side; lattice open along j
+  int ncls;                     // kernel classes in the tables: 2 lc_edge + 1, or 1
+  int nhex;                     // Kitaev hexagons: N, or L (L-1) with open columns
   double vb;
   double hb[kMaxK];
   double J[3];
@@ -377,6 +379,54 @@ static __device__ __noinline__ uint32_t recompute_visible(const JobDev& jb, cons
   return decide64(x, w);
 }
 
+// ------------------------------------------------- LCRBM (open columns)
+// Column class of hidden column j: left edge columns 0..e-1, right edge
+// columns e..2e-1, bulk 2e (Sec. IV, open boundary conditions).
+__device__ __forceinline__ int lc_class(int j, int L, int e) {
+  return j < e ? j : (j >= L - e ? e + (j - (L - e)) : 2 * e);
+}
+
+// FP64 pre-activation of filter f of an LCRBM at site n from the forward
+// codes m (computed with wrap): the window is cut at the open column edge
+// (bits b >= L - j dropped) and the table of the column's class is used.
+template <int kU>
+__device__ __forceinline__ double lc_preact64(const JobDev& jb, const double* f64, int f, const uint32_t (&m)[kU],
+                                              int n, int k, int T) {
+  const int L = jb.L, j = n % L;
+  const int base = (lc_class(j, L, jb.lc_edge) * jb.K + f) * k * T;
+  const uint32_t keep = (j + k > L) ? ((1u << (L - j)) - 1u) : 0xFFFFFFFFu;
+  double x = jb.hb[f];
+#pragma unroll
+  for (int a = 0; a < kU; ++a) {
+    if (a < k) {
+      const uint32_t code = (m[a] - (uint32_t)(a * T)) & keep;
+      x += f64[base + a * T + (int)code];
+    }
+  }
+  return x;
+}
+
+// FP64 visible pre-activation of an LCRBM at site n: v_bias plus, for every
+// hidden unit (f, i-a, j-b) with j - b >= 0, its class kernel's weight
+// W[c(j-b)][f][a][b] (the table entry of the single-bit code 1 << b) if set.
+__device__ inline double lc_visible64(const JobDev& jb, const double* f64, const uint32_t* h, int P, int n,
+                                      int k, int T) {
+  const int L = jb.L, i = n / L, j = n - i * L;
+  double x = jb.vb;
+  for (int a = 0; a < k; ++a) {
+    const int r = (i - a < 0) ? i - a + L : i - a;
+    for (int f = 0; f < jb.K; ++f) {
+      const uint32_t* pl = h + f * P;
+      for (int b = 0; b < k && b <= j; ++b) {
+        const int jc = j - b;
+        if (site_bit(pl, r * L + jc))
+          x += f64[((lc_class(jc, L, jb.lc_edge) * jb.K + f) * k + a) * T + (1 << b)];
+      }
+    }
+  }
+  return x;
+}
+
 // ------------------------------------------------- hidden half-step
 // h^f_ij = [u < sigma(h_bias^f + sum_ab W^f_ab v_(i+a)(j+b))]  (Eq. B2, Eq. 12)
 // FP64 order (shared with the mixed path's recompute): h_bias, then kernel
@@ -441,8 +491,12 @@ __device__ void hidden_phase(const JobDev& jb, const Tabs& tb, const Grp& g, con
         uint32_t bit;
         if (PREC == kFP64) {
           double x = jb.hb[f];
+          if (KC == 0 && jb.lc_edge) {
+            x = lc_preact64<kU>(jb, tb.f64, f, m[t], (act && 4 * q + t < N) ? 4 * q + t : 0, k, T);
+          } else {
 #pragma unroll
-          for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
+            for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
+          }
           bit = decide64(x, pick(w, t));
         } else {
           float x = jb.hb32[f];
@@ -556,6 +610,13 @@ __device__ void visible_phase(const JobDev& jb, const Tabs& tb, const Grp& g, co
         }
       }
     }
+    if (PREC == kFP64 && KC == 0 && jb.lc_edge) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int n = 4 * qq + t;
+        x64[t] = lc_visible64(jb, tb.f64, h, P, n < N ? n : 0, k, T);
+      }
+    }
     const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)q, (uint32_t)(sub * (K + 1) + K), step, g.cid), jb.rk);
     uint32_t nib = 0;
 #pragma unroll
@@ -639,8 +700,12 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
           for (int t = 0; t < 4; ++t) {
             if (4 * q + t < N) {
               double x = jb.hb[f];
+              if (KC == 0 && jb.lc_edge) {
+                x = lc_preact64<kU>(jb, tb.f64, f, m[t], 4 * q + t, k, T);
+              } else {
 #pragma unroll
-              for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
+                for (int a = 0; a < kU; ++a) if (kC || a < k) x += tb.f64[base + m[t][a]];
+              }
               s64 += softplus64(x);
             }
           }
@@ -685,9 +750,10 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
                                          : site_bit(v, (i + 1 == L ? 0 : i + 1) * L + j);
           pairs += (int)(b0 ^ right) + (int)(b0 ^ down);
         } else {
-          // the hexagon of cell r holds the z-bonds r and r - e1 + e2
+          // the hexagon of cell r holds the z-bonds r and r - e1 + e2 (with
+          // open columns the hexagons of column L-1 do not exist)
           const int i2 = (i == 0) ? L - 1 : i - 1, j2 = (j + 1 == L) ? 0 : j + 1;
-          pairs += (int)(b0 ^ site_bit(v, i2 * L + j2));
+          if (!(jb.lc_edge && j + 1 == L)) pairs += (int)(b0 ^ site_bit(v, i2 * L + j2));
         }
       }
     }
@@ -883,8 +949,11 @@ __device__ __forceinline__ void thermal_add(double eps, double beta, double& lp,
 }
 
 // eps_out (optional, device memory): the N energies eps, ascending.
+// open_cols: the lattice is open along j (the y-bonds from column L-1 to
+// column 0 are absent), the physics of the LCRBM's open boundary conditions.
 __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
-                               const KitaevWork& wk, double (&res)[3], double* eps_out = nullptr) {
+                               const KitaevWork& wk, double (&res)[3], double* eps_out = nullptr,
+                               bool open_cols = false) {
   const int N = L * L, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double* A = wk.A;
@@ -899,6 +968,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       int bi = i, bj = j;
       if (typ == 1) bi = (i == 0) ? L - 1 : i - 1;
       if (typ == 2) bj = (j == 0) ? L - 1 : j - 1;
+      if (typ == 2 && open_cols && j == 0) continue;      // this y-bond crosses the open cut
       const int b = bi * L + bj;
       const double mz = site_bit(v, b) ? tz : -tz;
       const double mw = (typ == 0) ? mz : (typ == 1 ? tx : ty);
@@ -907,7 +977,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       const int wy = bi * L + ((bj + 1 == L) ? 0 : bj + 1);
       if (wz <= w) row[wz] += mw * mz;
       if (wx <= w) row[wx] += mw * tx;
-      if (wy <= w) row[wy] += mw * ty;
+      if (wy <= w && !(open_cols && bj + 1 == L)) row[wy] += mw * ty;
     }
   }
   __syncthreads();

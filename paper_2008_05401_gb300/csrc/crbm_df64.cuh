@@ -70,7 +70,7 @@ __device__ __forceinline__ df df_from_float(float x) { return {x, 0.0f}; }
 // eigenvalue mu = eps^2 by at most dmu, and (ii) the slope of
 // log 2cosh(beta sqrt(mu)/2) in mu, at most min(beta^2/8, beta/(4 sqrt(mu))).
 __device__ inline void kitaev_logpi_df(const uint32_t* v, int L, const double* J, double beta,
-                                       const KitaevWork& wk, double (&res)[4]) {
+                                       const KitaevWork& wk, double (&res)[4], bool open_cols = false) {
   const int N = L * L, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   df* A = reinterpret_cast<df*>(wk.A);        // same footprint as the FP64 matrix
@@ -92,6 +92,7 @@ __device__ inline void kitaev_logpi_df(const uint32_t* v, int L, const double* J
       int bi = i, bj = j;
       if (typ == 1) bi = (i == 0) ? L - 1 : i - 1;
       if (typ == 2) bj = (j == 0) ? L - 1 : j - 1;
+      if (typ == 2 && open_cols && j == 0) continue;      // this y-bond crosses the open cut
       const int b = bi * L + bj;
       const df mz = site_bit(v, b) ? tz : df_neg(tz);
       const df mw = (typ == 0) ? mz : (typ == 1 ? tx : ty);
@@ -100,7 +101,7 @@ __device__ inline void kitaev_logpi_df(const uint32_t* v, int L, const double* J
       const int wy = bi * L + ((bj + 1 == L) ? 0 : bj + 1);
       if (wz <= w) row[wz] = df_add(row[wz], df_mul(mw, mz));
       if (wx <= w) row[wx] = df_add(row[wx], df_mul(mw, tx));
-      if (wy <= w) row[wy] = df_add(row[wy], df_mul(mw, ty));
+      if (wy <= w && !(open_cols && bj + 1 == L)) row[wy] = df_add(row[wy], df_mul(mw, ty));
     }
     for (int c = 0; c <= w; ++c) fro = fmaf((c == w ? 1.0f : 2.0f) * row[c].hi, row[c].hi, fro);
   }

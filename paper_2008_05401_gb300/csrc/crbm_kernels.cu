@@ -4,8 +4,8 @@
 
 namespace crbm {
 
-size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC) {
-  const size_t N = (size_t)L * L, P = (N + 31) / 32 + 1, nlut = (size_t)K * k * ((size_t)1 << k);
+size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int ncls) {
+  const size_t N = (size_t)L * L, P = (N + 31) / 32 + 1, nlut = (size_t)ncls * K * k * ((size_t)1 << k);
   const size_t nq = (size_t)k << k;
   size_t b = (prec == kFP64) ? 2 * align16(nlut * 8)
              : (KC == 4 ? 3 * align16(nq * 16 * 8) + align16(nlut * 4) : 4 * align16(nlut * 4));
@@ -58,9 +58,10 @@ void specialisation(int K, int k, int& KC, int& kC) {
 int threads_for(int kind, int max_N) { return (kind == kKitaev && max_N <= 64) ? 128 : 256; }
 
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool generic) {
   int KC, kC;
   specialisation(K, k, KC, kC);
+  if (generic) KC = kC = 0;
   if (kind == kIsing)
     return prec == kFP64 ? launch_kIsing_kFP64(KC, kC, nt, p, grid, smem, st)
                          : launch_kIsing_kMixed(KC, kC, nt, p, grid, smem, st);

@@ -11,15 +11,17 @@ struct JobDev;
 // Compiled specialisation (KC, kC) serving a filter bank of K filters k x k
 // (0 = runtime values).
 void specialisation(int K, int k, int& KC, int& kC);
-// Dynamic shared memory of one CTA of the fused kernel.
-size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC);
+// Dynamic shared memory of one CTA of the fused kernel (ncls kernel classes
+// in the tables: 1 for a CRBM, 2 edge + 1 for an LCRBM).
+size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int ncls = 1);
 // Threads per CTA for a launch whose largest lattice has max_N sites: 128 for
 // Kitaev matrices up to 64 x 64 (fewer idle warps at the eigen-stage barriers),
 // else 256 (measured).
 int threads_for(int kind, int max_N);
-// Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch).
+// Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch);
+// generic: use the runtime-shape variant even where a specialisation exists (LCRBM jobs).
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
-                        cudaStream_t st);
+                        cudaStream_t st, bool generic = false);
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Random initial lattices (init tag of the stream).

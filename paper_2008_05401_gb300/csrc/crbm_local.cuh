@@ -28,9 +28,10 @@ __device__ inline void lattice_counts(const JobDev& jb, const Grp& g, const uint
         pairs += (int)(b0 ^ site_bit(v, i * L + (j + 1 == L ? 0 : j + 1)));
         pairs += (int)(b0 ^ site_bit(v, (i + 1 == L ? 0 : i + 1) * L + j));
       } else {
-        // the hexagon of cell r holds the z-bonds r and r - e1 + e2
+        // the hexagon of cell r holds the z-bonds r and r - e1 + e2 (none in
+        // column L-1 when the columns are open)
         const int i2 = (i == 0) ? L - 1 : i - 1, j2 = (j + 1 == L) ? 0 : j + 1;
-        pairs += (int)(b0 ^ site_bit(v, i2 * L + j2));
+        if (!(jb.lc_edge && j + 1 == L)) pairs += (int)(b0 ^ site_bit(v, i2 * L + j2));
       }
     }
   }

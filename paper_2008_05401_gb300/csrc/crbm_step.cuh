@@ -57,7 +57,7 @@ __device__ inline void store_evaluation(const JobDev& jb, int c, double beta, co
   } else {
     lp = kr[0];
     E = kr[1];
-    ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)N;
+    ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)jb.nhex;
   }
   jb.F[c] = Fv;
   jb.Fb[c] = 0.0;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
   const JobDev& jb = prm.job[jid];
   const int ltile = (int)blockIdx.x - prm.tile_begin[jid];
   const int tid = threadIdx.x;
-  const int N = jb.N, P = jb.P, K = jb.K, T = 1 << jb.k, nlut = K * jb.k * T;
+  const int N = jb.N, P = jb.P, K = jb.K, T = 1 << jb.k, nlut = jb.ncls * K * jb.k * T;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sp = smem_raw;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
       kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
-                     g.active ? jb.eps + (size_t)g.c * N : nullptr);
+                     g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     if (g.active && g.r == 0) store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
     return;
   }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
       kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
-                     g.active ? jb.eps + (size_t)g.c * N : nullptr);
+                     g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     if (nrec) atomicAdd(&ch.rec, (unsigned long long)nrec);
     __syncthreads();
     if (g.active) {
@@ -288,10 +288,10 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
           __syncthreads();
           double kr[4] = {0.0, 0.0, 0.0, 0.0};
           if (PREC == kMixed) {
-            kitaev_logpi_df(vp, jb.L, jb.J, ch.beta, wk, kr);
+            kitaev_logpi_df(vp, jb.L, jb.J, ch.beta, wk, kr, jb.lc_edge > 0);
           } else {
             double k3[3];
-            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k3, eps_st);
+            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k3, eps_st, jb.lc_edge > 0);
             kr[0] = k3[0];
             kr[1] = k3[1];
             kr[2] = k3[2];
@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
             // when its log-weight came from the df64 stage)
             double k1v[3], k0v[3] = {0.0, 0.0, 0.0};
             const bool redo_v = ch.lpb != 0.0;
-            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st);
-            if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v);
+            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st, jb.lc_edge > 0);
+            if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
             if (tid == 0) {
               ch.lpp = k1v[0];
               ch.lppb = 0.0;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
           ch.lp = -ch.beta * E;
           ch.ot[0] = E; ch.ot[1] = E * E; ch.ot[2] = fabs(M); ch.ot[3] = M * M;
         } else {
-          ch.ot[3] = cn[1] / (double)N;
+          ch.ot[3] = cn[1] / (double)jb.nhex;
         }
         if (prm.correct) {
           for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
@@ -429,10 +429,10 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
     double kr[4] = {0.0, 0.0, 0.0, 0.0};
     if (KIND == kKitaev) {
       if (PREC == kMixed) {
-        kitaev_logpi_df(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr);
+        kitaev_logpi_df(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr, jb.lc_edge > 0);
       } else {
         double k3[3];
-        kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3);
+        kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3, nullptr, jb.lc_edge > 0);
         kr[0] = k3[0];
         kr[1] = k3[1];
         kr[2] = k3[2];
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
       } else {
         ch.Ep = kr[1];
         ch.lpp = kr[0];
-        ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2]; ch.otp[3] = fo[3] / (double)N;
+        ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2]; ch.otp[3] = fo[3] / (double)jb.nhex;
       }
       ch.lppb = kr[3];
       ch.Fp = -jb.vb * fo[2] - fo[0];
@@ -498,8 +498,8 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN
         double k1v[3] = {0.0, 0.0, 0.0}, k0v[3] = {0.0, 0.0, 0.0};
         const bool redo_v = ch.lpb != 0.0;
         if (KIND == kKitaev) {
-          kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v);
-          if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v);
+          kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, nullptr, jb.lc_edge > 0);
+          if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
         }
         if (g2.active && g.r == 0) {
           ch.Fp = -jb.vb * f1[2] - f1[0];
