@@ -126,7 +126,14 @@ def peaks():
         return {}
 
 
-def roofline(wd, kernel_ms, clocks, K, k, n_sites_step):
+# DRAM bytes (read + write) of one launch of the batch Ising workload's fused
+# kernel, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# one pass) of the current kernel; the lattices stay in shared memory for the
+# whole launch, so this is the lattice and table traffic only.
+BATCH_ISING_TRAFFIC_BYTES = 14.51e6 + 28.42e3
+
+
+def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
     """ALU roofline of the fused kernel: algorithmic FP32 flops = the three
     periodic convolutions of a proposal written directly (hidden, visible and
     free-energy pre-activations: 3 x K k^2 multiply-adds per site), against the
@@ -137,7 +144,7 @@ def roofline(wd, kernel_ms, clocks, K, k, n_sites_step):
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"FP32 FMA from unit counts x sampled SM clock {mhz:.0f} MHz"}
 
 
@@ -391,6 +398,46 @@ def train_run(ctx_cls, dev, stream, n_problems=24, L=8, K=2, k=5, n=10_000, batc
     return out
 
 
+def lcrbm_run(ctx_cls, dev, stream, L=8, n=1024, S=2, edge=3, K=2, k=5, oracle_s=2.0):
+    """Open-boundary Kitaev model with the locally connected CRBM (Sec. IV):
+    the paper's three unshared edge kernels per side and 2x5x5 kernels, the
+    small Kitaev workload's temperature ladder, FP64 (the LCRBM's only
+    precision).  value = proposals/s."""
+    import torch
+    from paper_2008_05401_gb300 import FP64, KITAEV
+    g = wl.rng(SEED + 4)
+    W = g.normal(0.0, 0.05, (2 * edge + 1, K, k, k))
+    hb, vb = g.normal(0.0, 0.05, K), float(g.normal(0.0, 0.05))
+    T = wl.kitaev_ladder(n, 24)
+    bits = wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L))
+    ctx = ctx_cls(dev)
+    mid = ctx.load_lcrbm(KITAEV, W, vb, hb)
+    job = ctx.new_job(mid, KITAEV, L, T, (1.0, 1.0, 1.0), SEED, 0, bits, FP64)
+    job.run(1, precision=FP64, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    job.run(S, precision=FP64, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    _, acc, _ = job.observables()
+    ctx.close()
+    out = {"workload": f"open-boundary Kitaev L={L} with an LCRBM ({edge} edge kernels per side, K={K} "
+                       f"{k}x{k}), {n} chains, 24 T log-spaced in [0.005,1]",
+           "precision": "fp64", "value": n * S / (ms * 1e-3), "unit": "proposals/s", "ms_per_step": ms,
+           "acceptance": float(acc.sum()) / (n * (S + 1))}
+    if oracle_s > 0:
+        from oracle import chain
+        nc = 16
+        och = chain.make_chains(chain.KITAEV, W, hb, vb, L, T[:nc], (1.0, 1.0, 1.0), SEED, np.arange(nc),
+                                edge=edge)
+        rate, c, dt = _oracle_rate(lambda: chain.step(och), oracle_s)
+        out["cpu_baseline"] = {"value": rate * nc, "unit": "proposals/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{nc} chains x {c} proposals in {dt:.1f}s"}
+    return out
+
+
 def serving_run(dev, n=60, rate=200.0):
     """Continuous batching of a Poisson request stream (mixed Ising / Kitaev
     jobs, 1-64 chains, 1e2-2e3 proposals each, mixed precision): p50/p99 latency
@@ -517,7 +564,9 @@ def main():
             "config": {"workload": spec["desc"], "proposals_per_step": S, "chains": n_chains,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"chains x{world}"},
-            "roofline": roofline(spec, total_ms / args.steps, clocks, K, k, sites),
+            "roofline": roofline(spec, total_ms / args.steps, clocks, K, k, sites,
+                                 traffic=(BATCH_ISING_TRAFFIC_BYTES if args.workload == "ising-batch" and
+                                          not args.chains and not args.Ls else None)),
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
     sums = [j.observables() for j in jobs]
     line["config"]["acceptance"] = sum(int(a.sum()) for _, a, _ in sums) / max(1, n_chains * jobs[0].step)
@@ -544,6 +593,7 @@ def main():
         line["serving"] = serving_run(dev)
         ob = 0.0 if args.no_cpu_baseline else 2.0
         line["train"] = train_run(Context, dev, stream, oracle_s=ob)
+        line["lcrbm"] = lcrbm_run(Context, dev, stream, oracle_s=ob)
         line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream, oracle_s=ob),
                        tau_run(Context, 64, 512, 2.269, 2000, dev, stream, oracle_s=ob)]
     if rank == 0 and not args.no_cpu_baseline:
