@@ -927,7 +927,15 @@ __device__ __forceinline__ double eigen_idx(const KitaevWork& wk, int N, int idx
     }
     const SturmNewton r = sturm_newton(wk.d, wk.vv, N, x);
     if (r.cnt > idx) hi = x; else lo = x;
-    double xn = x - r.p / r.dp;
+    const double step = r.p / r.dp;
+    double xn = x - step;
+    // a Newton step below the tolerance that stays in the bracket has found
+    // the root: stop before the bracket test below can turn it into bisection
+    // (x may sit on the root itself, which then is one end of the bracket)
+    if (fabs(step) <= tol && xn >= lo && xn <= hi) {
+      x = xn;
+      break;
+    }
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
     if (fabs(xn - x) <= tol) {
       x = xn;
