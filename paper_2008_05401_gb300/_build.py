@@ -17,9 +17,17 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcrbm.so")
-SOURCES = ["crbm_kernels.cu", "crbm_api.cu", "crbm_step_ising_fp64.cu", "crbm_step_ising_mixed.cu",
-           "crbm_step_kitaev_fp64.cu", "crbm_step_kitaev_mixed.cu", "crbm_tempering.cu",
-           "crbm_analysis.cu", "crbm_train.cu"]
+SOURCES = ["crbm_kernels.cu", "crbm_api.cu", "crbm_tempering.cu", "crbm_analysis.cu", "crbm_train.cu",
+           "crbm_step_ising_fp64_t256.cu",
+           "crbm_step_ising_mixed_t256.cu",
+           "crbm_step_kitaev_fp64_t256.cu",
+           "crbm_step_kitaev_fp64_t128.cu",
+           "crbm_step_kitaev_fp64_t64.cu",
+           "crbm_step_kitaev_fp64_t32.cu",
+           "crbm_step_kitaev_mixed_t256.cu",
+           "crbm_step_kitaev_mixed_t128.cu",
+           "crbm_step_kitaev_mixed_t64.cu",
+           "crbm_step_kitaev_mixed_t32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "crbm.h"
@@ -111,6 +112,12 @@ struct crbm_ctx {
   // non-blocking stream of the context's own copies and evaluation launches,
   // so that job set-up never waits for other streams' work
   cudaStream_t own = nullptr;
+  // side streams and events of a batch whose jobs need launches of different
+  // CTA sizes: the launches fork from the caller's stream and join it again,
+  // so they run side by side
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
   struct Graph {
     bool live = false;
     cudaGraph_t graph = nullptr;
@@ -270,17 +277,34 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
 
 static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
                        cudaStream_t st) {
-  for (int nt : {256, 128}) {
+  std::vector<std::pair<int, std::vector<int>>> parts;
+  for (int nt : {256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
       if (j.n > 0 && threads_for(j.kind, j.N) == nt) part.push_back(id);
     }
-    if (part.empty()) continue;
-    const int rc = launch_group(ctx, part, S, g, correct, prec, mode, nt, st);
-    if (rc) return rc;
+    if (!part.empty()) parts.emplace_back(nt, part);
   }
-  return CRBM_OK;
+  if (parts.size() <= 1) {
+    for (auto& pt : parts) {
+      const int rc = launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, st);
+      if (rc) return rc;
+    }
+    return CRBM_OK;
+  }
+  // several CTA sizes: the first launch on st, the others on side streams
+  // forked from st and joined back into it
+  CK(cudaEventRecord(ctx->fork, st), "fork event");
+  for (size_t i = 1; i < parts.size(); ++i) CK(cudaStreamWaitEvent(ctx->side[i - 1], ctx->fork, 0), "fork wait");
+  int rc = CRBM_OK;
+  for (size_t i = 0; i < parts.size() && rc == CRBM_OK; ++i)
+    rc = launch_group(ctx, parts[i].second, S, g, correct, prec, mode, parts[i].first, i == 0 ? st : ctx->side[i - 1]);
+  for (size_t i = 1; i < parts.size(); ++i) {
+    CK(cudaEventRecord(ctx->join[i - 1], ctx->side[i - 1]), "join event");
+    CK(cudaStreamWaitEvent(st, ctx->join[i - 1], 0), "join wait");
+  }
+  return rc;
 }
 
 extern "C" {
@@ -297,6 +321,11 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
+  for (int i = 0; i < crbm_ctx::kSide && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -326,6 +355,11 @@ int crbm_destroy(crbm_ctx* ctx) {
     if (gr.graph) cudaGraphDestroy(gr.graph);
   }
   if (ctx->own) cudaStreamDestroy(ctx->own);
+  for (int i = 0; i < crbm_ctx::kSide; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
   delete ctx;
   return CRBM_OK;
 }

@@ -37,14 +37,26 @@ __global__ void random_init_kernel(uint32_t* bits, int n_chains, int N, int Wd, 
   bits[idx] = out;
 }
 
-cudaError_t launch_kIsing_kFP64(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kIsing_kMixed(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kKitaev_kFP64(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t launch_kKitaev_kMixed(int, int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kIsing_kFP64(size_t);
-cudaError_t limit_kIsing_kMixed(size_t);
-cudaError_t limit_kKitaev_kFP64(size_t);
-cudaError_t limit_kKitaev_kMixed(size_t);
+cudaError_t launch_kIsing_kFP64_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kIsing_kFP64_256(size_t);
+cudaError_t launch_kIsing_kMixed_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kIsing_kMixed_256(size_t);
+cudaError_t launch_kKitaev_kFP64_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_256(size_t);
+cudaError_t launch_kKitaev_kFP64_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_128(size_t);
+cudaError_t launch_kKitaev_kFP64_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_64(size_t);
+cudaError_t launch_kKitaev_kFP64_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_32(size_t);
+cudaError_t launch_kKitaev_kMixed_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_256(size_t);
+cudaError_t launch_kKitaev_kMixed_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_128(size_t);
+cudaError_t launch_kKitaev_kMixed_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_64(size_t);
+cudaError_t launch_kKitaev_kMixed_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_32(size_t);
 
 void specialisation(int K, int k, int& KC, int& kC) {
   KC = 0;
@@ -55,7 +67,13 @@ void specialisation(int K, int k, int& KC, int& kC) {
   }
 }
 
-int threads_for(int kind, int max_N) { return (kind == kKitaev && max_N <= 64) ? 128 : 256; }
+// Kitaev CTA sizes measured on the Kitaev workloads: 32 threads up to 16
+// cells, 64 up to 64, 128 up to 100 and 256 above (per-column barriers of the
+// reduction cost less in small CTAs, of which more fit an SM).
+int threads_for(int kind, int max_N) {
+  if (kind != kKitaev) return 256;
+  return max_N <= 16 ? 32 : (max_N <= 64 ? 64 : (max_N <= 100 ? 128 : 256));
+}
 
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
                         cudaStream_t st, bool generic) {
@@ -63,17 +81,31 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
   specialisation(K, k, KC, kC);
   if (generic) KC = kC = 0;
   if (kind == kIsing)
-    return prec == kFP64 ? launch_kIsing_kFP64(KC, kC, nt, p, grid, smem, st)
-                         : launch_kIsing_kMixed(KC, kC, nt, p, grid, smem, st);
-  return prec == kFP64 ? launch_kKitaev_kFP64(KC, kC, nt, p, grid, smem, st)
-                       : launch_kKitaev_kMixed(KC, kC, nt, p, grid, smem, st);
+    return prec == kFP64 ? launch_kIsing_kFP64_256(KC, kC, p, grid, smem, st)
+                         : launch_kIsing_kMixed_256(KC, kC, p, grid, smem, st);
+  if (prec == kFP64) {
+    switch (nt) {
+      case 32: return launch_kKitaev_kFP64_32(KC, kC, p, grid, smem, st);
+      case 64: return launch_kKitaev_kFP64_64(KC, kC, p, grid, smem, st);
+      case 128: return launch_kKitaev_kFP64_128(KC, kC, p, grid, smem, st);
+      default: return launch_kKitaev_kFP64_256(KC, kC, p, grid, smem, st);
+    }
+  }
+  switch (nt) {
+    case 32: return launch_kKitaev_kMixed_32(KC, kC, p, grid, smem, st);
+    case 64: return launch_kKitaev_kMixed_64(KC, kC, p, grid, smem, st);
+    case 128: return launch_kKitaev_kMixed_128(KC, kC, p, grid, smem, st);
+    default: return launch_kKitaev_kMixed_256(KC, kC, p, grid, smem, st);
+  }
 }
 
 cudaError_t set_smem_limits(size_t bytes) {
-  cudaError_t e = limit_kIsing_kFP64(bytes);
-  if (e == cudaSuccess) e = limit_kIsing_kMixed(bytes);
-  if (e == cudaSuccess) e = limit_kKitaev_kFP64(bytes);
-  if (e == cudaSuccess) e = limit_kKitaev_kMixed(bytes);
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t (*f)(size_t) : {limit_kIsing_kFP64_256, limit_kIsing_kMixed_256, limit_kKitaev_kFP64_256,
+                                   limit_kKitaev_kFP64_128, limit_kKitaev_kFP64_64, limit_kKitaev_kFP64_32,
+                                   limit_kKitaev_kMixed_256, limit_kKitaev_kMixed_128, limit_kKitaev_kMixed_64,
+                                   limit_kKitaev_kMixed_32})
+    if (e == cudaSuccess) e = f(bytes);
   return e;
 }
 

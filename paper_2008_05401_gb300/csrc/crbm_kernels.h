@@ -14,9 +14,9 @@ void specialisation(int K, int k, int& KC, int& kC);
 // Dynamic shared memory of one CTA of the fused kernel (ncls kernel classes
 // in the tables: 1 for a CRBM, 2 edge + 1 for an LCRBM).
 size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int ncls = 1);
-// Threads per CTA for a launch whose largest lattice has max_N sites: 128 for
-// Kitaev matrices up to 64 x 64 (fewer idle warps at the eigen-stage barriers),
-// else 256 (measured).
+// Threads per CTA of a job whose lattice has max_N cells: 256 for the Ising
+// kind; for the Kitaev kind 32 up to 16 cells, 64 up to 64, 128 up to 100,
+// else 256 (measured: small CTAs wait less at the eigen-stage barriers).
 int threads_for(int kind, int max_N);
 // Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch);
 // generic: use the runtime-shape variant even where a specialisation exists (LCRBM jobs).

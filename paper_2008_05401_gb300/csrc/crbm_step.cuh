@@ -68,7 +68,7 @@ __device__ inline void store_evaluation(const JobDev& jb, int c, double beta, co
 }
 
 template <int KIND, int PREC, int KC, int kC, int NT>
-__global__ void __launch_bounds__(NT, NT >= 256 ? CRBM_MIN_BLOCKS : 2 * CRBM_MIN_BLOCKS) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
+__global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
   int jid = 0;
   while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
   const JobDev& jb = prm.job[jid];
@@ -605,18 +605,15 @@ cudaError_t limit_nt(size_t bytes) {
   return e;
 }
 
-// Variants compiled for each (kind, precision): (K, k) = (4, 5), (4, 3), runtime;
-// CTAs of 256 threads, plus 128 threads for the Kitaev kind (small matrices).
-#define CRBM_VARIANTS(KIND, PREC)                                                            \
-  cudaError_t launch_##KIND##_##PREC(int KC, int kC, int nt, const LaunchParams& p, int grid, \
-                                     size_t smem, cudaStream_t st) {                           \
-    if (KIND == kKitaev && nt == 128) return launch_nt<KIND, PREC, 128>(KC, kC, p, grid, smem, st); \
-    return launch_nt<KIND, PREC, 256>(KC, kC, p, grid, smem, st);                             \
+// One translation unit per (kind, precision, CTA size) instantiates the
+// (K, k) variants (4, 5), (4, 3) and runtime: CTAs of 256 threads, plus 128,
+// 64 and 32 threads for the Kitaev kind (small matrices); every CTA size gets
+// the same 128-register budget.  Separate units compile in parallel.
+#define CRBM_VARIANTS_NT(KIND, PREC, NT)                                                       \
+  cudaError_t launch_##KIND##_##PREC##_##NT(int KC, int kC, const LaunchParams& p, int grid,   \
+                                            size_t smem, cudaStream_t st) {                    \
+    return launch_nt<KIND, PREC, NT>(KC, kC, p, grid, smem, st);                               \
   }                                                                                            \
-  cudaError_t limit_##KIND##_##PREC(size_t bytes) {                                            \
-    cudaError_t e = limit_nt<KIND, PREC, 256>(bytes);                                          \
-    if (e == cudaSuccess && KIND == kKitaev) e = limit_nt<KIND, PREC, 128>(bytes);             \
-    return e;                                                                                  \
-  }
+  cudaError_t limit_##KIND##_##PREC##_##NT(size_t bytes) { return limit_nt<KIND, PREC, NT>(bytes); }
 
 }  // namespace crbm
