@@ -155,8 +155,10 @@ CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, 
              void* cuda_stream);
 
 /* As crbm_run for n_jobs jobs in ONE kernel launch (chains of different L and
- * temperature side by side; Kitaev jobs with at most 64 cells per lattice run
- * in CTAs of another size and form a second launch on the same stream).  The jobs must share the model kind and the
+ * temperature side by side; Kitaev jobs run in CTAs whose size depends on
+ * their lattice, one launch per size, forked from cuda_stream onto internal
+ * side streams and joined back, so the call stays ordered on cuda_stream).
+ * The jobs must share the model kind and the
  * filter-bank shape (K, k); their models may differ.  Each job keeps its own
  * step counter and random streams, so its result equals a crbm_run of that
  * job alone.  At most 16 jobs per call; a job may appear once. */
