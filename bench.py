@@ -249,15 +249,16 @@ def _oracle_rate(fn, budget_s):
     return n / dt, n, dt
 
 
-def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0, clocks=None):
+def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0, clocks=None, g=1, L_n=None):
     """Parallel-tempering exchange correction (App. B.2) on a workload's first
-    lattice size: the workload's chains are the physical ladder, as many RBM
-    chains run beside them.  value = chain-cycles/s (one RBM proposal, one
-    swap decision and one temperature-exchange decision per pair and cycle)."""
+    lattice size (or L_n = (L, chains)): the workload's chains are the physical
+    ladder, as many RBM chains run beside them.  value = chain-cycles/s (one RBM
+    proposal of g Gibbs steps, one swap decision and one temperature-exchange
+    decision per pair and cycle)."""
     import torch
     from paper_2008_05401_gb300 import MIXED
     spec = workload(name)
-    L, n = spec["jobs"][0]
+    L, n = L_n or spec["jobs"][0]
     ctx = ctx_cls(dev)
     W, hb, vb = spec["model"]
     mid = ctx.load_model(spec["kind"], W, vb, hb)
@@ -266,12 +267,12 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0,
                     wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec)
     y = ctx.new_job(mid, spec["kind"], L, T, spec["J"], SEED + 1, n,
                     wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L + 1)), prec)
-    ctx.pt_run(x, y, 2, precision=prec, stream=stream)
+    ctx.pt_run(x, y, 2, g=g, precision=prec, stream=stream)
     torch.cuda.synchronize(dev)
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.pt_run(x, y, cycles, precision=prec, stream=stream)
+    ctx.pt_run(x, y, cycles, g=g, precision=prec, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
@@ -279,7 +280,7 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0,
     ctx.close()
     model = "2D Ising" if spec["kind"] == 0 else "Kitaev"
     out = {"workload": f"parallel tempering, {model} L={L}, {n} physical + {n} RBM chains, one proposal "
-                       f"(g=1) per RBM chain and cycle, the workload's T ladder",
+                       f"(g={g}) per RBM chain and cycle, the workload's T ladder",
            "precision": "mixed" if prec == MIXED else "fp64", "value": n * cycles / (ms * 1e-3),
            "unit": "chain-cycles/s", "ms_per_cycle": ms / cycles, "cycles": cycles,
            "swap_rate": float(acc.sum()) / (n * (cycles + 2))}
@@ -292,7 +293,7 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0,
         nc = 32
         px = chain.make_chains(spec["kind"], W, hb, vb, L, T[:nc], spec["J"], SEED, np.arange(nc))
         py = chain.make_chains(spec["kind"], W, hb, vb, L, T[:nc], spec["J"], SEED + 1, np.arange(nc, 2 * nc))
-        rate, c, dt = _oracle_rate(lambda: tempering.cycle(px, py, 1), oracle_s)
+        rate, c, dt = _oracle_rate(lambda: tempering.cycle(px, py, g), oracle_s)
         out["cpu_baseline"] = {"value": rate * nc, "unit": "chain-cycles/s", "cores": 1, "kind": "oracle",
                                "sample": f"{nc} + {nc} chains x {c} cycles in {dt:.1f}s"}
     return out
@@ -588,7 +589,10 @@ def main():
             tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush, clocks=clocks,
                           oracle_s=0.0 if args.no_cpu_baseline else 3.0),
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
-                          oracle_s=0.0 if args.no_cpu_baseline else 2.0)]
+                          oracle_s=0.0 if args.no_cpu_baseline else 2.0),
+            # the paper's Kitaev protocol at L = 8: k = 4 Gibbs steps per correction (Table II)
+            tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
+                          oracle_s=0.0 if args.no_cpu_baseline else 2.0, g=4, L_n=(8, 1024))]
         line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
         ob = 0.0 if args.no_cpu_baseline else 2.0

@@ -187,9 +187,11 @@ CRBM_API int crbm_graph_destroy(crbm_ctx* ctx, int graph_id);
  * rbm_job the RBM chains y_i; both jobs must use the same model and have the
  * same L, couplings and temperatures, chain by chain.  One cycle:
  *   1. every RBM chain makes one proposal of g Gibbs steps without
- *      correction (Eq. B4); F, log pi_i, E and the observables of the new
- *      lattice are evaluated in FP64 (precision selects the arithmetic of the
- *      Gibbs steps only; CRBM_MIXED takes the FP64 path's Bernoulli draws);
+ *      correction (Eq. B4); log pi_i, E and the observables of the new
+ *      lattice are evaluated in FP64, F in the requested precision
+ *      (CRBM_MIXED: FP32 with its certified bound, so the physical and RBM
+ *      chains may hold such F values; every Bernoulli and swap decision is
+ *      the FP64 path's, recomputed in FP64 when inside the bounds);
  *   2. x_i and y_i are exchanged with probability min(1, a),
  *      log a = [log pi_i(y) - log pi_i(x)] + [F(y) - F(x)] (Eq. B5 with the
  *      pair (pi_i, P_CRBM)), uniform from tag 0xFFFFFFFD of chain i of
@@ -204,8 +206,9 @@ CRBM_API int crbm_graph_destroy(crbm_ctx* ctx, int graph_id);
  *      count counts the exchanges of step 2.
  * Both step counters advance by `cycles`.  The RBM job's sums and accept
  * counts are left unchanged.  If proposals (crbm_run and the like) ran on
- * phys_job since its last evaluation, its chains are first re-evaluated in
- * FP64 (synchronously).  Work enqueued earlier on either job must be ordered
+ * phys_job since its last evaluation (or, for CRBM_FP64, a mixed tempering
+ * call left FP32 free energies), its chains are first re-evaluated in FP64
+ * (synchronously).  Work enqueued earlier on either job must be ordered
  * before cuda_stream by the caller.
  * Errors: CRBM_EINVAL (mismatched jobs, g, precision, step counter past
  * 2^32), CRBM_ECUDA. */

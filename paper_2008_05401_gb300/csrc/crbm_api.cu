@@ -53,6 +53,7 @@ struct Job {
   // Kitaev kind, eps holds the spectra of the current lattices: true after an
   // evaluation or a tempering cycle, false after proposals (mode 0)
   bool exact = false;
+  bool fexact = false;       // F of every chain is an FP64 value (bound 0)
   // optional E_phys trace in caller-owned device memory (crbm_set_trace)
   double* trace = nullptr;
   uint64_t trace_base = 0;
@@ -229,7 +230,7 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
 // bit of its results -- is the same alone or batched; jobs of different CTA
 // sizes go to separate launches on the same stream.
 static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec,
-                        int mode, int nt, cudaStream_t st) {
+                        int mode, int nt, cudaStream_t st, const Job* partner = nullptr) {
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -261,6 +262,7 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
     k = m.k;
   }
   p.tile_begin[ids.size()] = tiles;
+  if (partner) p.job[ids.size()] = make_jobdev(ctx, *partner);    // tempering: the physical chains
   if (tiles == 0) return CRBM_OK;
   if (generic) {
     // every job of the launch runs the runtime-shape variant: size its shared memory so
@@ -276,7 +278,7 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
 }
 
 static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Job* partner = nullptr) {
   std::vector<std::pair<int, std::vector<int>>> parts;
   for (int nt : {256, 128, 64, 32}) {
     std::vector<int> part;
@@ -288,7 +290,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
   }
   if (parts.size() <= 1) {
     for (auto& pt : parts) {
-      const int rc = launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, st);
+      const int rc = launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, st, partner);
       if (rc) return rc;
     }
     return CRBM_OK;
@@ -560,7 +562,7 @@ int crbm_update_model(crbm_ctx* ctx, int model_id, const double* W, double v_bia
   const int rc = build_model(ctx, m, m.kind, m.K, m.k, W, v_bias, h_bias, false);
   if (rc) return rc;
   for (auto& j : ctx->jobs)
-    if (j.live && j.model == model_id) j.exact = false;
+    if (j.live && j.model == model_id) j.exact = j.fexact = false;
   return CRBM_OK;
 }
 
@@ -574,6 +576,7 @@ static int evaluate(crbm_ctx* ctx, int id) {
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->own), "evaluate");
   ctx->jobs[id].exact = true;
+  ctx->jobs[id].fexact = true;
   return CRBM_OK;
 }
 
@@ -716,7 +719,7 @@ int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int
   for (int id : ids) {
     ctx->jobs[id].step += (uint64_t)S;
     ctx->jobs[id].stream = st;
-    if (S > 0) ctx->jobs[id].exact = false;
+    if (S > 0) ctx->jobs[id].exact = ctx->jobs[id].fexact = false;
   }
   return CRBM_OK;
 }
@@ -773,7 +776,7 @@ int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream) {
   for (int id : gr.jobs) {
     ctx->jobs[id].step += gr.steps;
     ctx->jobs[id].stream = st;
-    if (gr.steps > 0) ctx->jobs[id].exact = false;
+    if (gr.steps > 0) ctx->jobs[id].exact = ctx->jobs[id].fexact = false;
   }
   return CRBM_OK;
 }
@@ -809,21 +812,25 @@ int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g,
     if (j->step + (uint64_t)cycles > (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step counter would pass 2^32");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (cycles == 0 || x->n == 0) return CRBM_OK;
-  // the exchange needs FP64 F and log pi (and Kitaev spectra) of the physical chains
-  if (!x->exact) {
+  // the exchanges need FP64 log pi (and Kitaev spectra) of the physical chains,
+  // and in CRBM_FP64 also FP64 F (the mixed path carries F's certified bound)
+  if (!x->exact || (precision == kFP64 && !x->fexact)) {
     if ((rc = crbm_sync(ctx, phys_job))) return rc;
     if ((rc = evaluate(ctx, phys_job))) return rc;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const JobDev xd = make_jobdev(ctx, *x), yd = make_jobdev(ctx, *y);
+  const JobDev xd = make_jobdev(ctx, *x);
   for (int64_t c = 0; c < cycles; ++c) {
-    if ((rc = launch_jobs(ctx, {rbm_job}, 1, g, 0, precision, 2, st))) return rc;
-    CK(launch_pt_exchange(xd, &yd, 0, true, st), "exchange launch");
+    // RBM proposals and their swaps with the physical chains, then the
+    // temperature exchanges, observables and the cycle counter
+    if ((rc = launch_jobs(ctx, {rbm_job}, 1, g, 0, precision, 2, st, x))) return rc;
+    CK(launch_pt_exchange(xd, 0, true, st), "exchange launch");
   }
   for (Job* j : {x, y}) {
     j->step += (uint64_t)cycles;
     j->stream = st;
     j->exact = true;
+    j->fexact = j->fexact && precision == kFP64;
   }
   return CRBM_OK;
 }
@@ -859,12 +866,13 @@ int crbm_local_run(crbm_ctx* ctx, int job_id, int64_t sweeps, int exchange, int 
     const JobDev xd = make_jobdev(ctx, *j);
     for (int64_t c = 0; c < sweeps; ++c) {
       if ((rc = launch_jobs(ctx, {job_id}, 1, 1, 0, prec, 3, st))) return rc;
-      CK(launch_pt_exchange(xd, nullptr, -1, false, st), "exchange launch");
+      CK(launch_pt_exchange(xd, -1, false, st), "exchange launch");
     }
   }
   j->step += (uint64_t)sweeps;
   j->stream = st;
   j->exact = (prec == kFP64);
+  j->fexact = true;       // each launch ends with the FP64 free energy
   return CRBM_OK;
 }
 

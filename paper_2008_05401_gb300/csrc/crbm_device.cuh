@@ -96,7 +96,8 @@ __device__ __forceinline__ void trace_store(const JobDev& jb, int c, unsigned lo
 
 struct LaunchParams {
   // mode 0: S proposals; 1: evaluate the current state; 2: one uncorrected
-  // proposal and the FP64 evaluation of the new state (tempering RBM chains);
+  // proposal of the tempering RBM chains of job[0] and its exchange with the
+  // physical chains of job[1] (n_jobs = 1);
   // 3: S local-update Metropolis sweeps, where correct = 1 adds each sweep's
   // observables to the sums (0: the exchange kernel that follows does)
   int n_jobs, S, g, correct, mode;

@@ -27,10 +27,10 @@ cudaError_t set_smem_limits(size_t bytes);
 // Random initial lattices (init tag of the stream).
 cudaError_t launch_random_init(uint32_t* bits, int n_chains, int N, int Wd, uint64_t seed,
                                uint64_t cid_base, cudaStream_t st);
-// Exchange step of one tempering cycle (crbm_tempering.cu): physical job x,
-// RBM job y (NULL: neighbour temperature exchange only); the cycle counter is
-// x's step counter + step_offset; `advance` then adds one to x's step counter.
-cudaError_t launch_pt_exchange(const JobDev& x, const JobDev* y, int step_offset, bool advance, cudaStream_t st);
+// Neighbour temperature exchange of one cycle (crbm_tempering.cu) on job x;
+// the cycle counter is x's step counter + step_offset; `advance` then adds
+// one to x's step counter.
+cudaError_t launch_pt_exchange(const JobDev& x, int step_offset, bool advance, cudaStream_t st);
 // Integrated autocorrelation time of every column of a time-major
 // [n][n_series] device array (crbm_analysis.cu); tau and w are device arrays.
 cudaError_t launch_tau(const double* x, int n_series, long long n, double c, double* tau, long long* w,

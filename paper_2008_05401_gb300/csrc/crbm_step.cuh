@@ -225,9 +225,15 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   }
 
   if (prm.mode == 2) {
-    // tempering RBM chains: g Gibbs steps without correction (Eq. B4), then
-    // the FP64 values of the new lattice that the exchange step needs
+    // tempering: the RBM chain makes g Gibbs steps without correction (Eq. B4),
+    // then its new lattice y' and the physical chain x of the same slot (job
+    // prm.job[1]) are exchanged with the Eq. (B5) probability for the pair
+    // (pi, P_CRBM):  log a = [log pi(y') - log pi(x)] + [F(y') - F(x)].  In the
+    // mixed path F(y') is the FP32 value with its certified bound and F(x) may
+    // carry one too; a decision inside the bounds is redone with FP64 F.
+    const JobDev& xj = prm.job[1];
     const uint32_t step = (uint32_t)*(volatile unsigned long long*)jb.step;
+    const uint32_t cycle = (uint32_t)*(volatile unsigned long long*)xj.step;
     uint32_t* vp = my + P;
     uint32_t* h = my + 2 * P;
     const uint32_t* src = my;
@@ -238,23 +244,129 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
       __syncthreads();
       src = vp;
     }
-    Tabs tb64 = tb;
-    tb64.f64 = jb.f64;       // FP64 tables from global memory (the mixed kernel
-    tb64.b64 = jb.b64;       // keeps only FP32 ones in shared memory)
     double fo[4];
-    free_energy64(jb, tb64, g, vp, fo);
+    free_phase<PREC, KC, kC>(jb, tb, g, vp, fo);
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
       kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
+    // the physical chain's lattice into the first hidden plane (free now)
+    if (g.active)
+      for (int w = g.r; w < jb.Wd; w += g.tpc) h[w] = xj.bits[(size_t)g.c * jb.Wd + w];
+    if (g.active && g.r == 0) {
+      ch.Fp = -jb.vb * fo[2] - fo[0];
+      ch.Bp = (PREC == kMixed)
+                  ? fo[1] + (double)K * (double)N * (1.5 * 0x1p-23 + (double)jb.csp) + 1e-12 * fabs(ch.Fp)
+                  : 0.0;
+      if (KIND == kIsing) {
+        const double E = -jb.J[0] * (double)(2 * N - 2 * (int)fo[3]);
+        const double M = 2.0 * fo[2] - (double)N;
+        ch.Ep = E;
+        ch.lpp = -ch.beta * E;
+        ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
+      } else {
+        ch.Ep = kr[1];
+        ch.lpp = kr[0];
+        ch.otp[0] = kr[1]; ch.otp[1] = kr[1] * kr[1]; ch.otp[2] = kr[2]; ch.otp[3] = fo[3] / (double)jb.nhex;
+      }
+      ch.F = xj.F[g.c];
+      ch.Fb = xj.Fb[g.c];
+      ch.lp = xj.logpi[g.c];
+      const double loga = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagSwap, cycle, (uint32_t)(xj.cid_base + (uint64_t)g.c)),
+                                       xj.rk);
+      const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+      ch.flag_rec = 0;
+      if (PREC == kFP64) {
+        ch.flag_acc = logu < loga;
+      } else {
+        const double Mg = ch.Bp + ch.Fb + 1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+        if (loga - logu > Mg) ch.flag_acc = 1;
+        else if (logu - loga > Mg) ch.flag_acc = 0;
+        else ch.flag_rec = 1;
+      }
+    }
+    if (PREC == kMixed) {
+      const int need = __syncthreads_or(g.active && g.r == 0 && ch.flag_rec);
+      if (need) {
+        // FP64 free energies of y' and (when only its FP32 value is known) of x
+        Tabs tb64g = tb;
+        tb64g.f64 = jb.f64;
+        tb64g.b64 = jb.b64;
+        Grp g2 = g;
+        g2.active = g.active && ch.flag_rec;
+        double f1[4];
+        free_energy64(jb, tb64g, g2, vp, f1);
+        grp_reduce<4>(f1, g2, scratch);
+        Grp g3 = g2;
+        g3.active = g2.active && ch.Fb != 0.0;
+        double f2[4];
+        free_energy64(jb, tb64g, g3, h, f2);
+        grp_reduce<4>(f2, g3, scratch);
+        if (g2.active && g.r == 0) {
+          ch.Fp = -jb.vb * f1[2] - f1[0];
+          ch.Bp = 0.0;
+          if (g3.active) {
+            ch.F = -jb.vb * f2[2] - f2[0];
+            ch.Fb = 0.0;
+          }
+          const double loga = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+          const uint4 w = philox4x32_10_rk(
+              make_uint4(0u, kTagSwap, cycle, (uint32_t)(xj.cid_base + (uint64_t)g.c)), xj.rk);
+          ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < loga;
+          ch.rec_mh += 1ull;
+        }
+      }
+    }
     if (nrec) atomicAdd(&ch.rec, (unsigned long long)nrec);
     __syncthreads();
     if (g.active) {
-      for (int w = g.r; w < jb.Wd; w += g.tpc) jb.bits[(size_t)g.c * jb.Wd + w] = vp[w];
+      const bool sw = ch.flag_acc != 0;
+      const size_t c = (size_t)g.c;
+      uint32_t* xb = xj.bits + c * jb.Wd;
+      uint32_t* yb = jb.bits + c * jb.Wd;
+      for (int w = g.r; w < jb.Wd; w += g.tpc) {
+        if (sw) {
+          xb[w] = vp[w];
+          yb[w] = h[w];
+        } else {
+          yb[w] = vp[w];
+        }
+      }
+      if (KIND == kKitaev && sw) {
+        for (int l = g.r; l < N; l += g.tpc) {
+          const double t = xj.eps[c * N + l];
+          xj.eps[c * N + l] = jb.eps[c * N + l];
+          jb.eps[c * N + l] = t;
+        }
+      }
       if (g.r == 0) {
-        store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
-        jb.rec[2 * (size_t)g.c] += ch.rec;
+        if (sw) {
+          // the RBM slot takes x (read before the physical slot is overwritten)
+          jb.F[c] = ch.F;
+          jb.Fb[c] = ch.Fb;
+          jb.Lb[c] = xj.Lb[c];
+          jb.logpi[c] = ch.lp;
+          jb.Ephys[c] = xj.Ephys[c];
+          for (int o = 0; o < kNobs; ++o) jb.obs_t[c * kNobs + o] = xj.obs_t[c * kNobs + o];
+          xj.F[c] = ch.Fp;
+          xj.Fb[c] = ch.Bp;
+          xj.Lb[c] = 0.0;
+          xj.logpi[c] = ch.lpp;
+          xj.Ephys[c] = ch.Ep;
+          for (int o = 0; o < kNobs; ++o) xj.obs_t[c * kNobs + o] = ch.otp[o];
+          xj.acc[c] += 1ull;
+        } else {
+          jb.F[c] = ch.Fp;
+          jb.Fb[c] = ch.Bp;
+          jb.Lb[c] = 0.0;
+          jb.logpi[c] = ch.lpp;
+          jb.Ephys[c] = ch.Ep;
+          for (int o = 0; o < kNobs; ++o) jb.obs_t[c * kNobs + o] = ch.otp[o];
+        }
+        jb.rec[2 * c] += ch.rec;
+        jb.rec[2 * c + 1] += ch.rec_mh;
       }
     }
     return;

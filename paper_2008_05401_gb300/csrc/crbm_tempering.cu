@@ -1,23 +1,21 @@
-// Exchange step of the parallel-tempering correction (App. B.2, Fig. 8b).
+// Temperature-exchange step of the parallel-tempering correction (App. B.2,
+// Fig. 8b) and of the local-update baselines with tempering.
 //
 // A ladder of physical chains x_i (target pi_i, temperature T_i fixed per
-// slot) runs beside RBM chains y_i (target P_CRBM ~ e^{-F}) of the same
-// temperatures.  After the RBM chains have made their uncorrected proposal
-// (mode 2 of the fused kernel: Gibbs steps, then F, log pi_i, E and the
-// observables of y_i in FP64), one launch of this kernel
-//  1. swaps x_i and y_i with the Eq. (B5) probability for the pair
-//     (pi_i, P_CRBM): log a = [log pi_i(y) - log pi_i(x)] + [F(y) - F(x)];
-//  2. exchanges neighbouring physical chains, pairs (0,1),(2,3),... on even
+// slot).  In a tempering cycle the RBM chains have already made their
+// proposal and been swapped with the physical chains (mode 2 of the fused
+// kernel); one launch of this kernel then
+//  1. exchanges neighbouring physical chains, pairs (0,1),(2,3),... on even
 //     cycles and (1,2),(3,4),... on odd ones, with Eq. (B5) for (pi_i, pi_j):
 //     log b = log pi_i(x_j) + log pi_j(x_i) - log pi_i(x_i) - log pi_j(x_j);
 //     a state's weight at another temperature comes from its energy (Ising)
 //     or from its cached spectrum eps (Kitaev): no new eigenvalue problem;
-//  3. adds every physical chain's observables to its sums.
-// One warp per unit of at most two neighbouring chains (a pair of step 2, or
-// a ladder end), so steps 1-3 of a unit need no grid-wide synchronisation.
-// The cycle counter is the physical job's step counter: the uniform of step 1
-// comes from (tag kTagSwap, chain i), that of step 2 from (kTagTemp, chain i
-// of the pair (i, i+1)).  Every value is FP64.
+//  2. adds every physical chain's observables to its sums (and its energy to
+//     the job's trace, if one is set).
+// One warp per unit of at most two neighbouring chains (a pair of step 1, or
+// a ladder end), so a unit needs no grid-wide synchronisation.  The cycle
+// counter is the job's step counter plus an offset; the uniform of the pair
+// (i, i+1) comes from tag kTagTemp of chain i.  Every value is FP64.
 #include "crbm_device.cuh"
 #include "crbm_kernels.h"
 
@@ -27,8 +25,6 @@ namespace {
 
 struct PtParams {
   JobDev x;          // physical chains
-  JobDev y;          // RBM chains (same model, L, chains and temperatures); unused without swap
-  int swap;          // 1: physical <-> RBM exchange first (tempering correction); 0: temperatures only
   int step_offset;   // cycle counter = x's step counter + step_offset
 };
 
@@ -101,7 +97,6 @@ __device__ void swap_state(const JobDev& a, int i, const JobDev& b, int j, int l
 
 __global__ void __launch_bounds__(128) pt_exchange_kernel(const __grid_constant__ PtParams p) {
   const JobDev& x = p.x;
-  const JobDev& y = p.y;
   const int lane = threadIdx.x & 31;
   const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const unsigned long long cyc = *x.step + (long long)p.step_offset;
@@ -110,19 +105,7 @@ __global__ void __launch_bounds__(128) pt_exchange_kernel(const __grid_constant_
   const int n = x.n_chains;
   const int lo = max(2 * u - par, 0), hi = min(2 * u + 2 - par, n);
   if (lo >= hi) return;
-  // 1. physical <-> RBM exchange at every temperature of the unit
-  for (int i = lo; i < hi && p.swap; ++i) {
-    int sw = 0;
-    if (lane == 0) {
-      const double log_a = (y.logpi[i] - x.logpi[i]) + (y.F[i] - x.F[i]);
-      sw = log_uniform(x, kTagSwap, cycle, i) < log_a;
-    }
-    sw = __shfl_sync(kFull, sw, 0);
-    if (sw) swap_state(x, i, y, i, lane);
-    if (lane == 0) x.acc[i] += (unsigned long long)sw;
-  }
-  __syncwarp();
-  // 2. temperature exchange of the pair (lo, lo + 1)
+  // 1. temperature exchange of the pair (lo, lo + 1)
   if (hi - lo == 2) {
     const int i = lo, j = lo + 1;
     const double bi = 1.0 / x.T[i], bj = 1.0 / x.T[j];
@@ -154,7 +137,7 @@ __global__ void __launch_bounds__(128) pt_exchange_kernel(const __grid_constant_
     }
   }
   __syncwarp();
-  // 3. observables of the physical chains
+  // 2. observables of the physical chains
   if (lane < (hi - lo) * kNobs) {
     const size_t e = (size_t)lo * kNobs + lane;
     x.obs[e] += x.obs_t[e];
@@ -166,12 +149,10 @@ __global__ void pt_advance_kernel(unsigned long long* step) { *step += 1ull; }
 
 }  // namespace
 
-cudaError_t launch_pt_exchange(const JobDev& x, const JobDev* y, int step_offset, bool advance, cudaStream_t st) {
+cudaError_t launch_pt_exchange(const JobDev& x, int step_offset, bool advance, cudaStream_t st) {
   if (x.n_chains == 0) return cudaSuccess;
   PtParams p;
   p.x = x;
-  p.y = y ? *y : x;
-  p.swap = y ? 1 : 0;
   p.step_offset = step_offset;
   const int units = (x.n_chains + 2) / 2;     // most units over both parities
   const int warps = 4;
