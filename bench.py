@@ -538,17 +538,18 @@ def main():
         b = torch.empty(j.state()[0].shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
         b[:] = j.state()[0]
         host_bits.append(b)
+    out_bits = [torch.empty(b.shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32) for b in host_bits]
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     h2d = d2h = 0
     for _ in range(e2e_steps):
         for j, hbits in zip(jobs, host_bits):
-            j.write_state(hbits, j.step)
+            j.write_state(hbits, j.step, prec)
             h2d += hbits.nbytes
         ctx.run_batch(jobs, S, precision=prec, stream=stream)
-        for j in jobs:
-            bits, _ = j.state()
+        for j, obits in zip(jobs, out_bits):
+            bits, _ = j.state(out=obits)
             sums, _, _ = j.observables()
             d2h += bits.nbytes + sums.nbytes
     e2e_s = time.perf_counter() - t0

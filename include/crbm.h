@@ -356,10 +356,13 @@ CRBM_API int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int6
  * ids this is a complete checkpoint. */
 CRBM_API int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step);
 
-/* Restore a checkpoint: overwrite the lattices and the step counter, then
- * re-evaluate F, log pi and observables in FP64 (sums are kept).  A resumed
- * chain continues bit-identically to an uninterrupted one. */
-CRBM_API int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step);
+/* Restore a checkpoint (or upload new lattices): overwrite the lattices and
+ * the step counter, then re-evaluate log pi and the observables in FP64 and
+ * F in `precision` (CRBM_MIXED: the FP32 value with its certified bound, as
+ * a mixed proposal leaves it; the sums are kept).  A resumed chain continues
+ * bit-identically to an uninterrupted one: every decision is the FP64 path's
+ * either way.  Errors: CRBM_EINVAL (null bits, step >= 2^32, precision). */
+CRBM_API int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step, int precision);
 
 /* Forget a job (its dev_mem may be freed afterwards) and return its bytes to
  * the context's budget. */

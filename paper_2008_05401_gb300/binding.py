@@ -72,7 +72,7 @@ _SIGS = {
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
-    "crbm_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64]),
+    "crbm_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_int]),
     "crbm_release": (C.c_int, [C.c_void_p, C.c_int]),
 }
 EXPORTS = tuple(_SIGS)
@@ -248,16 +248,19 @@ def crbm_read_observables(ctx, job_id, n):
     return sums, acc, rec
 
 
-def crbm_read_state(ctx, job_id, n, L):
-    bits = np.empty((n, (L * L + 31) // 32), dtype=np.uint32)
+def crbm_read_state(ctx, job_id, n, L, out=None):
+    """Lattices (into `out`, e.g. a pinned buffer, when given) and step counter."""
+    bits = np.empty((n, (L * L + 31) // 32), dtype=np.uint32) if out is None else out
+    if bits.dtype != np.uint32 or bits.shape != (n, (L * L + 31) // 32) or not bits.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous uint32 array of shape (n, ceil(L*L/32))")
     step = C.c_uint64()
     _check(ctx, load().crbm_read_state(ctx, job_id, _ptr(bits), C.byref(step)))
     return bits, step.value
 
 
-def crbm_write_state(ctx, job_id, bits, step):
+def crbm_write_state(ctx, job_id, bits, step, precision=FP64):
     bits = np.ascontiguousarray(bits, dtype=np.uint32)
-    _check(ctx, load().crbm_write_state(ctx, job_id, _ptr(bits), step))
+    _check(ctx, load().crbm_write_state(ctx, job_id, _ptr(bits), step, precision))
 
 
 def crbm_release(ctx, job_id):
@@ -284,11 +287,11 @@ class Job:
     def observables(self):
         return crbm_read_observables(self.ctx.h, self.id, self.n)
 
-    def state(self):
-        return crbm_read_state(self.ctx.h, self.id, self.n, self.L)
+    def state(self, out=None):
+        return crbm_read_state(self.ctx.h, self.id, self.n, self.L, out)
 
-    def write_state(self, bits, step):
-        crbm_write_state(self.ctx.h, self.id, bits, step)
+    def write_state(self, bits, step, precision=FP64):
+        crbm_write_state(self.ctx.h, self.id, bits, step, precision)
         self.step = step
 
     def local_run(self, sweeps, exchange=False, precision=FP64, stream=None):

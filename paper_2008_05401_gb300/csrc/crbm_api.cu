@@ -571,12 +571,13 @@ size_t crbm_job_bytes(int kind, int L, int n_chains, int precision) {
   return make_layout(kind, L, n_chains).total;
 }
 
-static int evaluate(crbm_ctx* ctx, int id) {
-  int rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, ctx->own);
+// F (in `prec`), log pi, E and observables (FP64) of a job's current lattices.
+static int evaluate(crbm_ctx* ctx, int id, int prec = kFP64) {
+  int rc = launch_jobs(ctx, {id}, 0, 1, 1, prec, 1, ctx->own);
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->own), "evaluate");
   ctx->jobs[id].exact = true;
-  ctx->jobs[id].fexact = true;
+  ctx->jobs[id].fexact = (prec == kFP64);
   return CRBM_OK;
 }
 
@@ -1094,11 +1095,12 @@ int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step) {
   return read_back(ctx, j, bits, j->lay.bits, (size_t)j->n * j->Wd * 4);
 }
 
-int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step) {
+int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step, int precision) {
   Job* j = get_job(ctx, job_id);
   if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;
   if (!bits && j->n > 0) return fail(ctx, CRBM_EINVAL, "null bits");
   if (step >= (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step must stay below 2^32");
+  if (precision != CRBM_FP64 && precision != CRBM_MIXED) return fail(ctx, CRBM_EINVAL, "bad precision");
   int rc = crbm_sync(ctx, job_id);
   if (rc) return rc;
   j->step = step;
@@ -1107,7 +1109,7 @@ int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t s
      "copy bits");
   const unsigned long long st = step;
   CK(cudaMemcpyAsync(j->mem + j->lay.step, &st, 8, cudaMemcpyHostToDevice, ctx->own), "copy step");
-  return evaluate(ctx, job_id);
+  return evaluate(ctx, job_id, precision);
 }
 
 int crbm_release(crbm_ctx* ctx, int job_id) {

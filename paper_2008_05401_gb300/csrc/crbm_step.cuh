@@ -45,7 +45,9 @@ static __device__ __noinline__ void free_energy64(const JobDev& jb, const Tabs& 
 // group sums fo (Eq. 13 sums, magnetisation count, bond/vison count) and, for
 // the Kitaev kind, kr = (log pi, e, c_f) of its spectrum.
 template <int KIND>
-__device__ inline void store_evaluation(const JobDev& jb, int c, double beta, const double* fo, const double* kr) {
+// Fb: bound on |F - F_fp64| of an FP32 free energy (0 for an FP64 one).
+__device__ inline void store_evaluation(const JobDev& jb, int c, double beta, const double* fo, const double* kr,
+                                        double Fb = 0.0) {
   const int N = jb.N;
   const double Fv = -jb.vb * fo[2] - fo[0];
   double lp, E, ot[kNobs];
@@ -60,7 +62,7 @@ __device__ inline void store_evaluation(const JobDev& jb, int c, double beta, co
     ot[0] = kr[1]; ot[1] = kr[1] * kr[1]; ot[2] = kr[2]; ot[3] = fo[3] / (double)jb.nhex;
   }
   jb.F[c] = Fv;
-  jb.Fb[c] = 0.0;
+  jb.Fb[c] = Fb;
   jb.Lb[c] = 0.0;
   jb.logpi[c] = lp;
   jb.Ephys[c] = E;
@@ -212,15 +214,25 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   unsigned nrec = 0;
 
   if (prm.mode == 1) {
-    // evaluate F (FP64), log pi and the observables of the current lattices
+    // evaluate F (FP64, or in the mixed path FP32 with its certified bound,
+    // as after a mixed proposal), log pi and the observables (FP64) of the
+    // current lattices
     double fo[4];
-    free_energy64(jb, tb, g, my, fo);
+    if (PREC == kMixed) free_phase<PREC, KC, kC>(jb, tb, g, my, fo);
+    else free_energy64(jb, tb, g, my, fo);
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
       kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
-    if (g.active && g.r == 0) store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr);
+    if (g.active && g.r == 0) {
+      double Fb = 0.0;
+      if (PREC == kMixed) {
+        const double Fv = -jb.vb * fo[2] - fo[0];
+        Fb = fo[1] + (double)K * (double)N * (1.5 * 0x1p-23 + (double)jb.csp) + 1e-12 * fabs(Fv);
+      }
+      store_evaluation<KIND>(jb, g.c, ch.beta, fo, kr, Fb);
+    }
     return;
   }
 

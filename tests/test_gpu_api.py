@@ -107,7 +107,14 @@ def test_split_runs_and_checkpoint_resume(ctx):
     np.testing.assert_array_equal(r["bits"], a["bits"])
     np.testing.assert_array_equal(r["acc"] + acc5, a["acc"])
     np.testing.assert_allclose(r["sums"] + sums5, a["sums"], rtol=1e-12)
-    for j in (straight, split, first, resumed):
+    # restoring with the mixed evaluation (FP32 F with its bound) continues identically
+    resumed_m = ctx.new_job(mid, ISING, 32, T, (1.0,), SEED, 0, bits0, MIXED)
+    resumed_m.write_state(ck_bits, ck_step, MIXED)
+    resumed_m.run(7, precision=MIXED)
+    rm = _snapshot(resumed_m)
+    np.testing.assert_array_equal(rm["bits"], a["bits"])
+    np.testing.assert_array_equal(rm["acc"] + acc5, a["acc"])
+    for j in (straight, split, first, resumed, resumed_m):
         j.release()
 
 
