@@ -226,10 +226,20 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
     acc = sum(int(a.sum()) for _, a, _ in sums) / (n_chains * spec["S"] * (steps + 1))
     rec = [sum(int(r[:, 0].sum()) for _, _, r in sums), sum(int(r[:, 1].sum()) for _, _, r in sums)]
     ctx.close()
-    return {"workload": spec["desc"], "precision": "mixed" if prec == MIXED else "fp64",
-            "value": n_chains * spec["S"] * steps / (ms * 1e-3), "unit": "proposals/s",
-            "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
-            "fp64_recomputes": rec}
+    out = {"workload": spec["desc"], "precision": "mixed" if prec == MIXED else "fp64",
+           "value": n_chains * spec["S"] * steps / (ms * 1e-3), "unit": "proposals/s",
+           "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
+           "fp64_recomputes": rec}
+    if spec["kind"] == 1:
+        # eigen-stage roofline: (8/3) N^3 flops per proposal (Golub-Kahan
+        # bidiagonalisation of M, values only) against GB300's nominal FP64 peak
+        flops = sum(n * (8.0 / 3.0) * (L * L) ** 3 for L, n in spec["jobs"]) * spec["S"] * steps
+        achieved = flops / (ms * 1e-3) / 1e12
+        out["roofline"] = {"bound": "fp64", "achieved": round(achieved, 4), "peak": 1.25, "unit": "TFLOP/s",
+                           "frac": round(achieved / 1.25, 4), "traffic": None,
+                           "peak_source": "nominal GB300 FP64 (no measured FP64 peak); flops = (8/3) N^3 per "
+                                          "proposal; the mixed path runs the reduction on the FP32 pipe"}
+    return out
 
 
 def _oracle_rate(fn, budget_s):
