@@ -69,7 +69,10 @@ __device__ inline void store_evaluation(const JobDev& jb, int c, double beta, co
   for (int o = 0; o < kNobs; ++o) jb.obs_t[(size_t)c * kNobs + o] = ot[o];
 }
 
-template <int KIND, int PREC, int KC, int kC, int NT>
+// AUX = 0: the proposal loop (mode 0) only; AUX = 1: modes 1-3.  Two kernels,
+// so that the hot proposal loop carries none of the other modes' code and
+// registers (with them it spilled).
+template <int KIND, int PREC, int KC, int kC, int NT, int AUX>
 __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
   int jid = 0;
   while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   __syncthreads();
   unsigned nrec = 0;
 
-  if (prm.mode == 1) {
+  if (AUX && prm.mode == 1) {
     // evaluate F (FP64, or in the mixed path FP32 with its certified bound,
     // as after a mixed proposal), log pi and the observables (FP64) of the
     // current lattices
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     return;
   }
 
-  if (prm.mode == 2) {
+  if (AUX && prm.mode == 2) {
     // tempering: the RBM chain makes g Gibbs steps without correction (Eq. B4),
     // then its new lattice y' and the physical chain x of the same slot (job
     // prm.job[1]) are exchanged with the Eq. (B5) probability for the pair
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     return;
   }
 
-  if (prm.mode == 3) {
+  if (AUX && prm.mode == 3) {
     // local-update Metropolis sweeps (Sec. III, Sec. IV baselines)
     const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
     if (KIND == kIsing && g.active && g.r == 0) {
@@ -529,6 +532,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     return;
   }
 
+  if (AUX) return;
   const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
   // the step counter lives in device memory (advanced by advance_steps after
   // the launch), so a captured CUDA graph can be replayed
@@ -699,7 +703,8 @@ static __global__ void advance_steps_kernel(const __grid_constant__ LaunchParams
 // Launch one instantiation; raise its dynamic shared-memory limit.
 template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  crbm_step_kernel<KIND, PREC, KC, kC, NT><<<grid, NT, smem, st>>>(p);
+  if (p.mode == 0) crbm_step_kernel<KIND, PREC, KC, kC, NT, 0><<<grid, NT, smem, st>>>(p);
+  else crbm_step_kernel<KIND, PREC, KC, kC, NT, 1><<<grid, NT, smem, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && p.mode != 1 && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
@@ -710,8 +715,12 @@ cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream
 
 template <int KIND, int PREC, int KC, int kC, int NT>
 cudaError_t limit_inst(size_t bytes) {
-  return cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC, NT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC, NT, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(crbm_step_kernel<KIND, PREC, KC, kC, NT, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
 }
 
 template <int KIND, int PREC, int NT>
