@@ -55,6 +55,8 @@ ISING_CASES = [
     (32, 4, 5, 6, 1, True, 0.15),
     (64, 4, 5, 3, 1, True, 0.1),      # several tiles of 4-site units, multi-word rows
     (96, 2, 3, 2, 1, True, 0.1),      # row of 3 words
+    (256, 8, 6, 2, 1, True, 0.05),    # the largest lattice, K = 8 filters, K k 2^k = 3072 table entries
+    (20, 4, 7, 3, 3, True, 0.1),      # k = 7 (largest kernel), g = 3
 ]
 
 
