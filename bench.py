@@ -192,24 +192,30 @@ def run_reference(args, spec):
     print(json.dumps(line), flush=True)
 
 
-def time_jobs(ctx, jobs, S, prec, steps, warmup, stream, dev, flush):
-    """Device time (ms) of `steps` batched launches, L2 flushed before each."""
+def time_jobs(ctx, jobs, S, prec, steps, warmup, stream, dev, flush, graph=False):
+    """Device time (ms) of `steps` batched launches (or, with graph, replays of
+    one captured batched run), L2 flushed before each."""
     import torch
+    g = ctx.graph(jobs, S, precision=prec) if graph else None
+    step = (lambda: g.launch(stream)) if graph else (lambda: ctx.run_batch(jobs, S, precision=prec, stream=stream))
     for _ in range(warmup):
-        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+        step()
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
         ev[i][0].record(stream)
-        ctx.run_batch(jobs, S, precision=prec, stream=stream)
+        step()
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    if g is not None:
+        g.destroy()
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
-def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
-    """Proposals/s of another workload or precision (no e2e, no clocks)."""
+def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False):
+    """Proposals/s of another workload or precision (no e2e, no clocks); graph:
+    replay a captured CUDA graph of the batched run."""
     from paper_2008_05401_gb300 import MIXED
     spec = workload(name)
     ctx = ctx_cls(dev)
@@ -220,13 +226,17 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush):
         jobs.append(ctx.new_job(mid, spec["kind"], L, spec["T"](n), spec["J"], SEED, base,
                                 wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec))
         base += n
-    ms = time_jobs(ctx, jobs, spec["S"], prec, steps, 1, stream, dev, flush)
+    if graph:
+        for L, _ in spec["jobs"]:
+            ctx.tune(mid, L, prec)            # autotuned tiles (Kitaev: one chain per CTA)
+    ms = time_jobs(ctx, jobs, spec["S"], prec, steps, 1, stream, dev, flush, graph=graph)
     n_chains = sum(n for _, n in spec["jobs"])
     sums = [j.observables() for j in jobs]
     acc = sum(int(a.sum()) for _, a, _ in sums) / (n_chains * spec["S"] * (steps + 1))
     rec = [sum(int(r[:, 0].sum()) for _, _, r in sums), sum(int(r[:, 1].sum()) for _, _, r in sums)]
     ctx.close()
-    out = {"workload": spec["desc"], "precision": "mixed" if prec == MIXED else "fp64",
+    out = {"workload": spec["desc"] + (", captured CUDA graph replayed" if graph else ""),
+           "precision": "mixed" if prec == MIXED else "fp64",
            "value": n_chains * spec["S"] * steps / (ms * 1e-3), "unit": "proposals/s",
            "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
            "fp64_recomputes": rec}
@@ -597,6 +607,7 @@ def main():
             secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush),
             secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
             secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush),
+            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush, graph=True),
             tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush, clocks=clocks,
                           oracle_s=0.0 if args.no_cpu_baseline else 3.0),
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
