@@ -323,6 +323,14 @@ typedef struct {
 CRBM_API int crbm_train_epochs(crbm_ctx* ctx, int n_problems, const crbm_train_problem* problems, int batch,
                                double lr, double b1, double b2, double eps, void* cuda_stream);
 
+/* Measure the device's FMA throughput: *fp32_tflops and *fp64_tflops (2
+ * flops per fused multiply-add) from a kernel of independent FMA chains on
+ * every SM, timed with CUDA events (the call allocates and frees a small
+ * device buffer and returns when done).  No counterpart in the paper: the
+ * peaks the rooflines of the FP32 (Ising) and FP64 (Kitaev eigen-stage,
+ * trainer) kernels are reported against.  Errors: CRBM_EINVAL, CRBM_ECUDA. */
+CRBM_API int crbm_probe_peaks(crbm_ctx* ctx, double* fp32_tflops, double* fp64_tflops);
+
 /* Autotune the tile shape (chains per 256-thread CTA) of model `model_id` at
  * lattice side L and `precision`: every admissible value is timed on a
  * temporary job that fills the GPU (device memory allocated and freed by this

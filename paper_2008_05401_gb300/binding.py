@@ -67,6 +67,7 @@ _SIGS = {
     "crbm_train_epochs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double,
                                     C.c_double, C.c_double, C.c_void_p]),
     "crbm_update_model": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
+    "crbm_probe_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -222,6 +223,13 @@ def crbm_update_model(ctx, model_id, W, v_bias, h_bias):
     W = np.ascontiguousarray(W, dtype=np.float64)
     hb = np.ascontiguousarray(h_bias, dtype=np.float64)
     _check(ctx, load().crbm_update_model(ctx, model_id, _ptr(W), float(v_bias), _ptr(hb)))
+
+
+def crbm_probe_peaks(ctx):
+    """Measured (FP32, FP64) FMA throughput of the context's device, TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(ctx, load().crbm_probe_peaks(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def crbm_tune(ctx, model_id, L, precision=FP64):

@@ -113,3 +113,68 @@ cudaError_t launch_tau_noalloc(const double* x, int n_series, long long n, doubl
 }
 
 }  // namespace crbm
+
+// ------------------------------------------------------------------ peak probes
+// FMA throughput of the FP32 and FP64 pipes: every thread runs 8 independent
+// dependency chains of fused multiply-adds (enough to hide the pipe latency),
+// the grid fills every SM several times over; a checksum of all chains is
+// stored so that the compiler keeps the work.
+namespace crbm {
+namespace {
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, R a, R b, R* sink) {
+  R x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = (R)(threadIdx.x + c) * (R)1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = x[c] * a + b;
+  }
+  R s = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+// Measured FMA rate (TFLOP/s, 2 flops per FMA) of one precision on the current device.
+template <typename R>
+static cudaError_t probe_one(int sms, R* sink, cudaStream_t st, double* tflops) {
+  const int blocks = sms * 8, threads = 256;
+  const int iters = sizeof(R) == 8 ? 256 : 4096;     // about a second of FP64, a quarter of FP32
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  fma_probe_kernel<R><<<blocks, threads, 0, st>>>(iters / 8, (R)0.999, (R)1e-4, sink);   // warm-up
+  cudaEventRecord(e0, st);
+  fma_probe_kernel<R><<<blocks, threads, 0, st>>>(iters, (R)0.999, (R)1e-4, sink);
+  cudaEventRecord(e1, st);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / ((double)ms * 1e-3) / 1e12;
+  return cudaGetLastError();
+}
+
+cudaError_t probe_fma_peaks(int device, double* fp32_tflops, double* fp64_tflops, cudaStream_t st) {
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  const size_t n = (size_t)sms * 8 * 256;
+  double* sink = nullptr;
+  e = cudaMalloc(&sink, n * sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = probe_one<float>(sms, (float*)sink, st, fp32_tflops);
+  if (e == cudaSuccess) e = probe_one<double>(sms, sink, st, fp64_tflops);
+  cudaStreamSynchronize(st);
+  cudaFree(sink);
+  return e;
+}
+
+}  // namespace crbm

@@ -961,6 +961,14 @@ int crbm_train_epochs(crbm_ctx* ctx, int n_problems, const crbm_train_problem* p
 }
 
 
+int crbm_probe_peaks(crbm_ctx* ctx, double* fp32_tflops, double* fp64_tflops) {
+  if (!ctx) return CRBM_EINVAL;
+  if (!fp32_tflops || !fp64_tflops) return fail(ctx, CRBM_EINVAL, "null pointer");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(probe_fma_peaks(ctx->device, fp32_tflops, fp64_tflops, ctx->own), "peak probe");
+  return CRBM_OK;
+}
+
 int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision, void* cuda_stream) {
   return crbm_run_batch(ctx, 1, &job_id, S, g, correct, precision, cuda_stream);
 }

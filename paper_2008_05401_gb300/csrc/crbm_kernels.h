@@ -46,6 +46,8 @@ cudaError_t launch_tau_noalloc(const double* x, int n_series, long long n, doubl
 #include "crbm.h"
 namespace crbm {
 size_t train_smem_bytes(const crbm_train_problem& q, int batch);
+// Measured FP32 / FP64 FMA throughput of `device` (crbm_analysis.cu).
+cudaError_t probe_fma_peaks(int device, double* fp32_tflops, double* fp64_tflops, cudaStream_t st);
 cudaError_t launch_train(const crbm_train_problem* pr, int n, int batch, double lr, double b1, double b2,
                          double eps, cudaStream_t st);
 }  // namespace crbm
