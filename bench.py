@@ -141,7 +141,7 @@ def peaks():
 # kernel, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # one pass) of the current kernel; the lattices stay in shared memory for the
 # whole launch, so this is the lattice and table traffic only.
-BATCH_ISING_TRAFFIC_BYTES = 14.51e6 + 28.42e3
+BATCH_ISING_TRAFFIC_BYTES = 13.97e6 + 12.54e3
 
 
 def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
