@@ -61,6 +61,114 @@ __device__ __forceinline__ df df_sqrt(df a) {
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df df_from_float(float x) { return {x, 0.0f}; }
 
+// ----------------------------------------------- double-FP32 eigenvalue refinement
+// The Sturm sequence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} and its
+// x-derivative in df64 arithmetic, for the mixed path's eigenvalues: the same
+// FP32 bisection as the FP64 solver isolates eigenvalue idx, two df64 Sturm
+// counts verify the padded bracket and safeguarded df64 Newton steps refine it
+// -- on the FP32 pipe instead of GB300's slow FP64 one.  Values are kept
+// between 2^-40 and 2^40 by exact power-of-two rescaling, so that the low
+// words stay normal.  The computed counts are exact for a tridiagonal whose
+// entries differ from (d, e^2) by a few units of 2^-46 relative (the
+// backward stability of the Sturm recurrence, after Kahan), which moves
+// every eigenvalue by at most 16 2^-46 (|d| + |e^2| scale); the log-weight
+// bound of the mixed stage includes this.
+__device__ __forceinline__ df df_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ df df_scale(df a, float s) { return {a.hi * s, a.lo * s}; }
+__device__ __forceinline__ int df_expo(df a) { return (int)((__float_as_uint(a.hi) >> 23) & 0xffu); }
+
+struct SturmNewtonDf {
+  int cnt;
+  df p, dp;
+};
+
+// Sign change count of the df64 Sturm sequence at x (with p_N and p_N').
+template <bool DERIV>
+__device__ inline SturmNewtonDf sturm_df(const df* d, const df* e2, int N, df x) {
+  df pp = {1.0f, 0.0f}, p = df_add(d[0], df_neg(x));
+  df dpp = {0.0f, 0.0f}, dp = {-1.0f, 0.0f};
+  uint32_t sprev = 0u;
+  uint32_t s = (p.hi == 0.0f) ? 1u : (__float_as_uint(p.hi) >> 31);
+  int cnt = (int)(s ^ sprev);
+  sprev = s;
+  for (int i = 1; i < N; ++i) {
+    const df dx = df_add(d[i], df_neg(x));
+    const df pn = df_add(df_mul(dx, p), df_neg(df_mul(e2[i - 1], pp)));
+    if (DERIV) {
+      const df dpn = df_add(df_add(df_mul(dx, dp), df_neg(p)), df_neg(df_mul(e2[i - 1], dpp)));
+      dpp = dp;
+      dp = dpn;
+    }
+    pp = p;
+    p = pn;
+    s = (p.hi == 0.0f) ? (sprev ^ 1u) : (__float_as_uint(p.hi) >> 31);
+    cnt += (int)(s ^ sprev);
+    sprev = s;
+    const int ex = DERIV ? max(df_expo(p), df_expo(dp)) : df_expo(p);
+    if (ex > 127 + 40) {
+      p = df_scale(p, 0x1p-40f);
+      pp = df_scale(pp, 0x1p-40f);
+      if (DERIV) {
+        dp = df_scale(dp, 0x1p-40f);
+        dpp = df_scale(dpp, 0x1p-40f);
+      }
+    } else if (ex < 127 - 40 && (DERIV ? max(df_expo(pp), df_expo(dpp)) : df_expo(pp)) < 127 - 40) {
+      p = df_scale(p, 0x1p+40f);
+      pp = df_scale(pp, 0x1p+40f);
+      if (DERIV) {
+        dp = df_scale(dp, 0x1p+40f);
+        dpp = df_scale(dpp, 0x1p+40f);
+      }
+    }
+  }
+  return {cnt, p, dp};
+}
+
+// Eigenvalue idx (ascending) of the tridiagonal (d, e^2) in df64: FP32
+// bisection (wk.d32 / wk.e32), df64 verification of the padded bracket
+// (falling back to the Gershgorin interval), safeguarded df64 Newton.
+__device__ inline double eigen_idx_df(const KitaevWork& wk, const df* d, const df* e2, int N, int idx, double glo,
+                                      double ghi) {
+  const double range = fmax(ghi - glo, 1e-300);
+  float lo32 = (float)glo, hi32 = (float)ghi;
+  const float w32 = (float)(range * 0x1p-20);
+  for (int it = 0; it < 48 && hi32 - lo32 > w32; ++it) {
+    const float mid = 0.5f * (lo32 + hi32);
+    if (!(mid > lo32 && mid < hi32)) break;
+    if (sturm_count32(wk.d32, wk.e32, N, mid) > idx) hi32 = mid; else lo32 = mid;
+  }
+  const double pad = 0x1p-14 * range;
+  double lo = fmax(glo, (double)lo32 - pad), hi = fmin(ghi, (double)hi32 + pad);
+  if (sturm_df<false>(d, e2, N, df_of(lo)).cnt > idx) lo = glo;
+  if (sturm_df<false>(d, e2, N, df_of(hi)).cnt <= idx) hi = ghi;
+  const double tol = 0x1p-42 * (range + fabs(glo));
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    if (hi - lo <= tol) {
+      x = 0.5 * (lo + hi);
+      break;
+    }
+    const SturmNewtonDf r = sturm_df<true>(d, e2, N, df_of(x));
+    if (r.cnt > idx) hi = x; else lo = x;
+    const double step = df_to_double(df_div(r.p, r.dp));
+    double xn = x - step;
+    if (fabs(step) <= tol && xn >= lo && xn <= hi) {
+      x = xn;
+      break;
+    }
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (fabs(xn - x) <= tol) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
+}
+
 // Kitaev log-weight with the Householder tridiagonalisation of A = M^T M in
 // df64 and the eigenvalues (FP32 isolation + FP64 Newton, as in the FP64
 // stage) and sums in FP64.  res = {log pi, e, c_f, bound}: |log pi - exact| <=
@@ -177,20 +285,28 @@ __device__ inline void kitaev_logpi_df(const uint32_t* v, int L, const double* J
   }
   __syncthreads();
   // the df64 matrix is no longer needed: vv/pw hold FP64 Sturm data again
+  // the matrix is reduced: its storage now holds the df64 tridiagonal (d, e^2)
+  df* ddf = reinterpret_cast<df*>(wk.A);
+  df* edf = ddf + N;
   for (int i = tid; i < N; i += nt) {
     wk.vv[i] = wk.e[i] * wk.e[i];
     wk.d32[i] = (float)wk.d[i];
     wk.e32[i] = (float)(wk.e[i] * wk.e[i]);
+    ddf[i] = df_of(wk.d[i]);
+    edf[i] = df_of(wk.e[i] * wk.e[i]);
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
   __syncthreads();
   // reduction backward error of this stage and of the FP64 stage it stands in
-  // for, plus the FP64 eigenvalue solver's own error on either tridiagonal
+  // for, the FP64 eigenvalue solver's own error on the FP64 path's tridiagonal,
+  // and this stage's df64 solver (Sturm backward error and Newton tolerance)
+  const double scale = ghi - glo + fabs(glo) + fabs(ghi);
   const double dmu = (8.0 * (double)N * (double)N * (0x1p-46 + 0x1p-53) * sqrt(fro_all) +
-                      4.0 * (double)N * 0x1p-52 * (ghi - glo + fabs(glo))) * 1.01;
+                      4.0 * (double)N * 0x1p-52 * (ghi - glo + fabs(glo)) +
+                      16.0 * 0x1p-46 * scale + 2.0 * 0x1p-42 * (ghi - glo + fabs(glo))) * 1.01;
   double lp = 0.0, en = 0.0, cf = 0.0, bd = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
-    const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
+    const double mu = fmax(eigen_idx_df(wk, ddf, edf, N, idx, glo, ghi), 0.0);
     thermal_add(sqrt(mu), beta, lp, en, cf);
     const double mlo = fmax(mu - dmu, 0.0);
     const double slope = (mlo > 0.0) ? fmin(0.125 * beta * beta, 0.25 * beta / sqrt(mlo)) : 0.125 * beta * beta;
