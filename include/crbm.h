@@ -340,6 +340,19 @@ CRBM_API int crbm_probe_peaks(crbm_ctx* ctx, double* fp32_tflops, double* fp64_t
 CRBM_API int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc,
                        double* best_us_per_proposal);
 
+/* Choose the kernel of later proposals (crbm_run, crbm_run_batch, graphs
+ * created afterwards) for eligible jobs: enable = 1 (default) runs them on the
+ * tensor-core form, enable = 0 on the table kernel.  Eligible: CRBM_ISING,
+ * CRBM_MIXED, L = 128, K <= 4, k <= 6.  There the three convolutions of a
+ * proposal (Eqs. B2, B3 and the pre-activations of F, Eq. 13) are tcgen05
+ * MMAs on fp16 operands: 0/1 units and integer digits of the filters
+ * (W = q (c2 2^22 + c1 2^11 + c0)), whose sums are exact in FP32; the chain
+ * and every decision are the same as the table kernel's and the FP64 path's,
+ * the FP32 free energy carries its own certified bound, and the Bernoulli
+ * redo counts differ.  Has no effect when the device lacks the shared memory.
+ * Errors: CRBM_EINVAL. */
+CRBM_API int crbm_set_tensor_cores(crbm_ctx* ctx, int enable);
+
 /* Wait for the job's last enqueued work and check the device error flag.
  * Errors: CRBM_ECUDA, CRBM_ETIMEOUT (a device wait hit its iteration cap). */
 CRBM_API int crbm_sync(crbm_ctx* ctx, int job_id);

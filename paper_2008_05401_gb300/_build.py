@@ -20,6 +20,7 @@ LIB = os.path.join(PKG, "libcrbm.so")
 SOURCES = ["crbm_kernels.cu", "crbm_api.cu", "crbm_tempering.cu", "crbm_analysis.cu", "crbm_train.cu",
            "crbm_step_ising_fp64_t256.cu",
            "crbm_step_ising_mixed_t256.cu",
+           "crbm_step_tc.cu",
            "crbm_step_kitaev_fp64_t256.cu",
            "crbm_step_kitaev_fp64_t128.cu",
            "crbm_step_kitaev_fp64_t64.cu",

@@ -70,6 +70,7 @@ _SIGS = {
     "crbm_probe_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
+    "crbm_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
@@ -242,6 +243,10 @@ def crbm_sync(ctx, job_id):
     _check(ctx, load().crbm_sync(ctx, job_id))
 
 
+def crbm_set_tensor_cores(ctx, enable):
+    _check(ctx, load().crbm_set_tensor_cores(ctx, int(enable)))
+
+
 def crbm_read_energies(ctx, job_id, n):
     lp, F, E = (np.empty(n) for _ in range(3))
     _check(ctx, load().crbm_read_energies(ctx, job_id, _ptr(lp), _ptr(F), _ptr(E)))
@@ -378,6 +383,11 @@ class Context:
     def update_model(self, model_id, W, v_bias, h_bias):
         """New parameters for an existing model (same K, k)."""
         crbm_update_model(self.h, model_id, W, v_bias, h_bias)
+
+    def set_tensor_cores(self, enable: bool):
+        """Run later proposals of eligible jobs (Ising, mixed, L = 128, K <= 4,
+        k <= 6) on the tensor-core kernel (True, default) or the table kernel."""
+        crbm_set_tensor_cores(self.h, enable)
 
     def tune(self, model_id, L, precision=FP64):
         """Pick the fastest chains-per-CTA for (model, L); returns (nc, us per chain-proposal)."""

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <map>
 #include <tuple>
 #include <cstdio>
@@ -33,6 +34,10 @@ struct Model {
   float hb32[kMaxK] = {}, hb_hi[kMaxK] = {}, hb_lo[kMaxK] = {};
   float vb32 = 0.f;
   float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f;
+  // tensor-core form (Ising, K <= 4, k <= 6): filter-digit operand images
+  uint4* d_tc = nullptr;
+  size_t tc_bytes = 0;
+  float tq2 = 0.f, tq1 = 0.f, tq0 = 0.f, tc0h = 0.f, tc0v = 0.f, tc1 = 0.f, tcft = 0.f;
 };
 
 struct Layout {
@@ -116,7 +121,7 @@ struct crbm_ctx {
   // side streams and events of a batch whose jobs need launches of different
   // CTA sizes: the launches fork from the caller's stream and join it again,
   // so they run side by side
-  static constexpr int kSide = 3;
+  static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
   struct Graph {
@@ -129,6 +134,9 @@ struct crbm_ctx {
   std::vector<Graph> graphs;
   // chains per CTA chosen by crbm_tune for (kind, L, K, k)
   std::map<std::tuple<int, int, int, int>, int> tuned;
+  // proposals of eligible jobs (crbm_step_tc.cu) run on the tensor-core form;
+  // tc_ok: the device grants its shared memory
+  bool use_tc = true, tc_ok = false;
 };
 
 static int fail(crbm_ctx* c, int code, const char* fmt, ...) {
@@ -192,6 +200,16 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
     d.bd = m.d_f32 + m.nlut;
     d.fh = m.d_f32 + 2 * m.nlut;
     d.fl = m.d_f32 + 3 * m.nlut;
+  }
+  if (m.d_tc) {
+    d.tcw = m.d_tc;
+    d.tq2 = m.tq2;
+    d.tq1 = m.tq1;
+    d.tq0 = m.tq0;
+    d.tc0h = m.tc0h;
+    d.tc0v = m.tc0v;
+    d.tc1 = m.tc1;
+    d.tcft = m.tcft;
   }
   if (m.d_q) {
     d.fd4 = m.d_q;
@@ -277,20 +295,61 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
   return CRBM_OK;
 }
 
+// Whether the proposals of job j run on the tensor-core form: a property of
+// the job alone (kind, precision, lattice, filter bank), so that its results
+// are the same alone or batched.
+static bool on_tc(const crbm_ctx* ctx, const Job& j, int prec, int mode) {
+  const Model& m = ctx->models[j.model];
+  return ctx->use_tc && ctx->tc_ok && mode == 0 && m.d_tc && !m.edge && tc_supported(j.kind, prec, j.L, m.K, m.k);
+}
+
+// One launch of the tensor-core kernel: one CTA per chain.
+static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, cudaStream_t st) {
+  LaunchParams p;
+  memset(&p, 0, sizeof p);
+  p.n_jobs = (int)ids.size();
+  p.S = S;
+  p.g = g;
+  p.correct = correct;
+  p.mode = 0;
+  p.err = ctx->d_err;
+  int tiles = 0;
+  size_t smem = 0;
+  for (size_t i = 0; i < ids.size(); ++i) {
+    const Job& j = ctx->jobs[ids[i]];
+    const Model& m = ctx->models[j.model];
+    p.tile_begin[i] = tiles;
+    p.job[i] = make_jobdev(ctx, j);
+    tiles += j.n;
+    smem = std::max(smem, tc_smem_bytes(m.K, m.k));
+  }
+  p.tile_begin[ids.size()] = tiles;
+  if (tiles == 0) return CRBM_OK;
+  CK(launch_tc(p, tiles, smem, st), "kernel launch");
+  return CRBM_OK;
+}
+
 static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
                        cudaStream_t st, const Job* partner = nullptr) {
+  // parts: (CTA size, jobs); CTA size 0 = the tensor-core form
   std::vector<std::pair<int, std::vector<int>>> parts;
-  for (int nt : {256, 128, 64, 32}) {
+  for (int nt : {0, 256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
-      if (j.n > 0 && threads_for(j.kind, j.N) == nt) part.push_back(id);
+      if (j.n == 0) continue;
+      const bool tc = !partner && on_tc(ctx, j, prec, mode);
+      if (nt == 0 ? tc : (!tc && threads_for(j.kind, j.N) == nt)) part.push_back(id);
     }
     if (!part.empty()) parts.emplace_back(nt, part);
   }
+  auto launch_part = [&](const std::pair<int, std::vector<int>>& pt, cudaStream_t s) {
+    return pt.first == 0 ? launch_tc_group(ctx, pt.second, S, g, correct, s)
+                         : launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, s, partner);
+  };
   if (parts.size() <= 1) {
     for (auto& pt : parts) {
-      const int rc = launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, st, partner);
+      const int rc = launch_part(pt, st);
       if (rc) return rc;
     }
     return CRBM_OK;
@@ -300,8 +359,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
   CK(cudaEventRecord(ctx->fork, st), "fork event");
   for (size_t i = 1; i < parts.size(); ++i) CK(cudaStreamWaitEvent(ctx->side[i - 1], ctx->fork, 0), "fork wait");
   int rc = CRBM_OK;
-  for (size_t i = 0; i < parts.size() && rc == CRBM_OK; ++i)
-    rc = launch_group(ctx, parts[i].second, S, g, correct, prec, mode, parts[i].first, i == 0 ? st : ctx->side[i - 1]);
+  for (size_t i = 0; i < parts.size() && rc == CRBM_OK; ++i) rc = launch_part(parts[i], i == 0 ? st : ctx->side[i - 1]);
   for (size_t i = 1; i < parts.size(); ++i) {
     CK(cudaEventRecord(ctx->join[i - 1], ctx->side[i - 1]), "join event");
     CK(cudaStreamWaitEvent(st, ctx->join[i - 1], 0), "join wait");
@@ -332,6 +390,10 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     e = set_smem_limits((size_t)optin);
+    if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(4, 6)) {
+      e = tc_set_smem_limit();
+      ctx->tc_ok = e == cudaSuccess;
+    }
   }
   if (e != cudaSuccess) {
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -350,6 +412,7 @@ int crbm_destroy(crbm_ctx* ctx) {
     if (m.d_f64) cudaFree(m.d_f64);
     if (m.d_f32) cudaFree(m.d_f32);
     if (m.d_q) cudaFree(m.d_q);
+    if (m.d_tc) cudaFree(m.d_tc);
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (auto& gr : ctx->graphs) {
@@ -367,6 +430,101 @@ int crbm_destroy(crbm_ctx* ctx) {
 }
 
 const char* crbm_last_error(const crbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// fp16 bit pattern of an integer |v| <= 2048 (exact).
+static uint16_t half_of_int(int v) {
+  if (v == 0) return 0;
+  const uint16_t sgn = v < 0 ? 0x8000u : 0u;
+  unsigned a = (unsigned)(v < 0 ? -v : v);
+  int e = 0;
+  while ((a >> (e + 1)) != 0u) ++e;                    // 2^e <= a < 2^(e+1), e <= 11
+  const unsigned man = e <= 10 ? ((a << (10 - e)) & 0x3FFu) : 0u;
+  return (uint16_t)(sgn | (unsigned)((e + 15) << 10) | man);
+}
+
+// Operand images and error constants of the tensor-core form (Ising, K <= 4,
+// k <= 6; crbm_step_tc.cu).  Every weight becomes W ~ qf (c2 2^22 + c1 2^11 + c0)
+// with qf = 2^e, |W / qf| <= 2^31, balanced digits c0, c1 in [-1024, 1023]
+// and |c2| <= 513, all exact in fp16.  Images (K-major, no swizzle: element
+// (row kk, column n) at (kk/8) LBO + (n/8) 128 + (n%8) 16 + (kk%8) 2):
+//   hidden / free energy, per kernel row a: K=16 x N=96, column n = e*32 + f*8 + jj
+//     holds digit e (c2, c1, c0) of W[f][a][kk - jj];
+//   visible, per (f, a, step s): K=16 x N=32, column n = e*16 + jj holds digit e of
+//     W[f][a][b], b = jj + 8 - kk (s = 0) or jj - kk for kk >= 8 (s = 1).
+static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, double v_bias, const double* h_bias,
+                    double sh, double sv, double common, bool alloc) {
+  double maxw = 0.0, maxhb = 0.0;
+  for (int i = 0; i < K * k * k; ++i) maxw = std::fmax(maxw, std::fabs(W[i]));
+  for (int f = 0; f < K; ++f) maxhb = std::fmax(maxhb, std::fabs(h_bias[f]));
+  const int e0 = (maxw > 0.0 ? (int)std::ceil(std::log2(maxw)) : -60) - 31;
+  const double qf = std::ldexp(1.0, e0);
+  auto bal = [](long long x, long long& rest) {
+    long long r = ((x % 2048) + 2048) % 2048;
+    if (r >= 1024) r -= 2048;
+    rest = (x - r) / 2048;
+    return r;
+  };
+  std::vector<int> dg((size_t)3 * K * k * k);      // digits e = 0, 1, 2 (c2, c1, c0) of W[f][a][b]
+  double e2v = 0.0, e2h = 0.0, t1 = 0.0;
+  for (int f = 0; f < K; ++f) {
+    double ef = 0.0, tf = 0.0;
+    for (int ab = 0; ab < k * k; ++ab) {
+      const size_t idx = (size_t)f * k * k + ab;
+      const long long wi = std::llround(W[idx] / qf);
+      long long w1, w2;
+      const long long c0 = bal(wi, w1), c1 = bal(w1, w2);
+      dg[0 * (size_t)K * k * k + idx] = (int)w2;
+      dg[1 * (size_t)K * k * k + idx] = (int)c1;
+      dg[2 * (size_t)K * k * k + idx] = (int)c0;
+      ef += qf * (0.5 + (double)std::llabs(c0));       // |W - qf (c2 2^22 + c1 2^11)|
+      tf += qf * (2048.0 * (double)std::llabs(c1) + (double)std::llabs(c0));
+    }
+    e2h = std::fmax(e2h, ef);
+    e2v += ef;
+    t1 = std::fmax(t1, tf);
+  }
+  auto digit = [&](int e, int f, int a, int b) { return dg[((size_t)e * K + f) * k * k + (size_t)a * k + b]; };
+  const size_t bh = (size_t)k * 3072, bytes = bh + (size_t)K * k * 2 * 1024;
+  std::vector<uint16_t> img(bytes / 2, 0);
+  for (int a = 0; a < k; ++a)
+    for (int kk = 0; kk < 16; ++kk)
+      for (int n = 0; n < 96; ++n) {
+        const int e = n / 32, f = (n / 8) % 4, jj = n % 8, b = kk - jj;
+        if (f >= K || b < 0 || b >= k) continue;
+        const size_t off = (size_t)a * 3072 + (kk / 8) * 1536 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2;
+        img[off / 2] = half_of_int(digit(e, f, a, b));
+      }
+  for (int f = 0; f < K; ++f)
+    for (int a = 0; a < k; ++a)
+      for (int st = 0; st < 2; ++st)
+        for (int kk = 0; kk < 16; ++kk)
+          for (int n = 0; n < 32; ++n) {
+            const int e = n / 16, jj = n % 16;
+            const int b = st == 0 ? jj + 8 - kk : (kk >= 8 ? jj - kk : -1);
+            if (b < 0 || b >= k) continue;
+            const size_t off = bh + ((size_t)(f * k + a) * 2 + st) * 1024 + (kk / 8) * 512 + (n / 8) * 128 +
+                               (n % 8) * 16 + (kk % 8) * 2;
+            img[off / 2] = half_of_int(digit(e, f, a, b));
+          }
+  m.tq2 = (float)std::ldexp(qf, 22);
+  m.tq1 = (float)std::ldexp(qf, 11);
+  m.tq0 = (float)qf;
+  // decisions (decide32 units of 2^-32): x = fl(fl(c2-sum q2 + c1-sum q1) + hb32) is
+  // within quantisation E2 + 2^-24 (2 |x| + 2 |hb|) of the exact pre-activation,
+  // the FP64 path's own sum within 2^-50 S; slope of sigma <= 1/4; factor 2 of safety
+  const double u24 = std::ldexp(1.0, -24), u50 = std::ldexp(1.0, -50);
+  m.tc0h = (float)std::ldexp(2.0 * (common + 0.25 * (e2h + 2.0 * u24 * maxhb + u50 * sh)) + 1e-14, 32);
+  m.tc0v = (float)std::ldexp(2.0 * (common + 0.25 * (e2v + 2.0 * u24 * std::fabs(v_bias) + u50 * sv)) + 1e-14, 32);
+  m.tc1 = (float)std::ldexp(2.0 * (std::ldexp(1.0, -25) + 0.25 * 2.0 * u24), 32);
+  // free energy, per unit beyond the 2^-23 |x| the kernel sums: quantisation
+  // k^2 qf / 2, rounding of the low digits 2^-24 T1, of hb 3 2^-24 |hb|; factor 1.5
+  m.tcft = (float)(1.5 * (0.5 * k * k * qf + u24 * t1 + 3.0 * u24 * maxhb + u50 * sh));
+  if (alloc) CK(cudaMalloc(&m.d_tc, bytes), "cudaMalloc tensor-core images");
+  else if (!m.d_tc || m.tc_bytes != bytes) return fail(ctx, CRBM_EINVAL, "tensor-core image size changed");
+  m.tc_bytes = bytes;
+  CK(cudaMemcpy(m.d_tc, img.data(), bytes, cudaMemcpyHostToDevice), "tensor-core image copy");
+  return CRBM_OK;
+}
 
 // Host tables and error constants of a model from its parameters, copied to
 // the device (into new buffers when alloc, else into the model's own).
@@ -463,6 +621,10 @@ static int build_model(crbm_ctx* ctx, Model& m, int kind, int K, int k, const do
   }
   m.nlut = nlut;
   m.nq = nq;
+  if (kind == kIsing && K <= 4 && k <= 6) {
+    const int rc = build_tc(ctx, m, K, k, W, v_bias, h_bias, sh, sv, common, alloc);
+    if (rc) return rc;
+  }
   if (alloc) CK(cudaMalloc(&m.d_q, 3 * nq * sizeof(float4)), "cudaMalloc tables");
   CK(cudaMemcpy(m.d_q, q4.data(), 3 * nq * sizeof(float4), cudaMemcpyHostToDevice), "table copy");
   if (alloc) {
@@ -1050,6 +1212,13 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
   ctx->tuned[std::make_tuple(m.kind, L, m.K, m.k)] = best;
   if (best_nc) *best_nc = best;
   if (best_ms) *best_ms = (double)best_t * 1e3 / 4.0;     // microseconds per chain-proposal
+  return CRBM_OK;
+}
+
+int crbm_set_tensor_cores(crbm_ctx* ctx, int enable) {
+  if (!ctx) return CRBM_EINVAL;
+  if (enable != 0 && enable != 1) return fail(ctx, CRBM_EINVAL, "enable must be 0 or 1");
+  ctx->use_tc = enable == 1;
   return CRBM_OK;
 }
 

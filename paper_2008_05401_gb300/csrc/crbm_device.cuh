@@ -66,6 +66,11 @@ struct JobDev {
   const float4* fd4;            // [k][2^k] filter-interleaved, K <= 4
   const float4* fh4;
   const float4* fl4;
+  // tensor-core form (Ising, L = 128, K <= 4, k <= 6; crbm_step_tc.cu):
+  // operand images of the filter digits, null when the model has none
+  const uint4* tcw;
+  float tq2, tq1, tq0;          // digit scales qf 2^22, qf 2^11, qf
+  float tc0h, tc0v, tc1, tcft;  // certified error constants of that form
   uint64_t seed, cid_base;
   uint32_t rk[20];              // Philox round keys (k0 + r W0, k1 + r W1), r = 0..9
   unsigned long long* step;     // device-resident step counter of the job (proposals made)

@@ -1,0 +1,737 @@
+// Tensor-core form of the fused CRBM proposal + Metropolis-Hastings kernel:
+// Ising kind, mixed precision, 128 x 128 lattices, K <= 4 filters of side
+// k <= 6, mode 0 (S proposals of g Gibbs steps).  One chain per CTA.  The
+// chain is the table kernel's chain: the same Philox words per unit, and every
+// Bernoulli and MH decision the FP64 path's.
+//
+// The three convolutions of a proposal are tcgen05 MMAs with FP32
+// accumulators in tensor memory, D[i][n] = sum_kk A[i][kk] B[kk][n] over the
+// M = 128 lattice rows i:
+//   hidden pre-activations of v  (Eq. B2; Eq. 12), one MMA per kernel row a
+//       reading the lattice rows i + a;
+//   visible pre-activations of h (Eq. B3), one MMA per (filter, kernel row a)
+//       reading the hidden rows i - a;
+//   hidden pre-activations of v' for F(v') (Eq. 13).
+// A operands: the 0/1 units in fp16, K-major without swizzle, rows 16 bytes
+// apart and 8-column groups one LBO apart, so the operand of kernel row a is
+// the same array started a rows further on; periodic halos are copies.
+// B operands: banded Toeplitz images of the filters (built on the host).  Each
+// weight is written as W = qf (c2 2^22 + c1 2^11 + c0), qf a power of two and
+// integer digits |c| <= 1024 (exact in fp16).  Units times digits summed over
+// a window are integers below 2^17, exact in FP32 whatever the order of the
+// tensor core's additions, so the only roundings are the quantisation
+// (|W - qf W_int| <= qf / 2) and the FP32 combination of the digit sums here.
+// Bernoulli decisions use c2, c1 and the certified margin of decide32 with this
+// form's constants (the FP64 tables decide inside it); the free energy uses all
+// three digits and carries its error bound into the MH decision like the table
+// kernel's FP32 free energy.
+//
+// Schedule per Gibbs step: 16 hidden tiles of 8 columns (H) and 8 visible
+// tiles of 16 columns (V), interleaved so that a V tile runs as soon as the
+// three H tiles it reads are done (H15 H0 H1 H2 V0 H3 H4 V1 ... H13 H14 V6 V7);
+// then 16 free-energy tiles (F).  Warp-specialised pipeline: the control warp
+// issues each stage's MMAs into one of four tensor-memory buffers and commits
+// them to that buffer's `full` mbarrier; the 16 epilogue warps (warp w: lanes
+// 32 (w % 4) .. + 31 = lattice rows, w / 4 = filter or column quarter) take
+// the stages in the same order, read the accumulators, arrive on the buffer's
+// `empty` mbarrier and make the stage's decisions.  A V stage's MMAs wait on
+// the `hrdy` mbarriers of its three H tiles (every warp's fp16 hidden units
+// written and fenced), the F stages on `vrdy` (every warp's v' written); CTA
+// barriers only at the end of a proposal (reductions, MH) and between Gibbs
+// steps.
+#include "crbm_step.cuh"
+
+namespace crbm {
+namespace {
+
+constexpr int kL = 128, kN = kL * kL, kWords = kN / 32;   // 4 words per lattice row
+constexpr int kEpi = 512, kThr = kEpi + 32;                // 16 epilogue warps + control warp
+constexpr int kRows = 136, kLbo = kRows * 16;              // one 8-column group of 136 rows
+constexpr int kOpv = 17 * kLbo;                            // 136 columns
+constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a V buffer: 3 groups
+constexpr int kVbuf = 4 * kPlane3;
+constexpr int kP15 = 4 * kLbo;
+constexpr int kBhA = 3072;                                 // per kernel row: K=16 x N=96
+constexpr int kBvS = 1024;                                 // per (filter, row, step): K=16 x N=32
+constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
+
+struct TcLayout {
+  uint32_t opv[2], vbuf, p15, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int K, int k) {
+  TcLayout l;
+  uint32_t o = 0;
+  l.opv[0] = o; o += kOpv;            // lattice operand (v or v', fp16), two buffers
+  l.opv[1] = o; o += kOpv;
+  l.vbuf = o; o += 2 * kVbuf;         // hidden operands of V tiles, two buffers of 3 groups
+  l.p15 = o; o += kP15;               // hidden tile 15 (columns 120..127), kept for V7
+  l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
+  l.bv = o; o += (uint32_t)(K * k * 2 * kBvS);   // visible
+  l.vbits = o; o += kWords * 4;       // packed current lattice
+  l.pb[0] = o; o += kWords * 4;       // packed proposals (ping-pong over Gibbs steps)
+  l.pb[1] = o; o += kWords * 4;
+  l.hbits = o; o += 4 * kWords * 4;   // packed hidden units, one plane per filter
+  l.scratch = o; o += 256 * 8;
+  l.ch = o; o += (uint32_t)align16(sizeof(ChainSm));
+  l.misc = o; o += 512;               // mbarriers, TMEM address, counters, reduction slots
+  l.total = o;
+  return l;
+}
+
+__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, rows 16 bytes apart
+// (SBO = 128 between 8-row groups), LBO between 8-column groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor: fp16 x fp16 -> FP32, A and B K-major, M = 128.
+__host__ __device__ constexpr uint32_t umma_idesc(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" :: "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tm_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tm_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Wait for the given phase parity of an mbarrier, for at most about a second
+// of SM clock; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+// CTA barrier with the tensor-memory and proxy fences around it.
+__device__ __forceinline__ void cta_sync() {
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(mbar) : "memory");
+}
+
+enum { kStH = 0, kStV = 1, kStF = 2 };
+
+// Stage z (0..23) of a Gibbs step: H15 H0 H1 H2, then (V_u H_{2u+3} H_{2u+4})
+// for u = 0..5, then V6 V7.  V_u reads H tiles 2u-1, 2u, 2u+1 (mod 16), all
+// finished two stages before it, so its MMAs can be issued one stage ahead.
+__device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
+  if (z < 4) {
+    type = kStH;
+    tile = z == 0 ? 15 : z - 1;
+  } else if (z >= 22) {
+    type = kStV;
+    tile = z - 16;
+  } else {
+    const int u = (z - 4) / 3, r = (z - 4) - 3 * u;
+    type = r == 0 ? kStV : kStH;
+    tile = r == 0 ? u : 2 * u + 2 + r;
+  }
+}
+
+// MMAs of one stage into tensor-memory columns dcol, then a commit to mbar.
+// H/F tile t: N = 64 (digits c2, c1) or 96 (c2, c1, c0), columns e*32 + f*8 + jj.
+// V tile u: N = 32, columns e*16 + jj; slots s, s+1 of the tile's V buffer.
+// dopv / dvbuf / dbh / dbv: descriptors of the operand bases (start fields
+// advance by byte offset / 16).  KT, kT > 0 fix K and k at compile time, so
+// that the issue sequence is straight-line code with immediate offsets: the
+// single issuing thread otherwise spends far longer per MMA than the tensor
+// core does on these small shapes.
+template <int KT, int kT>
+__device__ __forceinline__ void issue_stage(int type, int tile, uint32_t dcol, uint64_t dopv, uint64_t dvbuf,
+                                            uint64_t dbh, uint64_t dbv, int Kr, int kr, uint32_t mbar) {
+  const int K = KT ? KT : Kr, k = kT ? kT : kr;
+  if (type != kStV) {
+    const uint32_t id = type == kStH ? umma_idesc(64) : umma_idesc(96);
+    const uint64_t a0 = dopv + (uint64_t)(tile * (kLbo >> 4));
+#pragma unroll
+    for (int a = 0; a < (kT ? kT : 8); ++a)
+      if (kT || a < k) umma(dcol, a0 + (uint64_t)a, dbh + (uint64_t)(a * (kBhA >> 4)), id, a > 0);
+  } else {
+    const uint32_t id = umma_idesc(32);
+    const uint64_t a0 = dvbuf + (uint64_t)((tile & 1) * (kVbuf >> 4));
+#pragma unroll
+    for (int f = 0; f < (KT ? KT : 4); ++f)
+#pragma unroll
+      for (int a = 0; a < (kT ? kT : 8); ++a)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if ((KT || f < K) && (kT || a < k)) {
+            const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - a) * 16);
+            const uint32_t boff = (uint32_t)(((f * k + a) * 2 + s) * kBvS);
+            umma(dcol, a0 + (aoff >> 4), dbv + (boff >> 4), id, (f | a | s) != 0);
+          }
+  }
+  umma_commit(mbar);
+}
+
+// FP64 redo of hidden unit (f, n) from the packed source lattice: the FP64
+// path's sum (h_bias, then kernel rows a = 0..k-1 from the FP64 tables).
+static __device__ __noinline__ uint32_t tc_redo_hidden(const JobDev& jb, int f, const uint32_t* v, int n,
+                                                       uint32_t w) {
+  const int k = jb.k, T = 1 << k, i = n >> 7, j = n & (kL - 1);
+  double x = jb.hb[f];
+  for (int a = 0; a < k; ++a) x += __ldg(jb.f64 + (f * k + a) * T + row_window(v, kL, (i + a) & (kL - 1), j, k));
+  return decide64(x, w);
+}
+
+// fp16 units of a packed lattice into a lattice operand (136 x 136 with the
+// periodic copies of rows and columns 0..7).
+__device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t* bits, int tid, int nthr) {
+  const unsigned char* by = (const unsigned char*)bits;
+  for (int q = tid; q < kRows * 17; q += nthr) {
+    const int G = q / kRows, r = q - G * kRows;
+    const uint32_t x = by[(r & (kL - 1)) * (kL / 8) + (G & 15)];
+    const uint32_t z = x | (x << 15);       // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
+    uint4 o;
+    o.x = ((z >> 0) & 0x10001u) * 0x3C00u;
+    o.y = ((z >> 2) & 0x10001u) * 0x3C00u;
+    o.z = ((z >> 4) & 0x10001u) * 0x3C00u;
+    o.w = ((z >> 6) & 0x10001u) * 0x3C00u;
+    *(uint4*)(smem + opv + (uint32_t)G * kLbo + (uint32_t)r * 16) = o;
+  }
+}
+
+// H tile t, thread (row i, filter f), digit sums s2, s1 of its 8 units
+// (f, i, 8t .. 8t+7): the hidden units, packed and as fp16 operands.
+__device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
+                                           const float (&s2)[8], const float (&s1)[8], int i, int f, int t,
+                                           uint32_t tag, uint32_t step, uint32_t cid, const uint32_t* src,
+                                           unsigned& nrec) {
+  const int n0 = i * kL + 8 * t;
+  const uint32_t q0 = (uint32_t)(n0 >> 2);
+  const uint4 w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
+  const uint4 w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
+  const float hb = jb.hb32[f];
+  uint32_t byte = 0u, hv[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const float x = fmaf(s2[jj], jb.tq2, s1[jj] * jb.tq1) + hb;
+    const uint32_t w = pick(jj < 4 ? w0 : w1, jj & 3);
+    uint32_t bit = decide32(x, w, jb.tc0h, jb.tc1);
+    if (bit == 2u) {
+      bit = tc_redo_hidden(jb, f, src, n0 + jj, w);
+      ++nrec;
+    }
+    byte |= bit << jj;
+    hv[jj >> 1] |= bit ? (0x3C00u << (16 * (jj & 1))) : 0u;
+  }
+  smem[ly.hbits + (uint32_t)f * (kWords * 4) + (uint32_t)(n0 >> 3)] = (unsigned char)byte;
+  const uint4 h4 = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+  // rows i + 8 of the V operands; rows 120..127 also as rows -8..-1
+  auto put = [&](uint32_t base) {
+    *(uint4*)(smem + base + (uint32_t)(i + 8) * 16) = h4;
+    if (i >= kL - 8) *(uint4*)(smem + base + (uint32_t)(i - (kL - 8)) * 16) = h4;
+  };
+  const int u = t >> 1;
+  const uint32_t pf = (uint32_t)f * kPlane3;
+  if ((t & 1) == 0) {
+    put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 1 * kLbo);           // middle slot of V_u
+  } else {
+    if (t != 15) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);   // last slot of V_u
+    else put(ly.p15 + (uint32_t)f * kLbo);
+    put(ly.vbuf + (uint32_t)((u + 1) & 1) * kVbuf + pf);                // first slot of V_{u+1}
+  }
+}
+
+// V tile u, thread (row i, column quarter cq), digit sums of its 4 units
+// (i, 16u + 4cq .. + 3): the visible units, packed and as fp16 F operands.
+__device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
+                                            const float (&s2)[4], const float (&s1)[4], int i, int cq, int u,
+                                            uint32_t tag, uint32_t step, uint32_t cid, uint32_t* dbits,
+                                            uint32_t opv, uint32_t hbar, uint32_t parity, int* err,
+                                            unsigned& nrec) {
+  const int j0 = 16 * u + 4 * cq, n0 = i * kL + j0;
+  const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n0 >> 2), tag, step, cid), jb.rk);
+  const uint32_t* hb = (const uint32_t*)(smem + ly.hbits);
+  uint32_t nib = 0u, hv[2] = {0u, 0u};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float x = fmaf(s2[t], jb.tq2, s1[t] * jb.tq1) + jb.vb32;
+    uint32_t bit = decide32(x, pick(w, t), jb.tc0v, jb.tc1);
+    if (bit == 2u) {
+      // the packed hidden units of H tiles 2u-1, 2u, 2u+1 come from other warps:
+      // their hrdy mbarriers (completed before this tile's MMAs) order them
+      const int tt[3] = {(2 * u + 15) & 15, 2 * u, 2 * u + 1};
+      for (int q = 0; q < 3; ++q)
+        if (!mbar_wait(hbar + 8u * (uint32_t)tt[q], parity)) atomicExch(err, kErrTimeout);
+      bit = recompute_visible(jb, hb, kWords, n0 + t, pick(w, t));
+      ++nrec;
+    }
+    nib |= bit << t;
+    hv[t >> 1] |= bit ? (0x3C00u << (16 * (t & 1))) : 0u;
+  }
+  atomicOr(dbits + (n0 >> 5), nib << (n0 & 31));
+  const uint2 h2 = make_uint2(hv[0], hv[1]);
+  const uint32_t off = opv + (uint32_t)(j0 >> 3) * kLbo + (uint32_t)(j0 & 7) * 2;
+  *(uint2*)(smem + off + (uint32_t)i * 16) = h2;
+  if (i < 8) *(uint2*)(smem + off + (uint32_t)(i + kL) * 16) = h2;
+  if (j0 < 8) {        // columns 128..135 repeat columns 0..7
+    const uint32_t o2 = opv + 16 * kLbo + (uint32_t)(j0 & 7) * 2;
+    *(uint2*)(smem + o2 + (uint32_t)i * 16) = h2;
+    if (i < 8) *(uint2*)(smem + o2 + (uint32_t)(i + kL) * 16) = h2;
+  }
+}
+
+// F tile, thread (row i, filter f), digit sums of its 8 units: softplus of the
+// pre-activations, pairwise sum, Kahan-added into s32 (c32 its compensation).
+__device__ __forceinline__ void epi_free(const JobDev& jb, const float (&s2)[8], const float (&s1)[8],
+                                         const float (&s0)[8], int f, float& s32, float& c32, float& sabs,
+                                         float& ssp) {
+  const float hb = jb.hb32[f];
+  float sp[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const float xn = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, s0[jj] * jb.tq0));
+    const float x = xn + hb;
+    sp[jj] = softplus32(x);
+    sabs += fabsf(x);
+  }
+  const float us = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]));
+  ssp += us;
+  const float y = us - c32;
+  const float tt = s32 + y;
+  c32 = (tt - s32) - y;
+  s32 = tt;
+}
+
+// mbarriers in the misc area: full[4] (count 1, MMA commits), empty[4] (count
+// 16, epilogue warps), hrdy[16] (count 16: H tile's fp16 units written),
+// vrdy (count 16: every V tile's v' written), fin (count 1, last commit).
+constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kNbar = 26;
+constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = kMiscTslot + 8, kMiscRed = kMiscNrec + 8;   // reduction: 16 x 16 B
+
+template <int KT, int kT>
+__global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
+  int jid = 0;
+  while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
+  const JobDev& jb = prm.job[jid];
+  const int c = (int)blockIdx.x - prm.tile_begin[jid];      // one chain per CTA
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool epi = warp < 16;
+  const int K = jb.K, k = jb.k;
+  const TcLayout ly = tc_layout(K, k);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t sbase = sm_addr(smem);
+  uint32_t* vbits = (uint32_t*)(smem + ly.vbits);
+  ChainSm& ch = *(ChainSm*)(smem + ly.ch);
+  double* scratch = (double*)(smem + ly.scratch);
+  const uint32_t bar0 = sbase + ly.misc;
+  auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
+  uint32_t* tslot = (uint32_t*)(smem + ly.misc + kMiscTslot);
+  unsigned long long* nrec_sm = (unsigned long long*)(smem + ly.misc + kMiscNrec);
+  unsigned char* red = smem + ly.misc + kMiscRed;
+  const uint32_t cid = (uint32_t)(jb.cid_base + (uint64_t)c);
+
+  const int nimg = (k * kBhA + K * k * 2 * kBvS) / 16;     // B images: hidden/free, then visible
+  for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
+  for (int w = tid; w < kWords; w += kThr) {
+    vbits[w] = jb.bits[(size_t)c * kWords + w];
+    ((uint32_t*)(smem + ly.pb[0]))[w] = 0u;
+    ((uint32_t*)(smem + ly.pb[1]))[w] = 0u;
+  }
+  if (tid == 0) {
+    ch.F = jb.F[c];
+    ch.Fb = jb.Fb[c];
+    ch.lpb = jb.Lb[c];
+    ch.lppb = 0.0;
+    ch.lp = jb.logpi[c];
+    ch.E = jb.Ephys[c];
+    for (int o = 0; o < kNobs; ++o) {
+      ch.ot[o] = jb.obs_t[(size_t)c * kNobs + o];
+      ch.os[o] = jb.obs[(size_t)c * kNobs + o];
+    }
+    ch.beta = 1.0 / jb.T[c];
+    ch.acc = 0ull;
+    ch.rec_mh = 0ull;
+    ch.flag_rec = 0;
+    ch.flag_acc = 0;
+    *nrec_sm = 0ull;
+    for (int b = 0; b < kNbuf; ++b) {
+      mbar_init(bar(kBarFull + b), 1);
+      mbar_init(bar(kBarEmpty + b), 16);
+    }
+    for (int t = 0; t < 16; ++t) mbar_init(bar(kBarH + t), 16);
+    mbar_init(bar(kBarV), 16);
+    mbar_init(bar(kBarFin), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 16) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(sm_addr(tslot)),
+                 "r"(kTmCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  __syncthreads();
+  expand_lattice(smem, ly.opv[0], vbits, tid, kThr);
+  cta_sync();
+  const uint32_t tmem = *tslot;
+
+  // epilogue thread: lattice row i, filter / column quarter fq; its TMEM lanes
+  const int i = 32 * (warp & 3) + lane, fq = warp >> 2;
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  const bool issuer = warp == 16 && lane == 0;
+  Grp g;
+  g.tpc = kEpi;
+  g.gl = tid / kEpi;
+  g.r = tid - g.gl * kEpi;
+  g.c = c;
+  g.active = epi;
+  g.cid = cid;
+  Tabs tb64;
+  memset(&tb64, 0, sizeof tb64);
+  tb64.T = 1 << k;
+  tb64.f64 = jb.f64;
+  tb64.b64 = jb.b64;
+
+  const uint64_t dopv[2] = {umma_desc(sbase + ly.opv[0], kLbo), umma_desc(sbase + ly.opv[1], kLbo)};
+  const uint64_t dvbuf = umma_desc(sbase + ly.vbuf, kLbo), dbh = umma_desc(sbase + ly.bh, 1536),
+                 dbv = umma_desc(sbase + ly.bv, 512);
+  uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
+  uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
+  bool live = true;             // false once a wait gave up: no further waits
+  unsigned nrec = 0;
+  int cur = 0;                  // lattice operand holding v
+  const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
+  auto wait_bar = [&](uint32_t b, uint32_t parity) {
+    if (live && !mbar_wait(b, parity)) {
+      live = false;
+      atomicExch(prm.err, kErrTimeout);
+    }
+  };
+  // control warp: before the MMAs of stage zc, its buffer's previous use read by every epilogue warp
+  auto mma_claim = [&]() {
+    const uint32_t b = zc & (kNbuf - 1), use = zc / kNbuf;
+    if (use > 0) wait_bar(bar(kBarEmpty + b), (use - 1) & 1u);
+    tc_fence_after();
+    return tmem + b * kTmBuf;
+  };
+  // epilogue warp: the MMAs of stage zc are done
+  auto epi_claim = [&]() {
+    const uint32_t b = zc & (kNbuf - 1), use = zc / kNbuf;
+    wait_bar(bar(kBarFull + b), use & 1u);
+    tc_fence_after();
+    return tmem + tlane + b * kTmBuf;
+  };
+  // epilogue warp: accumulators of stage zc read
+  auto epi_release = [&]() {
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar(kBarEmpty + (zc & (kNbuf - 1))));
+  };
+  // epilogue warp: its generic-proxy operand writes visible to later MMAs, then arrive
+  auto epi_publish = [&](uint32_t b) {
+    proxy_fence();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b);
+  };
+
+  for (int s = 0; s < prm.S; ++s) {
+    const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
+    int src = cur;
+    for (int sub = 0; sub < prm.g; ++sub, ++gs) {
+      uint32_t* dbits = (uint32_t*)(smem + ly.pb[sub & 1]);
+      const uint32_t* sbits = sub == 0 ? vbits : (const uint32_t*)(smem + ly.pb[(sub - 1) & 1]);
+      const uint32_t taghid = (uint32_t)(sub * (K + 1)), tagvis = (uint32_t)(sub * (K + 1) + K);
+      const uint32_t opv_dst = ly.opv[src ^ 1];
+      const uint32_t zbase = zc;
+      if (issuer) {
+        for (int z = 0; z < 24; ++z, ++zc) {
+          int ty, tl;
+          hv_stage(z, ty, tl);
+          const uint32_t d = mma_claim();
+          if (ty == kStV) {
+            wait_bar(bar(kBarH + ((2 * tl + 15) & 15)), gs & 1u);
+            wait_bar(bar(kBarH + 2 * tl), gs & 1u);
+            wait_bar(bar(kBarH + 2 * tl + 1), gs & 1u);
+            tc_fence_after();
+          }
+          issue_stage<KT, kT>(ty, tl, d, dopv[src], dvbuf, dbh, dbv, K, k, bar(kBarFull + (zc & (kNbuf - 1))));
+        }
+      } else if (epi) {
+        for (int z = 0; z < 24; ++z, ++zc) {
+          int ty, tl;
+          hv_stage(z, ty, tl);
+          const uint32_t tcol = epi_claim();
+          if (ty == kStH) {
+            if (fq < K) {
+              float s2[8], s1[8];
+              tm_ld8(tcol + 8 * fq, s2);
+              tm_ld8(tcol + 32 + 8 * fq, s1);
+              tm_wait();
+              epi_release();
+              epi_hidden(jb, smem, ly, s2, s1, i, fq, tl, taghid + (uint32_t)fq, step, cid, sbits, nrec);
+            } else {
+              epi_release();
+            }
+            if (tl == 14 && fq < K) {
+              // this thread's rows of hidden tile 15 (written by it at H15) into
+              // the last slot of V7's buffer, read last by V5, whose MMAs this
+              // warp has waited for
+              const uint32_t dst = ly.vbuf + kVbuf + (uint32_t)fq * kPlane3 + 2 * kLbo, p15 = ly.p15 + (uint32_t)fq * kLbo;
+              *(uint4*)(smem + dst + (uint32_t)(i + 8) * 16) = *(const uint4*)(smem + p15 + (uint32_t)(i + 8) * 16);
+              if (i >= kL - 8)
+                *(uint4*)(smem + dst + (uint32_t)(i - (kL - 8)) * 16) =
+                    *(const uint4*)(smem + p15 + (uint32_t)(i - (kL - 8)) * 16);
+            }
+            epi_publish(bar(kBarH + tl));
+          } else {
+            float s2[4], s1[4];
+            tm_ld4(tcol + 4 * fq, s2);
+            tm_ld4(tcol + 16 + 4 * fq, s1);
+            tm_wait();
+            epi_release();
+            epi_visible(jb, smem, ly, s2, s1, i, fq, tl, tagvis, step, cid, dbits, opv_dst, bar(kBarH), gs & 1u,
+                        prm.err, nrec);
+            if (tl == 7) epi_publish(bar(kBarV));
+          }
+        }
+      }
+      zc = zbase + 24;
+      src ^= 1;
+      if (sub + 1 < prm.g) {
+        // next Gibbs step: its source is this step's v' (every write done), and
+        // the proposal buffer it fills is cleared
+        cta_sync();
+        if (tid < kWords) ((uint32_t*)(smem + ly.pb[(sub + 1) & 1]))[tid] = 0u;
+        __syncthreads();
+      }
+    }
+    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[(prm.g - 1) & 1]);   // v'
+
+    // free energy of v' from the F tiles
+    float s32 = 0.f, c32 = 0.f, sabs = 0.f, ssp = 0.f;
+    const uint32_t zbase = zc;
+    if (issuer) {
+      for (int t = 0; t < 16; ++t, ++zc) {
+        const uint32_t d = mma_claim();
+        if (t == 0) {
+          wait_bar(bar(kBarV), (gs - 1) & 1u);
+          tc_fence_after();
+        }
+        issue_stage<KT, kT>(kStF, t, d, dopv[src], dvbuf, dbh, dbv, K, k, bar(kBarFull + (zc & (kNbuf - 1))));
+      }
+    } else if (epi) {
+      for (int t = 0; t < 16; ++t, ++zc) {
+        const uint32_t tcol = epi_claim();
+        if (fq < K) {
+          float s2[8], s1[8], s0[8];
+          tm_ld8(tcol + 8 * fq, s2);
+          tm_ld8(tcol + 32 + 8 * fq, s1);
+          tm_ld8(tcol + 64 + 8 * fq, s0);
+          tm_wait();
+          epi_release();
+          epi_free(jb, s2, s1, s0, fq, s32, c32, sabs, ssp);
+        } else {
+          epi_release();
+        }
+      }
+    }
+    zc = zbase + 16;
+    cta_sync();                                 // every v' write and F tile done
+
+    // per-warp sums: F as an exact 2^-32 fixed-point integer, its error-bound
+    // part in FP32, ones and unequal nearest-neighbour pairs of v'
+    if (epi) {
+      long long fs = __float2ll_rn(s32 * 0x1p32f);
+      float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
+      const uint32_t x = pv[tid], xr = pv[(tid & ~3) | ((tid + 1) & 3)], xd = pv[(tid + 4) & (kWords - 1)];
+      uint32_t cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ ((x >> 1) | (xr << 31))) + __popc(x ^ xd)) << 16);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fs += __shfl_xor_sync(kFull, fs, o);
+        bnd += __shfl_xor_sync(kFull, bnd, o);
+        cnt += __shfl_xor_sync(kFull, cnt, o);
+      }
+      if (lane == 0) {
+        *(long long*)(red + 16 * warp) = fs;
+        *(float*)(red + 16 * warp + 8) = bnd;
+        *(uint32_t*)(red + 16 * warp + 12) = cnt;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long fs = 0;
+      double bnd = 0.0;
+      uint32_t ones = 0, pairs = 0;
+      for (int w = 0; w < 16; ++w) {
+        fs += *(const long long*)(red + 16 * w);
+        bnd += (double)*(const float*)(red + 16 * w + 8);
+        const uint32_t cn = *(const uint32_t*)(red + 16 * w + 12);
+        ones += cn & 0xFFFFu;
+        pairs += cn >> 16;
+      }
+      // the fixed-point conversion rounds each thread's sum by <= 2^-33; the FP32
+      // sums of the bound terms over 512 threads lose < 10 2^-24 relative
+      const double Fsp = (double)fs * 0x1p-32;
+      const double Fdata = bnd * 1.001 + 512.0 * 0x1p-33;
+      const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
+      const double M = 2.0 * (double)ones - (double)kN;
+      ch.Ep = E;
+      ch.lpp = -ch.beta * E;
+      ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
+      ch.lppb = 0.0;
+      ch.Fp = -jb.vb * (double)ones - Fsp;
+      ch.Bp = Fdata + (double)K * (double)kN * ((double)jb.csp + (double)jb.tcft) + 1e-12 * fabs(ch.Fp);
+      ch.flag_rec = 0;
+      if (!prm.correct) {
+        ch.flag_acc = 1;
+      } else {
+        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
+        const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+        const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
+                          1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+        if (logr - logu > Mg) ch.flag_acc = 1;
+        else if (logu - logr > Mg) ch.flag_acc = 0;
+        else ch.flag_rec = 1;
+      }
+    }
+    if (__syncthreads_or(tid == 0 && ch.flag_rec)) {
+      // the FP64 path's free energies of v' (and of v when only an FP32 value
+      // of it is known), by the same code and reduction order
+      Grp g2 = g;
+      g2.active = epi && ch.flag_rec;
+      double f1[4];
+      free_energy64(jb, tb64, g2, pv, f1);
+      grp_reduce<4>(f1, g2, scratch);
+      Grp g3 = g2;
+      g3.active = g2.active && ch.Fb != 0.0;
+      double f2[4];
+      free_energy64(jb, tb64, g3, vbits, f2);
+      grp_reduce<4>(f2, g3, scratch);
+      if (tid == 0) {
+        ch.Fp = -jb.vb * f1[2] - f1[0];
+        ch.Bp = 0.0;
+        if (g3.active) {
+          ch.F = -jb.vb * f2[2] - f2[0];
+          ch.Fb = 0.0;
+        }
+        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
+        ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < logr;
+        ch.rec_mh += 1ull;
+      }
+    }
+    if (tid == 0) {
+      if (ch.flag_acc) {
+        ch.F = ch.Fp;
+        ch.Fb = ch.Bp;
+        ch.lp = ch.lpp;
+        ch.lpb = ch.lppb;
+        ch.E = ch.Ep;
+        for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
+        ch.acc += 1ull;
+      }
+      for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+      trace_store(jb, c, step0 + (uint64_t)s, ch.E);
+    }
+    __syncthreads();
+    const bool accepted = ch.flag_acc != 0;
+    if (tid < kWords) {
+      uint32_t* pvw = (uint32_t*)pv;
+      if (accepted) vbits[tid] = pvw[tid];
+      pvw[tid] = 0u;                              // cleared for the next proposal
+    }
+    if (accepted) {
+      cur = src;                                  // the operand of v' is the new v
+    } else if (prm.g > 1) {
+      __syncthreads();
+      expand_lattice(smem, ly.opv[cur], vbits, tid, kThr);   // later Gibbs steps overwrote it
+    }
+    cta_sync();
+  }
+
+  if (nrec) atomicAdd(nrec_sm, (unsigned long long)nrec);
+  // every MMA issued has completed before tensor memory is released
+  if (issuer) {
+    umma_commit(bar(kBarFin));
+    wait_bar(bar(kBarFin), 0u);
+  }
+  cta_sync();
+  for (int w = tid; w < kWords; w += kThr) jb.bits[(size_t)c * kWords + w] = vbits[w];
+  if (tid == 0) {
+    jb.F[c] = ch.F;
+    jb.Fb[c] = ch.Fb;
+    jb.Lb[c] = ch.lpb;
+    jb.logpi[c] = ch.lp;
+    jb.Ephys[c] = ch.E;
+    for (int o = 0; o < kNobs; ++o) {
+      jb.obs_t[(size_t)c * kNobs + o] = ch.ot[o];
+      jb.obs[(size_t)c * kNobs + o] = ch.os[o];
+    }
+    jb.acc[c] += ch.acc;
+    jb.rec[2 * (size_t)c] += *nrec_sm;
+    jb.rec[2 * (size_t)c + 1] += ch.rec_mh;
+  }
+  if (warp == 16)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmCols));
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int K, int k) { return tc_layout(K, k).total; }
+
+bool tc_supported(int kind, int prec, int L, int K, int k) {
+  return kind == kIsing && prec == kMixed && L == kL && K >= 1 && K <= 4 && k >= 1 && k <= 6;
+}
+
+// the filter shape of every job of the launch: (K, k) of the first (launches
+// group jobs of one filter shape)
+cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (p.job[0].K == 4 && p.job[0].k == 5) crbm_tc_kernel<4, 5><<<grid, kThr, smem, st>>>(p);
+  else crbm_tc_kernel<0, 0><<<grid, kThr, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && p.S > 0) {
+    advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t tc_set_smem_limit() {
+  cudaError_t e = cudaFuncSetAttribute(crbm_tc_kernel<4, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_layout(4, 6).total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(crbm_tc_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_layout(4, 6).total);
+  return e;
+}
+
+}  // namespace crbm
