@@ -254,6 +254,16 @@ __device__ __forceinline__ uint32_t decide32(float x, uint32_t w, float c0, floa
   return fabsf(d) > delta ? (d > 0.0f ? 1u : 0u) : 2u;
 }
 
+// The same decision as decide32, returned as the FP32 bit and a flag that is
+// 1 when the margin does not separate it (then the FP64 path decides).
+__device__ __forceinline__ void decide32_split(float x, uint32_t w, float c0, float c1, uint32_t& bit,
+                                               uint32_t& amb) {
+  const float d = fmaf(sigmoid32(x), 0x1p32f, -__uint2float_rn(w));
+  const float delta = fmaf(c1, fabsf(x), c0);
+  bit = d > 0.0f ? 1u : 0u;
+  amb = fabsf(d) > delta ? 0u : 1u;
+}
+
 // log(1 + e^x) without overflow.
 __device__ __forceinline__ double softplus64(double x) {
   return fmax(x, 0.0) + log1p(exp(-fabs(x)));

@@ -27,8 +27,9 @@
 // kernel's FP32 free energy.
 //
 // Schedule per Gibbs step: 16 hidden tiles of 8 columns (H) and 8 visible
-// tiles of 16 columns (V), interleaved so that a V tile runs as soon as the
-// three H tiles it reads are done (H15 H0 H1 H2 V0 H3 H4 V1 ... H13 H14 V6 V7);
+// tiles of 16 columns (V), interleaved so that a V tile's MMAs run while the
+// epilogue warps work through the two H stages after its last input tile
+// (H15 H0 H1 H2 H3 V0 H4 H5 V1 ... H12 H13 V5 H14 V6 V7);
 // then 16 free-energy tiles (F).  Warp-specialised pipeline: the control warp
 // issues each stage's MMAs into one of four tensor-memory buffers and commits
 // them to that buffer's `full` mbarrier; the 16 epilogue warps (warp w: lanes
@@ -45,7 +46,7 @@ namespace crbm {
 namespace {
 
 constexpr int kL = 128, kN = kL * kL, kWords = kN / 32;   // 4 words per lattice row
-constexpr int kEpi = 512, kThr = kEpi + 32;                // 16 epilogue warps + control warp
+constexpr int kEpi = 512, kThr = kEpi + 64;                // 16 epilogue warps + 2 MMA-issuing warps
 constexpr int kRows = 136, kLbo = kRows * 16;              // one 8-column group of 136 rows
 constexpr int kOpv = 17 * kLbo;                            // 136 columns
 constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a V buffer: 3 groups
@@ -56,7 +57,7 @@ constexpr int kBvS = 1024;                                 // per (filter, row, 
 constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
 
 struct TcLayout {
-  uint32_t opv[2], vbuf, p15, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
+  uint32_t opv[2], vbuf, p15, hold, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int K, int k) {
@@ -66,6 +67,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   l.opv[1] = o; o += kOpv;
   l.vbuf = o; o += 2 * kVbuf;         // hidden operands of V tiles, two buffers of 3 groups
   l.p15 = o; o += kP15;               // hidden tile 15 (columns 120..127), kept for V7
+  l.hold = o; o += kP15;              // the last odd hidden tile, until the next even one moves it
   l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
   l.bv = o; o += (uint32_t)(K * k * 2 * kBvS);   // visible
   l.vbits = o; o += kWords * 4;       // packed current lattice
@@ -91,9 +93,16 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo) {
 __host__ __device__ constexpr uint32_t umma_idesc(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+// High word of every descriptor here: SBO = 128 bytes, version 1.  The low
+// word holds the start address and LBO, so operand offsets are 32-bit adds.
+constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);
+__device__ __forceinline__ uint32_t umma_desc_lo(uint32_t addr, uint32_t lbo) {
+  return ((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint32_t alo, uint32_t blo, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\n.reg .b64 da, db;\nsetp.ne.b32 p, %4, 0;\nmov.b64 da, {%1, %5};\n"
+               "mov.b64 db, {%2, %5};\ntcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n"
+               :: "r"(d), "r"(alo), "r"(blo), "r"(id), "r"(acc), "r"(kDescHi) : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" :: "r"(mbar)
@@ -149,55 +158,66 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 enum { kStH = 0, kStV = 1, kStF = 2 };
 
-// Stage z (0..23) of a Gibbs step: H15 H0 H1 H2, then (V_u H_{2u+3} H_{2u+4})
-// for u = 0..5, then V6 V7.  V_u reads H tiles 2u-1, 2u, 2u+1 (mod 16), all
-// finished two stages before it, so its MMAs can be issued one stage ahead.
+// Stage z (0..23) of a Gibbs step: H15 H0 H1 H2 H3, then (V_u H_{2u+4}
+// H_{2u+5}) for u = 0..4, then V5 H14 V6 V7.  V_u reads H tiles 2u-1, 2u, 2u+1
+// (mod 16); it comes two H stages after the last of them, so its MMAs run
+// while the epilogue warps work through those stages.
 __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
-  if (z < 4) {
+  if (z < 5) {
     type = kStH;
     tile = z == 0 ? 15 : z - 1;
-  } else if (z >= 22) {
-    type = kStV;
-    tile = z - 16;
+  } else if (z >= 20) {
+    type = z == 21 ? kStH : kStV;
+    tile = z == 20 ? 5 : (z == 21 ? 14 : z - 16);
   } else {
-    const int u = (z - 4) / 3, r = (z - 4) - 3 * u;
+    const int u = (z - 5) / 3, r = (z - 5) - 3 * u;
     type = r == 0 ? kStV : kStH;
-    tile = r == 0 ? u : 2 * u + 2 + r;
+    tile = r == 0 ? u : 2 * u + 3 + r;
   }
 }
 
-// MMAs of one stage into tensor-memory columns dcol, then a commit to mbar.
-// H/F tile t: N = 64 (digits c2, c1) or 96 (c2, c1, c0), columns e*32 + f*8 + jj.
-// V tile u: N = 32, columns e*16 + jj; slots s, s+1 of the tile's V buffer.
-// dopv / dvbuf / dbh / dbv: descriptors of the operand bases (start fields
+// MMAs of one stage into tensor-memory columns dcol, then a commit to mbar,
+// by issuer `role` (two issuing threads in different warps share the visible
+// stages, whose many small MMAs would otherwise be throttled by the issue
+// slots the epilogue warps take; role 1 commits at every stage, so `full`
+// counts two arrivals).
+// H/F tile t (role 0): N = 64 (digits c2, c1) or 96 (c2, c1, c0), columns
+// e*32 + f*8 + jj.  V tile u: N = 32, columns e*16 + jj, filters f < 2 into
+// dcol (role 0) and f >= 2 into dcol + 32 (role 1); slots s, s+1 of the tile's
+// V buffer.  *lo: low descriptor words of the operand bases (start fields
 // advance by byte offset / 16).  KT, kT > 0 fix K and k at compile time, so
-// that the issue sequence is straight-line code with immediate offsets: the
-// single issuing thread otherwise spends far longer per MMA than the tensor
-// core does on these small shapes.
+// that the issue sequence is straight-line code with immediate offsets.
 template <int KT, int kT>
-__device__ __forceinline__ void issue_stage(int type, int tile, uint32_t dcol, uint64_t dopv, uint64_t dvbuf,
-                                            uint64_t dbh, uint64_t dbv, int Kr, int kr, uint32_t mbar) {
+__device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32_t dcol, uint32_t opvlo,
+                                            uint32_t vbuflo, uint32_t bhlo, uint32_t bvlo, int Kr, int kr,
+                                            uint32_t mbar) {
   const int K = KT ? KT : Kr, k = kT ? kT : kr;
   if (type != kStV) {
-    const uint32_t id = type == kStH ? umma_idesc(64) : umma_idesc(96);
-    const uint64_t a0 = dopv + (uint64_t)(tile * (kLbo >> 4));
+    if (role == 0) {
+      const uint32_t id = type == kStH ? umma_idesc(64) : umma_idesc(96);
+      const uint32_t a0 = opvlo + (uint32_t)(tile * (kLbo >> 4));
 #pragma unroll
-    for (int a = 0; a < (kT ? kT : 8); ++a)
-      if (kT || a < k) umma(dcol, a0 + (uint64_t)a, dbh + (uint64_t)(a * (kBhA >> 4)), id, a > 0);
+      for (int a = 0; a < (kT ? kT : 8); ++a)
+        if (kT || a < k) umma(dcol, a0 + (uint32_t)a, bhlo + (uint32_t)(a * (kBhA >> 4)), id, a > 0);
+    }
   } else {
     const uint32_t id = umma_idesc(32);
-    const uint64_t a0 = dvbuf + (uint64_t)((tile & 1) * (kVbuf >> 4));
+    const uint32_t a0 = vbuflo + (uint32_t)((tile & 1) * (kVbuf >> 4));
+    const int f0 = role == 0 ? 0 : 2, f1 = role == 0 ? (K < 2 ? K : 2) : K;
+    const uint32_t dc = dcol + (role == 0 ? 0u : 32u);
 #pragma unroll
-    for (int f = 0; f < (KT ? KT : 4); ++f)
+    for (int ff = 0; ff < 2; ++ff)
 #pragma unroll
       for (int a = 0; a < (kT ? kT : 8); ++a)
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-          if ((KT || f < K) && (kT || a < k)) {
+        for (int s = 0; s < 2; ++s) {
+          const int f = f0 + ff;
+          if (f < f1 && (kT || a < k)) {
             const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - a) * 16);
             const uint32_t boff = (uint32_t)(((f * k + a) * 2 + s) * kBvS);
-            umma(dcol, a0 + (aoff >> 4), dbv + (boff >> 4), id, (f | a | s) != 0);
+            umma(dc, a0 + (aoff >> 4), bvlo + (boff >> 4), id, (ff | a | s) != 0);
           }
+        }
   }
   umma_commit(mbar);
 }
@@ -240,34 +260,49 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
   const uint4 w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
   const uint4 w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
   const float hb = jb.hb32[f];
-  uint32_t byte = 0u, hv[4] = {0u, 0u, 0u, 0u};
+  uint32_t byte = 0u, amb = 0u;
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
     const float x = fmaf(s2[jj], jb.tq2, s1[jj] * jb.tq1) + hb;
-    const uint32_t w = pick(jj < 4 ? w0 : w1, jj & 3);
-    uint32_t bit = decide32(x, w, jb.tc0h, jb.tc1);
-    if (bit == 2u) {
-      bit = tc_redo_hidden(jb, f, src, n0 + jj, w);
-      ++nrec;
-    }
+    uint32_t bit, a;
+    decide32_split(x, pick(jj < 4 ? w0 : w1, jj & 3), jb.tc0h, jb.tc1, bit, a);
     byte |= bit << jj;
-    hv[jj >> 1] |= bit ? (0x3C00u << (16 * (jj & 1))) : 0u;
+    amb |= a << jj;
+  }
+  if (amb) {
+    // units inside the certified margin: the FP64 path decides (rare)
+    for (int jj = 0; jj < 8; ++jj)
+      if ((amb >> jj) & 1u) {
+        const uint32_t bit = tc_redo_hidden(jb, f, src, n0 + jj, pick(jj < 4 ? w0 : w1, jj & 3));
+        byte = (byte & ~(1u << jj)) | (bit << jj);
+        ++nrec;
+      }
   }
   smem[ly.hbits + (uint32_t)f * (kWords * 4) + (uint32_t)(n0 >> 3)] = (unsigned char)byte;
-  const uint4 h4 = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+  const uint32_t z = byte | (byte << 15);     // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
+  const uint4 h4 = make_uint4(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u,
+                              ((z >> 4) & 0x10001u) * 0x3C00u, ((z >> 6) & 0x10001u) * 0x3C00u);
   // rows i + 8 of the V operands; rows 120..127 also as rows -8..-1
+  const uint32_t r0 = (uint32_t)(i + 8) * 16, r1 = (uint32_t)(i - (kL - 8)) * 16;
   auto put = [&](uint32_t base) {
-    *(uint4*)(smem + base + (uint32_t)(i + 8) * 16) = h4;
-    if (i >= kL - 8) *(uint4*)(smem + base + (uint32_t)(i - (kL - 8)) * 16) = h4;
+    *(uint4*)(smem + base + r0) = h4;
+    if (i >= kL - 8) *(uint4*)(smem + base + r1) = h4;
   };
+  // V_u reads slots (0, 1, 2) = tiles (2u-1, 2u, 2u+1) of buffer u % 2, last
+  // read by V_{u-2}, which precedes H_{2u} in the stage order.  An odd tile goes
+  // to the last slot of its V tile and to `hold`; the next (even) H stage moves
+  // this thread's rows of it from `hold` to the first slot of the next V tile.
   const int u = t >> 1;
-  const uint32_t pf = (uint32_t)f * kPlane3;
+  const uint32_t pf = (uint32_t)f * kPlane3, hf = ly.hold + (uint32_t)f * kLbo;
   if ((t & 1) == 0) {
-    put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 1 * kLbo);           // middle slot of V_u
+    const uint32_t vb = ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf;
+    put(vb + 1 * kLbo);
+    *(uint4*)(smem + vb + r0) = *(const uint4*)(smem + hf + r0);
+    if (i >= kL - 8) *(uint4*)(smem + vb + r1) = *(const uint4*)(smem + hf + r1);
   } else {
-    if (t != 15) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);   // last slot of V_u
-    else put(ly.p15 + (uint32_t)f * kLbo);
-    put(ly.vbuf + (uint32_t)((u + 1) & 1) * kVbuf + pf);                // first slot of V_{u+1}
+    if (t != 15) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);
+    else put(ly.p15 + (uint32_t)f * kLbo);      // V7's last slot is still in use by V1, V3, V5
+    put(hf);
   }
 }
 
@@ -281,25 +316,31 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
   const int j0 = 16 * u + 4 * cq, n0 = i * kL + j0;
   const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n0 >> 2), tag, step, cid), jb.rk);
   const uint32_t* hb = (const uint32_t*)(smem + ly.hbits);
-  uint32_t nib = 0u, hv[2] = {0u, 0u};
+  uint32_t nib = 0u, amb = 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const float x = fmaf(s2[t], jb.tq2, s1[t] * jb.tq1) + jb.vb32;
-    uint32_t bit = decide32(x, pick(w, t), jb.tc0v, jb.tc1);
-    if (bit == 2u) {
-      // the packed hidden units of H tiles 2u-1, 2u, 2u+1 come from other warps:
-      // their hrdy mbarriers (completed before this tile's MMAs) order them
-      const int tt[3] = {(2 * u + 15) & 15, 2 * u, 2 * u + 1};
-      for (int q = 0; q < 3; ++q)
-        if (!mbar_wait(hbar + 8u * (uint32_t)tt[q], parity)) atomicExch(err, kErrTimeout);
-      bit = recompute_visible(jb, hb, kWords, n0 + t, pick(w, t));
-      ++nrec;
-    }
+    uint32_t bit, a;
+    decide32_split(x, pick(w, t), jb.tc0v, jb.tc1, bit, a);
     nib |= bit << t;
-    hv[t >> 1] |= bit ? (0x3C00u << (16 * (t & 1))) : 0u;
+    amb |= a << t;
+  }
+  if (amb) {
+    // the packed hidden units of H tiles 2u-1, 2u, 2u+1 come from other warps:
+    // their hrdy mbarriers (completed before this tile's MMAs) order them
+    const int tt[3] = {(2 * u + 15) & 15, 2 * u, 2 * u + 1};
+    for (int q = 0; q < 3; ++q)
+      if (!mbar_wait(hbar + 8u * (uint32_t)tt[q], parity)) atomicExch(err, kErrTimeout);
+    for (int t = 0; t < 4; ++t)
+      if ((amb >> t) & 1u) {
+        const uint32_t bit = recompute_visible(jb, hb, kWords, n0 + t, pick(w, t));
+        nib = (nib & ~(1u << t)) | (bit << t);
+        ++nrec;
+      }
   }
   atomicOr(dbits + (n0 >> 5), nib << (n0 & 31));
-  const uint2 h2 = make_uint2(hv[0], hv[1]);
+  const uint32_t z = nib | (nib << 15);
+  const uint2 h2 = make_uint2(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u);
   const uint32_t off = opv + (uint32_t)(j0 >> 3) * kLbo + (uint32_t)(j0 & 7) * 2;
   *(uint2*)(smem + off + (uint32_t)i * 16) = h2;
   if (i < 8) *(uint2*)(smem + off + (uint32_t)(i + kL) * 16) = h2;
@@ -385,12 +426,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     ch.flag_acc = 0;
     *nrec_sm = 0ull;
     for (int b = 0; b < kNbuf; ++b) {
-      mbar_init(bar(kBarFull + b), 1);
+      mbar_init(bar(kBarFull + b), 2);
       mbar_init(bar(kBarEmpty + b), 16);
     }
     for (int t = 0; t < 16; ++t) mbar_init(bar(kBarH + t), 16);
     mbar_init(bar(kBarV), 16);
-    mbar_init(bar(kBarFin), 1);
+    mbar_init(bar(kBarFin), 2);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 16) {
@@ -406,23 +447,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   // epilogue thread: lattice row i, filter / column quarter fq; its TMEM lanes
   const int i = 32 * (warp & 3) + lane, fq = warp >> 2;
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
-  const bool issuer = warp == 16 && lane == 0;
-  Grp g;
-  g.tpc = kEpi;
-  g.gl = tid / kEpi;
-  g.r = tid - g.gl * kEpi;
-  g.c = c;
-  g.active = epi;
-  g.cid = cid;
-  Tabs tb64;
-  memset(&tb64, 0, sizeof tb64);
-  tb64.T = 1 << k;
-  tb64.f64 = jb.f64;
-  tb64.b64 = jb.b64;
+  const bool issuer = warp >= 16 && lane == 0;
+  const int role = warp - 16;                     // issuers: 0 and 1
 
-  const uint64_t dopv[2] = {umma_desc(sbase + ly.opv[0], kLbo), umma_desc(sbase + ly.opv[1], kLbo)};
-  const uint64_t dvbuf = umma_desc(sbase + ly.vbuf, kLbo), dbh = umma_desc(sbase + ly.bh, 1536),
-                 dbv = umma_desc(sbase + ly.bv, 512);
+  const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], kLbo);   // operand x at + x kOpv / 16
+  const uint32_t dvbuf = umma_desc_lo(sbase + ly.vbuf, kLbo), dbh = umma_desc_lo(sbase + ly.bh, 1536),
+                 dbv = umma_desc_lo(sbase + ly.bv, 512);
   uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
   uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
   bool live = true;             // false once a wait gave up: no further waits
@@ -466,10 +496,11 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
     int src = cur;
     for (int sub = 0; sub < prm.g; ++sub, ++gs) {
-      uint32_t* dbits = (uint32_t*)(smem + ly.pb[sub & 1]);
-      const uint32_t* sbits = sub == 0 ? vbits : (const uint32_t*)(smem + ly.pb[(sub - 1) & 1]);
+      uint32_t* dbits = (uint32_t*)(smem + ly.pb[0] + (uint32_t)(sub & 1) * (kWords * 4));
+      const uint32_t* sbits =
+          sub == 0 ? vbits : (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub - 1) & 1) * (kWords * 4));
       const uint32_t taghid = (uint32_t)(sub * (K + 1)), tagvis = (uint32_t)(sub * (K + 1) + K);
-      const uint32_t opv_dst = ly.opv[src ^ 1];
+      const uint32_t opv_dst = ly.opv[0] + (uint32_t)(src ^ 1) * kOpv;
       const uint32_t zbase = zc;
       if (issuer) {
         for (int z = 0; z < 24; ++z, ++zc) {
@@ -482,7 +513,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             wait_bar(bar(kBarH + 2 * tl + 1), gs & 1u);
             tc_fence_after();
           }
-          issue_stage<KT, kT>(ty, tl, d, dopv[src], dvbuf, dbh, dbv, K, k, bar(kBarFull + (zc & (kNbuf - 1))));
+          issue_stage<KT, kT>(role, ty, tl, d, dopv0 + (uint32_t)(src * (kOpv >> 4)), dvbuf, dbh, dbv, K, k,
+                              bar(kBarFull + (zc & (kNbuf - 1))));
         }
       } else if (epi) {
         for (int z = 0; z < 24; ++z, ++zc) {
@@ -503,7 +535,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             if (tl == 14 && fq < K) {
               // this thread's rows of hidden tile 15 (written by it at H15) into
               // the last slot of V7's buffer, read last by V5, whose MMAs this
-              // warp has waited for
+              // warp has waited for (V5 precedes H14)
               const uint32_t dst = ly.vbuf + kVbuf + (uint32_t)fq * kPlane3 + 2 * kLbo, p15 = ly.p15 + (uint32_t)fq * kLbo;
               *(uint4*)(smem + dst + (uint32_t)(i + 8) * 16) = *(const uint4*)(smem + p15 + (uint32_t)(i + 8) * 16);
               if (i >= kL - 8)
@@ -515,7 +547,20 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             float s2[4], s1[4];
             tm_ld4(tcol + 4 * fq, s2);
             tm_ld4(tcol + 16 + 4 * fq, s1);
-            tm_wait();
+            if (K > 2) {
+              // filters 2, 3 from the second issuer's accumulator (integer sums: exact)
+              float t2[4], t1[4];
+              tm_ld4(tcol + 32 + 4 * fq, t2);
+              tm_ld4(tcol + 48 + 4 * fq, t1);
+              tm_wait();
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                s2[q] += t2[q];
+                s1[q] += t1[q];
+              }
+            } else {
+              tm_wait();
+            }
             epi_release();
             epi_visible(jb, smem, ly, s2, s1, i, fq, tl, tagvis, step, cid, dbits, opv_dst, bar(kBarH), gs & 1u,
                         prm.err, nrec);
@@ -529,11 +574,11 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         // next Gibbs step: its source is this step's v' (every write done), and
         // the proposal buffer it fills is cleared
         cta_sync();
-        if (tid < kWords) ((uint32_t*)(smem + ly.pb[(sub + 1) & 1]))[tid] = 0u;
+        if (tid < kWords) ((uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub + 1) & 1) * (kWords * 4)))[tid] = 0u;
         __syncthreads();
       }
     }
-    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[(prm.g - 1) & 1]);   // v'
+    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((prm.g - 1) & 1) * (kWords * 4));   // v'
 
     // free energy of v' from the F tiles
     float s32 = 0.f, c32 = 0.f, sabs = 0.f, ssp = 0.f;
@@ -545,7 +590,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
           wait_bar(bar(kBarV), (gs - 1) & 1u);
           tc_fence_after();
         }
-        issue_stage<KT, kT>(kStF, t, d, dopv[src], dvbuf, dbh, dbv, K, k, bar(kBarFull + (zc & (kNbuf - 1))));
+        issue_stage<KT, kT>(role, kStF, t, d, dopv0 + (uint32_t)(src * (kOpv >> 4)), dvbuf, dbh, dbv, K, k,
+                            bar(kBarFull + (zc & (kNbuf - 1))));
       }
     } else if (epi) {
       for (int t = 0; t < 16; ++t, ++zc) {
@@ -626,8 +672,18 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     if (__syncthreads_or(tid == 0 && ch.flag_rec)) {
       // the FP64 path's free energies of v' (and of v when only an FP32 value
       // of it is known), by the same code and reduction order
-      Grp g2 = g;
+      Grp g2;
+      g2.tpc = kEpi;
+      g2.gl = tid / kEpi;
+      g2.r = tid - g2.gl * kEpi;
+      g2.c = c;
+      g2.cid = cid;
       g2.active = epi && ch.flag_rec;
+      Tabs tb64;
+      memset(&tb64, 0, sizeof tb64);
+      tb64.T = 1 << k;
+      tb64.f64 = jb.f64;
+      tb64.b64 = jb.b64;
       double f1[4];
       free_energy64(jb, tb64, g2, pv, f1);
       grp_reduce<4>(f1, g2, scratch);
@@ -673,7 +729,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       cur = src;                                  // the operand of v' is the new v
     } else if (prm.g > 1) {
       __syncthreads();
-      expand_lattice(smem, ly.opv[cur], vbits, tid, kThr);   // later Gibbs steps overwrote it
+      expand_lattice(smem, ly.opv[0] + (uint32_t)cur * kOpv, vbits, tid, kThr);   // later Gibbs steps overwrote it
     }
     cta_sync();
   }
