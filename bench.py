@@ -137,19 +137,24 @@ def peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one launch of the batch Ising workload's fused
-# kernel, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# one pass) of the current kernel; the lattices stay in shared memory for the
-# whole launch, so this is the lattice and table traffic only.
-BATCH_ISING_TRAFFIC_BYTES = 13.97e6 + 12.54e3
+# DRAM bytes (read + write) of one launch of the tensor-core kernel on the
+# batch Ising workload's L = 128 jobs (4096 chains x 10 proposals), from an ncu
+# capture of a 152-chain launch scaled by chains (per chain the traffic is its
+# lattice and state in and out and the filter images; the lattices stay in
+# shared memory for the whole launch).
+BATCH_ISING_TC_TRAFFIC_BYTES = 841728 * 4096 / 152   # 152-chain capture: 841,728 B read, 0 B written
 
 
 def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
-    """ALU roofline of the fused kernel: algorithmic FP32 flops = the three
+    """ALU roofline of a proposal kernel: algorithmic FP32 flops = the three
     periodic convolutions of a proposal written directly (hidden, visible and
     free-energy pre-activations: 3 x K k^2 multiply-adds per site), against the
     FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops) and the SM
-    clock sampled during the run."""
+    clock sampled during the run.  The table kernel does these sums by table
+    look-ups and the tensor-core kernel as fp16 digit MMAs; either way the
+    kernel is bound by its ALU work (Philox, sigmoids, softplus, decisions), and
+    the fraction measures convolution work per second against the pipe a
+    direct FP32 implementation would saturate."""
     flops = 6.0 * K * k * k * n_sites_step
     mhz = clocks.get("sm_mhz") or peaks().get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
@@ -591,6 +596,27 @@ def main():
 
     K, k = W.shape[0], W.shape[1]
     sites = sum(n * L * L for L, n in spec["jobs"]) * S
+    # the dominant kernel alone: the L = 128 jobs (the tensor-core kernel in the
+    # mixed path) on this stream, CUDA events around each launch, after the
+    # timed region
+    dom = [(L, n, j) for (L, n), j in zip(spec["jobs"], jobs) if L == max(Lj for Lj, _ in spec["jobs"])]
+    dom_jobs = [j for _, _, j in dom]
+    dev_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    ctx.run_batch(dom_jobs, S, precision=prec, stream=stream)
+    for a, b in dev_ev:
+        flush.zero_()
+        a.record(stream)
+        ctx.run_batch(dom_jobs, S, precision=prec, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    dom_ms = sum(a.elapsed_time(b) for a, b in dev_ev) / len(dev_ev)
+    dom_sites = sum(n * L * L for L, n, _ in dom) * S
+    dom_name = ("crbm_tc_kernel" if prec == MIXED and spec["kind"] == 0 and dom[0][0] == 128 else "crbm_step_kernel")
+    # kernels per step: one launch (and its step-counter update) per kernel the
+    # batch uses: the tensor-core kernel for L = 128 (mixed Ising), the table
+    # kernel for the rest
+    tc_used = prec == MIXED and spec["kind"] == 0 and any(L == 128 for L, _ in spec["jobs"])
+    n_parts = int(tc_used) + int(any(not (tc_used and L == 128) for L, _ in spec["jobs"]))
     line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -598,10 +624,16 @@ def main():
             "config": {"workload": spec["desc"], "proposals_per_step": S, "chains": n_chains,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"chains x{world}"},
-            "roofline": roofline(spec, total_ms / args.steps, clocks, K, k, sites,
-                                 traffic=(BATCH_ISING_TRAFFIC_BYTES if args.workload == "ising-batch" and
-                                          not args.chains and not args.Ls else None)),
-            "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+            "roofline": roofline(spec, dom_ms, clocks, K, k, dom_sites,
+                                 traffic=(BATCH_ISING_TC_TRAFFIC_BYTES if args.workload == "ising-batch" and
+                                          dom_name == "crbm_tc_kernel" and not args.chains and not args.Ls
+                                          else None)),
+            "e2e": e2e, "gpu_launches": args.steps * 2 * n_parts, "clocks": clocks}
+    line["roofline"]["kernel"] = (f"{dom_name}: the L = {dom[0][0]} jobs ({sum(n for _, n, _ in dom)} chains x {S} "
+                                  f"proposals) alone, {dom_ms:.3f} ms per launch")
+    step_rf = roofline(spec, total_ms / args.steps, clocks, K, k, sites)
+    line["roofline"]["whole_step"] = {"achieved": step_rf["achieved"], "frac": step_rf["frac"],
+                                      "note": "all lattice sizes of the step, both kernels"}
     sums = [j.observables() for j in jobs]
     line["config"]["acceptance"] = sum(int(a.sum()) for _, a, _ in sums) / max(1, n_chains * jobs[0].step)
     props_done = max(1, n_chains * jobs[0].step)

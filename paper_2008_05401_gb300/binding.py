@@ -386,7 +386,7 @@ class Context:
 
     def set_tensor_cores(self, enable: bool):
         """Run later proposals of eligible jobs (Ising, mixed, L = 128, K <= 4,
-        k <= 6) on the tensor-core kernel (True, default) or the table kernel."""
+        k <= 5) on the tensor-core kernel (True, default) or the table kernel."""
         crbm_set_tensor_cores(self.h, enable)
 
     def tune(self, model_id, L, precision=FP64):

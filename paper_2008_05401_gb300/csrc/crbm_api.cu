@@ -34,7 +34,7 @@ struct Model {
   float hb32[kMaxK] = {}, hb_hi[kMaxK] = {}, hb_lo[kMaxK] = {};
   float vb32 = 0.f;
   float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f;
-  // tensor-core form (Ising, K <= 4, k <= 6): filter-digit operand images
+  // tensor-core form (Ising, K <= 4, k <= 5): filter-digit operand images
   uint4* d_tc = nullptr;
   size_t tc_bytes = 0;
   float tq2 = 0.f, tq1 = 0.f, tq0 = 0.f, tc0h = 0.f, tc0v = 0.f, tc1 = 0.f, tcft = 0.f;
@@ -390,7 +390,7 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     e = set_smem_limits((size_t)optin);
-    if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(4, 6)) {
+    if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(4, 5)) {
       e = tc_set_smem_limit();
       ctx->tc_ok = e == cudaSuccess;
     }
@@ -443,14 +443,15 @@ static uint16_t half_of_int(int v) {
 }
 
 // Operand images and error constants of the tensor-core form (Ising, K <= 4,
-// k <= 6; crbm_step_tc.cu).  Every weight becomes W ~ qf (c2 2^22 + c1 2^11 + c0)
+// k <= 5; crbm_step_tc.cu).  Every weight becomes W ~ qf (c2 2^22 + c1 2^11 + c0)
 // with qf = 2^e, |W / qf| <= 2^31, balanced digits c0, c1 in [-1024, 1023]
 // and |c2| <= 513, all exact in fp16.  Images (K-major, no swizzle: element
 // (row kk, column n) at (kk/8) LBO + (n/8) 128 + (n%8) 16 + (kk%8) 2):
-//   hidden / free energy, per kernel row a: K=16 x N=96, column n = e*32 + f*8 + jj
-//     holds digit e (c2, c1, c0) of W[f][a][kk - jj];
-//   visible, per (f, a, step s): K=16 x N=32, column n = e*16 + jj holds digit e of
-//     W[f][a][b], b = jj + 8 - kk (s = 0) or jj - kk for kk >= 8 (s = 1).
+//   hidden / free energy, per kernel row a: K=16 x N=96, LBO 1536, column
+//     n = e*32 + f*8 + jj holds digit e (c2, c1, c0) of W[f][a][kk - jj];
+//   visible: a zero group (768 B), then per (f, a): step 0 K=16 x N=48, LBO 768,
+//     column n = e*16 + jj holding digit e of W[f][a][jj + 8 - kk]; step 1 its
+//     second K-group only (kk = 8..15, W[f][a][jj - kk]; the first is zero).
 static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, double v_bias, const double* h_bias,
                     double sh, double sv, double common, bool alloc) {
   double maxw = 0.0, maxhb = 0.0;
@@ -465,9 +466,9 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
     return r;
   };
   std::vector<int> dg((size_t)3 * K * k * k);      // digits e = 0, 1, 2 (c2, c1, c0) of W[f][a][b]
-  double e2v = 0.0, e2h = 0.0, t1 = 0.0;
+  double t1 = 0.0, t1v = 0.0;
   for (int f = 0; f < K; ++f) {
-    double ef = 0.0, tf = 0.0;
+    double tf = 0.0;
     for (int ab = 0; ab < k * k; ++ab) {
       const size_t idx = (size_t)f * k * k + ab;
       const long long wi = std::llround(W[idx] / qf);
@@ -476,15 +477,13 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
       dg[0 * (size_t)K * k * k + idx] = (int)w2;
       dg[1 * (size_t)K * k * k + idx] = (int)c1;
       dg[2 * (size_t)K * k * k + idx] = (int)c0;
-      ef += qf * (0.5 + (double)std::llabs(c0));       // |W - qf (c2 2^22 + c1 2^11)|
-      tf += qf * (2048.0 * (double)std::llabs(c1) + (double)std::llabs(c0));
+      tf += qf * (2048.0 * (double)std::llabs(c1) + (double)std::llabs(c0));   // |q1 c1-sum + q0 c0-sum|
     }
-    e2h = std::fmax(e2h, ef);
-    e2v += ef;
     t1 = std::fmax(t1, tf);
+    t1v += tf;
   }
   auto digit = [&](int e, int f, int a, int b) { return dg[((size_t)e * K + f) * k * k + (size_t)a * k + b]; };
-  const size_t bh = (size_t)k * 3072, bytes = bh + (size_t)K * k * 2 * 1024;
+  const size_t bh = (size_t)k * 3072, bytes = bh + 768 + (size_t)K * k * 2304;
   std::vector<uint16_t> img(bytes / 2, 0);
   for (int a = 0; a < k; ++a)
     for (int kk = 0; kk < 16; ++kk)
@@ -495,26 +494,32 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
         img[off / 2] = half_of_int(digit(e, f, a, b));
       }
   for (int f = 0; f < K; ++f)
-    for (int a = 0; a < k; ++a)
-      for (int st = 0; st < 2; ++st)
-        for (int kk = 0; kk < 16; ++kk)
-          for (int n = 0; n < 32; ++n) {
-            const int e = n / 16, jj = n % 16;
-            const int b = st == 0 ? jj + 8 - kk : (kk >= 8 ? jj - kk : -1);
-            if (b < 0 || b >= k) continue;
-            const size_t off = bh + ((size_t)(f * k + a) * 2 + st) * 1024 + (kk / 8) * 512 + (n / 8) * 128 +
-                               (n % 8) * 16 + (kk % 8) * 2;
-            img[off / 2] = half_of_int(digit(e, f, a, b));
-          }
+    for (int a = 0; a < k; ++a) {
+      const size_t fa = bh + 768 + (size_t)(f * k + a) * 2304;
+      for (int kk = 0; kk < 16; ++kk)
+        for (int n = 0; n < 48; ++n) {
+          const int e = n / 16, jj = n % 16;
+          int b = jj + 8 - kk;                                          // step 0
+          if (b >= 0 && b < k)
+            img[(fa + (kk / 8) * 768 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2) / 2] = half_of_int(digit(e, f, a, b));
+          b = jj - kk;                                                  // step 1, kk >= 8
+          if (kk >= 8 && b >= 0 && b < k)
+            img[(fa + 1536 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2) / 2] = half_of_int(digit(e, f, a, b));
+        }
+    }
   m.tq2 = (float)std::ldexp(qf, 22);
   m.tq1 = (float)std::ldexp(qf, 11);
   m.tq0 = (float)qf;
-  // decisions (decide32 units of 2^-32): x = fl(fl(c2-sum q2 + c1-sum q1) + hb32) is
-  // within quantisation E2 + 2^-24 (2 |x| + 2 |hb|) of the exact pre-activation,
-  // the FP64 path's own sum within 2^-50 S; slope of sigma <= 1/4; factor 2 of safety
+  // decisions (decide32 units of 2^-32): x = fl(fl(c2-sum q2 + fl(c1-sum q1 +
+  // c0-sum q0)) + b32) is within quantisation (k^2 or K k^2) qf / 2, the low
+  // digits' rounding 2^-24 T1 and 2^-24 (2 |x| + 2 |b|) of the exact
+  // pre-activation, the FP64 path's own sum within 2^-50 S; slope of sigma
+  // <= 1/4; factor 2 of safety
   const double u24 = std::ldexp(1.0, -24), u50 = std::ldexp(1.0, -50);
-  m.tc0h = (float)std::ldexp(2.0 * (common + 0.25 * (e2h + 2.0 * u24 * maxhb + u50 * sh)) + 1e-14, 32);
-  m.tc0v = (float)std::ldexp(2.0 * (common + 0.25 * (e2v + 2.0 * u24 * std::fabs(v_bias) + u50 * sv)) + 1e-14, 32);
+  const double eqh = 0.5 * k * k * qf, eqv = 0.5 * K * k * k * qf;
+  m.tc0h = (float)std::ldexp(2.0 * (common + 0.25 * (eqh + u24 * t1 + 2.0 * u24 * maxhb + u50 * sh)) + 1e-14, 32);
+  m.tc0v = (float)std::ldexp(
+      2.0 * (common + 0.25 * (eqv + u24 * t1v + 2.0 * u24 * std::fabs(v_bias) + u50 * sv)) + 1e-14, 32);
   m.tc1 = (float)std::ldexp(2.0 * (std::ldexp(1.0, -25) + 0.25 * 2.0 * u24), 32);
   // free energy, per unit beyond the 2^-23 |x| the kernel sums: quantisation
   // k^2 qf / 2, rounding of the low digits 2^-24 T1, of hb 3 2^-24 |hb|; factor 1.5
@@ -621,7 +626,7 @@ static int build_model(crbm_ctx* ctx, Model& m, int kind, int K, int k, const do
   }
   m.nlut = nlut;
   m.nq = nq;
-  if (kind == kIsing && K <= 4 && k <= 6) {
+  if (kind == kIsing && K <= 4 && k <= 5) {
     const int rc = build_tc(ctx, m, K, k, W, v_bias, h_bias, sh, sv, common, alloc);
     if (rc) return rc;
   }

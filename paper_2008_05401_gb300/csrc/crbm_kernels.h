@@ -25,7 +25,7 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Tensor-core form of the proposal kernel (crbm_step_tc.cu): Ising kind, mixed
-// precision, L = 128, K <= 4, k <= 6, one CTA per chain.
+// precision, L = 128, K <= 4, k <= 5, one CTA per chain.
 bool tc_supported(int kind, int prec, int L, int K, int k);
 size_t tc_smem_bytes(int K, int k);
 cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st);

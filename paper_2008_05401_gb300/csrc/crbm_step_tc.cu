@@ -1,6 +1,6 @@
 // Tensor-core form of the fused CRBM proposal + Metropolis-Hastings kernel:
 // Ising kind, mixed precision, 128 x 128 lattices, K <= 4 filters of side
-// k <= 6, mode 0 (S proposals of g Gibbs steps).  One chain per CTA.  The
+// k <= 5, mode 0 (S proposals of g Gibbs steps).  One chain per CTA.  The
 // chain is the table kernel's chain: the same Philox words per unit, and every
 // Bernoulli and MH decision the FP64 path's.
 //
@@ -21,10 +21,9 @@
 // a window are integers below 2^17, exact in FP32 whatever the order of the
 // tensor core's additions, so the only roundings are the quantisation
 // (|W - qf W_int| <= qf / 2) and the FP32 combination of the digit sums here.
-// Bernoulli decisions use c2, c1 and the certified margin of decide32 with this
-// form's constants (the FP64 tables decide inside it); the free energy uses all
-// three digits and carries its error bound into the MH decision like the table
-// kernel's FP32 free energy.
+// Bernoulli decisions use the certified margin of decide32 with this form's
+// constants (the FP64 tables decide inside it); the free energy carries its
+// error bound into the MH decision like the table kernel's FP32 free energy.
 //
 // Schedule per Gibbs step: 16 hidden tiles of 8 columns (H) and 8 visible
 // tiles of 16 columns (V), interleaved so that a V tile's MMAs run while the
@@ -53,7 +52,10 @@ constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a 
 constexpr int kVbuf = 4 * kPlane3;
 constexpr int kP15 = 4 * kLbo;
 constexpr int kBhA = 3072;                                 // per kernel row: K=16 x N=96
-constexpr int kBvS = 1024;                                 // per (filter, row, step): K=16 x N=32
+// visible images, per (filter, kernel row): step 0 K=16 x N=48 (1536 B), step
+// 1 only its second K-group (768 B; the first is zero and read from one shared
+// zero group through the descriptor's LBO); the zero group first
+constexpr int kBvZero = 768, kBvFA = 2304;
 constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
 
 struct TcLayout {
@@ -69,7 +71,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   l.p15 = o; o += kP15;               // hidden tile 15 (columns 120..127), kept for V7
   l.hold = o; o += kP15;              // the last odd hidden tile, until the next even one moves it
   l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
-  l.bv = o; o += (uint32_t)(K * k * 2 * kBvS);   // visible
+  l.bv = o; o += (uint32_t)(kBvZero + K * k * kBvFA);   // visible
   l.vbits = o; o += kWords * 4;       // packed current lattice
   l.pb[0] = o; o += kWords * 4;       // packed proposals (ping-pong over Gibbs steps)
   l.pb[1] = o; o += kWords * 4;
@@ -181,10 +183,9 @@ __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
 // stages, whose many small MMAs would otherwise be throttled by the issue
 // slots the epilogue warps take; role 1 commits at every stage, so `full`
 // counts two arrivals).
-// H/F tile t (role 0): N = 64 (digits c2, c1) or 96 (c2, c1, c0), columns
-// e*32 + f*8 + jj.  V tile u: N = 32, columns e*16 + jj, filters f < 2 into
-// dcol (role 0) and f >= 2 into dcol + 32 (role 1); slots s, s+1 of the tile's
-// V buffer.  *lo: low descriptor words of the operand bases (start fields
+// H/F tile t (role 0): N = 96, columns e*32 + f*8 + jj for the digits e = c2,
+// c1, c0.  V tile u: N = 48, columns e*16 + jj, filters f < 2 into dcol (role
+// 0) and f >= 2 into dcol + 48 (role 1); slots s, s+1 of the tile's V buffer.  *lo: low descriptor words of the operand bases (start fields
 // advance by byte offset / 16).  KT, kT > 0 fix K and k at compile time, so
 // that the issue sequence is straight-line code with immediate offsets.
 template <int KT, int kT>
@@ -194,17 +195,17 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
   const int K = KT ? KT : Kr, k = kT ? kT : kr;
   if (type != kStV) {
     if (role == 0) {
-      const uint32_t id = type == kStH ? umma_idesc(64) : umma_idesc(96);
+      const uint32_t id = umma_idesc(96);
       const uint32_t a0 = opvlo + (uint32_t)(tile * (kLbo >> 4));
 #pragma unroll
       for (int a = 0; a < (kT ? kT : 8); ++a)
         if (kT || a < k) umma(dcol, a0 + (uint32_t)a, bhlo + (uint32_t)(a * (kBhA >> 4)), id, a > 0);
     }
   } else {
-    const uint32_t id = umma_idesc(32);
+    const uint32_t id = umma_idesc(48);
     const uint32_t a0 = vbuflo + (uint32_t)((tile & 1) * (kVbuf >> 4));
     const int f0 = role == 0 ? 0 : 2, f1 = role == 0 ? (K < 2 ? K : 2) : K;
-    const uint32_t dc = dcol + (role == 0 ? 0u : 32u);
+    const uint32_t dc = dcol + (role == 0 ? 0u : 48u);
 #pragma unroll
     for (int ff = 0; ff < 2; ++ff)
 #pragma unroll
@@ -214,8 +215,12 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
           const int f = f0 + ff;
           if (f < f1 && (kT || a < k)) {
             const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - a) * 16);
-            const uint32_t boff = (uint32_t)(((f * k + a) * 2 + s) * kBvS);
-            umma(dc, a0 + (aoff >> 4), bvlo + (boff >> 4), id, (ff | a | s) != 0);
+            const uint32_t fa = (uint32_t)(kBvZero + (f * k + a) * kBvFA);
+            // step 0: start at its block, LBO 768; step 1: start at the zero
+            // group, LBO = distance to its block
+            const uint32_t blo = s == 0 ? bvlo + (fa >> 4) + ((768u >> 4) << 16)
+                                        : bvlo + (((fa + 1536u) >> 4) << 16);
+            umma(dc, a0 + (aoff >> 4), blo, id, (ff | a | s) != 0);
           }
         }
   }
@@ -249,12 +254,12 @@ __device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t
   }
 }
 
-// H tile t, thread (row i, filter f), digit sums s2, s1 of its 8 units
+// H tile t, thread (row i, filter f), digit sums s2, s1, s0 of its 8 units
 // (f, i, 8t .. 8t+7): the hidden units, packed and as fp16 operands.
 __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
-                                           const float (&s2)[8], const float (&s1)[8], int i, int f, int t,
-                                           uint32_t tag, uint32_t step, uint32_t cid, const uint32_t* src,
-                                           unsigned& nrec) {
+                                           const float (&s2)[8], const float (&s1)[8], const float (&s0)[8],
+                                           int i, int f, int t, uint32_t tag, uint32_t step, uint32_t cid,
+                                           const uint32_t* src, unsigned& nrec) {
   const int n0 = i * kL + 8 * t;
   const uint32_t q0 = (uint32_t)(n0 >> 2);
   const uint4 w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
@@ -263,7 +268,7 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
   uint32_t byte = 0u, amb = 0u;
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    const float x = fmaf(s2[jj], jb.tq2, s1[jj] * jb.tq1) + hb;
+    const float x = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, s0[jj] * jb.tq0)) + hb;
     uint32_t bit, a;
     decide32_split(x, pick(jj < 4 ? w0 : w1, jj & 3), jb.tc0h, jb.tc1, bit, a);
     byte |= bit << jj;
@@ -309,7 +314,8 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
 // V tile u, thread (row i, column quarter cq), digit sums of its 4 units
 // (i, 16u + 4cq .. + 3): the visible units, packed and as fp16 F operands.
 __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
-                                            const float (&s2)[4], const float (&s1)[4], int i, int cq, int u,
+                                            const float (&s2)[4], const float (&s1)[4], const float (&s0)[4],
+                                            int i, int cq, int u,
                                             uint32_t tag, uint32_t step, uint32_t cid, uint32_t* dbits,
                                             uint32_t opv, uint32_t hbar, uint32_t parity, int* err,
                                             unsigned& nrec) {
@@ -319,7 +325,7 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
   uint32_t nib = 0u, amb = 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const float x = fmaf(s2[t], jb.tq2, s1[t] * jb.tq1) + jb.vb32;
+    const float x = fmaf(s2[t], jb.tq2, fmaf(s1[t], jb.tq1, s0[t] * jb.tq0)) + jb.vb32;
     uint32_t bit, a;
     decide32_split(x, pick(w, t), jb.tc0v, jb.tc1, bit, a);
     nib |= bit << t;
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   unsigned char* red = smem + ly.misc + kMiscRed;
   const uint32_t cid = (uint32_t)(jb.cid_base + (uint64_t)c);
 
-  const int nimg = (k * kBhA + K * k * 2 * kBvS) / 16;     // B images: hidden/free, then visible
+  const int nimg = (k * kBhA + kBvZero + K * k * kBvFA) / 16;   // B images: hidden/free, then visible
   for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
   for (int w = tid; w < kWords; w += kThr) {
     vbits[w] = jb.bits[(size_t)c * kWords + w];
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
 
   const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], kLbo);   // operand x at + x kOpv / 16
   const uint32_t dvbuf = umma_desc_lo(sbase + ly.vbuf, kLbo), dbh = umma_desc_lo(sbase + ly.bh, 1536),
-                 dbv = umma_desc_lo(sbase + ly.bv, 512);
+                 dbv = umma_desc_lo(sbase + ly.bv, 0);     // LBO set per image
   uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
   uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
   bool live = true;             // false once a wait gave up: no further waits
@@ -523,12 +529,13 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
           const uint32_t tcol = epi_claim();
           if (ty == kStH) {
             if (fq < K) {
-              float s2[8], s1[8];
+              float s2[8], s1[8], s0[8];
               tm_ld8(tcol + 8 * fq, s2);
               tm_ld8(tcol + 32 + 8 * fq, s1);
+              tm_ld8(tcol + 64 + 8 * fq, s0);
               tm_wait();
               epi_release();
-              epi_hidden(jb, smem, ly, s2, s1, i, fq, tl, taghid + (uint32_t)fq, step, cid, sbits, nrec);
+              epi_hidden(jb, smem, ly, s2, s1, s0, i, fq, tl, taghid + (uint32_t)fq, step, cid, sbits, nrec);
             } else {
               epi_release();
             }
@@ -544,25 +551,28 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             }
             epi_publish(bar(kBarH + tl));
           } else {
-            float s2[4], s1[4];
+            float s2[4], s1[4], s0[4];
             tm_ld4(tcol + 4 * fq, s2);
             tm_ld4(tcol + 16 + 4 * fq, s1);
+            tm_ld4(tcol + 32 + 4 * fq, s0);
             if (K > 2) {
               // filters 2, 3 from the second issuer's accumulator (integer sums: exact)
-              float t2[4], t1[4];
-              tm_ld4(tcol + 32 + 4 * fq, t2);
-              tm_ld4(tcol + 48 + 4 * fq, t1);
+              float t2[4], t1[4], t0[4];
+              tm_ld4(tcol + 48 + 4 * fq, t2);
+              tm_ld4(tcol + 64 + 4 * fq, t1);
+              tm_ld4(tcol + 80 + 4 * fq, t0);
               tm_wait();
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 s2[q] += t2[q];
                 s1[q] += t1[q];
+                s0[q] += t0[q];
               }
             } else {
               tm_wait();
             }
             epi_release();
-            epi_visible(jb, smem, ly, s2, s1, i, fq, tl, tagvis, step, cid, dbits, opv_dst, bar(kBarH), gs & 1u,
+            epi_visible(jb, smem, ly, s2, s1, s0, i, fq, tl, tagvis, step, cid, dbits, opv_dst, bar(kBarH), gs & 1u,
                         prm.err, nrec);
             if (tl == 7) epi_publish(bar(kBarV));
           }
@@ -765,7 +775,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
 size_t tc_smem_bytes(int K, int k) { return tc_layout(K, k).total; }
 
 bool tc_supported(int kind, int prec, int L, int K, int k) {
-  return kind == kIsing && prec == kMixed && L == kL && K >= 1 && K <= 4 && k >= 1 && k <= 6;
+  return kind == kIsing && prec == kMixed && L == kL && K >= 1 && K <= 4 && k >= 1 && k <= 5;
 }
 
 // the filter shape of every job of the launch: (K, k) of the first (launches
@@ -783,10 +793,10 @@ cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t
 
 cudaError_t tc_set_smem_limit() {
   cudaError_t e = cudaFuncSetAttribute(crbm_tc_kernel<4, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_layout(4, 6).total);
+                                       (int)tc_layout(4, 5).total);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(crbm_tc_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc_layout(4, 6).total);
+                             (int)tc_layout(4, 5).total);
   return e;
 }
 
