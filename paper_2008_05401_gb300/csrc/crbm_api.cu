@@ -33,7 +33,7 @@ struct Model {
   size_t nlut = 0, nq = 0;
   float hb32[kMaxK] = {}, hb_hi[kMaxK] = {}, hb_lo[kMaxK] = {};
   float vb32 = 0.f;
-  float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f;
+  float c0h = 0.f, c0v = 0.f, c1 = 0.f, csp = 0.f, cdf = 0.f;
   // tensor-core form (Ising, K <= 4, k <= 5): filter-digit operand images
   uint4* d_tc = nullptr;
   size_t tc_bytes = 0;
@@ -193,6 +193,7 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
   d.c0v = m.c0v;
   d.c1 = m.c1;
   d.csp = m.csp;
+  d.cdf = m.cdf;
   d.f64 = m.d_f64;
   d.b64 = m.d_f64 + m.nlut;
   if (m.d_f32) {                 // an LCRBM has FP64 tables only
@@ -612,6 +613,10 @@ static int build_model(crbm_ctx* ctx, Model& m, int kind, int K, int k, const do
   const double lo1 = std::ldexp(1.0, -(gbits + 1));
   const double elo = (k + 2) * u24 * (k + 1) * lo1;
   m.csp = (float)(1.5 * (0.5 * ex2 + u24 + 0.69314718055994531 * lg2 + 0.7 * std::ldexp(1.0, -23)) + elo);
+  // the second-level (df64) free energy's pre-activation: hi sums exact, the
+  // lo entries rounded (2^-24 lo1 each) and summed in FP32, against the FP64
+  // path's sum of k + 1 terms (its own rounding (k + 1) 2^-52 S); factor 2
+  m.cdf = (float)(2.0 * (elo + (k + 1) * u24 * lo1 + (k + 1) * std::ldexp(1.0, -52) * std::fmax(sh, sv)));
   // filter-interleaved copies (entry (a*T + code)*4 + f), zero for f >= K
   const size_t nq = (size_t)k * T;
   std::vector<float> q4(3 * nq * 4, 0.0f);

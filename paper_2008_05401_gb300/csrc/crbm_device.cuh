@@ -57,6 +57,7 @@ struct JobDev {
   float vb32;
   float hb32[kMaxK], hb_hi[kMaxK], hb_lo[kMaxK];
   float c0h, c0v, c1, csp;      // FP32 error-bound constants (see host code)
+  float cdf;                    // per unit: |hi/lo-table pre-activation - FP64 path's|
   const double* f64;            // [K][k][2^k] row-sum tables, see struct Tabs
   const double* b64;
   const float* fd;

@@ -61,6 +61,119 @@ __device__ __forceinline__ df df_sqrt(df a) {
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df df_from_float(float x) { return {x, 0.0f}; }
 
+// ----------------------------------------------- double-FP32 softplus
+// softplus(x) = max(x, 0) + log1p(e^-|x|) in df64, for the mixed path's
+// second-level free energy (an MH decision that the FP32 bound cannot
+// separate is retried with this one before the FP64 path's code runs).
+//   e^-a, 0 <= a <= 40: a = n ln2 + m/64 + r with integers n, m (m <= 44) and
+//     |r| <= 1/128 (+ rounding), e^-a = 2^-n e^(-m/64) e^-r; e^(-m/64) from a
+//     table of df64 constants, e^-r by its Taylor series to r^6 (remainder
+//     < 4e-19), the terms beyond r^2 in FP32 (their FP32 error is < 1e-14);
+//   log1p(e) = y: y0 = ln2 lg2(1 + e) from the special-function unit
+//     (|y0 - y| < 2^-21), then one Newton step on e^y = 1 + e,
+//     y1 = y0 - 1 + (1 + e) e^-y0, whose error is < (y0 - y)^2 / 2 < 2^-43;
+//   a > 40: e^-a < 4.3e-18 and log1p(e) = e to within e^2, e from ex2.
+// With the df64 rounding (< 2^-46 relative per op) and the argument reduction
+// (n ln2 to about 1e-14) the result is within 1e-12 + 2^-44 softplus(x) of
+// the exact value (bound used by free_sum_df).
+struct DfConst {
+  float hi, lo;
+};
+constexpr DfConst dfc(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
+constexpr double exp_neg_m64(int m) {
+  // e^(-m/64) by its Taylor series in double (host-side constant folding)
+  double t = 1.0, s = 1.0, x = -(double)m / 64.0;
+  for (int j = 1; j < 40; ++j) {
+    t *= x / j;
+    s += t;
+  }
+  return s;
+}
+__constant__ DfConst kExpNegM64[45] = {
+    dfc(exp_neg_m64(0)),  dfc(exp_neg_m64(1)),  dfc(exp_neg_m64(2)),  dfc(exp_neg_m64(3)),  dfc(exp_neg_m64(4)),
+    dfc(exp_neg_m64(5)),  dfc(exp_neg_m64(6)),  dfc(exp_neg_m64(7)),  dfc(exp_neg_m64(8)),  dfc(exp_neg_m64(9)),
+    dfc(exp_neg_m64(10)), dfc(exp_neg_m64(11)), dfc(exp_neg_m64(12)), dfc(exp_neg_m64(13)), dfc(exp_neg_m64(14)),
+    dfc(exp_neg_m64(15)), dfc(exp_neg_m64(16)), dfc(exp_neg_m64(17)), dfc(exp_neg_m64(18)), dfc(exp_neg_m64(19)),
+    dfc(exp_neg_m64(20)), dfc(exp_neg_m64(21)), dfc(exp_neg_m64(22)), dfc(exp_neg_m64(23)), dfc(exp_neg_m64(24)),
+    dfc(exp_neg_m64(25)), dfc(exp_neg_m64(26)), dfc(exp_neg_m64(27)), dfc(exp_neg_m64(28)), dfc(exp_neg_m64(29)),
+    dfc(exp_neg_m64(30)), dfc(exp_neg_m64(31)), dfc(exp_neg_m64(32)), dfc(exp_neg_m64(33)), dfc(exp_neg_m64(34)),
+    dfc(exp_neg_m64(35)), dfc(exp_neg_m64(36)), dfc(exp_neg_m64(37)), dfc(exp_neg_m64(38)), dfc(exp_neg_m64(39)),
+    dfc(exp_neg_m64(40)), dfc(exp_neg_m64(41)), dfc(exp_neg_m64(42)), dfc(exp_neg_m64(43)), dfc(exp_neg_m64(44))};
+
+// e^-a for a df64 0 <= a <= 40.1.
+__device__ __forceinline__ df df_exp_neg(df a) {
+  constexpr DfConst ln2 = dfc(0.6931471805599453094172321);
+  const float n = floorf(a.hi * 1.4426950408889634f);
+  const df s = df_add(a, df_neg(df_add(two_prod(n, ln2.hi), {n * ln2.lo, 0.0f})));   // a - n ln2
+  const float mf = fminf(fmaxf(rintf(s.hi * 64.0f), 0.0f), 44.0f);
+  const df r = df_add(s, {-mf * 0.015625f, 0.0f});                                  // s - m/64
+  // e^-r = 1 + (-r) p, p = 1 + (-r)/2 + (-r) q, q = (-r)(1/6 + (-r)(1/24 + (-r)(1/120 + (-r)/720)));
+  // q and (-r) q in FP32: their error is scaled by |r| <= 1/128 in e^-r
+  const float q = -r.hi * fmaf(-r.hi, fmaf(-r.hi, fmaf(-r.hi, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
+                               1.0f / 6.0f);
+  const df nr = df_neg(r);
+  df p = df_add(df_mul(nr, {0.5f, 0.0f}), {1.0f, 0.0f});
+  p = df_add(p, {-r.hi * q, 0.0f});
+  p = df_add(df_mul(nr, p), {1.0f, 0.0f});
+  const int mi = (int)mf;
+  const df t = df_mul(p, {kExpNegM64[mi].hi, kExpNegM64[mi].lo});
+  const float sc = __int_as_float((127 - (int)n) << 23);     // 2^-n exactly (0 <= n <= 58)
+  return {t.hi * sc, t.lo * sc};
+}
+
+// softplus(x) for a df64 x (see above).
+__device__ __forceinline__ df softplus_df(df x) {
+  const df a = x.hi < 0.0f ? df_neg(x) : x;
+  const df pos = x.hi > 0.0f ? x : df{0.0f, 0.0f};
+  if (a.hi > 40.0f) return df_add(pos, {ex2_approx(-a.hi * 1.4426950408889634f), 0.0f});
+  const df e = df_exp_neg(a);
+  const df u = df_add({1.0f, 0.0f}, e);                       // 1 + e
+  const float y0 = 0.69314718055994531f * lg2_approx(u.hi);
+  const df d = df_add(df_mul(u, df_exp_neg({y0, 0.0f})), {-1.0f, 0.0f});   // (1 + e) e^-y0 - 1
+  return df_add(pos, df_add({y0, 0.0f}, d));
+}
+
+// Second-level free-energy sum of a lattice by a chain's group: the sum over
+// units of softplus(h_bias + (W * v)), pre-activations from the hi/lo tables
+// (hi sums exact in FP32, lo sums in FP32: within jb.cdf of the FP64 path's),
+// softplus in df64.  out[0] = the group's partial sum, out[1] = a bound on its
+// error against the FP64 path's terms, out[2] = ones of the lattice.
+static __device__ __noinline__ void free_sum_df(const JobDev& jb, const Grp& g, const uint32_t* v, double* out) {
+  const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = 1 << k;
+  const int nblk = (N + 3) >> 2, iters = (nblk + g.tpc - 1) / g.tpc;
+  df acc = {0.0f, 0.0f};
+  float ssp = 0.0f;
+  int units = 0, ones = 0;
+  for (int it = 0; it < iters; ++it) {
+    const int q = g.r + it * g.tpc;
+    if (!g.active || q >= nblk) continue;
+    uint32_t m[4][kMaxk];
+    fwd_codes<0>(v, L, N, k, T, q, m);
+    for (int t = 0; t < 4; ++t)
+      if (4 * q + t < N) ones += (int)(m[t][0] & 1u);
+    for (int f = 0; f < K; ++f) {
+      const int base = f * k * T;
+      for (int t = 0; t < 4; ++t) {
+        if (4 * q + t >= N) continue;
+        float xh = jb.hb_hi[f], xl = jb.hb_lo[f];
+        for (int a = 0; a < k; ++a) {
+          xh += __ldg(jb.fh + base + m[t][a]);
+          xl += __ldg(jb.fl + base + m[t][a]);
+        }
+        const df sp = softplus_df(two_sum(xh, xl));
+        acc = df_add(acc, sp);
+        ssp += sp.hi;
+        ++units;
+      }
+    }
+  }
+  out[0] = df_to_double(acc);
+  // per unit 1e-12 + 2^-44 softplus (evaluation) + cdf (pre-activation);
+  // the df64 running sum of <= 2^12 terms: 2^-34 of the sum of its terms
+  out[1] = (double)units * (1e-12 + (double)jb.cdf) + (double)ssp * (0x1p-44 + 0x1p-34);
+  out[2] = (double)ones;
+}
+
 // ----------------------------------------------- double-FP32 eigenvalue refinement
 // The Sturm sequence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} and its
 // x-derivative in df64 arithmetic, for the mixed path's eigenvalues: the same

@@ -602,6 +602,38 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         }
       }
     }
+    if (PREC == kMixed && KIND == kIsing) {
+      // second level: F of v' (and of v when only an FP32 value of it is
+      // known) with df64 softplus (bound ~1e-7); flag_rec = 2 sends a decision
+      // that still straddles the threshold on to the FP64 path's code below
+      if (__syncthreads_or(g.active && g.r == 0 && ch.flag_rec)) {
+        Grp g2 = g;
+        g2.active = g.active && ch.flag_rec;
+        Grp g3 = g2;
+        g3.active = g2.active && ch.Fb != 0.0;
+        double f1[3], f2[3];
+        free_sum_df(jb, g2, vp, f1);
+        grp_reduce<3>(f1, g2, scratch);
+        free_sum_df(jb, g3, v, f2);
+        grp_reduce<3>(f2, g3, scratch);
+        if (g2.active && g.r == 0) {
+          ch.Fp = -jb.vb * f1[2] - f1[0];
+          ch.Bp = f1[1] + 1e-15 * fabs(ch.Fp);
+          if (g3.active) {
+            ch.F = -jb.vb * f2[2] - f2[0];
+            ch.Fb = f2[1] + 1e-15 * fabs(ch.F);
+          }
+          const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+          const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g.cid), jb.rk);
+          const double lu = log(((double)w.x + 0.5) * 0x1p-32);
+          const double Mg = ch.Bp + ch.Fb + 1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+          if (logr - lu > Mg) ch.flag_acc = 1, ch.flag_rec = 0;
+          else if (lu - logr > Mg) ch.flag_acc = 0, ch.flag_rec = 0;
+          else ch.flag_rec = 2;
+          ch.rec_mh += 1ull;
+        }
+      }
+    }
     if (PREC == kMixed) {
       const int need = __syncthreads_or(g.active && g.r == 0 && ch.flag_rec);
       if (need) {
@@ -650,7 +682,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
           const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g.cid), jb.rk);
           const double lu = log(((double)w.x + 0.5) * 0x1p-32);
           ch.flag_acc = lu < logr;
-          ch.rec_mh += 1ull;
+          if (KIND == kKitaev) ch.rec_mh += 1ull;   // Ising: counted at the df64 level
         }
       }
     }

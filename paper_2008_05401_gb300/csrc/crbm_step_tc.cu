@@ -85,12 +85,6 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: K-major, no swizzle, rows 16 bytes apart
-// (SBO = 128 between 8-row groups), LBO between 8-column groups.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
-}
 // Instruction descriptor: fp16 x fp16 -> FP32, A and B K-major, M = 128.
 __host__ __device__ constexpr uint32_t umma_idesc(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -258,12 +252,9 @@ __device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t
 // (f, i, 8t .. 8t+7): the hidden units, packed and as fp16 operands.
 __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
                                            const float (&s2)[8], const float (&s1)[8], const float (&s0)[8],
-                                           int i, int f, int t, uint32_t tag, uint32_t step, uint32_t cid,
+                                           int i, int f, int t, const uint4& w0, const uint4& w1,
                                            const uint32_t* src, unsigned& nrec) {
   const int n0 = i * kL + 8 * t;
-  const uint32_t q0 = (uint32_t)(n0 >> 2);
-  const uint4 w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
-  const uint4 w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
   const float hb = jb.hb32[f];
   uint32_t byte = 0u, amb = 0u;
 #pragma unroll
@@ -315,12 +306,10 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
 // (i, 16u + 4cq .. + 3): the visible units, packed and as fp16 F operands.
 __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
                                             const float (&s2)[4], const float (&s1)[4], const float (&s0)[4],
-                                            int i, int cq, int u,
-                                            uint32_t tag, uint32_t step, uint32_t cid, uint32_t* dbits,
+                                            int i, int cq, int u, const uint4& w, uint32_t* dbits,
                                             uint32_t opv, uint32_t hbar, uint32_t parity, int* err,
                                             unsigned& nrec) {
   const int j0 = 16 * u + 4 * cq, n0 = i * kL + j0;
-  const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n0 >> 2), tag, step, cid), jb.rk);
   const uint32_t* hb = (const uint32_t*)(smem + ly.hbits);
   uint32_t nib = 0u, amb = 0u;
 #pragma unroll
@@ -377,6 +366,85 @@ __device__ __forceinline__ void epi_free(const JobDev& jb, const float (&s2)[8],
   const float tt = s32 + y;
   c32 = (tt - s32) - y;
   s32 = tt;
+}
+
+// The MH decision of a chain whose FP32 margin straddled the threshold (every
+// thread of the CTA calls): F of v' (and of v when only an FP32 value of it is
+// known) with df64 softplus, bound ~1e-7; the FP64 path's own code only if that
+// bound still straddles.  Out of line, away from the proposal loop's registers.
+static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm& ch, double* scratch, const uint32_t* pv,
+                                            const uint32_t* vbits, uint32_t step, uint32_t cid, int c) {
+  const int tid = threadIdx.x, k = jb.k;
+  const bool epi = tid < kEpi;
+  {
+      // second level: F of v' (and of v when only an FP32 value of it is
+      // known) with df64 softplus, bound ~1e-7; the FP64 path's own code only
+      // if that bound still straddles the threshold
+      Grp g2;
+      g2.tpc = kEpi;
+      g2.gl = tid / kEpi;
+      g2.r = tid - g2.gl * kEpi;
+      g2.c = c;
+      g2.cid = cid;
+      g2.active = epi;
+      Grp g3 = g2;
+      g3.active = epi && ch.Fb != 0.0;
+      double f1[3], f2[3];
+      free_sum_df(jb, g2, pv, f1);
+      grp_reduce<3>(f1, g2, scratch);
+      free_sum_df(jb, g3, vbits, f2);
+      grp_reduce<3>(f2, g3, scratch);
+      if (tid == 0) {
+        ch.Fp = -jb.vb * f1[2] - f1[0];
+        ch.Bp = f1[1] + 1e-15 * fabs(ch.Fp);
+        if (g3.active) {
+          ch.F = -jb.vb * f2[2] - f2[0];
+          ch.Fb = f2[1] + 1e-15 * fabs(ch.F);
+        }
+        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
+        const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+        const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
+                          1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+        if (logr - logu > Mg) ch.flag_acc = 1;
+        else if (logu - logr > Mg) ch.flag_acc = 0;
+        else ch.flag_rec = 2;
+        ch.rec_mh += 1ull;
+      }
+    }
+    if (__syncthreads_or(tid == 0 && ch.flag_rec == 2)) {
+      Grp g2;
+      g2.tpc = kEpi;
+      g2.gl = tid / kEpi;
+      g2.r = tid - g2.gl * kEpi;
+      g2.c = c;
+      g2.cid = cid;
+      g2.active = epi;
+      Tabs tb64;
+      memset(&tb64, 0, sizeof tb64);
+      tb64.T = 1 << k;
+      tb64.f64 = jb.f64;
+      tb64.b64 = jb.b64;
+      double f1[4];
+      free_energy64(jb, tb64, g2, pv, f1);
+      grp_reduce<4>(f1, g2, scratch);
+      Grp g3 = g2;
+      g3.active = epi && ch.Fb != 0.0;
+      double f2[4];
+      free_energy64(jb, tb64, g3, vbits, f2);
+      grp_reduce<4>(f2, g3, scratch);
+      if (tid == 0) {
+        ch.Fp = -jb.vb * f1[2] - f1[0];
+        ch.Bp = 0.0;
+        if (g3.active) {
+          ch.F = -jb.vb * f2[2] - f2[0];
+          ch.Fb = 0.0;
+        }
+        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
+        ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < logr;
+      }
+    }
 }
 
 // mbarriers in the misc area: full[4] (count 1, MMA commits), empty[4] (count
@@ -526,6 +594,20 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         for (int z = 0; z < 24; ++z, ++zc) {
           int ty, tl;
           hv_stage(z, ty, tl);
+          // this stage's Philox words do not depend on its MMAs: drawn before
+          // waiting for them, so the counter-based generator overlaps the
+          // tensor-core work and the accumulator loads
+          uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+          if (ty == kStH) {
+            if (fq < K) {
+              const uint32_t q0 = (uint32_t)((i * kL + 8 * tl) >> 2), tag = taghid + (uint32_t)fq;
+              w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
+              w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
+            }
+          } else {
+            w0 = philox4x32_10_rk(make_uint4((uint32_t)((i * kL + 16 * tl + 4 * fq) >> 2), tagvis, step, cid), jb.rk);
+            w1 = w0;
+          }
           const uint32_t tcol = epi_claim();
           if (ty == kStH) {
             if (fq < K) {
@@ -535,7 +617,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               tm_ld8(tcol + 64 + 8 * fq, s0);
               tm_wait();
               epi_release();
-              epi_hidden(jb, smem, ly, s2, s1, s0, i, fq, tl, taghid + (uint32_t)fq, step, cid, sbits, nrec);
+              epi_hidden(jb, smem, ly, s2, s1, s0, i, fq, tl, w0, w1, sbits, nrec);
             } else {
               epi_release();
             }
@@ -572,7 +654,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               tm_wait();
             }
             epi_release();
-            epi_visible(jb, smem, ly, s2, s1, s0, i, fq, tl, tagvis, step, cid, dbits, opv_dst, bar(kBarH), gs & 1u,
+            epi_visible(jb, smem, ly, s2, s1, s0, i, fq, tl, w0, dbits, opv_dst, bar(kBarH), gs & 1u,
                         prm.err, nrec);
             if (tl == 7) epi_publish(bar(kBarV));
           }
@@ -679,42 +761,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         else ch.flag_rec = 1;
       }
     }
-    if (__syncthreads_or(tid == 0 && ch.flag_rec)) {
-      // the FP64 path's free energies of v' (and of v when only an FP32 value
-      // of it is known), by the same code and reduction order
-      Grp g2;
-      g2.tpc = kEpi;
-      g2.gl = tid / kEpi;
-      g2.r = tid - g2.gl * kEpi;
-      g2.c = c;
-      g2.cid = cid;
-      g2.active = epi && ch.flag_rec;
-      Tabs tb64;
-      memset(&tb64, 0, sizeof tb64);
-      tb64.T = 1 << k;
-      tb64.f64 = jb.f64;
-      tb64.b64 = jb.b64;
-      double f1[4];
-      free_energy64(jb, tb64, g2, pv, f1);
-      grp_reduce<4>(f1, g2, scratch);
-      Grp g3 = g2;
-      g3.active = g2.active && ch.Fb != 0.0;
-      double f2[4];
-      free_energy64(jb, tb64, g3, vbits, f2);
-      grp_reduce<4>(f2, g3, scratch);
-      if (tid == 0) {
-        ch.Fp = -jb.vb * f1[2] - f1[0];
-        ch.Bp = 0.0;
-        if (g3.active) {
-          ch.F = -jb.vb * f2[2] - f2[0];
-          ch.Fb = 0.0;
-        }
-        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
-        ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < logr;
-        ch.rec_mh += 1ull;
-      }
-    }
+    if (__syncthreads_or(tid == 0 && ch.flag_rec)) mh_redo(jb, ch, scratch, pv, vbits, step, cid, c);
     if (tid == 0) {
       if (ch.flag_acc) {
         ch.F = ch.Fp;
