@@ -27,6 +27,7 @@ struct ChainSm {
   double otp[kNobs];
   double beta;
   double thr[5];         // local Ising sweeps: e^{-beta dE} 2^32 for 0..4 unequal neighbours
+  double logu;           // tensor-core kernel: log u of the current proposal's MH draw
   unsigned long long acc, rec, rec_mh;
   int cur, flag_rec, flag_acc, pad;
 };

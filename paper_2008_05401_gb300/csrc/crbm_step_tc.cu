@@ -569,6 +569,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   for (int s = 0; s < prm.S; ++s) {
     const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
     int src = cur;
+    if (warp == 17 && lane == 1 && prm.correct) {
+      // the MH draw of this proposal, ahead of the decision (read by thread 0
+      // after the barriers of the proposal's end)
+      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
+      ch.logu = log(((double)w.x + 0.5) * 0x1p-32);
+    }
     for (int sub = 0; sub < prm.g; ++sub, ++gs) {
       uint32_t* dbits = (uint32_t*)(smem + ly.pb[0] + (uint32_t)(sub & 1) * (kWords * 4));
       const uint32_t* sbits =
@@ -702,11 +708,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       }
     }
     zc = zbase + 16;
-    cta_sync();                                 // every v' write and F tile done
 
     // per-warp sums: F as an exact 2^-32 fixed-point integer, its error-bound
-    // part in FP32, ones and unequal nearest-neighbour pairs of v'
+    // part in FP32, ones and unequal nearest-neighbour pairs of v' (every
+    // warp's v' writes done: vrdy, completed before the F stages)
     if (epi) {
+      wait_bar(bar(kBarV), (gs - 1) & 1u);
       long long fs = __float2ll_rn(s32 * 0x1p32f);
       float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
       const uint32_t x = pv[tid], xr = pv[(tid & ~3) | ((tid + 1) & 3)], xd = pv[(tid + 4) & (kWords - 1)];
@@ -724,6 +731,19 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       }
     }
     __syncthreads();
+    auto settle = [&]() {        // thread 0: the chain after the decision
+      if (ch.flag_acc) {
+        ch.F = ch.Fp;
+        ch.Fb = ch.Bp;
+        ch.lp = ch.lpp;
+        ch.lpb = ch.lppb;
+        ch.E = ch.Ep;
+        for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
+        ch.acc += 1ull;
+      }
+      for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+      trace_store(jb, c, step0 + (uint64_t)s, ch.E);
+    };
     if (tid == 0) {
       long long fs = 0;
       double bnd = 0.0;
@@ -752,30 +772,20 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         ch.flag_acc = 1;
       } else {
         const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
-        const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+        const double logu = ch.logu;
         const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
                           1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
         if (logr - logu > Mg) ch.flag_acc = 1;
         else if (logu - logr > Mg) ch.flag_acc = 0;
         else ch.flag_rec = 1;
       }
+      if (!ch.flag_rec) settle();
     }
-    if (__syncthreads_or(tid == 0 && ch.flag_rec)) mh_redo(jb, ch, scratch, pv, vbits, step, cid, c);
-    if (tid == 0) {
-      if (ch.flag_acc) {
-        ch.F = ch.Fp;
-        ch.Fb = ch.Bp;
-        ch.lp = ch.lpp;
-        ch.lpb = ch.lppb;
-        ch.E = ch.Ep;
-        for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
-        ch.acc += 1ull;
-      }
-      for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
-      trace_store(jb, c, step0 + (uint64_t)s, ch.E);
+    if (__syncthreads_or(tid == 0 && ch.flag_rec)) {
+      mh_redo(jb, ch, scratch, pv, vbits, step, cid, c);
+      if (tid == 0) settle();
+      __syncthreads();
     }
-    __syncthreads();
     const bool accepted = ch.flag_acc != 0;
     if (tid < kWords) {
       uint32_t* pvw = (uint32_t*)pv;
