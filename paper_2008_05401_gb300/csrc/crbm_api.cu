@@ -121,7 +121,7 @@ struct crbm_ctx {
   // side streams and events of a batch whose jobs need launches of different
   // CTA sizes: the launches fork from the caller's stream and join it again,
   // so they run side by side
-  static constexpr int kSide = 4;
+  static constexpr int kSide = 6;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
   struct Graph {
@@ -304,8 +304,10 @@ static bool on_tc(const crbm_ctx* ctx, const Job& j, int prec, int mode) {
   return ctx->use_tc && ctx->tc_ok && mode == 0 && m.d_tc && !m.edge && tc_supported(j.kind, prec, j.L, m.K, m.k);
 }
 
-// One launch of the tensor-core kernel: one CTA per chain.
-static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, cudaStream_t st) {
+// One launch of the tensor-core kernel for the jobs of one lattice side L: a
+// CTA per 128 / L chains.
+static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int L, int S, int g, int correct,
+                           cudaStream_t st) {
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -321,32 +323,33 @@ static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, in
     const Model& m = ctx->models[j.model];
     p.tile_begin[i] = tiles;
     p.job[i] = make_jobdev(ctx, j);
-    tiles += j.n;
-    smem = std::max(smem, tc_smem_bytes(m.K, m.k));
+    const int ch = tc_chains_per_cta(L);
+    tiles += (j.n + ch - 1) / ch;
+    smem = std::max(smem, tc_smem_bytes(L, m.K, m.k));
   }
   p.tile_begin[ids.size()] = tiles;
   if (tiles == 0) return CRBM_OK;
-  CK(launch_tc(p, tiles, smem, st), "kernel launch");
+  CK(launch_tc(L, p, tiles, smem, st), "kernel launch");
   return CRBM_OK;
 }
 
 static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
                        cudaStream_t st, const Job* partner = nullptr) {
-  // parts: (CTA size, jobs); CTA size 0 = the tensor-core form
+  // parts: (CTA size, jobs); CTA size -L = the tensor-core form for side L
   std::vector<std::pair<int, std::vector<int>>> parts;
-  for (int nt : {0, 256, 128, 64, 32}) {
+  for (int nt : {-128, -64, 256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
       if (j.n == 0) continue;
       const bool tc = !partner && on_tc(ctx, j, prec, mode);
-      if (nt == 0 ? tc : (!tc && threads_for(j.kind, j.N) == nt)) part.push_back(id);
+      if (nt < 0 ? (tc && j.L == -nt) : (!tc && threads_for(j.kind, j.N) == nt)) part.push_back(id);
     }
     if (!part.empty()) parts.emplace_back(nt, part);
   }
   auto launch_part = [&](const std::pair<int, std::vector<int>>& pt, cudaStream_t s) {
-    return pt.first == 0 ? launch_tc_group(ctx, pt.second, S, g, correct, s)
-                         : launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, s, partner);
+    return pt.first < 0 ? launch_tc_group(ctx, pt.second, -pt.first, S, g, correct, s)
+                        : launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, s, partner);
   };
   if (parts.size() <= 1) {
     for (auto& pt : parts) {
@@ -391,7 +394,7 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     e = set_smem_limits((size_t)optin);
-    if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(4, 5)) {
+    if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(128, 4, 5)) {
       e = tc_set_smem_limit();
       ctx->tc_ok = e == cudaSuccess;
     }

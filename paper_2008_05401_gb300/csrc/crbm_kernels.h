@@ -25,10 +25,11 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Tensor-core form of the proposal kernel (crbm_step_tc.cu): Ising kind, mixed
-// precision, L = 128, K <= 4, k <= 5, one CTA per chain.
+// precision, L = 128 (one chain per CTA) or L = 64 (two), K <= 4, k <= 5.
 bool tc_supported(int kind, int prec, int L, int K, int k);
-size_t tc_smem_bytes(int K, int k);
-cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st);
+int tc_chains_per_cta(int L);
+size_t tc_smem_bytes(int L, int K, int k);
+cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t tc_set_smem_limit();
 // Random initial lattices (init tag of the stream).
 cudaError_t launch_random_init(uint32_t* bits, int n_chains, int N, int Wd, uint64_t seed,

@@ -1,20 +1,25 @@
 // Tensor-core form of the fused CRBM proposal + Metropolis-Hastings kernel:
-// Ising kind, mixed precision, 128 x 128 lattices, K <= 4 filters of side
-// k <= 5, mode 0 (S proposals of g Gibbs steps).  One chain per CTA.  The
-// chain is the table kernel's chain: the same Philox words per unit, and every
-// Bernoulli and MH decision the FP64 path's.
+// Ising kind, mixed precision, L x L lattices with L = 128 (one chain per CTA)
+// or L = 64 (two chains per CTA), K <= 4 filters of side k <= 5, mode 0 (S
+// proposals of g Gibbs steps).  The chains are the table kernel's chains: the
+// same Philox words per unit, and every Bernoulli and MH decision the FP64
+// path's.
 //
 // The three convolutions of a proposal are tcgen05 MMAs with FP32
-// accumulators in tensor memory, D[i][n] = sum_kk A[i][kk] B[kk][n] over the
-// M = 128 lattice rows i:
+// accumulators in tensor memory, D[m][n] = sum_kk A[m][kk] B[kk][n] over the
+// M = 128 operand rows m:
 //   hidden pre-activations of v  (Eq. B2; Eq. 12), one MMA per kernel row a
 //       reading the lattice rows i + a;
 //   visible pre-activations of h (Eq. B3), one MMA per (filter, kernel row a)
 //       reading the hidden rows i - a;
 //   hidden pre-activations of v' for F(v') (Eq. 13).
+// Operand row m holds lattice row i = m / CH of chain c = m % CH (CH = 128 / L
+// chains per CTA, rows interleaved), so that lattice row i + a is operand row
+// m + CH a for every chain at once.
 // A operands: the 0/1 units in fp16, K-major without swizzle, rows 16 bytes
 // apart and 8-column groups one LBO apart, so the operand of kernel row a is
-// the same array started a rows further on; periodic halos are copies.
+// the same array started CH a rows further on; periodic halos are copies
+// (operand rows 128.. repeat rows 0.., the last column group repeats the first).
 // B operands: banded Toeplitz images of the filters (built on the host).  Each
 // weight is written as W = qf (c2 2^22 + c1 2^11 + c0), qf a power of two and
 // integer digits |c| <= 1024 (exact in fp16).  Units times digits summed over
@@ -25,32 +30,30 @@
 // constants (the FP64 tables decide inside it); the free energy carries its
 // error bound into the MH decision like the table kernel's FP32 free energy.
 //
-// Schedule per Gibbs step: 16 hidden tiles of 8 columns (H) and 8 visible
-// tiles of 16 columns (V), interleaved so that a V tile's MMAs run while the
-// epilogue warps work through the two H stages after its last input tile
-// (H15 H0 H1 H2 H3 V0 H4 H5 V1 ... H12 H13 V5 H14 V6 V7);
-// then 16 free-energy tiles (F).  Warp-specialised pipeline: the control warp
-// issues each stage's MMAs into one of four tensor-memory buffers and commits
-// them to that buffer's `full` mbarrier; the 16 epilogue warps (warp w: lanes
-// 32 (w % 4) .. + 31 = lattice rows, w / 4 = filter or column quarter) take
-// the stages in the same order, read the accumulators, arrive on the buffer's
-// `empty` mbarrier and make the stage's decisions.  A V stage's MMAs wait on
-// the `hrdy` mbarriers of its three H tiles (every warp's fp16 hidden units
-// written and fenced), the F stages on `vrdy` (every warp's v' written); CTA
-// barriers only at the end of a proposal (reductions, MH) and between Gibbs
-// steps.
+// Schedule per Gibbs step: NT = L / 8 hidden tiles of 8 columns (H) and
+// NV = L / 16 visible tiles of 16 columns (V), interleaved so that a V tile's
+// MMAs run while the epilogue warps work through the two H stages after its
+// last input tile (L = 128: H15 H0 H1 H2 H3 V0 H4 H5 V1 ... H12 H13 V5 H14 V6
+// V7); then NT free-energy tiles (F).  Warp-specialised pipeline: two issuing
+// warps put each stage's MMAs into one of four tensor-memory buffers and
+// commit them to that buffer's `full` mbarrier; the 16 epilogue warps (warp
+// w: lanes 32 (w % 4) .. + 31 = operand rows, w / 4 = filter or column
+// quarter) take the stages in the same order, read the accumulators, arrive
+// on the buffer's `empty` mbarrier and make the stage's decisions.  A V
+// stage's MMAs wait on the `hrdy` mbarriers of its three H tiles (every warp's
+// fp16 hidden units written and fenced), the F stages on `vrdy` (every warp's
+// v' written); CTA barriers only at the end of a proposal (reductions, MH)
+// and between Gibbs steps.
 #include "crbm_step.cuh"
 
 namespace crbm {
 namespace {
 
-constexpr int kL = 128, kN = kL * kL, kWords = kN / 32;   // 4 words per lattice row
 constexpr int kEpi = 512, kThr = kEpi + 64;                // 16 epilogue warps + 2 MMA-issuing warps
-constexpr int kRows = 136, kLbo = kRows * 16;              // one 8-column group of 136 rows
-constexpr int kOpv = 17 * kLbo;                            // 136 columns
+constexpr int kRows = 136, kLbo = kRows * 16;              // one 8-column group of 136 operand rows
 constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a V buffer: 3 groups
 constexpr int kVbuf = 4 * kPlane3;
-constexpr int kP15 = 4 * kLbo;
+constexpr int kPgrp = 4 * kLbo;                            // one column group of 4 hidden planes
 constexpr int kBhA = 3072;                                 // per kernel row: K=16 x N=96
 // visible images, per (filter, kernel row): step 0 K=16 x N=48 (1536 B), step
 // 1 only its second K-group (768 B; the first is zero and read from one shared
@@ -58,27 +61,41 @@ constexpr int kBhA = 3072;                                 // per kernel row: K=
 constexpr int kBvZero = 768, kBvFA = 2304;
 constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
 
-struct TcLayout {
-  uint32_t opv[2], vbuf, p15, hold, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
+// Geometry of an L x L lattice in the 128-row operands.
+template <int LT>
+struct Geo {
+  static constexpr int CH = 128 / LT;               // chains per CTA
+  static constexpr int NT = LT / 8, NV = LT / 16;    // H / F tiles, V tiles
+  static constexpr int GROUPS = LT / 8 + 1;          // operand column groups (the last a halo)
+  static constexpr int OPV = GROUPS * kLbo;
+  static constexpr int WPR = LT / 32, WPC = LT * LT / 32;   // words per row / per chain
+  static constexpr int NHV = NT + NV;                // H and V stages per Gibbs step
+  static_assert(LT == 128 || LT == 64, "lattice side");
 };
 
+struct TcLayout {
+  uint32_t opv[2], vbuf, plast, hold, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
+};
+
+template <int LT>
 __host__ __device__ inline TcLayout tc_layout(int K, int k) {
+  using G = Geo<LT>;
   TcLayout l;
   uint32_t o = 0;
-  l.opv[0] = o; o += kOpv;            // lattice operand (v or v', fp16), two buffers
-  l.opv[1] = o; o += kOpv;
+  l.opv[0] = o; o += G::OPV;          // lattice operands (v; v'), two buffers
+  l.opv[1] = o; o += G::OPV;
   l.vbuf = o; o += 2 * kVbuf;         // hidden operands of V tiles, two buffers of 3 groups
-  l.p15 = o; o += kP15;               // hidden tile 15 (columns 120..127), kept for V7
-  l.hold = o; o += kP15;              // the last odd hidden tile, until the next even one moves it
+  l.plast = o; o += kPgrp;            // the last hidden tile, kept for the last V tile
+  l.hold = o; o += kPgrp;             // the last odd hidden tile, until the next even one moves it
   l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
   l.bv = o; o += (uint32_t)(kBvZero + K * k * kBvFA);   // visible
-  l.vbits = o; o += kWords * 4;       // packed current lattice
-  l.pb[0] = o; o += kWords * 4;       // packed proposals (ping-pong over Gibbs steps)
-  l.pb[1] = o; o += kWords * 4;
-  l.hbits = o; o += 4 * kWords * 4;   // packed hidden units, one plane per filter
+  l.vbits = o; o += G::CH * G::WPC * 4;         // packed current lattices, chain-major
+  l.pb[0] = o; o += G::CH * G::WPC * 4;         // packed proposals (ping-pong over Gibbs steps)
+  l.pb[1] = o; o += G::CH * G::WPC * 4;
+  l.hbits = o; o += G::CH * 4 * G::WPC * 4;     // packed hidden units: chain, then filter planes
   l.scratch = o; o += 256 * 8;
-  l.ch = o; o += (uint32_t)align16(sizeof(ChainSm));
-  l.misc = o; o += 512;               // mbarriers, TMEM address, counters, reduction slots
+  l.ch = o; o += (uint32_t)align16(G::CH * sizeof(ChainSm));
+  l.misc = o; o += 1024;              // mbarriers, TMEM address, counters, reduction slots
   l.total = o;
   return l;
 }
@@ -154,21 +171,26 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 enum { kStH = 0, kStV = 1, kStF = 2 };
 
-// Stage z (0..23) of a Gibbs step: H15 H0 H1 H2 H3, then (V_u H_{2u+4}
-// H_{2u+5}) for u = 0..4, then V5 H14 V6 V7.  V_u reads H tiles 2u-1, 2u, 2u+1
-// (mod 16); it comes two H stages after the last of them, so its MMAs run
-// while the epilogue warps work through those stages.
+// Stage z (0 .. NT+NV-1) of a Gibbs step: H_{NT-1} H0 H1 H2 H3, then
+// (V_u H_{2u+4} H_{2u+5}) for u = 0 .. NV-4, then V_{NV-3} H_{NT-2} V_{NV-2}
+// V_{NV-1}.  V_u reads H tiles 2u-1, 2u, 2u+1 (mod NT); it comes two H stages
+// after the last of them, so its MMAs run while the epilogue warps work
+// through those stages.
+template <int LT>
 __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
+  using G = Geo<LT>;
+  constexpr int kLoop = 5 + 3 * (G::NV - 3);
   if (z < 5) {
     type = kStH;
-    tile = z == 0 ? 15 : z - 1;
-  } else if (z >= 20) {
-    type = z == 21 ? kStH : kStV;
-    tile = z == 20 ? 5 : (z == 21 ? 14 : z - 16);
-  } else {
+    tile = z == 0 ? G::NT - 1 : z - 1;
+  } else if (z < kLoop) {
     const int u = (z - 5) / 3, r = (z - 5) - 3 * u;
     type = r == 0 ? kStV : kStH;
     tile = r == 0 ? u : 2 * u + 3 + r;
+  } else {
+    const int e = z - kLoop;
+    type = e == 1 ? kStH : kStV;
+    tile = e == 0 ? G::NV - 3 : (e == 1 ? G::NT - 2 : G::NV - 4 + e);
   }
 }
 
@@ -179,13 +201,15 @@ __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
 // counts two arrivals).
 // H/F tile t (role 0): N = 96, columns e*32 + f*8 + jj for the digits e = c2,
 // c1, c0.  V tile u: N = 48, columns e*16 + jj, filters f < 2 into dcol (role
-// 0) and f >= 2 into dcol + 48 (role 1); slots s, s+1 of the tile's V buffer.  *lo: low descriptor words of the operand bases (start fields
-// advance by byte offset / 16).  KT, kT > 0 fix K and k at compile time, so
-// that the issue sequence is straight-line code with immediate offsets.
-template <int KT, int kT>
+// 0) and f >= 2 into dcol + 48 (role 1); slots s, s+1 of the tile's V buffer.
+// *lo: low descriptor words of the operand bases (start fields advance by byte
+// offset / 16).  KT, kT > 0 fix K and k at compile time, so that the issue
+// sequence is straight-line code with immediate offsets.
+template <int LT, int KT, int kT>
 __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32_t dcol, uint32_t opvlo,
                                             uint32_t vbuflo, uint32_t bhlo, uint32_t bvlo, int Kr, int kr,
                                             uint32_t mbar) {
+  constexpr int CH = Geo<LT>::CH;
   const int K = KT ? KT : Kr, k = kT ? kT : kr;
   if (type != kStV) {
     if (role == 0) {
@@ -193,7 +217,7 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
       const uint32_t a0 = opvlo + (uint32_t)(tile * (kLbo >> 4));
 #pragma unroll
       for (int a = 0; a < (kT ? kT : 8); ++a)
-        if (kT || a < k) umma(dcol, a0 + (uint32_t)a, bhlo + (uint32_t)(a * (kBhA >> 4)), id, a > 0);
+        if (kT || a < k) umma(dcol, a0 + (uint32_t)(a * CH), bhlo + (uint32_t)(a * (kBhA >> 4)), id, a > 0);
     }
   } else {
     const uint32_t id = umma_idesc(48);
@@ -208,7 +232,7 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
         for (int s = 0; s < 2; ++s) {
           const int f = f0 + ff;
           if (f < f1 && (kT || a < k)) {
-            const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - a) * 16);
+            const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - CH * a) * 16);
             const uint32_t fa = (uint32_t)(kBvZero + (f * k + a) * kBvFA);
             // step 0: start at its block, LBO 768; step 1: start at the zero
             // group, LBO = distance to its block
@@ -221,40 +245,62 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
   umma_commit(mbar);
 }
 
-// FP64 redo of hidden unit (f, n) from the packed source lattice: the FP64
-// path's sum (h_bias, then kernel rows a = 0..k-1 from the FP64 tables).
+// FP64 redo of hidden unit (f, n) of a chain from its packed source lattice:
+// the FP64 path's sum (h_bias, then kernel rows a = 0..k-1 from the FP64 tables).
+template <int LT>
 static __device__ __noinline__ uint32_t tc_redo_hidden(const JobDev& jb, int f, const uint32_t* v, int n,
                                                        uint32_t w) {
-  const int k = jb.k, T = 1 << k, i = n >> 7, j = n & (kL - 1);
+  const int k = jb.k, T = 1 << k, i = n / LT, j = n - i * LT;
   double x = jb.hb[f];
-  for (int a = 0; a < k; ++a) x += __ldg(jb.f64 + (f * k + a) * T + row_window(v, kL, (i + a) & (kL - 1), j, k));
+  for (int a = 0; a < k; ++a) x += __ldg(jb.f64 + (f * k + a) * T + row_window(v, LT, (i + a) % LT, j, k));
   return decide64(x, w);
 }
 
-// fp16 units of a packed lattice into a lattice operand (136 x 136 with the
-// periodic copies of rows and columns 0..7).
-__device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t* bits, int tid, int nthr) {
+// fp16 units of packed lattices (chain-major) into a lattice operand (136
+// rows x GROUPS column groups, the periodic copies included); only the rows of
+// chain `only` when only >= 0.
+template <int LT>
+__device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t* bits, int tid, int nthr,
+                               int only = -1) {
+  using G = Geo<LT>;
   const unsigned char* by = (const unsigned char*)bits;
-  for (int q = tid; q < kRows * 17; q += nthr) {
-    const int G = q / kRows, r = q - G * kRows;
-    const uint32_t x = by[(r & (kL - 1)) * (kL / 8) + (G & 15)];
+  for (int q = tid; q < kRows * G::GROUPS; q += nthr) {
+    const int g = q / kRows, r = q - g * kRows;
+    const int rr = r & 127, c = rr % G::CH, i = rr / G::CH;
+    if (only >= 0 && c != only) continue;
+    const uint32_t x = by[c * (G::WPC * 4) + i * (LT / 8) + (g % G::NT)];
     const uint32_t z = x | (x << 15);       // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
     uint4 o;
     o.x = ((z >> 0) & 0x10001u) * 0x3C00u;
     o.y = ((z >> 2) & 0x10001u) * 0x3C00u;
     o.z = ((z >> 4) & 0x10001u) * 0x3C00u;
     o.w = ((z >> 6) & 0x10001u) * 0x3C00u;
-    *(uint4*)(smem + opv + (uint32_t)G * kLbo + (uint32_t)r * 16) = o;
+    *(uint4*)(smem + opv + (uint32_t)g * kLbo + (uint32_t)r * 16) = o;
   }
 }
 
-// H tile t, thread (row i, filter f), digit sums s2, s1, s0 of its 8 units
-// (f, i, 8t .. 8t+7): the hidden units, packed and as fp16 operands.
+// The rows of chain c from one lattice operand to another.
+template <int LT>
+__device__ void copy_chain_rows(unsigned char* smem, uint32_t dst, uint32_t src, int c, int tid, int nthr) {
+  using G = Geo<LT>;
+  for (int q = tid; q < kRows * G::GROUPS; q += nthr) {
+    const int g = q / kRows, r = q - g * kRows;
+    if ((r & 127) % G::CH != c) continue;
+    const uint32_t off = (uint32_t)g * kLbo + (uint32_t)r * 16;
+    *(uint4*)(smem + dst + off) = *(const uint4*)(smem + src + off);
+  }
+}
+
+// H tile t, thread (operand row m = lattice row i of its chain), filter f,
+// digit sums of its 8 units (f, i, 8t .. 8t+7), Philox words w0, w1: the hidden
+// units, packed (into its chain's planes hbc) and as fp16 operands.
+template <int LT>
 __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
                                            const float (&s2)[8], const float (&s1)[8], const float (&s0)[8],
-                                           int i, int f, int t, const uint4& w0, const uint4& w1,
-                                           const uint32_t* src, unsigned& nrec) {
-  const int n0 = i * kL + 8 * t;
+                                           int m, int i, int f, int t, const uint4& w0, const uint4& w1,
+                                           const uint32_t* src, uint32_t hbc, unsigned& nrec) {
+  using G = Geo<LT>;
+  const int n0 = i * LT + 8 * t;
   const float hb = jb.hb32[f];
   uint32_t byte = 0u, amb = 0u;
 #pragma unroll
@@ -269,20 +315,20 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
     // units inside the certified margin: the FP64 path decides (rare)
     for (int jj = 0; jj < 8; ++jj)
       if ((amb >> jj) & 1u) {
-        const uint32_t bit = tc_redo_hidden(jb, f, src, n0 + jj, pick(jj < 4 ? w0 : w1, jj & 3));
+        const uint32_t bit = tc_redo_hidden<LT>(jb, f, src, n0 + jj, pick(jj < 4 ? w0 : w1, jj & 3));
         byte = (byte & ~(1u << jj)) | (bit << jj);
         ++nrec;
       }
   }
-  smem[ly.hbits + (uint32_t)f * (kWords * 4) + (uint32_t)(n0 >> 3)] = (unsigned char)byte;
+  smem[hbc + (uint32_t)f * (G::WPC * 4) + (uint32_t)(n0 >> 3)] = (unsigned char)byte;
   const uint32_t z = byte | (byte << 15);     // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
   const uint4 h4 = make_uint4(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u,
                               ((z >> 4) & 0x10001u) * 0x3C00u, ((z >> 6) & 0x10001u) * 0x3C00u);
-  // rows i + 8 of the V operands; rows 120..127 also as rows -8..-1
-  const uint32_t r0 = (uint32_t)(i + 8) * 16, r1 = (uint32_t)(i - (kL - 8)) * 16;
+  // operand rows m + 8 of the V operands; rows 120..127 also as rows -8..-1
+  const uint32_t r0 = (uint32_t)(m + 8) * 16, r1 = (uint32_t)(m - 120) * 16;
   auto put = [&](uint32_t base) {
     *(uint4*)(smem + base + r0) = h4;
-    if (i >= kL - 8) *(uint4*)(smem + base + r1) = h4;
+    if (m >= 120) *(uint4*)(smem + base + r1) = h4;
   };
   // V_u reads slots (0, 1, 2) = tiles (2u-1, 2u, 2u+1) of buffer u % 2, last
   // read by V_{u-2}, which precedes H_{2u} in the stage order.  An odd tile goes
@@ -294,23 +340,25 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
     const uint32_t vb = ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf;
     put(vb + 1 * kLbo);
     *(uint4*)(smem + vb + r0) = *(const uint4*)(smem + hf + r0);
-    if (i >= kL - 8) *(uint4*)(smem + vb + r1) = *(const uint4*)(smem + hf + r1);
+    if (m >= 120) *(uint4*)(smem + vb + r1) = *(const uint4*)(smem + hf + r1);
   } else {
-    if (t != 15) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);
-    else put(ly.p15 + (uint32_t)f * kLbo);      // V7's last slot is still in use by V1, V3, V5
+    if (t != G::NT - 1) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);
+    else put(ly.plast + (uint32_t)f * kLbo);    // the last V tile's last slot is in use by earlier V tiles
     put(hf);
   }
 }
 
-// V tile u, thread (row i, column quarter cq), digit sums of its 4 units
-// (i, 16u + 4cq .. + 3): the visible units, packed and as fp16 F operands.
-__device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const TcLayout& ly,
-                                            const float (&s2)[4], const float (&s1)[4], const float (&s0)[4],
-                                            int i, int cq, int u, const uint4& w, uint32_t* dbits,
-                                            uint32_t opv, uint32_t hbar, uint32_t parity, int* err,
+// V tile u, thread (operand row m = lattice row i of its chain), column
+// quarter cq, digit sums of its 4 units (i, 16u + 4cq .. + 3), Philox word w:
+// the visible units, packed (into its chain's dbc) and as fp16 F operands.
+template <int LT>
+__device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const float (&s2)[4],
+                                            const float (&s1)[4], const float (&s0)[4], int m, int i, int cq,
+                                            int u, const uint4& w, uint32_t* dbc, uint32_t opv,
+                                            const uint32_t* hbc, uint32_t hbar, uint32_t parity, int* err,
                                             unsigned& nrec) {
-  const int j0 = 16 * u + 4 * cq, n0 = i * kL + j0;
-  const uint32_t* hb = (const uint32_t*)(smem + ly.hbits);
+  using G = Geo<LT>;
+  const int j0 = 16 * u + 4 * cq, n0 = i * LT + j0;
   uint32_t nib = 0u, amb = 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -323,26 +371,26 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
   if (amb) {
     // the packed hidden units of H tiles 2u-1, 2u, 2u+1 come from other warps:
     // their hrdy mbarriers (completed before this tile's MMAs) order them
-    const int tt[3] = {(2 * u + 15) & 15, 2 * u, 2 * u + 1};
+    const int tt[3] = {(2 * u + G::NT - 1) % G::NT, 2 * u, 2 * u + 1};
     for (int q = 0; q < 3; ++q)
       if (!mbar_wait(hbar + 8u * (uint32_t)tt[q], parity)) atomicExch(err, kErrTimeout);
     for (int t = 0; t < 4; ++t)
       if ((amb >> t) & 1u) {
-        const uint32_t bit = recompute_visible(jb, hb, kWords, n0 + t, pick(w, t));
+        const uint32_t bit = recompute_visible(jb, hbc, G::WPC, n0 + t, pick(w, t));
         nib = (nib & ~(1u << t)) | (bit << t);
         ++nrec;
       }
   }
-  atomicOr(dbits + (n0 >> 5), nib << (n0 & 31));
+  atomicOr(dbc + (n0 >> 5), nib << (n0 & 31));
   const uint32_t z = nib | (nib << 15);
   const uint2 h2 = make_uint2(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u);
   const uint32_t off = opv + (uint32_t)(j0 >> 3) * kLbo + (uint32_t)(j0 & 7) * 2;
-  *(uint2*)(smem + off + (uint32_t)i * 16) = h2;
-  if (i < 8) *(uint2*)(smem + off + (uint32_t)(i + kL) * 16) = h2;
-  if (j0 < 8) {        // columns 128..135 repeat columns 0..7
-    const uint32_t o2 = opv + 16 * kLbo + (uint32_t)(j0 & 7) * 2;
-    *(uint2*)(smem + o2 + (uint32_t)i * 16) = h2;
-    if (i < 8) *(uint2*)(smem + o2 + (uint32_t)(i + kL) * 16) = h2;
+  *(uint2*)(smem + off + (uint32_t)m * 16) = h2;
+  if (m < 8) *(uint2*)(smem + off + (uint32_t)(m + 128) * 16) = h2;
+  if (j0 < 8) {        // the last column group repeats the first
+    const uint32_t o2 = opv + (uint32_t)G::NT * kLbo + (uint32_t)(j0 & 7) * 2;
+    *(uint2*)(smem + o2 + (uint32_t)m * 16) = h2;
+    if (m < 8) *(uint2*)(smem + o2 + (uint32_t)(m + 128) * 16) = h2;
   }
 }
 
@@ -368,137 +416,146 @@ __device__ __forceinline__ void epi_free(const JobDev& jb, const float (&s2)[8],
   s32 = tt;
 }
 
-// The MH decision of a chain whose FP32 margin straddled the threshold (every
-// thread of the CTA calls): F of v' (and of v when only an FP32 value of it is
-// known) with df64 softplus, bound ~1e-7; the FP64 path's own code only if that
-// bound still straddles.  Out of line, away from the proposal loop's registers.
-static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm& ch, double* scratch, const uint32_t* pv,
-                                            const uint32_t* vbits, uint32_t step, uint32_t cid, int c) {
+// The MH decisions of the chains whose FP32 margin straddled the threshold
+// (every thread of the CTA calls; the CH chains' groups of 512 / CH epilogue
+// threads work side by side): F of v' (and of v when only an FP32 value of it
+// is known) with df64 softplus, bound ~1e-7; the FP64 path's own code only if
+// that bound still straddles.  Out of line, away from the proposal loop's
+// registers.  c0: the chain index of the CTA's first chain.
+template <int LT>
+static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, double* scratch, const uint32_t* pv,
+                                            const uint32_t* vbits, uint32_t step, int c0) {
+  using G = Geo<LT>;
   const int tid = threadIdx.x, k = jb.k;
-  const bool epi = tid < kEpi;
+  Grp g2;
+  g2.tpc = kEpi / G::CH;
+  g2.gl = tid / g2.tpc;
+  g2.r = tid - g2.gl * g2.tpc;
+  const int c = g2.gl < G::CH ? g2.gl : 0;          // this thread's chain (the issuing warps: none)
+  ChainSm& ch = chs[c];
+  g2.c = c0 + c;
+  g2.cid = (uint32_t)(jb.cid_base + (uint64_t)g2.c);
+  g2.active = tid < kEpi && ch.flag_rec != 0;
   {
-      // second level: F of v' (and of v when only an FP32 value of it is
-      // known) with df64 softplus, bound ~1e-7; the FP64 path's own code only
-      // if that bound still straddles the threshold
-      Grp g2;
-      g2.tpc = kEpi;
-      g2.gl = tid / kEpi;
-      g2.r = tid - g2.gl * kEpi;
-      g2.c = c;
-      g2.cid = cid;
-      g2.active = epi;
-      Grp g3 = g2;
-      g3.active = epi && ch.Fb != 0.0;
-      double f1[3], f2[3];
-      free_sum_df(jb, g2, pv, f1);
-      grp_reduce<3>(f1, g2, scratch);
-      free_sum_df(jb, g3, vbits, f2);
-      grp_reduce<3>(f2, g3, scratch);
-      if (tid == 0) {
-        ch.Fp = -jb.vb * f1[2] - f1[0];
-        ch.Bp = f1[1] + 1e-15 * fabs(ch.Fp);
-        if (g3.active) {
-          ch.F = -jb.vb * f2[2] - f2[0];
-          ch.Fb = f2[1] + 1e-15 * fabs(ch.F);
-        }
-        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
-        const double logu = log(((double)w.x + 0.5) * 0x1p-32);
-        const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
-                          1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
-        if (logr - logu > Mg) ch.flag_acc = 1;
-        else if (logu - logr > Mg) ch.flag_acc = 0;
-        else ch.flag_rec = 2;
-        ch.rec_mh += 1ull;
+    Grp g3 = g2;
+    g3.active = g2.active && ch.Fb != 0.0;
+    double f1[3], f2[3];
+    free_sum_df(jb, g2, pv + c * G::WPC, f1);
+    grp_reduce<3>(f1, g2, scratch);
+    free_sum_df(jb, g3, vbits + c * G::WPC, f2);
+    grp_reduce<3>(f2, g3, scratch);
+    if (g2.active && g2.r == 0) {
+      ch.Fp = -jb.vb * f1[2] - f1[0];
+      ch.Bp = f1[1] + 1e-15 * fabs(ch.Fp);
+      if (g3.active) {
+        ch.F = -jb.vb * f2[2] - f2[0];
+        ch.Fb = f2[1] + 1e-15 * fabs(ch.F);
       }
+      const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g2.cid), jb.rk);
+      const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+      const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
+                        1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+      if (logr - logu > Mg) ch.flag_acc = 1;
+      else if (logu - logr > Mg) ch.flag_acc = 0;
+      else ch.flag_rec = 2;
+      ch.rec_mh += 1ull;
     }
-    if (__syncthreads_or(tid == 0 && ch.flag_rec == 2)) {
-      Grp g2;
-      g2.tpc = kEpi;
-      g2.gl = tid / kEpi;
-      g2.r = tid - g2.gl * kEpi;
-      g2.c = c;
-      g2.cid = cid;
-      g2.active = epi;
-      Tabs tb64;
-      memset(&tb64, 0, sizeof tb64);
-      tb64.T = 1 << k;
-      tb64.f64 = jb.f64;
-      tb64.b64 = jb.b64;
-      double f1[4];
-      free_energy64(jb, tb64, g2, pv, f1);
-      grp_reduce<4>(f1, g2, scratch);
-      Grp g3 = g2;
-      g3.active = epi && ch.Fb != 0.0;
-      double f2[4];
-      free_energy64(jb, tb64, g3, vbits, f2);
-      grp_reduce<4>(f2, g3, scratch);
-      if (tid == 0) {
-        ch.Fp = -jb.vb * f1[2] - f1[0];
-        ch.Bp = 0.0;
-        if (g3.active) {
-          ch.F = -jb.vb * f2[2] - f2[0];
-          ch.Fb = 0.0;
-        }
-        const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
-        ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < logr;
+  }
+  if (__syncthreads_or(g2.active && g2.r == 0 && ch.flag_rec == 2)) {
+    Grp g4 = g2;
+    g4.active = g2.active && ch.flag_rec == 2;
+    Tabs tb64;
+    memset(&tb64, 0, sizeof tb64);
+    tb64.T = 1 << k;
+    tb64.f64 = jb.f64;
+    tb64.b64 = jb.b64;
+    double f1[4];
+    free_energy64(jb, tb64, g4, pv + c * G::WPC, f1);
+    grp_reduce<4>(f1, g4, scratch);
+    Grp g3 = g4;
+    g3.active = g4.active && ch.Fb != 0.0;
+    double f2[4];
+    free_energy64(jb, tb64, g3, vbits + c * G::WPC, f2);
+    grp_reduce<4>(f2, g3, scratch);
+    if (g4.active && g4.r == 0) {
+      ch.Fp = -jb.vb * f1[2] - f1[0];
+      ch.Bp = 0.0;
+      if (g3.active) {
+        ch.F = -jb.vb * f2[2] - f2[0];
+        ch.Fb = 0.0;
       }
+      const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g4.cid), jb.rk);
+      ch.flag_acc = log(((double)w.x + 0.5) * 0x1p-32) < logr;
     }
+  }
 }
 
-// mbarriers in the misc area: full[4] (count 1, MMA commits), empty[4] (count
+// mbarriers in the misc area: full[4] (count 2, MMA commits), empty[4] (count
 // 16, epilogue warps), hrdy[16] (count 16: H tile's fp16 units written),
-// vrdy (count 16: every V tile's v' written), fin (count 1, last commit).
+// vrdy (count 16: every V tile's v' written), fin (count 2, last commits);
+// then the TMEM address, per-chain Bernoulli redo counts, and the reduction
+// slots: per (warp, chain) the F partial (int64) and its bound (FP32), per
+// warp the lattice counts of the chain its count-pass words belong to.
 constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kNbar = 26;
-constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = kMiscTslot + 8, kMiscRed = kMiscNrec + 8;   // reduction: 16 x 16 B
+constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224, kMiscRedF = 256, kMiscRedC = 768;
 
-template <int KT, int kT>
+template <int LT, int KT, int kT>
 __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
+  using G = Geo<LT>;
+  constexpr int CH = G::CH, WPC = G::WPC;
   int jid = 0;
   while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
   const JobDev& jb = prm.job[jid];
-  const int c = (int)blockIdx.x - prm.tile_begin[jid];      // one chain per CTA
+  const int c0 = ((int)blockIdx.x - prm.tile_begin[jid]) * CH;   // the CTA's first chain
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = warp < 16;
   const int K = jb.K, k = jb.k;
-  const TcLayout ly = tc_layout(K, k);
+  const TcLayout ly = tc_layout<LT>(K, k);
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t sbase = sm_addr(smem);
   uint32_t* vbits = (uint32_t*)(smem + ly.vbits);
-  ChainSm& ch = *(ChainSm*)(smem + ly.ch);
+  ChainSm* chs = (ChainSm*)(smem + ly.ch);
   double* scratch = (double*)(smem + ly.scratch);
   const uint32_t bar0 = sbase + ly.misc;
   auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
   uint32_t* tslot = (uint32_t*)(smem + ly.misc + kMiscTslot);
   unsigned long long* nrec_sm = (unsigned long long*)(smem + ly.misc + kMiscNrec);
-  unsigned char* red = smem + ly.misc + kMiscRed;
-  const uint32_t cid = (uint32_t)(jb.cid_base + (uint64_t)c);
+  unsigned char* redf = smem + ly.misc + kMiscRedF;
+  uint32_t* redc = (uint32_t*)(smem + ly.misc + kMiscRedC);
+  auto ch_of = [&](int c) -> ChainSm& { return chs[c]; };
 
   const int nimg = (k * kBhA + kBvZero + K * k * kBvFA) / 16;   // B images: hidden/free, then visible
   for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
-  for (int w = tid; w < kWords; w += kThr) {
-    vbits[w] = jb.bits[(size_t)c * kWords + w];
+  for (int w = tid; w < CH * WPC; w += kThr) {
+    const int c = c0 + w / WPC;
+    vbits[w] = c < jb.n_chains ? jb.bits[(size_t)c * WPC + (w % WPC)] : 0u;
     ((uint32_t*)(smem + ly.pb[0]))[w] = 0u;
     ((uint32_t*)(smem + ly.pb[1]))[w] = 0u;
   }
-  if (tid == 0) {
-    ch.F = jb.F[c];
-    ch.Fb = jb.Fb[c];
-    ch.lpb = jb.Lb[c];
+  if (tid < CH) {
+    ChainSm& ch = ch_of(tid);
+    const int c = c0 + tid;
+    const bool on = c < jb.n_chains;
+    ch.F = on ? jb.F[c] : 0.0;
+    ch.Fb = on ? jb.Fb[c] : 0.0;
+    ch.lpb = on ? jb.Lb[c] : 0.0;
     ch.lppb = 0.0;
-    ch.lp = jb.logpi[c];
-    ch.E = jb.Ephys[c];
+    ch.lp = on ? jb.logpi[c] : 0.0;
+    ch.E = on ? jb.Ephys[c] : 0.0;
     for (int o = 0; o < kNobs; ++o) {
-      ch.ot[o] = jb.obs_t[(size_t)c * kNobs + o];
-      ch.os[o] = jb.obs[(size_t)c * kNobs + o];
+      ch.ot[o] = on ? jb.obs_t[(size_t)c * kNobs + o] : 0.0;
+      ch.os[o] = on ? jb.obs[(size_t)c * kNobs + o] : 0.0;
     }
-    ch.beta = 1.0 / jb.T[c];
+    ch.beta = on ? 1.0 / jb.T[c] : 1.0;
     ch.acc = 0ull;
     ch.rec_mh = 0ull;
     ch.flag_rec = 0;
     ch.flag_acc = 0;
-    *nrec_sm = 0ull;
+    nrec_sm[tid] = 0ull;
+  }
+  if (tid == 0) {
     for (int b = 0; b < kNbuf; ++b) {
       mbar_init(bar(kBarFull + b), 2);
       mbar_init(bar(kBarEmpty + b), 16);
@@ -514,24 +571,27 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   __syncthreads();
-  expand_lattice(smem, ly.opv[0], vbits, tid, kThr);
+  expand_lattice<LT>(smem, ly.opv[0], vbits, tid, kThr);
   cta_sync();
   const uint32_t tmem = *tslot;
 
-  // epilogue thread: lattice row i, filter / column quarter fq; its TMEM lanes
-  const int i = 32 * (warp & 3) + lane, fq = warp >> 2;
+  // epilogue thread: operand row m = lattice row i of chain cm; filter /
+  // column quarter fq; its TMEM lanes
+  const int m = 32 * (warp & 3) + lane, fq = warp >> 2, i = m / CH, cm = m % CH;
+  const uint32_t cid = (uint32_t)(jb.cid_base + (uint64_t)(c0 + cm));
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  uint32_t* vb_m = vbits + cm * WPC;                           // this thread's chain's planes
+  const uint32_t hbc = ly.hbits + (uint32_t)cm * (4 * WPC * 4);
   const bool issuer = warp >= 16 && lane == 0;
   const int role = warp - 16;                     // issuers: 0 and 1
 
-  const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], kLbo);   // operand x at + x kOpv / 16
+  const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], kLbo);   // operand x at + x OPV / 16
   const uint32_t dvbuf = umma_desc_lo(sbase + ly.vbuf, kLbo), dbh = umma_desc_lo(sbase + ly.bh, 1536),
                  dbv = umma_desc_lo(sbase + ly.bv, 0);     // LBO set per image
   uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
   uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
   bool live = true;             // false once a wait gave up: no further waits
   unsigned nrec = 0;
-  int cur = 0;                  // lattice operand holding v
   const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
   auto wait_bar = [&](uint32_t b, uint32_t parity) {
     if (live && !mbar_wait(b, parity)) {
@@ -539,7 +599,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       atomicExch(prm.err, kErrTimeout);
     }
   };
-  // control warp: before the MMAs of stage zc, its buffer's previous use read by every epilogue warp
+  // issuing warp: before the MMAs of stage zc, its buffer's previous use read by every epilogue warp
   auto mma_claim = [&]() {
     const uint32_t b = zc & (kNbuf - 1), use = zc / kNbuf;
     if (use > 0) wait_bar(bar(kBarEmpty + b), (use - 1) & 1u);
@@ -568,50 +628,55 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
 
   for (int s = 0; s < prm.S; ++s) {
     const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
-    int src = cur;
-    if (warp == 17 && lane == 1 && prm.correct) {
-      // the MH draw of this proposal, ahead of the decision (read by thread 0
-      // after the barriers of the proposal's end)
-      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, cid), jb.rk);
-      ch.logu = log(((double)w.x + 0.5) * 0x1p-32);
+    if (warp == 17 && lane >= 1 && lane <= CH && prm.correct) {
+      // the MH draws of this proposal, ahead of the decisions (read after the
+      // barriers of the proposal's end)
+      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, (uint32_t)(jb.cid_base + (uint64_t)(c0 + lane - 1))),
+                                       jb.rk);
+      ch_of(lane - 1).logu = log(((double)w.x + 0.5) * 0x1p-32);
     }
+    // Gibbs step sub reads operand sub % 2 and writes the other: v is in
+    // operand 0 at the start of a proposal, v' in operand g % 2 at its end
     for (int sub = 0; sub < prm.g; ++sub, ++gs) {
-      uint32_t* dbits = (uint32_t*)(smem + ly.pb[0] + (uint32_t)(sub & 1) * (kWords * 4));
-      const uint32_t* sbits =
-          sub == 0 ? vbits : (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub - 1) & 1) * (kWords * 4));
+      const int src = sub & 1;
+      const uint32_t pbs = ly.pb[0] + (uint32_t)(sub & 1) * (CH * WPC * 4);
+      uint32_t* dbc = (uint32_t*)(smem + pbs) + cm * WPC;
+      const uint32_t* sbc =
+          sub == 0 ? vb_m : (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub - 1) & 1) * (CH * WPC * 4)) + cm * WPC;
       const uint32_t taghid = (uint32_t)(sub * (K + 1)), tagvis = (uint32_t)(sub * (K + 1) + K);
-      const uint32_t opv_dst = ly.opv[0] + (uint32_t)(src ^ 1) * kOpv;
+      const uint32_t opv_dst = ly.opv[0] + (uint32_t)(src ^ 1) * G::OPV;
       const uint32_t zbase = zc;
       if (issuer) {
-        for (int z = 0; z < 24; ++z, ++zc) {
+        for (int z = 0; z < G::NHV; ++z, ++zc) {
           int ty, tl;
-          hv_stage(z, ty, tl);
+          hv_stage<LT>(z, ty, tl);
           const uint32_t d = mma_claim();
           if (ty == kStV) {
-            wait_bar(bar(kBarH + ((2 * tl + 15) & 15)), gs & 1u);
+            wait_bar(bar(kBarH + ((2 * tl + G::NT - 1) % G::NT)), gs & 1u);
             wait_bar(bar(kBarH + 2 * tl), gs & 1u);
             wait_bar(bar(kBarH + 2 * tl + 1), gs & 1u);
             tc_fence_after();
           }
-          issue_stage<KT, kT>(role, ty, tl, d, dopv0 + (uint32_t)(src * (kOpv >> 4)), dvbuf, dbh, dbv, K, k,
-                              bar(kBarFull + (zc & (kNbuf - 1))));
+          issue_stage<LT, KT, kT>(role, ty, tl, d, dopv0 + (uint32_t)(src * (G::OPV >> 4)), dvbuf, dbh, dbv, K,
+                                  k, bar(kBarFull + (zc & (kNbuf - 1))));
         }
       } else if (epi) {
-        for (int z = 0; z < 24; ++z, ++zc) {
+        for (int z = 0; z < G::NHV; ++z, ++zc) {
           int ty, tl;
-          hv_stage(z, ty, tl);
+          hv_stage<LT>(z, ty, tl);
           // this stage's Philox words do not depend on its MMAs: drawn before
           // waiting for them, so the counter-based generator overlaps the
           // tensor-core work and the accumulator loads
           uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
           if (ty == kStH) {
             if (fq < K) {
-              const uint32_t q0 = (uint32_t)((i * kL + 8 * tl) >> 2), tag = taghid + (uint32_t)fq;
+              const uint32_t q0 = (uint32_t)((i * LT + 8 * tl) >> 2), tag = taghid + (uint32_t)fq;
               w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
               w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
             }
           } else {
-            w0 = philox4x32_10_rk(make_uint4((uint32_t)((i * kL + 16 * tl + 4 * fq) >> 2), tagvis, step, cid), jb.rk);
+            w0 = philox4x32_10_rk(make_uint4((uint32_t)((i * LT + 16 * tl + 4 * fq) >> 2), tagvis, step, cid),
+                                  jb.rk);
             w1 = w0;
           }
           const uint32_t tcol = epi_claim();
@@ -623,19 +688,19 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               tm_ld8(tcol + 64 + 8 * fq, s0);
               tm_wait();
               epi_release();
-              epi_hidden(jb, smem, ly, s2, s1, s0, i, fq, tl, w0, w1, sbits, nrec);
+              epi_hidden<LT>(jb, smem, ly, s2, s1, s0, m, i, fq, tl, w0, w1, sbc, hbc, nrec);
             } else {
               epi_release();
             }
-            if (tl == 14 && fq < K) {
-              // this thread's rows of hidden tile 15 (written by it at H15) into
-              // the last slot of V7's buffer, read last by V5, whose MMAs this
-              // warp has waited for (V5 precedes H14)
-              const uint32_t dst = ly.vbuf + kVbuf + (uint32_t)fq * kPlane3 + 2 * kLbo, p15 = ly.p15 + (uint32_t)fq * kLbo;
-              *(uint4*)(smem + dst + (uint32_t)(i + 8) * 16) = *(const uint4*)(smem + p15 + (uint32_t)(i + 8) * 16);
-              if (i >= kL - 8)
-                *(uint4*)(smem + dst + (uint32_t)(i - (kL - 8)) * 16) =
-                    *(const uint4*)(smem + p15 + (uint32_t)(i - (kL - 8)) * 16);
+            if (tl == G::NT - 2 && fq < K) {
+              // this thread's rows of the last hidden tile (written by it at the
+              // first H stage) into the last slot of the last V tile's buffer,
+              // read last by V_{NV-3}, whose MMAs this warp has waited for
+              const uint32_t dst = ly.vbuf + (uint32_t)((G::NV - 1) & 1) * kVbuf + (uint32_t)fq * kPlane3 + 2 * kLbo,
+                             pl = ly.plast + (uint32_t)fq * kLbo;
+              *(uint4*)(smem + dst + (uint32_t)(m + 8) * 16) = *(const uint4*)(smem + pl + (uint32_t)(m + 8) * 16);
+              if (m >= 120)
+                *(uint4*)(smem + dst + (uint32_t)(m - 120) * 16) = *(const uint4*)(smem + pl + (uint32_t)(m - 120) * 16);
             }
             epi_publish(bar(kBarH + tl));
           } else {
@@ -660,39 +725,40 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               tm_wait();
             }
             epi_release();
-            epi_visible(jb, smem, ly, s2, s1, s0, i, fq, tl, w0, dbits, opv_dst, bar(kBarH), gs & 1u,
-                        prm.err, nrec);
-            if (tl == 7) epi_publish(bar(kBarV));
+            epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
+                            (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.err, nrec);
+            if (tl == G::NV - 1) epi_publish(bar(kBarV));
           }
         }
       }
-      zc = zbase + 24;
-      src ^= 1;
+      zc = zbase + G::NHV;
       if (sub + 1 < prm.g) {
         // next Gibbs step: its source is this step's v' (every write done), and
         // the proposal buffer it fills is cleared
         cta_sync();
-        if (tid < kWords) ((uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub + 1) & 1) * (kWords * 4)))[tid] = 0u;
+        for (int w = tid; w < CH * WPC; w += kThr)
+          ((uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub + 1) & 1) * (CH * WPC * 4)))[w] = 0u;
         __syncthreads();
       }
     }
-    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((prm.g - 1) & 1) * (kWords * 4));   // v'
+    const int fin = prm.g & 1;                                     // operand holding v'
+    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((prm.g - 1) & 1) * (CH * WPC * 4));
 
     // free energy of v' from the F tiles
     float s32 = 0.f, c32 = 0.f, sabs = 0.f, ssp = 0.f;
     const uint32_t zbase = zc;
     if (issuer) {
-      for (int t = 0; t < 16; ++t, ++zc) {
+      for (int t = 0; t < G::NT; ++t, ++zc) {
         const uint32_t d = mma_claim();
         if (t == 0) {
           wait_bar(bar(kBarV), (gs - 1) & 1u);
           tc_fence_after();
         }
-        issue_stage<KT, kT>(role, kStF, t, d, dopv0 + (uint32_t)(src * (kOpv >> 4)), dvbuf, dbh, dbv, K, k,
-                            bar(kBarFull + (zc & (kNbuf - 1))));
+        issue_stage<LT, KT, kT>(role, kStF, t, d, dopv0 + (uint32_t)(fin * (G::OPV >> 4)), dvbuf, dbh, dbv, K, k,
+                                bar(kBarFull + (zc & (kNbuf - 1))));
       }
     } else if (epi) {
-      for (int t = 0; t < 16; ++t, ++zc) {
+      for (int t = 0; t < G::NT; ++t, ++zc) {
         const uint32_t tcol = epi_claim();
         if (fq < K) {
           float s2[8], s1[8], s0[8];
@@ -707,31 +773,40 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         }
       }
     }
-    zc = zbase + 16;
+    zc = zbase + G::NT;
 
-    // per-warp sums: F as an exact 2^-32 fixed-point integer, its error-bound
-    // part in FP32, ones and unequal nearest-neighbour pairs of v' (every
-    // warp's v' writes done: vrdy, completed before the F stages)
+    // per-warp sums: F as an exact 2^-32 fixed-point integer and its
+    // error-bound part in FP32 per chain (a thread's units are all of its
+    // chain cm: lane parity for CH = 2), ones and unequal nearest-neighbour
+    // pairs of the count-pass words (every warp's v' writes done: vrdy,
+    // completed before the F stages)
     if (epi) {
       wait_bar(bar(kBarV), (gs - 1) & 1u);
       long long fs = __float2ll_rn(s32 * 0x1p32f);
       float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
-      const uint32_t x = pv[tid], xr = pv[(tid & ~3) | ((tid + 1) & 3)], xd = pv[(tid + 4) & (kWords - 1)];
-      uint32_t cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ ((x >> 1) | (xr << 31))) + __popc(x ^ xd)) << 16);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 16; o >= CH; o >>= 1) {
         fs += __shfl_xor_sync(kFull, fs, o);
         bnd += __shfl_xor_sync(kFull, bnd, o);
-        cnt += __shfl_xor_sync(kFull, cnt, o);
       }
-      if (lane == 0) {
-        *(long long*)(red + 16 * warp) = fs;
-        *(float*)(red + 16 * warp + 8) = bnd;
-        *(uint32_t*)(red + 16 * warp + 12) = cnt;
+      if (lane < CH) {
+        *(long long*)(redf + 16 * (warp * CH + lane)) = fs;
+        *(float*)(redf + 16 * (warp * CH + lane) + 8) = bnd;
       }
+      uint32_t cnt = 0;
+      if (tid < CH * WPC) {
+        const uint32_t* p = pv + (tid / WPC) * WPC;
+        const int w = tid % WPC;
+        const uint32_t x = p[w], xr = p[(w & ~(G::WPR - 1)) | ((w + 1) & (G::WPR - 1))], xd = p[(w + G::WPR) % WPC];
+        cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ ((x >> 1) | (xr << 31))) + __popc(x ^ xd)) << 16);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+      if (lane == 0) redc[warp] = cnt;
     }
     __syncthreads();
-    auto settle = [&]() {        // thread 0: the chain after the decision
+    // thread c < CH: the MH decision of chain c0 + c
+    auto settle = [&](ChainSm& ch, int c) {
       if (ch.flag_acc) {
         ch.F = ch.Fp;
         ch.Fb = ch.Bp;
@@ -742,31 +817,35 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         ch.acc += 1ull;
       }
       for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
-      trace_store(jb, c, step0 + (uint64_t)s, ch.E);
+      if (c0 + c < jb.n_chains) trace_store(jb, c0 + c, step0 + (uint64_t)s, ch.E);
     };
-    if (tid == 0) {
+    if (tid < CH) {
+      ChainSm& ch = ch_of(tid);
       long long fs = 0;
       double bnd = 0.0;
       uint32_t ones = 0, pairs = 0;
       for (int w = 0; w < 16; ++w) {
-        fs += *(const long long*)(red + 16 * w);
-        bnd += (double)*(const float*)(red + 16 * w + 8);
-        const uint32_t cn = *(const uint32_t*)(red + 16 * w + 12);
-        ones += cn & 0xFFFFu;
-        pairs += cn >> 16;
+        fs += *(const long long*)(redf + 16 * (w * CH + tid));
+        bnd += (double)*(const float*)(redf + 16 * (w * CH + tid) + 8);
       }
+      for (int w = 0; w < 16; ++w)
+        if (w * 32 < CH * WPC && (w * 32) / WPC == tid) {
+          ones += redc[w] & 0xFFFFu;
+          pairs += redc[w] >> 16;
+        }
       // the fixed-point conversion rounds each thread's sum by <= 2^-33; the FP32
-      // sums of the bound terms over 512 threads lose < 10 2^-24 relative
+      // sums of the bound terms over 512 / CH threads lose < 10 2^-24 relative
+      const double N = (double)(LT * LT);
       const double Fsp = (double)fs * 0x1p-32;
-      const double Fdata = bnd * 1.001 + 512.0 * 0x1p-33;
-      const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
-      const double M = 2.0 * (double)ones - (double)kN;
+      const double Fdata = bnd * 1.001 + (512.0 / CH) * 0x1p-33;
+      const double E = -jb.J[0] * (2.0 * N - 2.0 * (double)pairs);
+      const double M = 2.0 * (double)ones - N;
       ch.Ep = E;
       ch.lpp = -ch.beta * E;
       ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
       ch.lppb = 0.0;
       ch.Fp = -jb.vb * (double)ones - Fsp;
-      ch.Bp = Fdata + (double)K * (double)kN * ((double)jb.csp + (double)jb.tcft) + 1e-12 * fabs(ch.Fp);
+      ch.Bp = Fdata + (double)K * N * ((double)jb.csp + (double)jb.tcft) + 1e-12 * fabs(ch.Fp);
       ch.flag_rec = 0;
       if (!prm.correct) {
         ch.flag_acc = 1;
@@ -779,37 +858,45 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         else if (logu - logr > Mg) ch.flag_acc = 0;
         else ch.flag_rec = 1;
       }
-      if (!ch.flag_rec) settle();
+      if (!ch.flag_rec) settle(ch, tid);
     }
-    if (__syncthreads_or(tid == 0 && ch.flag_rec)) {
-      mh_redo(jb, ch, scratch, pv, vbits, step, cid, c);
-      if (tid == 0) settle();
+    if (__syncthreads_or(tid < CH && ch_of(tid).flag_rec)) {
+      mh_redo<LT>(jb, &ch_of(0), scratch, pv, vbits, step, c0);
+      if (tid < CH && ch_of(tid).flag_rec) settle(ch_of(tid), tid);
       __syncthreads();
     }
-    const bool accepted = ch.flag_acc != 0;
-    if (tid < kWords) {
-      uint32_t* pvw = (uint32_t*)pv;
-      if (accepted) vbits[tid] = pvw[tid];
-      pvw[tid] = 0u;                              // cleared for the next proposal
+    // accepted: v' becomes v (packed, and its operand rows into operand 0 when
+    // they are in operand 1); rejected after several Gibbs steps: operand 0
+    // was overwritten, so v is expanded again
+    for (int c = 0; c < CH; ++c) {
+      const bool acc = ch_of(c).flag_acc != 0;
+      for (int w = tid; w < WPC; w += kThr) {
+        uint32_t* pvw = (uint32_t*)pv + c * WPC;
+        if (acc) vbits[c * WPC + w] = pvw[w];
+        pvw[w] = 0u;                              // cleared for the next proposal
+      }
+      if (acc && fin == 1) copy_chain_rows<LT>(smem, ly.opv[0], ly.opv[1], c, tid, kThr);
     }
-    if (accepted) {
-      cur = src;                                  // the operand of v' is the new v
-    } else if (prm.g > 1) {
-      __syncthreads();
-      expand_lattice(smem, ly.opv[0] + (uint32_t)cur * kOpv, vbits, tid, kThr);   // later Gibbs steps overwrote it
-    }
+    __syncthreads();
+    for (int c = 0; c < CH; ++c)
+      if (!ch_of(c).flag_acc && prm.g > 1) expand_lattice<LT>(smem, ly.opv[0], vbits, tid, kThr, c);
     cta_sync();
   }
 
-  if (nrec) atomicAdd(nrec_sm, (unsigned long long)nrec);
+  if (nrec) atomicAdd(nrec_sm + cm, (unsigned long long)nrec);
   // every MMA issued has completed before tensor memory is released
   if (issuer) {
     umma_commit(bar(kBarFin));
     wait_bar(bar(kBarFin), 0u);
   }
   cta_sync();
-  for (int w = tid; w < kWords; w += kThr) jb.bits[(size_t)c * kWords + w] = vbits[w];
-  if (tid == 0) {
+  for (int w = tid; w < CH * WPC; w += kThr) {
+    const int c = c0 + w / WPC;
+    if (c < jb.n_chains) jb.bits[(size_t)c * WPC + (w % WPC)] = vbits[w];
+  }
+  if (tid < CH && c0 + tid < jb.n_chains) {
+    const ChainSm& ch = ch_of(tid);
+    const int c = c0 + tid;
     jb.F[c] = ch.F;
     jb.Fb[c] = ch.Fb;
     jb.Lb[c] = ch.lpb;
@@ -820,27 +907,42 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       jb.obs[(size_t)c * kNobs + o] = ch.os[o];
     }
     jb.acc[c] += ch.acc;
-    jb.rec[2 * (size_t)c] += *nrec_sm;
+    jb.rec[2 * (size_t)c] += nrec_sm[tid];
     jb.rec[2 * (size_t)c + 1] += ch.rec_mh;
   }
   if (warp == 16)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmCols));
 }
 
-}  // namespace
-
-size_t tc_smem_bytes(int K, int k) { return tc_layout(K, k).total; }
-
-bool tc_supported(int kind, int prec, int L, int K, int k) {
-  return kind == kIsing && prec == kMixed && L == kL && K >= 1 && K <= 4 && k >= 1 && k <= 5;
+template <int LT, int KT, int kT>
+cudaError_t tc_launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  crbm_tc_kernel<LT, KT, kT><<<grid, kThr, smem, st>>>(p);
+  return cudaGetLastError();
 }
 
-// the filter shape of every job of the launch: (K, k) of the first (launches
-// group jobs of one filter shape)
-cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  if (p.job[0].K == 4 && p.job[0].k == 5) crbm_tc_kernel<4, 5><<<grid, kThr, smem, st>>>(p);
-  else crbm_tc_kernel<0, 0><<<grid, kThr, smem, st>>>(p);
-  cudaError_t e = cudaGetLastError();
+template <int LT, int KT, int kT>
+cudaError_t tc_limit_inst() {
+  return cudaFuncSetAttribute(crbm_tc_kernel<LT, KT, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_layout<LT>(4, 5).total);
+}
+
+}  // namespace
+
+int tc_chains_per_cta(int L) { return 128 / L; }
+
+size_t tc_smem_bytes(int L, int K, int k) {
+  return L == 128 ? tc_layout<128>(K, k).total : tc_layout<64>(K, k).total;
+}
+
+bool tc_supported(int kind, int prec, int L, int K, int k) {
+  return kind == kIsing && prec == kMixed && (L == 128 || L == 64) && K >= 1 && K <= 4 && k >= 1 && k <= 5;
+}
+
+// One launch per lattice side and filter shape (the jobs of p share both).
+cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  const bool k45 = p.job[0].K == 4 && p.job[0].k == 5;
+  cudaError_t e = L == 128 ? (k45 ? tc_launch_inst<128, 4, 5>(p, grid, smem, st) : tc_launch_inst<128, 0, 0>(p, grid, smem, st))
+                           : (k45 ? tc_launch_inst<64, 4, 5>(p, grid, smem, st) : tc_launch_inst<64, 0, 0>(p, grid, smem, st));
   if (e == cudaSuccess && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
     e = cudaGetLastError();
@@ -849,11 +951,10 @@ cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t
 }
 
 cudaError_t tc_set_smem_limit() {
-  cudaError_t e = cudaFuncSetAttribute(crbm_tc_kernel<4, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_layout(4, 5).total);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(crbm_tc_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc_layout(4, 5).total);
+  cudaError_t e = tc_limit_inst<128, 4, 5>();
+  if (e == cudaSuccess) e = tc_limit_inst<128, 0, 0>();
+  if (e == cudaSuccess) e = tc_limit_inst<64, 4, 5>();
+  if (e == cudaSuccess) e = tc_limit_inst<64, 0, 0>();
   return e;
 }
 

@@ -1,10 +1,12 @@
-"""The tensor-core form of the Ising proposal kernel (L = 128, mixed precision).
+"""The tensor-core form of the Ising proposal kernel (L = 128: one chain per
+CTA; L = 64: two chains per CTA with interleaved rows; mixed precision).
 
 Its chain is the FP64 path's: lattices and accept counts identical to the
 oracle's and to the table kernel's, bit for bit, on the same Philox streams;
 the lattice sums (log pi, E, observable sums) are exact integers times
 constants and identical too; the FP32 free energy agrees with the FP64 one
-within its certified bound.  Cases cover K < 4 (unused filter slots), k = 3..5,
+within its certified bound.  Cases cover both sides (an odd chain count at
+L = 64 leaves the second chain of the last CTA empty), K < 4 (unused filter slots), k = 3..5,
 g > 1 Gibbs steps (ping-pong lattice operands), uncorrected Gibbs, a batch
 mixing the tensor-core form with the table kernel, CUDA-graph replay, and the
 analytic CRBM (log r = 0: every MH decision sits within the FP32 bound and is
@@ -19,7 +21,6 @@ from _common import decisions_are_clear, gpu_ctx, oracle_chains, run_oracle
 pytestmark = pytest.mark.gpu
 
 SEED = 2008054010
-L = 128
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +30,7 @@ def ctx():
     c.close()
 
 
-def _run(ctx, mid, T, bits0, S, g, correct, tc, prec):
+def _run(ctx, mid, L, T, bits0, S, g, correct, tc, prec):
     from paper_2008_05401_gb300 import ISING
     ctx.set_tensor_cores(tc)
     job = ctx.new_job(mid, ISING, L, T, (1.0,), SEED, 0, bits0, prec)
@@ -43,30 +44,33 @@ def _run(ctx, mid, T, bits0, S, g, correct, tc, prec):
 
 
 TC_CASES = [
-    # K, k, n, g, correct, std
-    (4, 5, 8, 1, True, 0.1),       # the batch Ising workload's filter bank
-    (4, 4, 4, 1, True, 0.15),      # k = 4
-    (2, 3, 6, 2, True, 0.3),       # K < 4, g = 2
-    (3, 4, 4, 3, False, 0.25),     # uncorrected, g = 3
-    (1, 5, 4, 1, True, 0.4),       # one filter
+    # L, K, k, n, g, correct, std
+    (128, 4, 5, 8, 1, True, 0.1),       # the batch Ising workload's filter bank
+    (128, 4, 4, 4, 1, True, 0.15),      # k = 4
+    (128, 2, 3, 6, 2, True, 0.3),       # K < 4, g = 2
+    (128, 3, 4, 4, 3, False, 0.25),     # uncorrected, g = 3
+    (128, 1, 5, 4, 1, True, 0.4),       # one filter
+    (64, 4, 5, 9, 1, True, 0.12),       # two chains per CTA, the last CTA half empty
+    (64, 2, 3, 6, 2, True, 0.3),        # g = 2 with two chains per CTA
+    (64, 3, 4, 5, 3, False, 0.25),      # uncorrected, g = 3
 ]
 
 
-@pytest.mark.parametrize("K,k,n,g,correct,std", TC_CASES)
-def test_tensor_core_form_matches_oracle_and_table_kernel(ctx, K, k, n, g, correct, std):
+@pytest.mark.parametrize("L,K,k,n,g,correct,std", TC_CASES)
+def test_tensor_core_form_matches_oracle_and_table_kernel(ctx, L, K, k, n, g, correct, std):
     from paper_2008_05401_gb300 import FP64, ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(K, k, std, seed=1000 + 10 * K + k)
     T = wl.ising_ladder(n, 8)
-    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=K + k))
+    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=K + k + L))
     S = 10
     ref = oracle_chains("ising", W, hb, vb, L, T, (1.0,), SEED, n, bits0)
     worst = run_oracle(ref, S, g=g, correct=correct)
     if not decisions_are_clear(worst):
         pytest.skip(f"oracle reports a decision inside the FP64 margin: {worst}")
     mid = ctx.load_model(ISING, W, vb, hb)
-    tc = _run(ctx, mid, T, bits0, S, g, correct, True, MIXED)
-    tab = _run(ctx, mid, T, bits0, S, g, correct, False, MIXED)
-    f64 = _run(ctx, mid, T, bits0, S, g, correct, True, FP64)
+    tc = _run(ctx, mid, L, T, bits0, S, g, correct, True, MIXED)
+    tab = _run(ctx, mid, L, T, bits0, S, g, correct, False, MIXED)
+    f64 = _run(ctx, mid, L, T, bits0, S, g, correct, True, FP64)
     assert tc["step"] == S
     np.testing.assert_array_equal(tc["bits"], wl.pack_bits(ref.v))
     np.testing.assert_array_equal(tc["acc"], ref.accepts)
@@ -80,8 +84,8 @@ def test_tensor_core_form_matches_oracle_and_table_kernel(ctx, K, k, n, g, corre
 
 
 def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
-    """A batch holding L = 128 jobs (tensor-core form, a side stream) and
-    L = 64 / 32 jobs (table kernel) gives every job the results it has alone."""
+    """A batch holding L = 128 and L = 64 jobs (tensor-core form, side streams)
+    and L = 32 jobs (table kernel) gives every job the results it has alone."""
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.1, seed=77)
     mid = ctx.load_model(ISING, W, vb, hb)
@@ -107,7 +111,8 @@ def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
         j.release()
 
 
-def test_tensor_core_form_graph_replay_equals_direct_runs(ctx):
+@pytest.mark.parametrize("L", [128, 64])
+def test_tensor_core_form_graph_replay_equals_direct_runs(ctx, L):
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.12, seed=78)
     mid = ctx.load_model(ISING, W, vb, hb)
@@ -129,7 +134,8 @@ def test_tensor_core_form_graph_replay_equals_direct_runs(ctx):
     replay.release()
 
 
-def test_tensor_core_form_mh_redo_on_the_analytic_crbm(ctx):
+@pytest.mark.parametrize("L", [128, 64])
+def test_tensor_core_form_mh_redo_on_the_analytic_crbm(ctx, L):
     """App. C: log r = 0 exactly, so the FP32 bound straddles it whenever
     |log u| is small and the FP64 redo decides; every proposal is accepted and
     F after the run is the FP64 value wherever a redo happened last."""
