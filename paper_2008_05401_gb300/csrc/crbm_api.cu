@@ -453,9 +453,11 @@ static uint16_t half_of_int(int v) {
 // (row kk, column n) at (kk/8) LBO + (n/8) 128 + (n%8) 16 + (kk%8) 2):
 //   hidden / free energy, per kernel row a: K=16 x N=96, LBO 1536, column
 //     n = e*32 + f*8 + jj holds digit e (c2, c1, c0) of W[f][a][kk - jj];
-//   visible: a zero group (768 B), then per (f, a): step 0 K=16 x N=48, LBO 768,
-//     column n = e*16 + jj holding digit e of W[f][a][jj + 8 - kk]; step 1 its
-//     second K-group only (kk = 8..15, W[f][a][jj - kk]; the first is zero).
+//   visible, per (a, K-step j < J = ceil(3K / 2)): K=16 x N=48, LBO 768; row kk
+//     is column c = kk % 8 of group G = 2j + kk / 8 of a V buffer (filter
+//     f = G / 3, slot s = G % 3: hidden columns 8 (s - 1) + c of the tile's
+//     16), column n = e*16 + jj holds digit e of W[f][a][jj + 8 - 8s - c]
+//     (zero for f >= K).
 static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, double v_bias, const double* h_bias,
                     double sh, double sv, double common, bool alloc) {
   double maxw = 0.0, maxhb = 0.0;
@@ -487,7 +489,8 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
     t1v += tf;
   }
   auto digit = [&](int e, int f, int a, int b) { return dg[((size_t)e * K + f) * k * k + (size_t)a * k + b]; };
-  const size_t bh = (size_t)k * 3072, bytes = bh + 768 + (size_t)K * k * 2304;
+  const int J = (3 * K + 1) / 2;
+  const size_t bh = (size_t)k * 3072, bytes = bh + (size_t)k * J * 1536;
   std::vector<uint16_t> img(bytes / 2, 0);
   for (int a = 0; a < k; ++a)
     for (int kk = 0; kk < 16; ++kk)
@@ -497,19 +500,18 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
         const size_t off = (size_t)a * 3072 + (kk / 8) * 1536 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2;
         img[off / 2] = half_of_int(digit(e, f, a, b));
       }
-  for (int f = 0; f < K; ++f)
-    for (int a = 0; a < k; ++a) {
-      const size_t fa = bh + 768 + (size_t)(f * k + a) * 2304;
-      for (int kk = 0; kk < 16; ++kk)
+  for (int a = 0; a < k; ++a)
+    for (int j = 0; j < J; ++j) {
+      const size_t aj = bh + (size_t)(a * J + j) * 1536;
+      for (int kk = 0; kk < 16; ++kk) {
+        const int G = 2 * j + kk / 8, f = G / 3, s = G % 3, c = kk % 8;
+        if (f >= K) continue;
         for (int n = 0; n < 48; ++n) {
-          const int e = n / 16, jj = n % 16;
-          int b = jj + 8 - kk;                                          // step 0
+          const int e = n / 16, jj = n % 16, b = jj + 8 - 8 * s - c;
           if (b >= 0 && b < k)
-            img[(fa + (kk / 8) * 768 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2) / 2] = half_of_int(digit(e, f, a, b));
-          b = jj - kk;                                                  // step 1, kk >= 8
-          if (kk >= 8 && b >= 0 && b < k)
-            img[(fa + 1536 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2) / 2] = half_of_int(digit(e, f, a, b));
+            img[(aj + (kk / 8) * 768 + (n / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2) / 2] = half_of_int(digit(e, f, a, b));
         }
+      }
     }
   m.tq2 = (float)std::ldexp(qf, 22);
   m.tq1 = (float)std::ldexp(qf, 11);

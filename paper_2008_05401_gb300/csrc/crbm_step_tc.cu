@@ -55,10 +55,10 @@ constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a 
 constexpr int kVbuf = 4 * kPlane3;
 constexpr int kPgrp = 4 * kLbo;                            // one column group of 4 hidden planes
 constexpr int kBhA = 3072;                                 // per kernel row: K=16 x N=96
-// visible images, per (filter, kernel row): step 0 K=16 x N=48 (1536 B), step
-// 1 only its second K-group (768 B; the first is zero and read from one shared
-// zero group through the descriptor's LBO); the zero group first
-constexpr int kBvZero = 768, kBvFA = 2304;
+// visible images, per (kernel row a, K-step j): K=16 x N=48 (1536 B, LBO 768);
+// K-step j contracts column groups 2j, 2j+1 of a V buffer's 3K groups
+constexpr int kBvStep = 1536;
+__host__ __device__ constexpr int v_ksteps(int K) { return (3 * K + 1) / 2; }
 constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
 
 // Geometry of an L x L lattice in the 128-row operands.
@@ -88,7 +88,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   l.plast = o; o += kPgrp;            // the last hidden tile, kept for the last V tile
   l.hold = o; o += kPgrp;             // the last odd hidden tile, until the next even one moves it
   l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
-  l.bv = o; o += (uint32_t)(kBvZero + K * k * kBvFA);   // visible
+  l.bv = o; o += (uint32_t)(k * v_ksteps(K) * kBvStep);   // visible
   l.vbits = o; o += G::CH * G::WPC * 4;         // packed current lattices, chain-major
   l.pb[0] = o; o += G::CH * G::WPC * 4;         // packed proposals (ping-pong over Gibbs steps)
   l.pb[1] = o; o += G::CH * G::WPC * 4;
@@ -200,8 +200,10 @@ __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
 // slots the epilogue warps take; role 1 commits at every stage, so `full`
 // counts two arrivals).
 // H/F tile t (role 0): N = 96, columns e*32 + f*8 + jj for the digits e = c2,
-// c1, c0.  V tile u: N = 48, columns e*16 + jj, filters f < 2 into dcol (role
-// 0) and f >= 2 into dcol + 48 (role 1); slots s, s+1 of the tile's V buffer.
+// c1, c0.  V tile u: N = 48, columns e*16 + jj; the tile's V buffer holds 3K
+// column groups (filter f, slot s) at group 3f + s, one LBO apart, so K-step j
+// contracts groups 2j, 2j+1 whatever filters they belong to: K-steps j < 3 into
+// dcol (role 0), j >= 3 into dcol + 48 (role 1).
 // *lo: low descriptor words of the operand bases (start fields advance by byte
 // offset / 16).  KT, kT > 0 fix K and k at compile time, so that the issue
 // sequence is straight-line code with immediate offsets.
@@ -222,25 +224,19 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
   } else {
     const uint32_t id = umma_idesc(48);
     const uint32_t a0 = vbuflo + (uint32_t)((tile & 1) * (kVbuf >> 4));
-    const int f0 = role == 0 ? 0 : 2, f1 = role == 0 ? (K < 2 ? K : 2) : K;
+    const int J = v_ksteps(K), j0 = role == 0 ? 0 : 3, j1 = role == 0 ? (J < 3 ? J : 3) : J;
     const uint32_t dc = dcol + (role == 0 ? 0u : 48u);
 #pragma unroll
-    for (int ff = 0; ff < 2; ++ff)
+    for (int a = 0; a < (kT ? kT : 8); ++a)
 #pragma unroll
-      for (int a = 0; a < (kT ? kT : 8); ++a)
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const int f = f0 + ff;
-          if (f < f1 && (kT || a < k)) {
-            const uint32_t aoff = (uint32_t)(f * kPlane3 + s * kLbo + (8 - CH * a) * 16);
-            const uint32_t fa = (uint32_t)(kBvZero + (f * k + a) * kBvFA);
-            // step 0: start at its block, LBO 768; step 1: start at the zero
-            // group, LBO = distance to its block
-            const uint32_t blo = s == 0 ? bvlo + (fa >> 4) + ((768u >> 4) << 16)
-                                        : bvlo + (((fa + 1536u) >> 4) << 16);
-            umma(dc, a0 + (aoff >> 4), blo, id, (ff | a | s) != 0);
-          }
+      for (int jj = 0; jj < 3; ++jj) {
+        const int j = j0 + jj;
+        if (j < j1 && (kT || a < k)) {
+          const uint32_t aoff = (uint32_t)(2 * j * kLbo + (8 - CH * a) * 16);
+          const uint32_t blo = bvlo + (uint32_t)(((a * J + j) * kBvStep) >> 4) + ((768u >> 4) << 16);
+          umma(dc, a0 + (aoff >> 4), blo, id, (a | jj) != 0);
         }
+      }
   }
   umma_commit(mbar);
 }
@@ -526,8 +522,11 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   uint32_t* redc = (uint32_t*)(smem + ly.misc + kMiscRedC);
   auto ch_of = [&](int c) -> ChainSm& { return chs[c]; };
 
-  const int nimg = (k * kBhA + kBvZero + K * k * kBvFA) / 16;   // B images: hidden/free, then visible
+  const int nimg = (k * kBhA + k * v_ksteps(K) * kBvStep) / 16;   // B images: hidden/free, then visible
   for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
+  // V buffers zeroed: the groups of filters f >= K are read (with zero weights)
+  // by the last K-step when 3K is odd, and must hold finite values
+  for (int q = tid; q < 2 * kVbuf / 16; q += kThr) ((uint4*)(smem + ly.vbuf))[q] = make_uint4(0u, 0u, 0u, 0u);
   for (int w = tid; w < CH * WPC; w += kThr) {
     const int c = c0 + w / WPC;
     vbits[w] = c < jb.n_chains ? jb.bits[(size_t)c * WPC + (w % WPC)] : 0u;
