@@ -65,17 +65,26 @@ __device__ __forceinline__ df df_from_float(float x) { return {x, 0.0f}; }
 // softplus(x) = max(x, 0) + log1p(e^-|x|) in df64, for the mixed path's
 // second-level free energy (an MH decision that the FP32 bound cannot
 // separate is retried with this one before the FP64 path's code runs).
-//   e^-a, 0 <= a <= 40: a = n ln2 + m/64 + r with integers n, m (m <= 44) and
-//     |r| <= 1/128 (+ rounding), e^-a = 2^-n e^(-m/64) e^-r; e^(-m/64) from a
-//     table of df64 constants, e^-r by its Taylor series to r^6 (remainder
-//     < 4e-19), the terms beyond r^2 in FP32 (their FP32 error is < 1e-14);
-//   log1p(e) = y: y0 = ln2 lg2(1 + e) from the special-function unit
-//     (|y0 - y| < 2^-21), then one Newton step on e^y = 1 + e,
-//     y1 = y0 - 1 + (1 + e) e^-y0, whose error is < (y0 - y)^2 / 2 < 2^-43;
+// Table-driven exponential and logarithm in the manner of Tang (ACM TOMS 1989,
+// 1990), with the leading terms kept exact by error-free transforms:
+//   e^-a, 0 <= a <= 40: n = floor(a / ln2), s = a - n ln2 (n ln2.hi exact by
+//     the FMA product, a.hi - n ln2.hi exact by Sterbenz; the low words in
+//     FP32: |error| < 2.5 2^-42), m = rint(64 s) in [0, 44], r = s - m/64
+//     (hi word exact, |r| <= 1/128 + 2^-25); e^-r = 1 - r + r^2/2 - r^3/6 +
+//     r^4/24 - r^5/120 (remainder < 4e-16) with 1 - r.hi and r.hi^2 exact, the
+//     terms beyond r^2 in FP32 (< 1e-7, error < 3e-14) and the low word of r
+//     as - r.lo e^-r.hi; then e^-a = 2^-n e^(-m/64) e^-r with e^(-m/64) a df64
+//     table entry (2^-48 relative) and one df64 product: relative error below
+//     6.5e-13 in all;
+//   log1p(e) = log u, u = 1 + e in [1, 2]: c = 1 + i/64 the nearest table
+//     point, d = (u - c) / c with u - c exact (Sterbenz) and 1/c a df64 table
+//     entry, |d| <= 2^-7; log u = log c + d - d^2/2 + d^3/3 - d^4/4 + d^5/5
+//     (remainder < 4e-14), log c from the table, d - d.hi^2/2 exact, d.hi d.lo
+//     and the terms beyond d^2 in FP32: absolute error below 2e-13 plus e's
+//     relative error times e / (1 + e) <= 1/2;
 //   a > 40: e^-a < 4.3e-18 and log1p(e) = e to within e^2, e from ex2.
-// With the df64 rounding (< 2^-46 relative per op) and the argument reduction
-// (n ln2 to about 1e-14) the result is within 1e-12 + 2^-44 softplus(x) of
-// the exact value (bound used by free_sum_df).
+// With the final df64 sum (2^-46 relative) the result is within
+// 1e-12 + 2^-44 softplus(x) of the exact value (bound used by free_sum_df).
 struct DfConst {
   float hi, lo;
 };
@@ -89,36 +98,76 @@ constexpr double exp_neg_m64(int m) {
   }
   return s;
 }
-__constant__ DfConst kExpNegM64[45] = {
-    dfc(exp_neg_m64(0)),  dfc(exp_neg_m64(1)),  dfc(exp_neg_m64(2)),  dfc(exp_neg_m64(3)),  dfc(exp_neg_m64(4)),
-    dfc(exp_neg_m64(5)),  dfc(exp_neg_m64(6)),  dfc(exp_neg_m64(7)),  dfc(exp_neg_m64(8)),  dfc(exp_neg_m64(9)),
-    dfc(exp_neg_m64(10)), dfc(exp_neg_m64(11)), dfc(exp_neg_m64(12)), dfc(exp_neg_m64(13)), dfc(exp_neg_m64(14)),
-    dfc(exp_neg_m64(15)), dfc(exp_neg_m64(16)), dfc(exp_neg_m64(17)), dfc(exp_neg_m64(18)), dfc(exp_neg_m64(19)),
-    dfc(exp_neg_m64(20)), dfc(exp_neg_m64(21)), dfc(exp_neg_m64(22)), dfc(exp_neg_m64(23)), dfc(exp_neg_m64(24)),
-    dfc(exp_neg_m64(25)), dfc(exp_neg_m64(26)), dfc(exp_neg_m64(27)), dfc(exp_neg_m64(28)), dfc(exp_neg_m64(29)),
-    dfc(exp_neg_m64(30)), dfc(exp_neg_m64(31)), dfc(exp_neg_m64(32)), dfc(exp_neg_m64(33)), dfc(exp_neg_m64(34)),
-    dfc(exp_neg_m64(35)), dfc(exp_neg_m64(36)), dfc(exp_neg_m64(37)), dfc(exp_neg_m64(38)), dfc(exp_neg_m64(39)),
-    dfc(exp_neg_m64(40)), dfc(exp_neg_m64(41)), dfc(exp_neg_m64(42)), dfc(exp_neg_m64(43)), dfc(exp_neg_m64(44))};
+constexpr double log_c64(int i) {
+  // log(1 + i/64) = 2 atanh(z), z = i / (128 + i) <= 1/3: the odd series,
+  // summed from its smallest term
+  const double z = (double)i / (128.0 + (double)i), z2 = z * z;
+  double t[40] = {};
+  t[0] = z;
+  for (int j = 1; j < 40; ++j) t[j] = t[j - 1] * z2;
+  double s = 0.0;
+  for (int j = 39; j >= 0; --j) s += t[j] / (double)(2 * j + 1);
+  return 2.0 * s;
+}
+template <int N>
+struct DfTable {
+  DfConst v[N];
+};
+constexpr DfTable<45> make_exp_table() {
+  DfTable<45> t{};
+  for (int m = 0; m < 45; ++m) t.v[m] = dfc(exp_neg_m64(m));
+  return t;
+}
+constexpr DfTable<65> make_log_table() {
+  DfTable<65> t{};
+  for (int i = 0; i < 65; ++i) t.v[i] = dfc(log_c64(i));
+  return t;
+}
+constexpr DfTable<65> make_rcp_table() {
+  DfTable<65> t{};
+  for (int i = 0; i < 65; ++i) t.v[i] = dfc(64.0 / (64.0 + (double)i));
+  return t;
+}
+// in global memory (L1-cached): the lanes of a warp index them at different
+// points, which the constant cache would serve one address at a time
+static __device__ const DfTable<45> kExpNegM64 = make_exp_table();   // e^(-m/64)
+static __device__ const DfTable<65> kLogC64 = make_log_table();      // log(1 + i/64)
+static __device__ const DfTable<65> kRcpC64 = make_rcp_table();      // 1 / (1 + i/64)
 
 // e^-a for a df64 0 <= a <= 40.1.
 __device__ __forceinline__ df df_exp_neg(df a) {
   constexpr DfConst ln2 = dfc(0.6931471805599453094172321);
   const float n = floorf(a.hi * 1.4426950408889634f);
-  const df s = df_add(a, df_neg(df_add(two_prod(n, ln2.hi), {n * ln2.lo, 0.0f})));   // a - n ln2
+  const df p = two_prod(n, ln2.hi);
+  const df s = two_sum(a.hi - p.hi, fmaf(-n, ln2.lo, a.lo - p.lo));           // a - n ln2
   const float mf = fminf(fmaxf(rintf(s.hi * 64.0f), 0.0f), 44.0f);
-  const df r = df_add(s, {-mf * 0.015625f, 0.0f});                                  // s - m/64
-  // e^-r = 1 + (-r) p, p = 1 + (-r)/2 + (-r) q, q = (-r)(1/6 + (-r)(1/24 + (-r)(1/120 + (-r)/720)));
-  // q and (-r) q in FP32: their error is scaled by |r| <= 1/128 in e^-r
-  const float q = -r.hi * fmaf(-r.hi, fmaf(-r.hi, fmaf(-r.hi, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
-                               1.0f / 6.0f);
-  const df nr = df_neg(r);
-  df p = df_add(df_mul(nr, {0.5f, 0.0f}), {1.0f, 0.0f});
-  p = df_add(p, {-r.hi * q, 0.0f});
-  p = df_add(df_mul(nr, p), {1.0f, 0.0f});
-  const int mi = (int)mf;
-  const df t = df_mul(p, {kExpNegM64[mi].hi, kExpNegM64[mi].lo});
+  const float rh = s.hi - mf * 0.015625f, rl = s.lo;                          // r = s - m/64
+  const df A = fast_two_sum(1.0f, -rh);
+  const df q2 = two_prod(rh, rh);
+  const df B = two_sum(A.hi, 0.5f * q2.hi);                                   // 1 - rh + rh^2/2
+  const float R = rh * rh * rh * fmaf(rh, fmaf(rh, -1.0f / 120.0f, 1.0f / 24.0f), -1.0f / 6.0f);
+  const float low = fmaf(-rl, B.hi, ((A.lo + B.lo) + 0.5f * q2.lo) + R);
+  const df er = fast_two_sum(B.hi, low);                                      // e^-r
+  const DfConst tm = kExpNegM64.v[(int)mf];
+  const df t = df_mul(er, {tm.hi, tm.lo});
   const float sc = __int_as_float((127 - (int)n) << 23);     // 2^-n exactly (0 <= n <= 58)
   return {t.hi * sc, t.lo * sc};
+}
+
+// log(1 + e) for a df64 0 <= e <= 1.
+__device__ __forceinline__ df df_log1p_unit(df e) {
+  const df u0 = fast_two_sum(1.0f, e.hi);
+  const float uh = u0.hi, ul = u0.lo + e.lo;                                  // u = 1 + e
+  const int i = min(max(__float2int_rn((uh - 1.0f) * 64.0f), 0), 64);
+  const float c = 1.0f + (float)i * 0.015625f;
+  const DfConst rc = kRcpC64.v[i], lc = kLogC64.v[i];
+  const df d = df_mul(two_sum(uh - c, ul), {rc.hi, rc.lo});                  // (u - c) / c
+  const df s2 = two_prod(d.hi, d.hi);
+  const df D = two_sum(d.hi, -0.5f * s2.hi);                                  // d.hi - d.hi^2/2
+  const float C = d.hi * d.hi * d.hi * fmaf(d.hi, fmaf(d.hi, 0.2f, -0.25f), 1.0f / 3.0f);
+  const df A = two_sum(lc.hi, D.hi);
+  const float low = (((A.lo + D.lo) + (lc.lo + d.lo)) - fmaf(d.hi, d.lo, 0.5f * s2.lo)) + C;
+  return fast_two_sum(A.hi, low);
 }
 
 // softplus(x) for a df64 x (see above).
@@ -126,11 +175,7 @@ __device__ __forceinline__ df softplus_df(df x) {
   const df a = x.hi < 0.0f ? df_neg(x) : x;
   const df pos = x.hi > 0.0f ? x : df{0.0f, 0.0f};
   if (a.hi > 40.0f) return df_add(pos, {ex2_approx(-a.hi * 1.4426950408889634f), 0.0f});
-  const df e = df_exp_neg(a);
-  const df u = df_add({1.0f, 0.0f}, e);                       // 1 + e
-  const float y0 = 0.69314718055994531f * lg2_approx(u.hi);
-  const df d = df_add(df_mul(u, df_exp_neg({y0, 0.0f})), {-1.0f, 0.0f});   // (1 + e) e^-y0 - 1
-  return df_add(pos, df_add({y0, 0.0f}, d));
+  return df_add(pos, df_log1p_unit(df_exp_neg(a)));
 }
 
 // Second-level free-energy sum of a lattice by a chain's group: the sum over
@@ -138,34 +183,50 @@ __device__ __forceinline__ df softplus_df(df x) {
 // (hi sums exact in FP32, lo sums in FP32: within jb.cdf of the FP64 path's),
 // softplus in df64.  out[0] = the group's partial sum, out[1] = a bound on its
 // error against the FP64 path's terms, out[2] = ones of the lattice.
+// KU: an upper bound on K known at compile time (the size of the register
+// arrays; K <= KU).
+template <int KU = kMaxK>
 static __device__ __noinline__ void free_sum_df(const JobDev& jb, const Grp& g, const uint32_t* v, double* out) {
   const int L = jb.L, N = jb.N, K = jb.K, k = jb.k, T = 1 << k;
-  const int nblk = (N + 3) >> 2, iters = (nblk + g.tpc - 1) / g.tpc;
   df acc = {0.0f, 0.0f};
   float ssp = 0.0f;
   int units = 0, ones = 0;
-  for (int it = 0; it < iters; ++it) {
-    const int q = g.r + it * g.tpc;
-    if (!g.active || q >= nblk) continue;
-    uint32_t m[4][kMaxk];
-    fwd_codes<0>(v, L, N, k, T, q, m);
-    for (int t = 0; t < 4; ++t)
-      if (4 * q + t < N) ones += (int)(m[t][0] & 1u);
-    for (int f = 0; f < K; ++f) {
-      const int base = f * k * T;
-      for (int t = 0; t < 4; ++t) {
-        if (4 * q + t >= N) continue;
-        float xh = jb.hb_hi[f], xl = jb.hb_lo[f];
-        for (int a = 0; a < k; ++a) {
-          xh += __ldg(jb.fh + base + m[t][a]);
-          xl += __ldg(jb.fl + base + m[t][a]);
-        }
-        const df sp = softplus_df(two_sum(xh, xl));
+  // one site per step; its k window codes index the tables as they are formed
+  // (no per-thread code array, which would live in local memory) and the
+  // pre-activations of its K hidden units stay in registers
+  for (int n = g.active ? g.r : N; n < N; n += g.tpc) {
+    const int i = n / L, j = n - i * L;
+    ones += (int)((v[n >> 5] >> (n & 31)) & 1u);
+    float xh[KU > 4 ? KU : 4], xl[KU > 4 ? KU : 4];
+#pragma unroll
+    for (int f = 0; f < (KU > 4 ? KU : 4); ++f) {
+      xh[f] = f < K ? jb.hb_hi[f] : 0.0f;
+      xl[f] = f < K ? jb.hb_lo[f] : 0.0f;
+    }
+    for (int a = 0; a < k; ++a) {
+      const int r = i + a < L ? i + a : i + a - L;
+      const int code = a * T + (int)row_window(v, L, r, j, k);
+      if (K <= 4) {
+        const float4 eh = __ldg(jb.fh4 + code), el = __ldg(jb.fl4 + code);
+        xh[0] += eh.x; xh[1] += eh.y; xh[2] += eh.z; xh[3] += eh.w;
+        xl[0] += el.x; xl[1] += el.y; xl[2] += el.z; xl[3] += el.w;
+      } else {
+#pragma unroll
+        for (int f = 0; f < KU; ++f)
+          if (f < K) {
+            xh[f] += __ldg(jb.fh + f * k * T + code);
+            xl[f] += __ldg(jb.fl + f * k * T + code);
+          }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < KU; ++f)
+      if (f < K) {
+        const df sp = softplus_df(two_sum(xh[f], xl[f]));
         acc = df_add(acc, sp);
         ssp += sp.hi;
         ++units;
       }
-    }
   }
   out[0] = df_to_double(acc);
   // per unit 1e-12 + 2^-44 softplus (evaluation) + cdf (pre-activation);

@@ -436,9 +436,9 @@ static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, doub
     Grp g3 = g2;
     g3.active = g2.active && ch.Fb != 0.0;
     double f1[3], f2[3];
-    free_sum_df(jb, g2, pv + c * G::WPC, f1);
+    free_sum_df<4>(jb, g2, pv + c * G::WPC, f1);
     grp_reduce<3>(f1, g2, scratch);
-    free_sum_df(jb, g3, vbits + c * G::WPC, f2);
+    free_sum_df<4>(jb, g3, vbits + c * G::WPC, f2);
     grp_reduce<3>(f2, g3, scratch);
     if (g2.active && g2.r == 0) {
       ch.Fp = -jb.vb * f1[2] - f1[0];
