@@ -613,9 +613,9 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         Grp g3 = g2;
         g3.active = g2.active && ch.Fb != 0.0;
         double f1[3], f2[3];
-        free_sum_df(jb, g2, vp, f1);
+        free_sum_df<KC ? KC : kMaxK>(jb, g2, vp, f1);
         grp_reduce<3>(f1, g2, scratch);
-        free_sum_df(jb, g3, v, f2);
+        free_sum_df<KC ? KC : kMaxK>(jb, g3, v, f2);
         grp_reduce<3>(f2, g3, scratch);
         if (g2.active && g.r == 0) {
           ch.Fp = -jb.vb * f1[2] - f1[0];
