@@ -140,9 +140,11 @@ def peaks():
 # DRAM bytes (read + write) of one launch of the tensor-core kernel on the
 # batch Ising workload's L = 128 jobs (4096 chains x 10 proposals), from an ncu
 # capture of a 152-chain launch scaled by chains (per chain the traffic is its
-# lattice and state in and out and the filter images; the lattices stay in
-# shared memory for the whole launch).
-BATCH_ISING_TC_TRAFFIC_BYTES = 841728 * 4096 / 152   # 152-chain capture: 841,728 B read, 0 B written
+# lattice and state in and out, the filter images and the recompute tables; the
+# lattices stay in shared memory for the whole launch).  The capture is
+# cold-cache, so the scaling counts the fixed part once per 152 chains: an upper
+# bound.
+BATCH_ISING_TC_TRAFFIC_BYTES = (1245440 + 9216) * 4096 / 152   # 152-chain capture: 1,245,440 B read, 9,216 B written
 
 
 def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
