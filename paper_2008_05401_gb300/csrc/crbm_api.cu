@@ -337,7 +337,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
                        cudaStream_t st, const Job* partner = nullptr) {
   // parts: (CTA size, jobs); CTA size -L = the tensor-core form for side L
   std::vector<std::pair<int, std::vector<int>>> parts;
-  for (int nt : {-128, -64, 256, 128, 64, 32}) {
+  for (int nt : {-128, -64, -32, 256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];

@@ -1,6 +1,6 @@
 // Tensor-core form of the fused CRBM proposal + Metropolis-Hastings kernel:
-// Ising kind, mixed precision, L x L lattices with L = 128 (one chain per CTA)
-// or L = 64 (two chains per CTA), K <= 4 filters of side k <= 5, mode 0 (S
+// Ising kind, mixed precision, L x L lattices with L = 128 (one chain per CTA),
+// 64 (two) or 32 (four), K <= 4 filters of side k <= 5, mode 0 (S
 // proposals of g Gibbs steps).  The chains are the table kernel's chains: the
 // same Philox words per unit, and every Bernoulli and MH decision the FP64
 // path's.
@@ -10,8 +10,8 @@
 // M = 128 operand rows m:
 //   hidden pre-activations of v  (Eq. B2; Eq. 12), one MMA per kernel row a
 //       reading the lattice rows i + a;
-//   visible pre-activations of h (Eq. B3), one MMA per (filter, kernel row a)
-//       reading the hidden rows i - a;
+//   visible pre-activations of h (Eq. B3), per kernel row a the hidden rows
+//       i - a, contracted over (filter, hidden column) pairs;
 //   hidden pre-activations of v' for F(v') (Eq. 13).
 // Operand row m holds lattice row i = m / CH of chain c = m % CH (CH = 128 / L
 // chains per CTA, rows interleaved), so that lattice row i + a is operand row
@@ -19,7 +19,8 @@
 // A operands: the 0/1 units in fp16, K-major without swizzle, rows 16 bytes
 // apart and 8-column groups one LBO apart, so the operand of kernel row a is
 // the same array started CH a rows further on; periodic halos are copies
-// (operand rows 128.. repeat rows 0.., the last column group repeats the first).
+// (operand rows 128.. repeat rows 0.., the last column group repeats the first;
+// hidden planes keep their last rows before row 0).
 // B operands: banded Toeplitz images of the filters (built on the host).  Each
 // weight is written as W = qf (c2 2^22 + c1 2^11 + c0), qf a power of two and
 // integer digits |c| <= 1024 (exact in fp16).  Units times digits summed over
@@ -34,7 +35,7 @@
 // NV = L / 16 visible tiles of 16 columns (V), interleaved so that a V tile's
 // MMAs run while the epilogue warps work through the two H stages after its
 // last input tile (L = 128: H15 H0 H1 H2 H3 V0 H4 H5 V1 ... H12 H13 V5 H14 V6
-// V7); then NT free-energy tiles (F).  Warp-specialised pipeline: two issuing
+// V7; L = 32: H3 H0 H1 H2 V0 V1); then NT free-energy tiles (F).  Warp-specialised pipeline: two issuing
 // warps put each stage's MMAs into one of four tensor-memory buffers and
 // commit them to that buffer's `full` mbarrier; the 16 epilogue warps (warp
 // w: lanes 32 (w % 4) .. + 31 = operand rows, w / 4 = filter or column
@@ -50,10 +51,6 @@ namespace crbm {
 namespace {
 
 constexpr int kEpi = 512, kThr = kEpi + 64;                // 16 epilogue warps + 2 MMA-issuing warps
-constexpr int kRows = 136, kLbo = kRows * 16;              // one 8-column group of 136 operand rows
-constexpr int kPlane3 = 3 * kLbo;                          // hidden plane of a V buffer: 3 groups
-constexpr int kVbuf = 4 * kPlane3;
-constexpr int kPgrp = 4 * kLbo;                            // one column group of 4 hidden planes
 constexpr int kBhA = 3072;                                 // per kernel row: K=16 x N=96
 // visible images, per (kernel row a, K-step j): K=16 x N=48 (1536 B, LBO 768);
 // K-step j contracts column groups 2j, 2j+1 of a V buffer's 3K groups
@@ -61,16 +58,26 @@ constexpr int kBvStep = 1536;
 __host__ __device__ constexpr int v_ksteps(int K) { return (3 * K + 1) / 2; }
 constexpr int kTmCols = 512, kTmBuf = 128, kNbuf = 4;
 
-// Geometry of an L x L lattice in the 128-row operands.
+// Geometry of an L x L lattice in the 128-row operands.  A column group holds
+// 128 operand rows and HH halo rows: a lattice operand repeats rows 0 .. HH-1
+// after row 127 (kernel rows a < 5 read rows m + CH a), a hidden plane of a V
+// buffer keeps rows 128-HH .. 127 before row 0 (it is read from row -CH a).
 template <int LT>
 struct Geo {
   static constexpr int CH = 128 / LT;               // chains per CTA
   static constexpr int NT = LT / 8, NV = LT / 16;    // H / F tiles, V tiles
   static constexpr int GROUPS = LT / 8 + 1;          // operand column groups (the last a halo)
-  static constexpr int OPV = GROUPS * kLbo;
+  static constexpr int HH = 4 * CH < 8 ? 8 : 4 * CH; // halo rows (>= CH (k - 1), a multiple of 8)
+  static constexpr int ROWS = 128 + HH;
+  static constexpr int LBO = ROWS * 16;              // one 8-column group
+  static constexpr int PLANE3 = 3 * LBO;             // hidden plane of a V buffer: 3 groups
+  static constexpr int VBUF = 4 * PLANE3;
+  static constexpr int PGRP = 4 * LBO;               // one column group of 4 hidden planes
+  static constexpr int OPV = GROUPS * LBO;
   static constexpr int WPR = LT / 32, WPC = LT * LT / 32;   // words per row / per chain
   static constexpr int NHV = NT + NV;                // H and V stages per Gibbs step
-  static_assert(LT == 128 || LT == 64, "lattice side");
+  static constexpr int MISC = CH <= 2 ? 1024 : 1536; // mbarriers, counters, reduction slots
+  static_assert(LT == 128 || LT == 64 || LT == 32, "lattice side");
 };
 
 struct TcLayout {
@@ -84,9 +91,9 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   uint32_t o = 0;
   l.opv[0] = o; o += G::OPV;          // lattice operands (v; v'), two buffers
   l.opv[1] = o; o += G::OPV;
-  l.vbuf = o; o += 2 * kVbuf;         // hidden operands of V tiles, two buffers of 3 groups
-  l.plast = o; o += kPgrp;            // the last hidden tile, kept for the last V tile
-  l.hold = o; o += kPgrp;             // the last odd hidden tile, until the next even one moves it
+  l.vbuf = o; o += 2 * G::VBUF;       // hidden operands of V tiles, two buffers of 3 groups
+  l.plast = o; o += G::PGRP;          // the last hidden tile, kept for the last V tile
+  l.hold = o; o += G::PGRP;           // the last odd hidden tile, until the next even one moves it
   l.bh = o; o += (uint32_t)(k * kBhA);           // filter images: hidden / free energy
   l.bv = o; o += (uint32_t)(k * v_ksteps(K) * kBvStep);   // visible
   l.vbits = o; o += G::CH * G::WPC * 4;         // packed current lattices, chain-major
@@ -95,7 +102,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   l.hbits = o; o += G::CH * 4 * G::WPC * 4;     // packed hidden units: chain, then filter planes
   l.scratch = o; o += 256 * 8;
   l.ch = o; o += (uint32_t)align16(G::CH * sizeof(ChainSm));
-  l.misc = o; o += 1024;              // mbarriers, TMEM address, counters, reduction slots
+  l.misc = o; o += G::MISC;           // mbarriers, TMEM address, counters, reduction slots
   l.total = o;
   return l;
 }
@@ -179,6 +186,11 @@ enum { kStH = 0, kStV = 1, kStF = 2 };
 template <int LT>
 __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
   using G = Geo<LT>;
+  if (G::NV == 2) {           // H3 H0 H1 H2 V0 V1
+    type = z < 4 ? kStH : kStV;
+    tile = z == 0 ? 3 : (z < 4 ? z - 1 : z - 4);
+    return;
+  }
   constexpr int kLoop = 5 + 3 * (G::NV - 3);
   if (z < 5) {
     type = kStH;
@@ -211,19 +223,20 @@ template <int LT, int KT, int kT>
 __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32_t dcol, uint32_t opvlo,
                                             uint32_t vbuflo, uint32_t bhlo, uint32_t bvlo, int Kr, int kr,
                                             uint32_t mbar) {
-  constexpr int CH = Geo<LT>::CH;
+  using G = Geo<LT>;
+  constexpr int CH = G::CH;
   const int K = KT ? KT : Kr, k = kT ? kT : kr;
   if (type != kStV) {
     if (role == 0) {
       const uint32_t id = umma_idesc(96);
-      const uint32_t a0 = opvlo + (uint32_t)(tile * (kLbo >> 4));
+      const uint32_t a0 = opvlo + (uint32_t)(tile * (G::LBO >> 4));
 #pragma unroll
       for (int a = 0; a < (kT ? kT : 8); ++a)
         if (kT || a < k) umma(dcol, a0 + (uint32_t)(a * CH), bhlo + (uint32_t)(a * (kBhA >> 4)), id, a > 0);
     }
   } else {
     const uint32_t id = umma_idesc(48);
-    const uint32_t a0 = vbuflo + (uint32_t)((tile & 1) * (kVbuf >> 4));
+    const uint32_t a0 = vbuflo + (uint32_t)((tile & 1) * (G::VBUF >> 4));
     const int J = v_ksteps(K), j0 = role == 0 ? 0 : 3, j1 = role == 0 ? (J < 3 ? J : 3) : J;
     const uint32_t dc = dcol + (role == 0 ? 0u : 48u);
 #pragma unroll
@@ -232,7 +245,7 @@ __device__ __forceinline__ void issue_stage(int role, int type, int tile, uint32
       for (int jj = 0; jj < 3; ++jj) {
         const int j = j0 + jj;
         if (j < j1 && (kT || a < k)) {
-          const uint32_t aoff = (uint32_t)(2 * j * kLbo + (8 - CH * a) * 16);
+          const uint32_t aoff = (uint32_t)(2 * j * G::LBO + (G::HH - CH * a) * 16);
           const uint32_t blo = bvlo + (uint32_t)(((a * J + j) * kBvStep) >> 4) + ((768u >> 4) << 16);
           umma(dc, a0 + (aoff >> 4), blo, id, (a | jj) != 0);
         }
@@ -252,7 +265,7 @@ static __device__ __noinline__ uint32_t tc_redo_hidden(const JobDev& jb, int f, 
   return decide64(x, w);
 }
 
-// fp16 units of packed lattices (chain-major) into a lattice operand (136
+// fp16 units of packed lattices (chain-major) into a lattice operand (ROWS
 // rows x GROUPS column groups, the periodic copies included); only the rows of
 // chain `only` when only >= 0.
 template <int LT>
@@ -260,8 +273,8 @@ __device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t
                                int only = -1) {
   using G = Geo<LT>;
   const unsigned char* by = (const unsigned char*)bits;
-  for (int q = tid; q < kRows * G::GROUPS; q += nthr) {
-    const int g = q / kRows, r = q - g * kRows;
+  for (int q = tid; q < G::ROWS * G::GROUPS; q += nthr) {
+    const int g = q / G::ROWS, r = q - g * G::ROWS;
     const int rr = r & 127, c = rr % G::CH, i = rr / G::CH;
     if (only >= 0 && c != only) continue;
     const uint32_t x = by[c * (G::WPC * 4) + i * (LT / 8) + (g % G::NT)];
@@ -271,7 +284,7 @@ __device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t
     o.y = ((z >> 2) & 0x10001u) * 0x3C00u;
     o.z = ((z >> 4) & 0x10001u) * 0x3C00u;
     o.w = ((z >> 6) & 0x10001u) * 0x3C00u;
-    *(uint4*)(smem + opv + (uint32_t)g * kLbo + (uint32_t)r * 16) = o;
+    *(uint4*)(smem + opv + (uint32_t)g * G::LBO + (uint32_t)r * 16) = o;
   }
 }
 
@@ -279,10 +292,10 @@ __device__ void expand_lattice(unsigned char* smem, uint32_t opv, const uint32_t
 template <int LT>
 __device__ void copy_chain_rows(unsigned char* smem, uint32_t dst, uint32_t src, int c, int tid, int nthr) {
   using G = Geo<LT>;
-  for (int q = tid; q < kRows * G::GROUPS; q += nthr) {
-    const int g = q / kRows, r = q - g * kRows;
+  for (int q = tid; q < G::ROWS * G::GROUPS; q += nthr) {
+    const int g = q / G::ROWS, r = q - g * G::ROWS;
     if ((r & 127) % G::CH != c) continue;
-    const uint32_t off = (uint32_t)g * kLbo + (uint32_t)r * 16;
+    const uint32_t off = (uint32_t)g * G::LBO + (uint32_t)r * 16;
     *(uint4*)(smem + dst + off) = *(const uint4*)(smem + src + off);
   }
 }
@@ -320,26 +333,26 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
   const uint32_t z = byte | (byte << 15);     // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
   const uint4 h4 = make_uint4(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u,
                               ((z >> 4) & 0x10001u) * 0x3C00u, ((z >> 6) & 0x10001u) * 0x3C00u);
-  // operand rows m + 8 of the V operands; rows 120..127 also as rows -8..-1
-  const uint32_t r0 = (uint32_t)(m + 8) * 16, r1 = (uint32_t)(m - 120) * 16;
+  // operand rows m + HH of the V operands; rows 128-HH..127 also as rows -HH..-1
+  const uint32_t r0 = (uint32_t)(m + G::HH) * 16, r1 = (uint32_t)(m - (128 - G::HH)) * 16;
   auto put = [&](uint32_t base) {
     *(uint4*)(smem + base + r0) = h4;
-    if (m >= 120) *(uint4*)(smem + base + r1) = h4;
+    if (m >= 128 - G::HH) *(uint4*)(smem + base + r1) = h4;
   };
   // V_u reads slots (0, 1, 2) = tiles (2u-1, 2u, 2u+1) of buffer u % 2, last
   // read by V_{u-2}, which precedes H_{2u} in the stage order.  An odd tile goes
   // to the last slot of its V tile and to `hold`; the next (even) H stage moves
   // this thread's rows of it from `hold` to the first slot of the next V tile.
   const int u = t >> 1;
-  const uint32_t pf = (uint32_t)f * kPlane3, hf = ly.hold + (uint32_t)f * kLbo;
+  const uint32_t pf = (uint32_t)f * G::PLANE3, hf = ly.hold + (uint32_t)f * G::LBO;
   if ((t & 1) == 0) {
-    const uint32_t vb = ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf;
-    put(vb + 1 * kLbo);
+    const uint32_t vb = ly.vbuf + (uint32_t)(u & 1) * G::VBUF + pf;
+    put(vb + 1 * G::LBO);
     *(uint4*)(smem + vb + r0) = *(const uint4*)(smem + hf + r0);
-    if (m >= 120) *(uint4*)(smem + vb + r1) = *(const uint4*)(smem + hf + r1);
+    if (m >= 128 - G::HH) *(uint4*)(smem + vb + r1) = *(const uint4*)(smem + hf + r1);
   } else {
-    if (t != G::NT - 1) put(ly.vbuf + (uint32_t)(u & 1) * kVbuf + pf + 2 * kLbo);
-    else put(ly.plast + (uint32_t)f * kLbo);    // the last V tile's last slot is in use by earlier V tiles
+    if (t != G::NT - 1) put(ly.vbuf + (uint32_t)(u & 1) * G::VBUF + pf + 2 * G::LBO);
+    else put(ly.plast + (uint32_t)f * G::LBO);   // the last V tile's last slot is in use by earlier V tiles
     put(hf);
   }
 }
@@ -380,13 +393,13 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
   atomicOr(dbc + (n0 >> 5), nib << (n0 & 31));
   const uint32_t z = nib | (nib << 15);
   const uint2 h2 = make_uint2(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u);
-  const uint32_t off = opv + (uint32_t)(j0 >> 3) * kLbo + (uint32_t)(j0 & 7) * 2;
+  const uint32_t off = opv + (uint32_t)(j0 >> 3) * G::LBO + (uint32_t)(j0 & 7) * 2;
   *(uint2*)(smem + off + (uint32_t)m * 16) = h2;
-  if (m < 8) *(uint2*)(smem + off + (uint32_t)(m + 128) * 16) = h2;
+  if (m < G::HH) *(uint2*)(smem + off + (uint32_t)(m + 128) * 16) = h2;
   if (j0 < 8) {        // the last column group repeats the first
-    const uint32_t o2 = opv + (uint32_t)G::NT * kLbo + (uint32_t)(j0 & 7) * 2;
+    const uint32_t o2 = opv + (uint32_t)G::NT * G::LBO + (uint32_t)(j0 & 7) * 2;
     *(uint2*)(smem + o2 + (uint32_t)m * 16) = h2;
-    if (m < 8) *(uint2*)(smem + o2 + (uint32_t)(m + 128) * 16) = h2;
+    if (m < G::HH) *(uint2*)(smem + o2 + (uint32_t)(m + 128) * 16) = h2;
   }
 }
 
@@ -495,7 +508,7 @@ static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, doub
 // slots: per (warp, chain) the F partial (int64) and its bound (FP32), per
 // warp the lattice counts of the chain its count-pass words belong to.
 constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kNbar = 26;
-constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224, kMiscRedF = 256, kMiscRedC = 768;
+constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224, kMiscRedF = 256;   // redc at kMiscRedF + 256 CH
 
 template <int LT, int KT, int kT>
 __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
@@ -519,14 +532,14 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   uint32_t* tslot = (uint32_t*)(smem + ly.misc + kMiscTslot);
   unsigned long long* nrec_sm = (unsigned long long*)(smem + ly.misc + kMiscNrec);
   unsigned char* redf = smem + ly.misc + kMiscRedF;
-  uint32_t* redc = (uint32_t*)(smem + ly.misc + kMiscRedC);
+  uint32_t* redc = (uint32_t*)(smem + ly.misc + kMiscRedF + 256 * CH);
   auto ch_of = [&](int c) -> ChainSm& { return chs[c]; };
 
   const int nimg = (k * kBhA + k * v_ksteps(K) * kBvStep) / 16;   // B images: hidden/free, then visible
   for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
   // V buffers zeroed: the groups of filters f >= K are read (with zero weights)
   // by the last K-step when 3K is odd, and must hold finite values
-  for (int q = tid; q < 2 * kVbuf / 16; q += kThr) ((uint4*)(smem + ly.vbuf))[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (int q = tid; q < 2 * G::VBUF / 16; q += kThr) ((uint4*)(smem + ly.vbuf))[q] = make_uint4(0u, 0u, 0u, 0u);
   for (int w = tid; w < CH * WPC; w += kThr) {
     const int c = c0 + w / WPC;
     vbits[w] = c < jb.n_chains ? jb.bits[(size_t)c * WPC + (w % WPC)] : 0u;
@@ -584,8 +597,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   const bool issuer = warp >= 16 && lane == 0;
   const int role = warp - 16;                     // issuers: 0 and 1
 
-  const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], kLbo);   // operand x at + x OPV / 16
-  const uint32_t dvbuf = umma_desc_lo(sbase + ly.vbuf, kLbo), dbh = umma_desc_lo(sbase + ly.bh, 1536),
+  const uint32_t dopv0 = umma_desc_lo(sbase + ly.opv[0], G::LBO);   // operand x at + x OPV / 16
+  const uint32_t dvbuf = umma_desc_lo(sbase + ly.vbuf, G::LBO), dbh = umma_desc_lo(sbase + ly.bh, 1536),
                  dbv = umma_desc_lo(sbase + ly.bv, 0);     // LBO set per image
   uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
   uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
@@ -695,11 +708,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               // this thread's rows of the last hidden tile (written by it at the
               // first H stage) into the last slot of the last V tile's buffer,
               // read last by V_{NV-3}, whose MMAs this warp has waited for
-              const uint32_t dst = ly.vbuf + (uint32_t)((G::NV - 1) & 1) * kVbuf + (uint32_t)fq * kPlane3 + 2 * kLbo,
-                             pl = ly.plast + (uint32_t)fq * kLbo;
-              *(uint4*)(smem + dst + (uint32_t)(m + 8) * 16) = *(const uint4*)(smem + pl + (uint32_t)(m + 8) * 16);
-              if (m >= 120)
-                *(uint4*)(smem + dst + (uint32_t)(m - 120) * 16) = *(const uint4*)(smem + pl + (uint32_t)(m - 120) * 16);
+              const uint32_t dst = ly.vbuf + (uint32_t)((G::NV - 1) & 1) * G::VBUF + (uint32_t)fq * G::PLANE3 +
+                                   2 * G::LBO,
+                             pl = ly.plast + (uint32_t)fq * G::LBO;
+              const uint32_t r0 = (uint32_t)(m + G::HH) * 16, r1 = (uint32_t)(m - (128 - G::HH)) * 16;
+              *(uint4*)(smem + dst + r0) = *(const uint4*)(smem + pl + r0);
+              if (m >= 128 - G::HH) *(uint4*)(smem + dst + r1) = *(const uint4*)(smem + pl + r1);
             }
             epi_publish(bar(kBarH + tl));
           } else {
@@ -930,18 +944,21 @@ cudaError_t tc_limit_inst() {
 int tc_chains_per_cta(int L) { return 128 / L; }
 
 size_t tc_smem_bytes(int L, int K, int k) {
-  return L == 128 ? tc_layout<128>(K, k).total : tc_layout<64>(K, k).total;
+  return L == 128 ? tc_layout<128>(K, k).total : (L == 64 ? tc_layout<64>(K, k).total : tc_layout<32>(K, k).total);
 }
 
 bool tc_supported(int kind, int prec, int L, int K, int k) {
-  return kind == kIsing && prec == kMixed && (L == 128 || L == 64) && K >= 1 && K <= 4 && k >= 1 && k <= 5;
+  return kind == kIsing && prec == kMixed && (L == 128 || L == 64 || L == 32) && K >= 1 && K <= 4 && k >= 1 &&
+         k <= 5;
 }
 
 // One launch per lattice side and filter shape (the jobs of p share both).
 cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
   const bool k45 = p.job[0].K == 4 && p.job[0].k == 5;
-  cudaError_t e = L == 128 ? (k45 ? tc_launch_inst<128, 4, 5>(p, grid, smem, st) : tc_launch_inst<128, 0, 0>(p, grid, smem, st))
-                           : (k45 ? tc_launch_inst<64, 4, 5>(p, grid, smem, st) : tc_launch_inst<64, 0, 0>(p, grid, smem, st));
+  cudaError_t e =
+      L == 128 ? (k45 ? tc_launch_inst<128, 4, 5>(p, grid, smem, st) : tc_launch_inst<128, 0, 0>(p, grid, smem, st))
+      : L == 64 ? (k45 ? tc_launch_inst<64, 4, 5>(p, grid, smem, st) : tc_launch_inst<64, 0, 0>(p, grid, smem, st))
+                : (k45 ? tc_launch_inst<32, 4, 5>(p, grid, smem, st) : tc_launch_inst<32, 0, 0>(p, grid, smem, st));
   if (e == cudaSuccess && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
     e = cudaGetLastError();
@@ -954,6 +971,8 @@ cudaError_t tc_set_smem_limit() {
   if (e == cudaSuccess) e = tc_limit_inst<128, 0, 0>();
   if (e == cudaSuccess) e = tc_limit_inst<64, 4, 5>();
   if (e == cudaSuccess) e = tc_limit_inst<64, 0, 0>();
+  if (e == cudaSuccess) e = tc_limit_inst<32, 4, 5>();
+  if (e == cudaSuccess) e = tc_limit_inst<32, 0, 0>();
   return e;
 }
 

@@ -1,12 +1,13 @@
 """The tensor-core form of the Ising proposal kernel (L = 128: one chain per
-CTA; L = 64: two chains per CTA with interleaved rows; mixed precision).
+CTA; L = 64 and 32: two and four chains per CTA with interleaved rows; mixed
+precision).
 
 Its chain is the FP64 path's: lattices and accept counts identical to the
 oracle's and to the table kernel's, bit for bit, on the same Philox streams;
 the lattice sums (log pi, E, observable sums) are exact integers times
 constants and identical too; the FP32 free energy agrees with the FP64 one
-within its certified bound.  Cases cover both sides (an odd chain count at
-L = 64 leaves the second chain of the last CTA empty), K < 4 (unused filter slots), k = 3..5,
+within its certified bound.  Cases cover the three sides (chain counts that
+leave the last CTA partly empty), K < 4 (unused filter slots), k = 3..5,
 g > 1 Gibbs steps (ping-pong lattice operands), uncorrected Gibbs, a batch
 mixing the tensor-core form with the table kernel, CUDA-graph replay, and the
 analytic CRBM (log r = 0: every MH decision sits within the FP32 bound and is
@@ -53,6 +54,10 @@ TC_CASES = [
     (64, 4, 5, 9, 1, True, 0.12),       # two chains per CTA, the last CTA half empty
     (64, 2, 3, 6, 2, True, 0.3),        # g = 2 with two chains per CTA
     (64, 3, 4, 5, 3, False, 0.25),      # uncorrected, g = 3
+    (32, 4, 5, 11, 1, True, 0.12),      # four chains per CTA, the last CTA three
+    (32, 2, 3, 6, 2, True, 0.3),        # g = 2 with four chains per CTA
+    (32, 3, 4, 9, 3, False, 0.25),      # uncorrected, g = 3, one chain in the last CTA
+    (32, 1, 5, 4, 1, True, 0.4),        # one filter
 ]
 
 
@@ -84,12 +89,12 @@ def test_tensor_core_form_matches_oracle_and_table_kernel(ctx, L, K, k, n, g, co
 
 
 def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
-    """A batch holding L = 128 and L = 64 jobs (tensor-core form, side streams)
-    and L = 32 jobs (table kernel) gives every job the results it has alone."""
+    """A batch holding L = 128, 64 and 32 jobs (tensor-core form, side streams)
+    and L = 16 jobs (table kernel) gives every job the results it has alone."""
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.1, seed=77)
     mid = ctx.load_model(ISING, W, vb, hb)
-    specs = [(128, 6, 1), (64, 5, 2), (128, 3, 3), (32, 7, 4)]
+    specs = [(128, 6, 1), (64, 5, 2), (128, 3, 3), (32, 7, 4), (16, 5, 5)]
 
     def make():
         return [ctx.new_job(mid, ISING, Lj, wl.ising_ladder(n, 4), (1.0,), SEED, base * 1000,
@@ -111,7 +116,7 @@ def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
         j.release()
 
 
-@pytest.mark.parametrize("L", [128, 64])
+@pytest.mark.parametrize("L", [128, 64, 32])
 def test_tensor_core_form_graph_replay_equals_direct_runs(ctx, L):
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.12, seed=78)
@@ -134,7 +139,7 @@ def test_tensor_core_form_graph_replay_equals_direct_runs(ctx, L):
     replay.release()
 
 
-@pytest.mark.parametrize("L", [128, 64])
+@pytest.mark.parametrize("L", [128, 64, 32])
 def test_tensor_core_form_mh_redo_on_the_analytic_crbm(ctx, L):
     """App. C: log r = 0 exactly, so the FP32 bound straddles it whenever
     |log u| is small and the FP64 redo decides; every proposal is accepted and
