@@ -144,6 +144,15 @@ __device__ __forceinline__ void tm_ld4(uint32_t taddr, float (&v)[4]) {
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tm_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// Ties loaded accumulator registers to a point after tm_wait(): volatile asm
+// statements keep their order, and every later use of the values now depends
+// on this one, so no use can be scheduled before the wait.
+__device__ __forceinline__ void tm_tie(float (&v)[4]) {
+  asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
+}
+__device__ __forceinline__ void tm_tie(float (&v)[8]) {
+  asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]));
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -427,10 +436,11 @@ __device__ __forceinline__ void epi_free(const JobDev& jb, const float (&s2)[8],
 
 // The MH decisions of the chains whose FP32 margin straddled the threshold
 // (every thread of the CTA calls; the CH chains' groups of 512 / CH epilogue
-// threads work side by side): F of v' (and of v when only an FP32 value of it
-// is known) with df64 softplus, bound ~1e-7; the FP64 path's own code only if
-// that bound still straddles.  Out of line, away from the proposal loop's
-// registers.  c0: the chain index of the CTA's first chain.
+// threads work side by side): F of v' with df64 softplus (bound ~1e-7), then
+// F of v the same way if only an FP32 value of it is known and the decision
+// still straddles; the FP64 path's own code only if that bound still does.
+// Out of line, away from the proposal loop's registers.  c0: the chain index
+// of the CTA's first chain.
 template <int LT>
 static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, double* scratch, const uint32_t* pv,
                                             const uint32_t* vbits, uint32_t step, int c0) {
@@ -445,30 +455,43 @@ static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, doub
   g2.c = c0 + c;
   g2.cid = (uint32_t)(jb.cid_base + (uint64_t)g2.c);
   g2.active = tid < kEpi && ch.flag_rec != 0;
+  // the decision with the values known so far: settled (flag_rec 1, flag_acc
+  // set) or left to `undecided`
+  auto decide = [&](int undecided) {
+    const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
+    const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g2.cid), jb.rk);
+    const double logu = log(((double)w.x + 0.5) * 0x1p-32);
+    const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
+                      1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
+    ch.flag_rec = 1;
+    if (logr - logu > Mg) ch.flag_acc = 1;
+    else if (logu - logr > Mg) ch.flag_acc = 0;
+    else ch.flag_rec = undecided;
+  };
   {
-    Grp g3 = g2;
-    g3.active = g2.active && ch.Fb != 0.0;
-    double f1[3], f2[3];
+    // F(v') first; F(v), when only its FP32 value is known, only if the
+    // decision still straddles (3), since the FP32 bound of F(v) alone is
+    // often narrow enough
+    double f1[3];
     free_sum_df<4>(jb, g2, pv + c * G::WPC, f1);
     grp_reduce<3>(f1, g2, scratch);
-    free_sum_df<4>(jb, g3, vbits + c * G::WPC, f2);
-    grp_reduce<3>(f2, g3, scratch);
     if (g2.active && g2.r == 0) {
       ch.Fp = -jb.vb * f1[2] - f1[0];
       ch.Bp = f1[1] + 1e-15 * fabs(ch.Fp);
-      if (g3.active) {
+      decide(ch.Fb != 0.0 ? 3 : 2);
+      ch.rec_mh += 1ull;
+    }
+    if (__syncthreads_or(g2.active && g2.r == 0 && ch.flag_rec == 3)) {
+      Grp g3 = g2;
+      g3.active = g2.active && ch.flag_rec == 3;
+      double f2[3];
+      free_sum_df<4>(jb, g3, vbits + c * G::WPC, f2);
+      grp_reduce<3>(f2, g3, scratch);
+      if (g3.active && g3.r == 0) {
         ch.F = -jb.vb * f2[2] - f2[0];
         ch.Fb = f2[1] + 1e-15 * fabs(ch.F);
+        decide(2);
       }
-      const double logr = (ch.lpp - ch.lp) + (ch.Fp - ch.F);
-      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, g2.cid), jb.rk);
-      const double logu = log(((double)w.x + 0.5) * 0x1p-32);
-      const double Mg = ch.Bp + ch.Fb + ch.lppb + ch.lpb +
-                        1e-12 * (fabs(ch.lpp) + fabs(ch.lp) + fabs(ch.Fp) + fabs(ch.F)) + 1e-300;
-      if (logr - logu > Mg) ch.flag_acc = 1;
-      else if (logu - logr > Mg) ch.flag_acc = 0;
-      else ch.flag_rec = 2;
-      ch.rec_mh += 1ull;
     }
   }
   if (__syncthreads_or(g2.active && g2.r == 0 && ch.flag_rec == 2)) {
@@ -699,6 +722,9 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               tm_ld8(tcol + 32 + 8 * fq, s1);
               tm_ld8(tcol + 64 + 8 * fq, s0);
               tm_wait();
+              tm_tie(s2);
+              tm_tie(s1);
+              tm_tie(s0);
               epi_release();
               epi_hidden<LT>(jb, smem, ly, s2, s1, s0, m, i, fq, tl, w0, w1, sbc, hbc, nrec);
             } else {
@@ -722,12 +748,18 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             tm_ld4(tcol + 16 + 4 * fq, s1);
             tm_ld4(tcol + 32 + 4 * fq, s0);
             if (K > 2) {
-              // filters 2, 3 from the second issuer's accumulator (integer sums: exact)
+              // K-steps 3.. from the second issuer's accumulator (integer sums: exact)
               float t2[4], t1[4], t0[4];
               tm_ld4(tcol + 48 + 4 * fq, t2);
               tm_ld4(tcol + 64 + 4 * fq, t1);
               tm_ld4(tcol + 80 + 4 * fq, t0);
               tm_wait();
+              tm_tie(s2);
+              tm_tie(s1);
+              tm_tie(s0);
+              tm_tie(t2);
+              tm_tie(t1);
+              tm_tie(t0);
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 s2[q] += t2[q];
@@ -736,6 +768,9 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
               }
             } else {
               tm_wait();
+              tm_tie(s2);
+              tm_tie(s1);
+              tm_tie(s0);
             }
             epi_release();
             epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
@@ -779,6 +814,9 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
           tm_ld8(tcol + 32 + 8 * fq, s1);
           tm_ld8(tcol + 64 + 8 * fq, s0);
           tm_wait();
+          tm_tie(s2);
+          tm_tie(s1);
+          tm_tie(s0);
           epi_release();
           epi_free(jb, s2, s1, s0, fq, s32, c32, sabs, ssp);
         } else {
