@@ -615,9 +615,9 @@ def main():
     dom_sites = sum(n * L * L for L, n, _ in dom) * S
     dom_name = ("crbm_tc_kernel" if prec == MIXED and spec["kind"] == 0 and dom[0][0] == 128 else "crbm_step_kernel")
     # kernels per step: one launch (and its step-counter update) per kernel the
-    # batch uses: the tensor-core kernel per side L in {128, 64, 32} (mixed Ising),
+    # batch uses: the tensor-core kernel per side L in {128, 64, 32, 16} (mixed Ising),
     # the table kernel for the rest
-    tc_sides = {L for L, _ in spec["jobs"] if prec == MIXED and spec["kind"] == 0 and L in (128, 64, 32)}
+    tc_sides = {L for L, _ in spec["jobs"] if prec == MIXED and spec["kind"] == 0 and L in (128, 64, 32, 16)}
     n_parts = len(tc_sides) + int(any(L not in tc_sides for L, _ in spec["jobs"]))
     line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -343,7 +343,7 @@ CRBM_API int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* b
 /* Choose the kernel of later proposals (crbm_run, crbm_run_batch, graphs
  * created afterwards) for eligible jobs: enable = 1 (default) runs them on the
  * tensor-core form, enable = 0 on the table kernel.  Eligible: CRBM_ISING,
- * CRBM_MIXED, L = 128, 64 or 32, K <= 4, k <= 5.  There the three convolutions of a
+ * CRBM_MIXED, L = 128, 64, 32 or 16, K <= 4, k <= 5.  There the three convolutions of a
  * proposal (Eqs. B2, B3 and the pre-activations of F, Eq. 13) are tcgen05
  * MMAs on fp16 operands: 0/1 units and integer digits of the filters
  * (W = q (c2 2^22 + c1 2^11 + c0)), whose sums are exact in FP32; the chain

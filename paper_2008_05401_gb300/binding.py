@@ -385,7 +385,7 @@ class Context:
         crbm_update_model(self.h, model_id, W, v_bias, h_bias)
 
     def set_tensor_cores(self, enable: bool):
-        """Run later proposals of eligible jobs (Ising, mixed, L = 128, 64 or 32, K <= 4,
+        """Run later proposals of eligible jobs (Ising, mixed, L = 128, 64, 32 or 16, K <= 4,
         k <= 5) on the tensor-core kernel (True, default) or the table kernel."""
         crbm_set_tensor_cores(self.h, enable)
 

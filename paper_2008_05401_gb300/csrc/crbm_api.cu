@@ -121,7 +121,7 @@ struct crbm_ctx {
   // side streams and events of a batch whose jobs need launches of different
   // CTA sizes: the launches fork from the caller's stream and join it again,
   // so they run side by side
-  static constexpr int kSide = 6;
+  static constexpr int kSide = 7;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
   struct Graph {
@@ -337,7 +337,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
                        cudaStream_t st, const Job* partner = nullptr) {
   // parts: (CTA size, jobs); CTA size -L = the tensor-core form for side L
   std::vector<std::pair<int, std::vector<int>>> parts;
-  for (int nt : {-128, -64, -32, 256, 128, 64, 32}) {
+  for (int nt : {-128, -64, -32, -16, 256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
@@ -360,6 +360,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
   }
   // several CTA sizes: the first launch on st, the others on side streams
   // forked from st and joined back into it
+  if (parts.size() > (size_t)crbm_ctx::kSide + 1) return fail(ctx, CRBM_EINVAL, "too many kernel kinds in one batch");
   CK(cudaEventRecord(ctx->fork, st), "fork event");
   for (size_t i = 1; i < parts.size(); ++i) CK(cudaStreamWaitEvent(ctx->side[i - 1], ctx->fork, 0), "fork wait");
   int rc = CRBM_OK;

@@ -25,7 +25,8 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Tensor-core form of the proposal kernel (crbm_step_tc.cu): Ising kind, mixed
-// precision, L = 128 (one chain per CTA), 64 (two) or 32 (four), K <= 4, k <= 5.
+// precision, L = 128 (one chain per CTA), 64 (two), 32 (four) or 16 (eight),
+// K <= 4, k <= 5.
 bool tc_supported(int kind, int prec, int L, int K, int k);
 int tc_chains_per_cta(int L);
 size_t tc_smem_bytes(int L, int K, int k);

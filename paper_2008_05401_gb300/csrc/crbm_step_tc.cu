@@ -1,6 +1,6 @@
 // Tensor-core form of the fused CRBM proposal + Metropolis-Hastings kernel:
 // Ising kind, mixed precision, L x L lattices with L = 128 (one chain per CTA),
-// 64 (two) or 32 (four), K <= 4 filters of side k <= 5, mode 0 (S
+// 64 (two), 32 (four) or 16 (eight), K <= 4 filters of side k <= 5, mode 0 (S
 // proposals of g Gibbs steps).  The chains are the table kernel's chains: the
 // same Philox words per unit, and every Bernoulli and MH decision the FP64
 // path's.
@@ -35,7 +35,7 @@
 // NV = L / 16 visible tiles of 16 columns (V), interleaved so that a V tile's
 // MMAs run while the epilogue warps work through the two H stages after its
 // last input tile (L = 128: H15 H0 H1 H2 H3 V0 H4 H5 V1 ... H12 H13 V5 H14 V6
-// V7; L = 32: H3 H0 H1 H2 V0 V1); then NT free-energy tiles (F).  Warp-specialised pipeline: two issuing
+// V7; L = 32: H3 H0 H1 H2 V0 V1; L = 16: H1 H0 V0); then NT free-energy tiles (F).  Warp-specialised pipeline: two issuing
 // warps put each stage's MMAs into one of four tensor-memory buffers and
 // commit them to that buffer's `full` mbarrier; the 16 epilogue warps (warp
 // w: lanes 32 (w % 4) .. + 31 = operand rows, w / 4 = filter or column
@@ -76,8 +76,13 @@ struct Geo {
   static constexpr int OPV = GROUPS * LBO;
   static constexpr int WPR = LT / 32, WPC = LT * LT / 32;   // words per row / per chain
   static constexpr int NHV = NT + NV;                // H and V stages per Gibbs step
-  static constexpr int MISC = CH <= 2 ? 1024 : 1536; // mbarriers, counters, reduction slots
-  static_assert(LT == 128 || LT == 64 || LT == 32, "lattice side");
+  // misc area: mbarriers and the TMEM address (0 .. 211), per-chain redo
+  // counters at 224, then per (warp, chain) F partials and per-part counts
+  static constexpr int REDF = CH <= 4 ? 256 : 288, REDC = REDF + 256 * CH;
+  static constexpr int MISC = CH <= 2 ? 1024 : (CH == 4 ? 1536 : 2560);
+  static constexpr int SPAN = WPC < 32 ? WPC : 32;   // count-pass lanes per part (one chain's)
+  static_assert(LT == 128 || LT == 64 || LT == 32 || LT == 16, "lattice side");
+  static_assert(REDC + 64 <= MISC && 224 + 8 * CH <= REDF, "misc area");
 };
 
 struct TcLayout {
@@ -198,6 +203,11 @@ __device__ __forceinline__ void hv_stage(int z, int& type, int& tile) {
   if (G::NV == 2) {           // H3 H0 H1 H2 V0 V1
     type = z < 4 ? kStH : kStV;
     tile = z == 0 ? 3 : (z < 4 ? z - 1 : z - 4);
+    return;
+  }
+  if (G::NV == 1) {           // H1 H0 V0
+    type = z < 2 ? kStH : kStV;
+    tile = z == 0 ? 1 : 0;
     return;
   }
   constexpr int kLoop = 5 + 3 * (G::NV - 3);
@@ -531,7 +541,7 @@ static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, doub
 // slots: per (warp, chain) the F partial (int64) and its bound (FP32), per
 // warp the lattice counts of the chain its count-pass words belong to.
 constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kNbar = 26;
-constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224, kMiscRedF = 256;   // redc at kMiscRedF + 256 CH
+constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224;
 
 template <int LT, int KT, int kT>
 __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
@@ -554,8 +564,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
   uint32_t* tslot = (uint32_t*)(smem + ly.misc + kMiscTslot);
   unsigned long long* nrec_sm = (unsigned long long*)(smem + ly.misc + kMiscNrec);
-  unsigned char* redf = smem + ly.misc + kMiscRedF;
-  uint32_t* redc = (uint32_t*)(smem + ly.misc + kMiscRedF + 256 * CH);
+  unsigned char* redf = smem + ly.misc + G::REDF;
+  uint32_t* redc = (uint32_t*)(smem + ly.misc + G::REDC);
   auto ch_of = [&](int c) -> ChainSm& { return chs[c]; };
 
   const int nimg = (k * kBhA + k * v_ksteps(K) * kBvStep) / 16;   // B images: hidden/free, then visible
@@ -848,12 +858,21 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       if (tid < CH * WPC) {
         const uint32_t* p = pv + (tid / WPC) * WPC;
         const int w = tid % WPC;
-        const uint32_t x = p[w], xr = p[(w & ~(G::WPR - 1)) | ((w + 1) & (G::WPR - 1))], xd = p[(w + G::WPR) % WPC];
-        cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ ((x >> 1) | (xr << 31))) + __popc(x ^ xd)) << 16);
+        const uint32_t x = p[w];
+        uint32_t right, down;
+        if constexpr (LT >= 32) {          // whole rows of WPR words
+          const uint32_t xr = p[(w & ~(G::WPR - 1)) | ((w + 1) & (G::WPR - 1))];
+          right = (x >> 1) | (xr << 31);
+          down = p[(w + G::WPR) % WPC];
+        } else {                           // L = 16: two rows per word
+          right = ((x >> 1) & 0x7FFF7FFFu) | ((x << 15) & 0x80008000u);
+          down = (x >> 16) | (p[(w + 1) % WPC] << 16);
+        }
+        cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ right) + __popc(x ^ down)) << 16);
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
-      if (lane == 0) redc[warp] = cnt;
+      for (int o = G::SPAN / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+      if (tid % G::SPAN == 0 && tid < 16 * G::SPAN) redc[tid / G::SPAN] = cnt;   // part = chain's words
     }
     __syncthreads();
     // thread c < CH: the MH decision of chain c0 + c
@@ -880,7 +899,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         bnd += (double)*(const float*)(redf + 16 * (w * CH + tid) + 8);
       }
       for (int w = 0; w < 16; ++w)
-        if (w * 32 < CH * WPC && (w * 32) / WPC == tid) {
+        if (w * G::SPAN < CH * WPC && (w * G::SPAN) / WPC == tid) {
           ones += redc[w] & 0xFFFFu;
           pairs += redc[w] >> 16;
         }
@@ -982,12 +1001,15 @@ cudaError_t tc_limit_inst() {
 int tc_chains_per_cta(int L) { return 128 / L; }
 
 size_t tc_smem_bytes(int L, int K, int k) {
-  return L == 128 ? tc_layout<128>(K, k).total : (L == 64 ? tc_layout<64>(K, k).total : tc_layout<32>(K, k).total);
+  return L == 128 ? tc_layout<128>(K, k).total
+         : L == 64 ? tc_layout<64>(K, k).total
+         : L == 32 ? tc_layout<32>(K, k).total
+                   : tc_layout<16>(K, k).total;
 }
 
 bool tc_supported(int kind, int prec, int L, int K, int k) {
-  return kind == kIsing && prec == kMixed && (L == 128 || L == 64 || L == 32) && K >= 1 && K <= 4 && k >= 1 &&
-         k <= 5;
+  return kind == kIsing && prec == kMixed && (L == 128 || L == 64 || L == 32 || L == 16) && K >= 1 && K <= 4 &&
+         k >= 1 && k <= 5;
 }
 
 // One launch per lattice side and filter shape (the jobs of p share both).
@@ -996,7 +1018,8 @@ cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaS
   cudaError_t e =
       L == 128 ? (k45 ? tc_launch_inst<128, 4, 5>(p, grid, smem, st) : tc_launch_inst<128, 0, 0>(p, grid, smem, st))
       : L == 64 ? (k45 ? tc_launch_inst<64, 4, 5>(p, grid, smem, st) : tc_launch_inst<64, 0, 0>(p, grid, smem, st))
-                : (k45 ? tc_launch_inst<32, 4, 5>(p, grid, smem, st) : tc_launch_inst<32, 0, 0>(p, grid, smem, st));
+      : L == 32 ? (k45 ? tc_launch_inst<32, 4, 5>(p, grid, smem, st) : tc_launch_inst<32, 0, 0>(p, grid, smem, st))
+                : (k45 ? tc_launch_inst<16, 4, 5>(p, grid, smem, st) : tc_launch_inst<16, 0, 0>(p, grid, smem, st));
   if (e == cudaSuccess && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
     e = cudaGetLastError();
@@ -1011,6 +1034,8 @@ cudaError_t tc_set_smem_limit() {
   if (e == cudaSuccess) e = tc_limit_inst<64, 0, 0>();
   if (e == cudaSuccess) e = tc_limit_inst<32, 4, 5>();
   if (e == cudaSuccess) e = tc_limit_inst<32, 0, 0>();
+  if (e == cudaSuccess) e = tc_limit_inst<16, 4, 5>();
+  if (e == cudaSuccess) e = tc_limit_inst<16, 0, 0>();
   return e;
 }
 

@@ -1,12 +1,12 @@
 """The tensor-core form of the Ising proposal kernel (L = 128: one chain per
-CTA; L = 64 and 32: two and four chains per CTA with interleaved rows; mixed
-precision).
+CTA; L = 64, 32 and 16: two, four and eight chains per CTA with interleaved
+rows; mixed precision).
 
 Its chain is the FP64 path's: lattices and accept counts identical to the
 oracle's and to the table kernel's, bit for bit, on the same Philox streams;
 the lattice sums (log pi, E, observable sums) are exact integers times
 constants and identical too; the FP32 free energy agrees with the FP64 one
-within its certified bound.  Cases cover the three sides (chain counts that
+within its certified bound.  Cases cover the four sides (chain counts that
 leave the last CTA partly empty), K < 4 (unused filter slots), k = 3..5,
 g > 1 Gibbs steps (ping-pong lattice operands), uncorrected Gibbs, a batch
 mixing the tensor-core form with the table kernel, CUDA-graph replay, and the
@@ -58,6 +58,9 @@ TC_CASES = [
     (32, 2, 3, 6, 2, True, 0.3),        # g = 2 with four chains per CTA
     (32, 3, 4, 9, 3, False, 0.25),      # uncorrected, g = 3, one chain in the last CTA
     (32, 1, 5, 4, 1, True, 0.4),        # one filter
+    (16, 4, 5, 13, 1, True, 0.12),      # eight chains per CTA, the last CTA five
+    (16, 2, 3, 8, 2, True, 0.3),        # g = 2 with eight chains per CTA
+    (16, 3, 4, 9, 3, False, 0.25),      # uncorrected, g = 3, one chain in the last CTA
 ]
 
 
@@ -89,12 +92,13 @@ def test_tensor_core_form_matches_oracle_and_table_kernel(ctx, L, K, k, n, g, co
 
 
 def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
-    """A batch holding L = 128, 64 and 32 jobs (tensor-core form, side streams)
-    and L = 16 jobs (table kernel) gives every job the results it has alone."""
+    """A batch holding L = 128, 64, 32 and 16 jobs (tensor-core form, side
+    streams) and L = 8 jobs (table kernel) gives every job the results it has
+    alone."""
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.1, seed=77)
     mid = ctx.load_model(ISING, W, vb, hb)
-    specs = [(128, 6, 1), (64, 5, 2), (128, 3, 3), (32, 7, 4), (16, 5, 5)]
+    specs = [(128, 6, 1), (64, 5, 2), (128, 3, 3), (32, 7, 4), (16, 5, 5), (8, 6, 6)]
 
     def make():
         return [ctx.new_job(mid, ISING, Lj, wl.ising_ladder(n, 4), (1.0,), SEED, base * 1000,
@@ -116,7 +120,7 @@ def test_tensor_core_form_batched_with_table_kernel_jobs(ctx):
         j.release()
 
 
-@pytest.mark.parametrize("L", [128, 64, 32])
+@pytest.mark.parametrize("L", [128, 64, 32, 16])
 def test_tensor_core_form_graph_replay_equals_direct_runs(ctx, L):
     from paper_2008_05401_gb300 import ISING, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 5, 0.12, seed=78)
@@ -139,7 +143,7 @@ def test_tensor_core_form_graph_replay_equals_direct_runs(ctx, L):
     replay.release()
 
 
-@pytest.mark.parametrize("L", [128, 64, 32])
+@pytest.mark.parametrize("L", [128, 64, 32, 16])
 def test_tensor_core_form_mh_redo_on_the_analytic_crbm(ctx, L):
     """App. C: log r = 0 exactly, so the FP32 bound straddles it whenever
     |log u| is small and the FP64 redo decides; every proposal is accepted and
@@ -149,9 +153,12 @@ def test_tensor_core_form_mh_redo_on_the_analytic_crbm(ctx, L):
     beta = 1 / 2.269
     W, hb, vb = ising.analytic_crbm(beta, 3)
     mid = ctx.load_model(ISING, W, vb, hb)
-    job = ctx.new_job(mid, ISING, L, np.full(16, 1 / beta), (1.0,), SEED, 0, None, MIXED)
-    job.run(12, precision=MIXED)
+    # the FP32 bound shrinks with the lattice (K N units): more draws at small L
+    # so that some |log u| fall inside it
+    n, S = 16 * (128 // L), 24
+    job = ctx.new_job(mid, ISING, L, np.full(n, 1 / beta), (1.0,), SEED, 0, None, MIXED)
+    job.run(S, precision=MIXED)
     _, acc, rec = job.observables()
-    assert np.all(acc == 12)
+    assert np.all(acc == S)
     assert rec[:, 1].sum() > 0
     job.release()
