@@ -911,13 +911,15 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       // sums of the non-negative bound terms over 512 / CH threads and then over
       // 16 warps lose < 26 2^-24 relative, inside the factor 1.001
       constexpr int kN = LT * LT;
-      const double Fsp = (double)fs * 0x1p-32;
-      const double Fdata = (double)bnd * 1.001 + (512.0 / CH) * 0x1p-33;
+      // margin terms known before this proposal's sums, off the dependent chain
+      const double cst = (double)K * (double)kN * ((double)jb.csp + (double)jb.tcft) + (512.0 / CH) * 0x1p-33;
+      const double mg0 = ((Fb + lpb) + 1e-12 * (fabs(lp) + fabs(F))) + (cst + 1e-300);
+      const double Fdata = (double)bnd * 1.001;
       const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
       const double M = (double)(2 * (int)ones - kN);
       const double lpp = -beta * E;
-      const double Fp = -jb.vb * (double)ones - Fsp;
-      const double Bp = (Fdata + (double)K * (double)kN * ((double)jb.csp + (double)jb.tcft)) + 1e-12 * fabs(Fp);
+      const double Fp = fma((double)fs, -0x1p-32, -jb.vb * (double)ones);
+      const double Bp = (Fdata + cst) + 1e-12 * fabs(Fp);
       ch.Ep = E;
       ch.lpp = lpp;
       ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
@@ -929,7 +931,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
         ch.flag_acc = 1;
       } else {
         const double logr = (lpp - lp) + (Fp - F);
-        const double Mg = ((Bp + Fb) + lpb) + 1e-12 * ((fabs(lpp) + fabs(lp)) + (fabs(Fp) + fabs(F))) + 1e-300;
+        // = Bp + Fb + lpb + 1e-12 (|lpp| + |lp| + |Fp| + |F|) + 1e-300
+        const double Mg = (Fdata + mg0) + 1e-12 * (2.0 * fabs(Fp) + fabs(lpp));
         if (logr - logu > Mg) ch.flag_acc = 1;
         else if (logu - logr > Mg) ch.flag_acc = 0;
         else ch.flag_rec = 1;
