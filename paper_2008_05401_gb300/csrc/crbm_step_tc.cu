@@ -890,9 +890,9 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
       if (c0 + c < jb.n_chains) trace_store(jb, c0 + c, step0 + (uint64_t)s, ch.E);
     };
     if (tid < CH) {
-      // one thread per chain; GB300's FP64 pipe has a long latency, so the
-      // dependent FP64 chain is kept short: partial sums in integers and FP32,
-      // values in registers, independent terms side by side
+      // one thread per chain; each FP64 instruction (conversions included)
+      // holds the SMSP's slow FP64 pipe for tens of cycles, so FP64 work is
+      // kept small: partial sums in integers and FP32, values in registers
       ChainSm& ch = ch_of(tid);
       const double lp = ch.lp, F = ch.F, Fb = ch.Fb, lpb = ch.lpb, beta = ch.beta, logu = ch.logu;
       long long fs = 0;
