@@ -144,7 +144,7 @@ def peaks():
 # lattices stay in shared memory for the whole launch).  The capture is
 # cold-cache, so the scaling counts the fixed part once per 152 chains: an upper
 # bound.
-BATCH_ISING_TC_TRAFFIC_BYTES = (1244416 + 1792) * 4096 / 152   # 152-chain capture: 1,244,416 B read, 1,792 B written
+BATCH_ISING_TC_TRAFFIC_BYTES = (1241344 + 1792) * 4096 / 152   # 152-chain capture: 1,241,344 B read, 1,792 B written
 
 
 def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
