@@ -237,6 +237,16 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// log u of an MH draw u = (w + 1/2) 2^-32 in FP32, within 2^-20 (1 + |log u|)
+// of the exact value: u = m 2^e with m in [1, 2) split off its float exactly,
+// lg2 of m from the special-function unit (absolute error 2^-22 on [1, 2]),
+// the float rounding of u within 2^-23 relative, the sum and the ln 2
+// product within 2^-24 relative each.
+__device__ __forceinline__ float log_u32(uint32_t w) {
+  const uint32_t ub = __float_as_uint(((float)w + 0.5f) * 0x1p-32f);
+  const float lg2u = (float)((int)(ub >> 23) - 127) + lg2_approx(__uint_as_float((ub & 0x7FFFFFu) | 0x3F800000u));
+  return lg2u * 0.69314718055994531f;
+}
 
 // sigma(x) in FP32: e = 2^(-x log2 e), p = 1/(1 + e).
 __device__ __forceinline__ float sigmoid32(float x) {

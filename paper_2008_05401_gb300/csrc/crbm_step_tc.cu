@@ -676,17 +676,12 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     if (warp == 17 && lane >= 1 && lane <= CH && prm.correct) {
       // the MH draws of this proposal, ahead of the decisions (read after the
       // barriers of the proposal's end).  In FP32, within 2^-20 (1 + |log u|)
-      // of the FP64 log u, which the decision adds to its margin (the FP64 log
+      // of the FP64 log u, which the decision adds to its margin: the FP64 log
       // would hold this warp's issuing lane, whose commits every stage waits
-      // for, for thousands of cycles on the 1/64-rate FP64 pipe): u =
-      // (w + 1/2) 2^-32 = m 2^e with m in [1, 2) exactly split off its float,
-      // lg2 of m from the special-function unit (absolute error 2^-22 on
-      // [1, 2], tested), the float rounding of u within 2^-23 relative
+      // for, for thousands of cycles on the 1/64-rate FP64 pipe
       const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, (uint32_t)(jb.cid_base + (uint64_t)(c0 + lane - 1))),
                                        jb.rk);
-      const uint32_t ub = __float_as_uint(((float)w.x + 0.5f) * 0x1p-32f);
-      const float lg2u = (float)((int)(ub >> 23) - 127) + lg2_approx(__uint_as_float((ub & 0x7FFFFFu) | 0x3F800000u));
-      ch_of(lane - 1).logu = (double)(lg2u * 0.69314718055994531f);
+      ch_of(lane - 1).logu = (double)log_u32(w.x);
     }
     // Gibbs step sub reads operand sub % 2 and writes the other: v is in
     // operand 0 at the start of a proposal, v' in operand g % 2 at its end
