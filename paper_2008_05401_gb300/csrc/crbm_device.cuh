@@ -67,7 +67,7 @@ struct JobDev {
   const float4* fd4;            // [k][2^k] filter-interleaved, K <= 4
   const float4* fh4;
   const float4* fl4;
-  // tensor-core form (Ising, L = 128, K <= 4, k <= 6; crbm_step_tc.cu):
+  // tensor-core form (Ising, L = 128, 64, 32 or 16, K <= 4, k <= 5; crbm_step_tc.cu):
   // operand images of the filter digits, null when the model has none
   const uint4* tcw;
   float tq2, tq1, tq0;          // digit scales qf 2^22, qf 2^11, qf
