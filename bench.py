@@ -137,75 +137,142 @@ def peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one launch of the tensor-core kernel on the
-# batch Ising workload's L = 128 jobs (4096 chains x 10 proposals), from an ncu
-# capture of a 152-chain launch scaled by chains (per chain the traffic is its
-# lattice and state in and out, the filter images and the recompute tables; the
-# lattices stay in shared memory for the whole launch).  The capture is
-# cold-cache, so the scaling counts the fixed part once per 152 chains: an upper
-# bound.
-BATCH_ISING_TC_TRAFFIC_BYTES = (1241344 + 1792) * 4096 / 152   # 152-chain capture: 1,241,344 B read, 1,792 B written
+# DRAM bytes (read + write) of one launch of the persistent tensor-core
+# kernel on the batch Ising workload, from an ncu capture (None: not captured
+# since the kernel last changed).
+BATCH_ISING_TC_TRAFFIC_BYTES = None
 
 
-def roofline(wd, kernel_ms, clocks, K, k, n_sites_step, traffic=None):
-    """ALU roofline of a proposal kernel: algorithmic FP32 flops = the three
-    periodic convolutions of a proposal written directly (hidden, visible and
-    free-energy pre-activations: 3 x K k^2 multiply-adds per site), against the
-    FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops) and the SM
-    clock sampled during the run.  The table kernel does these sums by table
-    look-ups and the tensor-core kernel as fp16 digit MMAs; either way the
-    kernel is bound by its ALU work (Philox, sigmoids, softplus, decisions), and
-    the fraction measures convolution work per second against the pipe a
-    direct FP32 implementation would saturate."""
-    flops = 6.0 * K * k * k * n_sites_step
-    mhz = clocks.get("sm_mhz") or peaks().get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
+def _sm_mhz(clocks):
+    return (clocks or {}).get("sm_mhz") or peaks().get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
+
+
+def roofline(kernel_ms, clocks, K, k, n_sites, traffic=None):
+    """ALU roofline of an Ising proposal kernel with the algorithmic count of
+    the method: per site and proposal the hidden and visible convolutions,
+    2 K k^2 multiply-adds = 4 K k^2 flops (400 at K = 4, k = 5; the free
+    energy's pre-activations are the next proposal's hidden ones when v' is
+    kept, so a proposal needs two convolution passes), against the FP32 FMA
+    peak from unit counts (152 SMs x 128 lanes x 2 flops) at the SM clock
+    sampled during the run.  The other pipes the method needs bound it no
+    tighter: (4K + 2) special-function operations per site at 16 per SM and
+    clock, and (K + 1) / 4 Philox blocks of about 80 integer operations at 64
+    per SM and clock (the same 1.56 clocks per site as the FMA count).  The
+    kernels compute all three convolutions (the F pass recomputed, 6 K k^2
+    flops per site): that executed count is reported beside, labelled."""
+    mhz = _sm_mhz(clocks)
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    flops = 4.0 * K * k * k * n_sites
     achieved = flops / (kernel_ms * 1e-3) / 1e12
+    executed = 6.0 * K * k * k * n_sites / (kernel_ms * 1e-3) / 1e12
+    clk_site = {"fma": 2 * K * k * k / 128.0, "sfu": (4 * K + 2) / 16.0, "int_philox": (K + 1) / 4.0 * 80 / 64.0}
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
-            "peak_source": f"FP32 FMA from unit counts x sampled SM clock {mhz:.0f} MHz"}
+            "peak_source": f"FP32 FMA from unit counts x sampled SM clock {mhz:.0f} MHz",
+            "algorithmic_flops_per_site": 4 * K * k * k,
+            "pipe_clk_per_site_per_sm": clk_site,
+            "measured_clk_per_site_per_sm": round(kernel_ms * 1e-3 * mhz * 1e6 * 152 / n_sites, 3),
+            "executed_3pass": {"flops_per_site": 6 * K * k * k, "achieved": round(executed, 3),
+                               "frac": round(executed / peak, 4),
+                               "note": "direct-FP32-equivalent of the three convolutions the kernel computes"}}
 
 
-def cpu_baseline_run(spec, budget_s=15.0):
-    """Time the oracle on a bounded sample of the workload (one process, BLAS 1 thread)."""
+# FP32 instructions of one double-FP32 multiply-add (df_mul: two_prod 2, two
+# FMAs, fast_two_sum 3; df_add: two two_sums of 6, two adds, two
+# fast_two_sums of 3): the mixed Kitaev path emulates each FP64 multiply-add
+# of the reduction with them on the FP32 pipe
+DF64_FP32_OPS_PER_FMA = 27
+
+
+def kitaev_roofline(spec, ms, steps, prec, clocks):
+    """Eigen-stage roofline with the survey's algorithmic count, (8/3) N^3
+    flops per proposal ((4/3) N^3 multiply-adds: a Golub-Kahan
+    bidiagonalisation of M, values only).  FP64 path: against the FP64 FMA
+    peak the library's probe measures.  Mixed path: those multiply-adds run as
+    double-FP32 on the FP32 pipe, 27 FP32 instructions each, against the FP32
+    pipe's instruction rate from unit counts (152 SMs x 128 lanes) at the
+    sampled SM clock."""
+    fmas = sum(n * (4.0 / 3.0) * (L * L) ** 3 for L, n in spec["jobs"]) * spec["S"] * steps
+    if prec == 0:
+        pk, src = fp64_peak()
+        achieved = 2 * fmas / (ms * 1e-3) / 1e12
+        return {"bound": "fp64", "achieved": round(achieved, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / pk, 4), "traffic": None,
+                "peak_source": src + "; flops = (8/3) N^3 per proposal"}
+    mhz = _sm_mhz(clocks)
+    peak = 152 * 128 * mhz * 1e6 / 1e12                     # FP32 instructions per second, 1e12
+    achieved = fmas * DF64_FP32_OPS_PER_FMA / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFP32-inst/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": f"FP32 pipe from unit counts x SM clock {mhz:.0f} MHz; (4/3) N^3 FP64 multiply-adds "
+                           f"per proposal x {DF64_FP32_OPS_PER_FMA} FP32 instructions each (double-FP32)"}
+
+
+def _oracle_worker(args):
+    """One process of the all-core oracle timing: `chains` chains of side L
+    (chain ids from `base`) step for about budget_s seconds."""
+    name, L, base, chains, budget_s = args
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     from oracle import chain
-    try:
-        from threadpoolctl import threadpool_limits
-        lim = threadpool_limits(1)
-    except Exception:  # noqa: BLE001
-        lim = None
+    spec = workload(name)
     W, hb, vb = spec["model"]
-    props, t_total, samples = 0, 0.0, []
-    for L, n in spec["jobs"]:
-        nc = min(n, 64 if spec["kind"] == 0 else 32)
-        ch = chain.make_chains(spec["kind"], W, hb, vb, L, spec["T"](nc), spec["J"], SEED, np.arange(nc))
-        t0 = time.perf_counter()
-        s = 0
-        while time.perf_counter() - t0 < budget_s / len(spec["jobs"]):
-            chain.step(ch)
-            s += 1
-        dt = time.perf_counter() - t0
-        props += nc * s * L * L
-        t_total += dt
-        samples.append(f"L={L}: {nc} chains x {s} proposals in {dt:.1f}s")
-    if lim is not None:
-        lim.unregister() if hasattr(lim, "unregister") else None
-    # scale to the workload's mix: site-weighted rate -> proposals/s of the full mix
-    sites_per_prop = sum(n * L * L for L, n in spec["jobs"]) / sum(n for _, n in spec["jobs"])
-    rate = props / t_total / sites_per_prop
-    return {"value": rate, "unit": "proposals/s", "cores": 1, "kind": "oracle",
-            "sample": "; ".join(samples) + " (site-weighted to the workload's L mix)"}
+    ch = chain.make_chains(spec["kind"], W, hb, vb, L, spec["T"](base + chains)[base:], spec["J"], SEED,
+                           np.arange(base, base + chains))
+    t0 = time.perf_counter()
+    s = 0
+    while s == 0 or time.perf_counter() - t0 < budget_s:
+        chain.step(ch)
+        s += 1
+    return chains * s, time.perf_counter() - t0
+
+
+def cpu_baseline_run(spec, name, budget_s=15.0, cores=None):
+    """The oracle (numpy FP64, one BLAS thread per process) on a bounded sample
+    of the workload: for every lattice size of the mix, `cores` processes
+    (spawned: no fork of a process that holds a CUDA context) each step their
+    own chains for about budget_s / n_sizes seconds; the per-size rates give
+    the proposals/s of the workload's mix (its chains per L).  cores = 1 gives
+    the single-core figure."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    per = 64 if spec["kind"] == 0 else 32
+    sizes = spec["jobs"]
+    t_each = budget_s / len(sizes)
+    tasks = [(name, L, w * per, per, t_each) for L, _ in sizes for w in range(cores)]
+    if cores == 1:
+        res = [_oracle_worker(t) for t in tasks]
+    else:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, tasks, chunksize=1)
+    secs_per_mix, samples = 0.0, []
+    for i, (L, n) in enumerate(sizes):
+        part = res[i * cores:(i + 1) * cores]
+        props = sum(p for p, _ in part)
+        dt = max(t for _, t in part)
+        secs_per_mix += n / (props / dt)          # time for this size's share of one mix proposal round
+        samples.append(f"L={L}: {cores} x {per} chains, {props} proposals in {dt:.1f}s")
+    rate = sum(n for _, n in sizes) / secs_per_mix
+    return {"value": rate, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+            "sample": "; ".join(samples) + " (rates combined over the workload's chains per L)"}
+
+
+def bench_config(spec, args, world):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": spec["desc"], "proposals_per_step": spec["S"], "chains": sum(n for _, n in spec["jobs"]),
+            "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"chains x{world}"}
 
 
 def run_reference(args, spec):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline_run(spec, budget_s=max(5.0, 2.0 * args.steps))
+    cb = cpu_baseline_run(spec, args.workload, budget_s=max(8.0, 1.0 * args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "proposals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": spec["desc"], "parallelism": "chains"}, "cpu_baseline": cb,
+            "config": bench_config(spec, args, world), "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "proposals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -231,7 +298,7 @@ def time_jobs(ctx, jobs, S, prec, steps, warmup, stream, dev, flush, graph=False
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
-def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False):
+def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False, clocks=None):
     """Proposals/s of another workload or precision (no e2e, no clocks); graph:
     replay a captured CUDA graph of the batched run."""
     from paper_2008_05401_gb300 import MIXED
@@ -259,15 +326,7 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False):
            "ms_per_step": ms / steps, "proposals_per_step": spec["S"], "acceptance": acc,
            "fp64_recomputes": rec}
     if spec["kind"] == 1:
-        # eigen-stage roofline: (8/3) N^3 flops per proposal (Golub-Kahan
-        # bidiagonalisation of M, values only) against GB300's nominal FP64 peak
-        flops = sum(n * (8.0 / 3.0) * (L * L) ** 3 for L, n in spec["jobs"]) * spec["S"] * steps
-        achieved = flops / (ms * 1e-3) / 1e12
-        pk, src = fp64_peak()
-        out["roofline"] = {"bound": "fp64", "achieved": round(achieved, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
-                           "frac": round(achieved / pk, 4), "traffic": None,
-                           "peak_source": src + "; flops = (8/3) N^3 per proposal; the mixed path runs the "
-                                                "reduction on the FP32 pipe"}
+        out["roofline"] = kitaev_roofline(spec, ms, steps, prec, clocks)
     return out
 
 
@@ -326,7 +385,7 @@ def tempering_run(ctx_cls, name, prec, cycles, dev, stream, flush, oracle_s=3.0,
     if spec["kind"] == 0:
         # the RBM proposal (mode-2 kernel) dominates: the headline's conv-flop count per site
         K, k = W.shape[0], W.shape[1]
-        out["roofline"] = roofline(None, ms / cycles, clocks or {}, K, k, n * L * L)
+        out["roofline"] = roofline(ms / cycles, clocks or {}, K, k, n * L * L)
     if oracle_s > 0:
         from oracle import chain, tempering
         nc = 32
@@ -598,10 +657,16 @@ def main():
 
     K, k = W.shape[0], W.shape[1]
     sites = sum(n * L * L for L, n in spec["jobs"]) * S
-    # the dominant kernel alone: the L = 128 jobs (the tensor-core kernel in the
-    # mixed path) on this stream, CUDA events around each launch, after the
-    # timed region
-    dom = [(L, n, j) for (L, n), j in zip(spec["jobs"], jobs) if L == max(Lj for Lj, _ in spec["jobs"])]
+    # the dominant kernel alone, on this stream, CUDA events around each launch
+    # (after the timed region): in the mixed Ising path the persistent
+    # tensor-core kernel, one launch for the jobs of every side it serves; else
+    # the largest lattice's jobs on the table kernel
+    tc_L = (128, 64, 32, 16) if prec == MIXED and spec["kind"] == 0 and K <= 4 and k <= 5 else ()
+    dom = [(L, n, j) for (L, n), j in zip(spec["jobs"], jobs) if L in tc_L]
+    dom_name = "crbm_tc_kernel (persistent, every side in one launch)"
+    if not dom:
+        dom = [(L, n, j) for (L, n), j in zip(spec["jobs"], jobs) if L == max(Lj for Lj, _ in spec["jobs"])]
+        dom_name = "crbm_step_kernel"
     dom_jobs = [j for _, _, j in dom]
     dev_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
     ctx.run_batch(dom_jobs, S, precision=prec, stream=stream)
@@ -613,37 +678,35 @@ def main():
     torch.cuda.synchronize(dev)
     dom_ms = sum(a.elapsed_time(b) for a, b in dev_ev) / len(dev_ev)
     dom_sites = sum(n * L * L for L, n, _ in dom) * S
-    dom_name = ("crbm_tc_kernel" if prec == MIXED and spec["kind"] == 0 and dom[0][0] == 128 else "crbm_step_kernel")
-    # kernels per step: one launch (and its step-counter update) per kernel the
-    # batch uses: the tensor-core kernel per side L in {128, 64, 32, 16} (mixed Ising),
-    # the table kernel for the rest
-    tc_sides = {L for L, _ in spec["jobs"] if prec == MIXED and spec["kind"] == 0 and L in (128, 64, 32, 16)}
-    n_parts = len(tc_sides) + int(any(L not in tc_sides for L, _ in spec["jobs"]))
+    # kernels per step: a proposal kernel and its step-counter update per part
+    # of the batch (the tensor-core jobs form one part; table-kernel jobs one
+    # per CTA size)
+    n_parts = int(bool(tc_L and any(L in tc_L for L, _ in spec["jobs"]))) + \
+        len({L for L, _ in spec["jobs"] if L not in tc_L})
     line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == MIXED else "f64", "data": "synthetic",
-            "config": {"workload": spec["desc"], "proposals_per_step": S, "chains": n_chains,
-                       "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"chains x{world}"},
-            "roofline": roofline(spec, dom_ms, clocks, K, k, dom_sites,
+            "config": bench_config(spec, args, world),
+            "roofline": roofline(dom_ms, clocks, K, k, dom_sites,
                                  traffic=(BATCH_ISING_TC_TRAFFIC_BYTES if args.workload == "ising-batch" and
-                                          dom_name == "crbm_tc_kernel" and not args.chains and not args.Ls
+                                          dom_name.startswith("crbm_tc") and not args.chains and not args.Ls
                                           else None)),
             "e2e": e2e, "gpu_launches": args.steps * 2 * n_parts, "clocks": clocks}
-    line["roofline"]["kernel"] = (f"{dom_name}: the L = {dom[0][0]} jobs ({sum(n for _, n, _ in dom)} chains x {S} "
-                                  f"proposals) alone, {dom_ms:.3f} ms per launch")
-    step_rf = roofline(spec, total_ms / args.steps, clocks, K, k, sites)
+    line["roofline"]["kernel"] = (f"{dom_name}: L = {sorted({L for L, _, _ in dom}, reverse=True)} "
+                                  f"({sum(n for _, n, _ in dom)} chains x {S} proposals), {dom_ms:.3f} ms per launch")
+    step_rf = roofline(total_ms / args.steps, clocks, K, k, sites)
     line["roofline"]["whole_step"] = {"achieved": step_rf["achieved"], "frac": step_rf["frac"],
-                                      "note": "all lattice sizes of the step, both kernels"}
+                                      "note": "every lattice size and kernel of the timed step"}
     sums = [j.observables() for j in jobs]
-    line["config"]["acceptance"] = sum(int(a.sum()) for _, a, _ in sums) / max(1, n_chains * jobs[0].step)
     props_done = max(1, n_chains * jobs[0].step)
-    line["config"]["fp64_recomputes_per_proposal"] = {
-        "bernoulli": sum(int(r[:, 0].sum()) for _, _, r in sums) / props_done,
-        "mh": sum(int(r[:, 1].sum()) for _, _, r in sums) / props_done,
-        "mh_by_L": {str(L): int(r[:, 1].sum()) / max(1, len(r) * j.step)
-                    for (L, _), j, (_, _, r) in zip(spec["jobs"], jobs, sums)},
+    line["stats"] = {
+        "acceptance": sum(int(a.sum()) for _, a, _ in sums) / props_done,
+        "fp64_recomputes_per_proposal": {
+            "bernoulli": sum(int(r[:, 0].sum()) for _, _, r in sums) / props_done,
+            "mh": sum(int(r[:, 1].sum()) for _, _, r in sums) / props_done,
+            "mh_by_L": {str(L): int(r[:, 1].sum()) / max(1, len(r) * j.step)
+                        for (L, _), j, (_, _, r) in zip(spec["jobs"], jobs, sums)}},
         "acceptance_by_L": {str(L): int(a.sum()) / max(1, len(a) * j.step)
                             for (L, _), j, (_, a, _) in zip(spec["jobs"], jobs, sums)}}
     if rank == 0 and not args.no_secondary:
@@ -656,10 +719,10 @@ def main():
         line["secondary"] = [
             secondary(Context, "ising-batch", FP64, 2, dev, stream, flush),
             secondary(Context, "kitaev-small", FP64, 3, dev, stream, flush),
-            secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush),
+            secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush, clocks=clocks),
             secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
-            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush),
-            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush, graph=True),
+            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush, clocks=clocks),
+            secondary(Context, "kitaev-batch", MIXED, 2, dev, stream, flush, graph=True, clocks=clocks),
             tempering_run(Context, "ising-batch", MIXED, 20, dev, stream, flush, clocks=clocks,
                           oracle_s=0.0 if args.no_cpu_baseline else 3.0),
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
@@ -667,7 +730,7 @@ def main():
             # the paper's Kitaev protocol at L = 8: k = 4 Gibbs steps per correction (Table II)
             tempering_run(Context, "kitaev-small", MIXED, 4, dev, stream, flush,
                           oracle_s=0.0 if args.no_cpu_baseline else 2.0, g=4, L_n=(8, 1024))]
-        line["config"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
+        line["stats"]["mixed_vs_fp64_path"] = value / line["secondary"][0]["value"]
         line["serving"] = serving_run(dev)
         ob = 0.0 if args.no_cpu_baseline else 2.0
         line["train"] = train_run(Context, dev, stream, oracle_s=ob)
@@ -675,7 +738,10 @@ def main():
         line["tau"] = [tau_run(Context, 16, 1024, 2.269, 2000, dev, stream, oracle_s=ob),
                        tau_run(Context, 64, 512, 2.269, 2000, dev, stream, oracle_s=ob)]
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_run(spec)
+        line["cpu_baseline"] = cpu_baseline_run(spec, args.workload)
+        line["cpu_baseline"]["single_core"] = {
+            k_: v_ for k_, v_ in cpu_baseline_run(spec, args.workload, budget_s=8.0, cores=1).items()
+            if k_ in ("value", "cores", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -353,15 +353,42 @@ CRBM_API int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* b
  * Errors: CRBM_EINVAL. */
 CRBM_API int crbm_set_tensor_cores(crbm_ctx* ctx, int enable);
 
-/* Wait for the job's last enqueued work and check the device error flag.
- * Errors: CRBM_ECUDA, CRBM_ETIMEOUT (a device wait hit its iteration cap). */
+/* Wait for the job's last enqueued work and check the context's device error
+ * flag.  A raised flag is reported once and then cleared, so the context
+ * stays usable; the results of the launches that raised it are void.
+ * Errors: CRBM_ECUDA, CRBM_ETIMEOUT (a device-side wait ran out of cycles,
+ * see crbm_set_wait_limit). */
 CRBM_API int crbm_sync(crbm_ctx* ctx, int job_id);
+
+/* Cycle limit of every device-side wait in later launches (default 2^28 SM
+ * clock cycles, about 0.13 s at 2.07 GHz).  The tensor-core kernel's
+ * warp-specialised pipeline waits on shared-memory mbarriers; a wait that runs
+ * out raises the CTA's abort flag (its other waits then return at once),
+ * raises the context's error flag, and the CTA drains its issued MMAs,
+ * releases its tensor memory and ends, so a launch never stalls the device.
+ * No counterpart in the paper (failure handling of the GPU pipeline).
+ * Errors: CRBM_EINVAL (cycles outside [1000, 2^40]). */
+CRBM_API int crbm_set_wait_limit(crbm_ctx* ctx, int64_t cycles);
+
+/* Check of that bounded wait, enqueued on cuda_stream: one CTA of 32 threads
+ * waits for phase 0 of a shared-memory mbarrier with the tensor-core
+ * pipeline's wait routine, giving up after limit_cycles cycles.  arrive = 1:
+ * one thread arrives first and the wait succeeds at once; arrive = 0: nothing
+ * arrives, the wait runs out and raises the context's error flag, which the
+ * next crbm_sync (of any job of the context) reports as CRBM_ETIMEOUT.  No
+ * counterpart in the paper.  Errors: CRBM_EINVAL (limit_cycles outside
+ * [1000, 2^40], arrive not 0 or 1), CRBM_ECUDA. */
+CRBM_API int crbm_probe_wait(crbm_ctx* ctx, int64_t limit_cycles, int arrive, void* cuda_stream);
 
 /* Copy per-chain FP64 values of the current states to host arrays of
  * n_chains entries each (any may be NULL): log pi, CRBM free energy F
- * (Eq. 13; in CRBM_MIXED this is the FP32-path value, within the bound the
- * decisions used, unless a recompute made it exact), and E_phys (Ising E,
- * Kitaev e(eta)). */
+ * (Eq. 13) and E_phys (Ising E, Kitaev e(eta)), always the FP64 path's
+ * values.  After a CRBM_MIXED run the job holds F (and, for the Kitaev kind,
+ * log pi) only within the certified bounds its decisions used; the call then
+ * evaluates a copy of the job's lattices in FP64 (in a device buffer the
+ * context owns and grows to the job's size) and returns those values,
+ * leaving the job's own state unchanged.  Synchronises the job first.
+ * Errors: CRBM_EINVAL (bad job id), CRBM_ECUDA, CRBM_ETIMEOUT (see crbm_sync). */
 CRBM_API int crbm_read_energies(crbm_ctx* ctx, int job_id, double* logpi, double* F_crbm, double* E_phys);
 
 /* Copy observable sums (n_chains * CRBM_NOBS FP64, chain-major), accepted

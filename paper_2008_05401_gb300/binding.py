@@ -70,6 +70,8 @@ _SIGS = {
     "crbm_probe_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "crbm_tune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "crbm_sync": (C.c_int, [C.c_void_p, C.c_int]),
+    "crbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "crbm_probe_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
     "crbm_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int]),
     "crbm_read_energies": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -241,6 +243,14 @@ def crbm_tune(ctx, model_id, L, precision=FP64):
 
 def crbm_sync(ctx, job_id):
     _check(ctx, load().crbm_sync(ctx, job_id))
+
+
+def crbm_set_wait_limit(ctx, cycles):
+    _check(ctx, load().crbm_set_wait_limit(ctx, int(cycles)))
+
+
+def crbm_probe_wait(ctx, limit_cycles, arrive, stream=0):
+    _check(ctx, load().crbm_probe_wait(ctx, int(limit_cycles), int(arrive), C.c_void_p(stream)))
 
 
 def crbm_set_tensor_cores(ctx, enable):

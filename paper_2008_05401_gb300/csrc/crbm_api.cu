@@ -41,7 +41,7 @@ struct Model {
 };
 
 struct Layout {
-  size_t bits, T, F, Fb, Lb, lp, E, ot, os, acc, rec, step, eps, total;
+  size_t bits, T, F, Fb, Lb, lp, E, ot, os, acc, rec, step, sched, eps, total;
 };
 
 struct Job {
@@ -59,6 +59,10 @@ struct Job {
   // evaluation or a tempering cycle, false after proposals (mode 0)
   bool exact = false;
   bool fexact = false;       // F of every chain is an FP64 value (bound 0)
+  // log pi, F and E_phys of every chain are the FP64 path's values (after an
+  // FP64 evaluation or an FP64 run; false after a mixed run, whose F carries
+  // an FP32 bound and, for the Kitaev kind, whose log pi a double-FP32 one)
+  bool f64vals = false;
   // optional E_phys trace in caller-owned device memory (crbm_set_trace)
   double* trace = nullptr;
   uint64_t trace_base = 0;
@@ -86,6 +90,7 @@ Layout make_layout(int kind, int L, int n) {
   y.acc = take((size_t)n * 8);
   y.rec = take((size_t)n * 16);
   y.step = take(8);
+  y.sched = take(16);     // work-queue counter of the tensor-core kernel's launches led by this job
   y.eps = take(kind == kKitaev ? (size_t)n * L * L * 8 : 0);
   y.total = n > 0 ? off : 0;   // an empty job needs no device memory
   return y;
@@ -130,6 +135,7 @@ struct crbm_ctx {
     cudaGraphExec_t exec = nullptr;
     std::vector<int> jobs;
     uint64_t steps = 0;   // proposals per replay
+    int precision = 0;
   };
   std::vector<Graph> graphs;
   // chains per CTA chosen by crbm_tune for (kind, L, K, k)
@@ -137,6 +143,12 @@ struct crbm_ctx {
   // proposals of eligible jobs (crbm_step_tc.cu) run on the tensor-core form;
   // tc_ok: the device grants its shared memory
   bool use_tc = true, tc_ok = false;
+  int sms = 1;                          // SMs of the device: persistent grid size
+  long long wait_limit = 1ll << 28;     // cycles before a device-side wait gives up
+  // device buffer of crbm_read_energies' FP64 re-evaluation (a copy of one
+  // job's memory), grown on demand
+  unsigned char* scratch = nullptr;
+  size_t scratch_bytes = 0;
 };
 
 static int fail(crbm_ctx* c, int code, const char* fmt, ...) {
@@ -258,6 +270,7 @@ static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g
   p.correct = correct;
   p.mode = mode;
   p.err = ctx->d_err;
+  p.wait_limit = ctx->wait_limit;
   size_t smem = 0;
   int tiles = 0, kind = -1, K = 0, k = 0;
   bool generic = false;
@@ -304,10 +317,12 @@ static bool on_tc(const crbm_ctx* ctx, const Job& j, int prec, int mode) {
   return ctx->use_tc && ctx->tc_ok && mode == 0 && m.d_tc && !m.edge && tc_supported(j.kind, prec, j.L, m.K, m.k);
 }
 
-// One launch of the tensor-core kernel for the jobs of one lattice side L: a
-// CTA per 128 / L chains.
-static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int L, int S, int g, int correct,
-                           cudaStream_t st) {
+// One persistent launch of the tensor-core kernel for the given jobs (any of
+// the four sides): a tile of 128 / L chains per work item, the jobs ordered by
+// decreasing L so that the longest items go first; the work-queue counter is
+// the first job's.
+static int launch_tc_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int correct, cudaStream_t st) {
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ctx->jobs[a].L > ctx->jobs[b].L; });
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -316,6 +331,7 @@ static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int L, in
   p.correct = correct;
   p.mode = 0;
   p.err = ctx->d_err;
+  p.wait_limit = ctx->wait_limit;
   int tiles = 0;
   size_t smem = 0;
   for (size_t i = 0; i < ids.size(); ++i) {
@@ -323,32 +339,35 @@ static int launch_tc_group(crbm_ctx* ctx, const std::vector<int>& ids, int L, in
     const Model& m = ctx->models[j.model];
     p.tile_begin[i] = tiles;
     p.job[i] = make_jobdev(ctx, j);
-    const int ch = tc_chains_per_cta(L);
+    const int ch = tc_chains_per_cta(j.L);
     tiles += (j.n + ch - 1) / ch;
-    smem = std::max(smem, tc_smem_bytes(L, m.K, m.k));
+    smem = std::max(smem, tc_smem_bytes(j.L, m.K, m.k));
   }
   p.tile_begin[ids.size()] = tiles;
-  if (tiles == 0) return CRBM_OK;
-  CK(launch_tc(L, p, tiles, smem, st), "kernel launch");
+  p.total_items = tiles;
+  if (tiles == 0 || S == 0) return CRBM_OK;
+  const Job& lead = ctx->jobs[ids[0]];
+  p.queue = (int*)(lead.mem + lead.lay.sched);
+  CK(launch_tc(p, std::min(tiles, ctx->sms), smem, st), "kernel launch");
   return CRBM_OK;
 }
 
 static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec, int mode,
                        cudaStream_t st, const Job* partner = nullptr) {
-  // parts: (CTA size, jobs); CTA size -L = the tensor-core form for side L
+  // parts: (CTA size, jobs); CTA size -1 = the tensor-core form (one persistent launch for every side)
   std::vector<std::pair<int, std::vector<int>>> parts;
-  for (int nt : {-128, -64, -32, -16, 256, 128, 64, 32}) {
+  for (int nt : {-1, 256, 128, 64, 32}) {
     std::vector<int> part;
     for (int id : ids) {
       const Job& j = ctx->jobs[id];
       if (j.n == 0) continue;
       const bool tc = !partner && on_tc(ctx, j, prec, mode);
-      if (nt < 0 ? (tc && j.L == -nt) : (!tc && threads_for(j.kind, j.N) == nt)) part.push_back(id);
+      if (nt < 0 ? tc : (!tc && threads_for(j.kind, j.N) == nt)) part.push_back(id);
     }
     if (!part.empty()) parts.emplace_back(nt, part);
   }
   auto launch_part = [&](const std::pair<int, std::vector<int>>& pt, cudaStream_t s) {
-    return pt.first < 0 ? launch_tc_group(ctx, pt.second, -pt.first, S, g, correct, s)
+    return pt.first < 0 ? launch_tc_group(ctx, pt.second, S, g, correct, s)
                         : launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, s, partner);
   };
   if (parts.size() <= 1) {
@@ -394,6 +413,8 @@ int crbm_create(crbm_ctx** out, int device, size_t hbm_budget_bytes) {
   if (e == cudaSuccess) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->sms < 1) ctx->sms = 1;
     e = set_smem_limits((size_t)optin);
     if (e == cudaSuccess && (size_t)optin >= tc_smem_bytes(128, 4, 5)) {
       e = tc_set_smem_limit();
@@ -420,6 +441,7 @@ int crbm_destroy(crbm_ctx* ctx) {
     if (m.d_tc) cudaFree(m.d_tc);
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->scratch) cudaFree(ctx->scratch);
   for (auto& gr : ctx->graphs) {
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (gr.graph) cudaGraphDestroy(gr.graph);
@@ -756,6 +778,7 @@ static int evaluate(crbm_ctx* ctx, int id, int prec = kFP64) {
   CK(cudaStreamSynchronize(ctx->own), "evaluate");
   ctx->jobs[id].exact = true;
   ctx->jobs[id].fexact = (prec == kFP64);
+  ctx->jobs[id].f64vals = (prec == kFP64);
   return CRBM_OK;
 }
 
@@ -827,6 +850,7 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
     CK(cudaMemsetAsync(b + lay.acc, 0, (size_t)n_chains * 8, o), "zero accepts");
     CK(cudaMemsetAsync(b + lay.rec, 0, (size_t)n_chains * 16, o), "zero recomputes");
     CK(cudaMemsetAsync(b + lay.step, 0, 8, o), "zero step");
+    CK(cudaMemsetAsync(b + lay.sched, 0, 16, o), "zero work queue");
   }
   ctx->jobs.push_back(j);
   const int id = (int)ctx->jobs.size() - 1;
@@ -898,7 +922,10 @@ int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int
   for (int id : ids) {
     ctx->jobs[id].step += (uint64_t)S;
     ctx->jobs[id].stream = st;
-    if (S > 0) ctx->jobs[id].exact = ctx->jobs[id].fexact = false;
+    if (S > 0) {
+      ctx->jobs[id].exact = false;
+      ctx->jobs[id].fexact = ctx->jobs[id].f64vals = (precision == kFP64);
+    }
   }
   return CRBM_OK;
 }
@@ -937,6 +964,7 @@ int crbm_graph_create(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, 
   gr.exec = exec;
   gr.jobs = ids;
   gr.steps = (uint64_t)S * (uint64_t)repeats;
+  gr.precision = precision;
   ctx->graphs.push_back(gr);
   *graph_id = (int)ctx->graphs.size() - 1;
   return CRBM_OK;
@@ -955,7 +983,10 @@ int crbm_graph_launch(crbm_ctx* ctx, int graph_id, void* cuda_stream) {
   for (int id : gr.jobs) {
     ctx->jobs[id].step += gr.steps;
     ctx->jobs[id].stream = st;
-    if (gr.steps > 0) ctx->jobs[id].exact = ctx->jobs[id].fexact = false;
+    if (gr.steps > 0) {
+      ctx->jobs[id].exact = false;
+      ctx->jobs[id].fexact = ctx->jobs[id].f64vals = (gr.precision == kFP64);
+    }
   }
   return CRBM_OK;
 }
@@ -1010,6 +1041,7 @@ int crbm_pt_run(crbm_ctx* ctx, int phys_job, int rbm_job, int64_t cycles, int g,
     j->stream = st;
     j->exact = true;
     j->fexact = j->fexact && precision == kFP64;
+    j->f64vals = j->fexact;
   }
   return CRBM_OK;
 }
@@ -1052,6 +1084,7 @@ int crbm_local_run(crbm_ctx* ctx, int job_id, int64_t sweeps, int exchange, int 
   j->stream = st;
   j->exact = (prec == kFP64);
   j->fexact = true;       // each launch ends with the FP64 free energy
+  j->f64vals = j->exact || j->kind == kIsing;
   return CRBM_OK;
 }
 
@@ -1144,6 +1177,24 @@ int crbm_probe_peaks(crbm_ctx* ctx, double* fp32_tflops, double* fp64_tflops) {
   if (!fp32_tflops || !fp64_tflops) return fail(ctx, CRBM_EINVAL, "null pointer");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   CK(probe_fma_peaks(ctx->device, fp32_tflops, fp64_tflops, ctx->own), "peak probe");
+  return CRBM_OK;
+}
+
+int crbm_set_wait_limit(crbm_ctx* ctx, int64_t cycles) {
+  if (!ctx) return CRBM_EINVAL;
+  if (cycles < 1000 || cycles > (1ll << 40)) return fail(ctx, CRBM_EINVAL, "wait limit %lld outside [1000, 2^40]",
+                                                         (long long)cycles);
+  ctx->wait_limit = (long long)cycles;
+  return CRBM_OK;
+}
+
+int crbm_probe_wait(crbm_ctx* ctx, int64_t limit_cycles, int arrive, void* cuda_stream) {
+  if (!ctx) return CRBM_EINVAL;
+  if (limit_cycles < 1000 || limit_cycles > (1ll << 40))
+    return fail(ctx, CRBM_EINVAL, "limit %lld outside [1000, 2^40]", (long long)limit_cycles);
+  if (arrive != 0 && arrive != 1) return fail(ctx, CRBM_EINVAL, "arrive must be 0 or 1");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(launch_wait_probe((long long)limit_cycles, arrive, ctx->d_err, (cudaStream_t)cuda_stream), "probe launch");
   return CRBM_OK;
 }
 
@@ -1246,9 +1297,12 @@ int crbm_sync(crbm_ctx* ctx, int job_id) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->own), "read error flag");
   CK(cudaStreamSynchronize(ctx->own), "read error flag");
-  if (h == kErrTimeout) return fail(ctx, CRBM_ETIMEOUT, "a device-side wait reached its iteration limit");
-  if (h != 0) return fail(ctx, CRBM_EINVAL, "device reported configuration error %d", h);
-  return CRBM_OK;
+  if (h == 0) return CRBM_OK;
+  // reported once: the flag is cleared so that the context stays usable
+  CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->own), "clear error flag");
+  CK(cudaStreamSynchronize(ctx->own), "clear error flag");
+  if (h == kErrTimeout) return fail(ctx, CRBM_ETIMEOUT, "a device-side wait reached its cycle limit");
+  return fail(ctx, CRBM_EINVAL, "device reported configuration error %d", h);
 }
 
 static int read_back(crbm_ctx* ctx, Job* j, void* dst, size_t off, size_t bytes) {
@@ -1264,6 +1318,36 @@ int crbm_read_energies(crbm_ctx* ctx, int job_id, double* logpi, double* F_crbm,
   int rc = crbm_sync(ctx, job_id);
   if (rc) return rc;
   const size_t b = (size_t)j->n * 8;
+  if (!j->f64vals && j->n > 0 && (logpi || F_crbm || E_phys)) {
+    // the stored values of a mixed run are within their certified bounds of
+    // the FP64 ones (the decisions are the FP64 path's either way); the values
+    // returned here are the FP64 path's: a copy of the job's memory is
+    // evaluated in FP64 (Eq. 13 for F), the job itself is left as it is
+    const Job jc = *j;
+    if (ctx->scratch_bytes < jc.bytes) {
+      if (ctx->scratch) CK(cudaFree(ctx->scratch), "cudaFree");
+      ctx->scratch = nullptr;
+      ctx->scratch_bytes = 0;
+      CK(cudaMalloc(&ctx->scratch, jc.bytes), "cudaMalloc (FP64 read-back copy)");
+      ctx->scratch_bytes = jc.bytes;
+    }
+    CK(cudaMemcpyAsync(ctx->scratch, jc.mem, jc.bytes, cudaMemcpyDeviceToDevice, ctx->own), "copy job memory");
+    Job tmp = jc;
+    tmp.mem = ctx->scratch;
+    tmp.stream = ctx->own;
+    tmp.trace = nullptr;
+    tmp.trace_cap = 0;
+    ctx->jobs.push_back(tmp);
+    const int tid = (int)ctx->jobs.size() - 1;
+    rc = launch_jobs(ctx, {tid}, 0, 1, 1, kFP64, 1, ctx->own);
+    ctx->jobs.pop_back();       // the launch holds its own copy of the job's pointers
+    if (rc) return rc;
+    for (auto [dst, off] : {std::make_pair(logpi, jc.lay.lp), std::make_pair(F_crbm, jc.lay.F),
+                            std::make_pair(E_phys, jc.lay.E)})
+      if (dst) CK(cudaMemcpyAsync(dst, ctx->scratch + off, b, cudaMemcpyDeviceToHost, ctx->own), "device to host copy");
+    CK(cudaStreamSynchronize(ctx->own), "FP64 re-evaluation");
+    return CRBM_OK;
+  }
   if ((rc = read_back(ctx, j, logpi, j->lay.lp, b))) return rc;
   if ((rc = read_back(ctx, j, F_crbm, j->lay.F, b))) return rc;
   return read_back(ctx, j, E_phys, j->lay.E, b);

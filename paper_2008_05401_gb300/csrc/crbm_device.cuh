@@ -109,6 +109,12 @@ struct LaunchParams {
   int n_jobs, S, g, correct, mode;
   int tile_begin[kMaxJobs + 1];
   int* err;
+  // tensor-core kernel (persistent CTAs): work items 0 .. total_items - 1
+  // handed out by the counter *queue (zero at launch, cleared after it);
+  // every device-side wait gives up after wait_limit SM clock cycles
+  int* queue;
+  int total_items;
+  long long wait_limit;
   JobDev job[kMaxJobs];
 };
 

@@ -25,13 +25,18 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Tensor-core form of the proposal kernel (crbm_step_tc.cu): Ising kind, mixed
-// precision, L = 128 (one chain per CTA), 64 (two), 32 (four) or 16 (eight),
-// K <= 4, k <= 5.
+// precision, L = 128 (one chain per CTA tile), 64 (two), 32 (four) or 16
+// (eight), K <= 4, k <= 5.  One persistent launch serves jobs of every side:
+// grid CTAs take the p.total_items tiles from the counter p.queue (zero at
+// launch; cleared again after it).
 bool tc_supported(int kind, int prec, int L, int K, int k);
 int tc_chains_per_cta(int L);
 size_t tc_smem_bytes(int L, int K, int k);
-cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t tc_set_smem_limit();
+// One CTA waiting on an mbarrier with the tensor-core pipeline's bounded wait
+// (arrive = 0: nothing arrives; after `limit` cycles *err = timeout).
+cudaError_t launch_wait_probe(long long limit, int arrive, int* err, cudaStream_t st);
 // Random initial lattices (init tag of the stream).
 cudaError_t launch_random_init(uint32_t* bits, int n_chains, int N, int Wd, uint64_t seed,
                                uint64_t cid_base, cudaStream_t st);

@@ -76,8 +76,8 @@ struct Geo {
   static constexpr int OPV = GROUPS * LBO;
   static constexpr int WPR = LT / 32, WPC = LT * LT / 32;   // words per row / per chain
   static constexpr int NHV = NT + NV;                // H and V stages per Gibbs step
-  // misc area: mbarriers and the TMEM address (0 .. 211), per-chain redo
-  // counters at 224, then per (warp, chain) F partials and per-part counts
+  // misc area: per-chain redo counters at 224 (bytes 0 .. 223 unused), then
+  // per (warp, chain) F partials and per-part counts
   static constexpr int REDF = CH <= 4 ? 256 : 288, REDC = REDF + 256 * CH;
   static constexpr int MISC = CH <= 2 ? 1024 : (CH == 4 ? 1536 : 2560);
   static constexpr int SPAN = WPC < 32 ? WPC : 32;   // count-pass lanes per part (one chain's)
@@ -162,16 +162,26 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// Wait for the given phase parity of an mbarrier, for at most about a second
-// of SM clock; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Wait for the given phase parity of an mbarrier for at most `limit` SM clock
+// cycles.  On running out the wait raises the CTA's abort flag (if given) and
+// the launch's error flag and returns false; once the abort flag is up every
+// wait of the CTA returns false at once, so that the CTA runs to its end
+// instead of stalling wait after wait (its results are void and the host
+// reports CRBM_ETIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit, volatile int* abort,
+                                          int* err) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (abort != nullptr && *abort != 0) return false;
+    if (clock64() - t0 > limit) {
+      if (abort != nullptr) *abort = 1;
+      if (err != nullptr) atomicExch(err, kErrTimeout);
+      return false;
+    }
   }
 }
 
@@ -383,8 +393,8 @@ template <int LT>
 __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* smem, const float (&s2)[4],
                                             const float (&s1)[4], const float (&s0)[4], int m, int i, int cq,
                                             int u, const uint4& w, uint32_t* dbc, uint32_t opv,
-                                            const uint32_t* hbc, uint32_t hbar, uint32_t parity, int* err,
-                                            unsigned& nrec) {
+                                            const uint32_t* hbc, uint32_t hbar, uint32_t parity, long long limit,
+                                            volatile int* abort, int* err, unsigned& nrec) {
   using G = Geo<LT>;
   const int j0 = 16 * u + 4 * cq, n0 = i * LT + j0;
   uint32_t nib = 0u, amb = 0u;
@@ -400,8 +410,7 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
     // the packed hidden units of H tiles 2u-1, 2u, 2u+1 come from other warps:
     // their hrdy mbarriers (completed before this tile's MMAs) order them
     const int tt[3] = {(2 * u + G::NT - 1) % G::NT, 2 * u, 2 * u + 1};
-    for (int q = 0; q < 3; ++q)
-      if (!mbar_wait(hbar + 8u * (uint32_t)tt[q], parity)) atomicExch(err, kErrTimeout);
+    for (int q = 0; q < 3; ++q) mbar_wait(hbar + 8u * (uint32_t)tt[q], parity, limit, abort, err);
     for (int t = 0; t < 4; ++t)
       if ((amb >> t) & 1u) {
         const uint32_t bit = recompute_visible(jb, hbc, G::WPC, n0 + t, pick(w, t));
@@ -534,55 +543,96 @@ static __device__ __noinline__ void mh_redo(const JobDev& jb, ChainSm* chs, doub
   }
 }
 
-// mbarriers in the misc area: full[4] (count 2, MMA commits), empty[4] (count
-// 16, epilogue warps), hrdy[16] (count 16: H tile's fp16 units written),
-// vrdy (count 16: every V tile's v' written), fin (count 2, last commits);
-// then the TMEM address, per-chain Bernoulli redo counts, and the reduction
-// slots: per (warp, chain) the F partial (int64) and its bound (FP32), per
-// warp the lattice counts of the chain its count-pass words belong to.
-constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kNbar = 26;
-constexpr int kMiscTslot = 8 * kNbar, kMiscNrec = 224;
+// mbarriers, in a static shared array (the dynamic layout depends on the
+// lattice side of the work item, the barriers' place must not): full[4]
+// (count 2, MMA commits), empty[4] (count 16, epilogue warps), hrdy[16]
+// (count 16: H tile's fp16 units written), vrdy (count 16: every V tile's v'
+// written), fin (count 2, last commits), ld (count 1 plus the byte count of
+// the bulk copy of the packed lattices).  Misc area: per-chain Bernoulli redo
+// counts at kMiscNrec, then the reduction slots: per (warp, chain) the F
+// partial (int64) and its bound (FP32), per warp the lattice counts of the
+// chain its count-pass words belong to.
+constexpr int kBarFull = 0, kBarEmpty = 4, kBarH = 8, kBarV = 24, kBarFin = 25, kBarLd = 26, kNbar = 27;
+constexpr int kMiscNrec = 224;
 
+// Bulk copies between global and shared memory (the TMA unit's untiled form):
+// both addresses 16-byte aligned, the size a multiple of 16 bytes.  The load
+// completes on an mbarrier that expects its byte count; the store is waited
+// for in full (the writes done) before the issuing thread goes on.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" :: "r"(mbar),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" :: "l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
+// One work item of the persistent kernel below: S proposals of the chains
+// c0 .. c0 + CH - 1 of job jb (one CTA tile; the last tile of a job may hold
+// fewer), the whole pipeline in this CTA's shared memory and in its tensor
+// memory at column tmem; bar0: shared address of the CTA's mbarriers (set
+// up here, invalidated at the end).  abort: the CTA's abort flag (up once a
+// wait has run out; the launch's results are then void).
 template <int LT, int KT, int kT>
-__global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
+__device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& jb, int c0, unsigned char* smem,
+                                        uint32_t bar0, uint32_t tmem, volatile int* abort) {
   using G = Geo<LT>;
   constexpr int CH = G::CH, WPC = G::WPC;
-  int jid = 0;
-  while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
-  const JobDev& jb = prm.job[jid];
-  const int c0 = ((int)blockIdx.x - prm.tile_begin[jid]) * CH;   // the CTA's first chain
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = warp < 16;
   const int K = jb.K, k = jb.k;
   const TcLayout ly = tc_layout<LT>(K, k);
-  extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t sbase = sm_addr(smem);
   uint32_t* vbits = (uint32_t*)(smem + ly.vbits);
   ChainSm* chs = (ChainSm*)(smem + ly.ch);
   double* scratch = (double*)(smem + ly.scratch);
-  const uint32_t bar0 = sbase + ly.misc;
   auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
-  uint32_t* tslot = (uint32_t*)(smem + ly.misc + kMiscTslot);
   unsigned long long* nrec_sm = (unsigned long long*)(smem + ly.misc + kMiscNrec);
   unsigned char* redf = smem + ly.misc + G::REDF;
   uint32_t* redc = (uint32_t*)(smem + ly.misc + G::REDC);
   auto ch_of = [&](int c) -> ChainSm& { return chs[c]; };
+  const int nval = jb.n_chains - c0 < CH ? jb.n_chains - c0 : CH;   // chains of this tile
+  const uint32_t vbytes = (uint32_t)(nval * WPC * 4);               // their packed lattices
 
+  if (tid == 0) {
+    for (int b = 0; b < kNbuf; ++b) {
+      mbar_init(bar(kBarFull + b), 2);
+      mbar_init(bar(kBarEmpty + b), 16);
+    }
+    for (int t = 0; t < 16; ++t) mbar_init(bar(kBarH + t), 16);
+    mbar_init(bar(kBarV), 16);
+    mbar_init(bar(kBarFin), 2);
+    mbar_init(bar(kBarLd), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // the tile's packed lattices (chain-major, contiguous in the job) by one
+    // bulk copy: offsets and sizes are multiples of 32 bytes
+    mbar_expect_tx(bar(kBarLd), vbytes);
+    bulk_load(sbase + ly.vbits, jb.bits + (size_t)c0 * WPC, vbytes, bar(kBarLd));
+  }
   const int nimg = (k * kBhA + k * v_ksteps(K) * kBvStep) / 16;   // B images: hidden/free, then visible
   for (int q = tid; q < nimg; q += kThr) ((uint4*)(smem + ly.bh))[q] = __ldg(jb.tcw + q);
   // V buffers zeroed: the groups of filters f >= K are read (with zero weights)
   // by the last K-step when 3K is odd, and must hold finite values
   for (int q = tid; q < 2 * G::VBUF / 16; q += kThr) ((uint4*)(smem + ly.vbuf))[q] = make_uint4(0u, 0u, 0u, 0u);
   for (int w = tid; w < CH * WPC; w += kThr) {
-    const int c = c0 + w / WPC;
-    vbits[w] = c < jb.n_chains ? jb.bits[(size_t)c * WPC + (w % WPC)] : 0u;
+    if (w >= nval * WPC) vbits[w] = 0u;       // empty chain slots of a short last tile
     ((uint32_t*)(smem + ly.pb[0]))[w] = 0u;
     ((uint32_t*)(smem + ly.pb[1]))[w] = 0u;
   }
   if (tid < CH) {
     ChainSm& ch = ch_of(tid);
     const int c = c0 + tid;
-    const bool on = c < jb.n_chains;
+    const bool on = tid < nval;
     ch.F = on ? jb.F[c] : 0.0;
     ch.Fb = on ? jb.Fb[c] : 0.0;
     ch.lpb = on ? jb.Lb[c] : 0.0;
@@ -600,25 +650,11 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     ch.flag_acc = 0;
     nrec_sm[tid] = 0ull;
   }
-  if (tid == 0) {
-    for (int b = 0; b < kNbuf; ++b) {
-      mbar_init(bar(kBarFull + b), 2);
-      mbar_init(bar(kBarEmpty + b), 16);
-    }
-    for (int t = 0; t < 16; ++t) mbar_init(bar(kBarH + t), 16);
-    mbar_init(bar(kBarV), 16);
-    mbar_init(bar(kBarFin), 2);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  if (warp == 16) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(sm_addr(tslot)),
-                 "r"(kTmCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
+  // the bulk copy is waited for whatever the abort flag says: it completes by itself
+  mbar_wait(bar(kBarLd), 0u, prm.wait_limit, nullptr, prm.err);
   __syncthreads();
   expand_lattice<LT>(smem, ly.opv[0], vbits, tid, kThr);
   cta_sync();
-  const uint32_t tmem = *tslot;
 
   // epilogue thread: operand row m = lattice row i of chain cm; filter /
   // column quarter fq; its TMEM lanes
@@ -635,15 +671,9 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
                  dbv = umma_desc_lo(sbase + ly.bv, 0);     // LBO set per image
   uint32_t zc = 0;              // stages so far: buffer zc % 4, its (zc / 4)-th use
   uint32_t gs = 0;              // Gibbs steps so far: phase of hrdy / vrdy
-  bool live = true;             // false once a wait gave up: no further waits
   unsigned nrec = 0;
   const unsigned long long step0 = *(volatile unsigned long long*)jb.step;
-  auto wait_bar = [&](uint32_t b, uint32_t parity) {
-    if (live && !mbar_wait(b, parity)) {
-      live = false;
-      atomicExch(prm.err, kErrTimeout);
-    }
-  };
+  auto wait_bar = [&](uint32_t b, uint32_t parity) { mbar_wait(b, parity, prm.wait_limit, abort, prm.err); };
   // issuing warp: before the MMAs of stage zc, its buffer's previous use read by every epilogue warp
   auto mma_claim = [&]() {
     const uint32_t b = zc & (kNbuf - 1), use = zc / kNbuf;
@@ -787,7 +817,8 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
             }
             epi_release();
             epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
-                            (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.err, nrec);
+                            (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.wait_limit, abort,
+                            prm.err, nrec);
             if (tl == G::NV - 1) epi_publish(bar(kBarV));
           }
         }
@@ -966,17 +997,16 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   }
 
   if (nrec) atomicAdd(nrec_sm + cm, (unsigned long long)nrec);
-  // every MMA issued has completed before tensor memory is released
+  // every MMA of the item has completed before the next item (or the end of
+  // the kernel) reuses shared and tensor memory: the issuers' last commit,
+  // waited for whatever the abort flag says (issued MMAs always finish)
   if (issuer) {
     umma_commit(bar(kBarFin));
-    wait_bar(bar(kBarFin), 0u);
+    mbar_wait(bar(kBarFin), 0u, prm.wait_limit, nullptr, prm.err);
   }
-  cta_sync();
-  for (int w = tid; w < CH * WPC; w += kThr) {
-    const int c = c0 + w / WPC;
-    if (c < jb.n_chains) jb.bits[(size_t)c * WPC + (w % WPC)] = vbits[w];
-  }
-  if (tid < CH && c0 + tid < jb.n_chains) {
+  cta_sync();      // with the proxy fence: the packed lattices visible to the bulk copy
+  if (tid == 0) bulk_store(jb.bits + (size_t)c0 * WPC, sbase + ly.vbits, vbytes);
+  if (tid < nval) {
     const ChainSm& ch = ch_of(tid);
     const int c = c0 + tid;
     jb.F[c] = ch.F;
@@ -992,20 +1022,86 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     jb.rec[2 * (size_t)c] += nrec_sm[tid];
     jb.rec[2 * (size_t)c + 1] += ch.rec_mh;
   }
+  if (tid == 0)        // no wait or arrival is pending: the next item initialises them afresh
+    for (int b = 0; b < kNbar; ++b) asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" :: "r"(bar(b)) : "memory");
+  __syncthreads();   // the store has completed (thread 0 waited) before the next item's loads
+}
+
+// The persistent tensor-core kernel: one CTA per SM takes work items, the CTA
+// tiles of the launch's jobs (items tile_begin[i] .. tile_begin[i+1] - 1 of
+// job i, the jobs ordered by decreasing lattice side), from the launch's
+// queue counter until none is left.  Lattices of every side share one launch,
+// and a tile that takes longer (an MH recompute) delays only its own CTA's
+// next pick instead of the end of a wave.  Tensor memory is allocated once
+// per CTA; after an abort the CTA takes no further item.
+template <int KT, int kT>
+__global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long s_bar[kNbar];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_item, s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) s_abort = 0;
+  if (warp == 16) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(sm_addr(&s_tmem)),
+                 "r"(kTmCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem, bar0 = sm_addr(s_bar);
+  volatile int* abort = &s_abort;
+  while (true) {
+    if (tid == 0) s_item = *abort ? prm.total_items : atomicAdd(prm.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= prm.total_items) break;
+    int jid = 0;
+    while (jid + 1 < prm.n_jobs && item >= prm.tile_begin[jid + 1]) ++jid;
+    const JobDev& jb = prm.job[jid];
+    const int t = item - prm.tile_begin[jid];
+    if (jb.L == 128) tc_tile<128, KT, kT>(prm, jb, t, smem, bar0, tmem, abort);
+    else if (jb.L == 64) tc_tile<64, KT, kT>(prm, jb, 2 * t, smem, bar0, tmem, abort);
+    else if (jb.L == 32) tc_tile<32, KT, kT>(prm, jb, 4 * t, smem, bar0, tmem, abort);
+    else tc_tile<16, KT, kT>(prm, jb, 8 * t, smem, bar0, tmem, abort);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
   if (warp == 16)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmCols));
 }
 
-template <int LT, int KT, int kT>
-cudaError_t tc_launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  crbm_tc_kernel<LT, KT, kT><<<grid, kThr, smem, st>>>(p);
-  return cudaGetLastError();
+// After a launch, in stream order (and in captured graphs): every job's step
+// counter advances by S, and the queue counter is cleared for the next launch.
+__global__ void tc_advance_kernel(const __grid_constant__ LaunchParams p) {
+  const int i = threadIdx.x;
+  if (i < p.n_jobs) *p.job[i].step += (unsigned long long)p.S;
+  if (i == 0) *p.queue = 0;
 }
 
-template <int LT, int KT, int kT>
-cudaError_t tc_limit_inst() {
-  return cudaFuncSetAttribute(crbm_tc_kernel<LT, KT, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_layout<LT>(4, 5).total);
+// A bounded wait that runs out: one CTA waits for phase 0 of an mbarrier with
+// the routine of the tensor-core pipeline (arrive = 1: after one arrival, so
+// the wait succeeds at once; arrive = 0: nothing arrives, the wait gives up
+// after `limit` cycles and raises the error flag).
+__global__ void wait_probe_kernel(long long limit, int arrive, int* err) {
+  __shared__ __align__(8) unsigned long long mb;
+  __shared__ int ab;
+  const uint32_t b = sm_addr(&mb);
+  if (threadIdx.x == 0) {
+    ab = 0;
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(b);
+  mbar_wait(b, 0u, limit, &ab, err);
+}
+
+template <int KT, int kT>
+cudaError_t tc_limit_inst(size_t bytes) {
+  return cudaFuncSetAttribute(crbm_tc_kernel<KT, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -1024,31 +1120,31 @@ bool tc_supported(int kind, int prec, int L, int K, int k) {
          k >= 1 && k <= 5;
 }
 
-// One launch per lattice side and filter shape (the jobs of p share both).
-cudaError_t launch_tc(int L, const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+// One persistent launch for the jobs of p (one filter shape; any of the four
+// sides), then the step counters and the queue counter.
+cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (p.S <= 0 || p.total_items <= 0) return cudaSuccess;
   const bool k45 = p.job[0].K == 4 && p.job[0].k == 5;
-  cudaError_t e =
-      L == 128 ? (k45 ? tc_launch_inst<128, 4, 5>(p, grid, smem, st) : tc_launch_inst<128, 0, 0>(p, grid, smem, st))
-      : L == 64 ? (k45 ? tc_launch_inst<64, 4, 5>(p, grid, smem, st) : tc_launch_inst<64, 0, 0>(p, grid, smem, st))
-      : L == 32 ? (k45 ? tc_launch_inst<32, 4, 5>(p, grid, smem, st) : tc_launch_inst<32, 0, 0>(p, grid, smem, st))
-                : (k45 ? tc_launch_inst<16, 4, 5>(p, grid, smem, st) : tc_launch_inst<16, 0, 0>(p, grid, smem, st));
-  if (e == cudaSuccess && p.S > 0) {
-    advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
+  if (k45) crbm_tc_kernel<4, 5><<<grid, kThr, smem, st>>>(p);
+  else crbm_tc_kernel<0, 0><<<grid, kThr, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    tc_advance_kernel<<<1, kMaxJobs, 0, st>>>(p);
     e = cudaGetLastError();
   }
   return e;
 }
 
 cudaError_t tc_set_smem_limit() {
-  cudaError_t e = tc_limit_inst<128, 4, 5>();
-  if (e == cudaSuccess) e = tc_limit_inst<128, 0, 0>();
-  if (e == cudaSuccess) e = tc_limit_inst<64, 4, 5>();
-  if (e == cudaSuccess) e = tc_limit_inst<64, 0, 0>();
-  if (e == cudaSuccess) e = tc_limit_inst<32, 4, 5>();
-  if (e == cudaSuccess) e = tc_limit_inst<32, 0, 0>();
-  if (e == cudaSuccess) e = tc_limit_inst<16, 4, 5>();
-  if (e == cudaSuccess) e = tc_limit_inst<16, 0, 0>();
+  const size_t b = tc_layout<128>(4, 5).total;
+  cudaError_t e = tc_limit_inst<4, 5>(b);
+  if (e == cudaSuccess) e = tc_limit_inst<0, 0>(b);
   return e;
+}
+
+cudaError_t launch_wait_probe(long long limit, int arrive, int* err, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit, arrive, err);
+  return cudaGetLastError();
 }
 
 }  // namespace crbm

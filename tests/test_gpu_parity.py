@@ -81,8 +81,11 @@ def test_ising_matches_oracle(ctx, L, K, k, n, g, correct, std):
     np.testing.assert_array_equal(bm, bits64)
     _, accm, recm = jm.observables()
     np.testing.assert_array_equal(accm, acc64)
-    _, Fm, _ = jm.energies()
-    np.testing.assert_allclose(Fm, F64, rtol=1e-5, atol=1e-5)
+    # read back in FP64 (crbm_read_energies re-evaluates a mixed job's lattices)
+    lpm, Fm, Em = jm.energies()
+    np.testing.assert_allclose(Fm, ref.F, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(lpm, ref.logpi, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(Em, ref.E_phys, rtol=1e-10, atol=1e-10)
     job.release()
     jm.release()
 
@@ -117,6 +120,9 @@ def test_kitaev_matches_oracle(ctx, L, K, k, n, correct):
     jm.run(S, correct=correct, precision=MIXED)
     bm, _ = jm.state()
     np.testing.assert_array_equal(bm, bits64)
+    lpm, Fm, _ = jm.energies()
+    np.testing.assert_allclose(Fm, ref.F, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(lpm, ref.logpi, rtol=1e-10, atol=1e-9)
     job.release()
     jm.release()
 

@@ -36,6 +36,33 @@ def test_noalloc_equals_allocating_entry_twice():
         ctx.close()
 
 
+def test_noalloc_at_the_largest_size_allocates_nothing():
+    """At CRBM_AUTOCORR_NOALLOC_MAX_SERIES series (the window results then fill
+    the scratch array's second half up to its end) the results equal
+    crbm_autocorr's, and a warm call leaves the device's free memory as it
+    was: the entry point allocates nothing."""
+    import torch
+    from paper_2008_05401_gb300 import binding
+    ctx = gpu_ctx()
+    try:
+        cols, n = 16384, 48
+        rng = np.random.default_rng(11)
+        x = torch.tensor(np.cumsum(rng.normal(size=(n, cols)), axis=0) * 0.1 + rng.normal(size=(n, cols)),
+                         device="cuda:0")
+        ref_tau, ref_w = binding.crbm_autocorr(ctx.h, x.data_ptr(), cols, n)
+        binding.crbm_autocorr_noalloc(ctx.h, x.data_ptr(), cols, n)        # warm: module and scratch set up
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        tau, w = binding.crbm_autocorr_noalloc(ctx.h, x.data_ptr(), cols, n)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 >= free0, (free0, free1)
+        np.testing.assert_array_equal(w, ref_w)
+        np.testing.assert_array_equal(tau, ref_tau)
+    finally:
+        ctx.close()
+
+
 def test_noalloc_rejects_oversize():
     import torch
     from paper_2008_05401_gb300 import binding
