@@ -27,6 +27,10 @@ An epoch visits its samples in a given order, in consecutive minibatches of M
 Metropolis chains, a buffer of RBM samples refreshed by g uncorrected Gibbs
 steps of ub chains per epoch (new samples in front, the buffer cut to n_train),
 and one epoch over buffer + physical samples after each refresh.
+
+``pretrain`` is the pre-training step (App. A; Sec. IV; App. D): the same
+loss and ADAM epochs on uniformly random lattices, whose targets are computed
+once, until the epoch loss no longer decreases.
 """
 from __future__ import annotations
 
@@ -111,7 +115,7 @@ def targets_of(model, v, beta, J):
 
 
 def algorithm1(model, L, T, J, K, k, theta0, n_phys, phys_sweeps, phys_seed, n_train, ub, g,
-               rbm_seed, epochs, order_seed, M=20, **adam):
+               rbm_seed, epochs, order_seed, M=20, pre=None, **adam):
     """Algorithm 1 at one temperature; returns (theta, adam state, per-epoch losses).
 
     Physical samples: the final lattices of n_phys local-Metropolis chains
@@ -119,7 +123,13 @@ def algorithm1(model, L, T, J, K, k, theta0, n_phys, phys_sweeps, phys_seed, n_t
     phys_sweeps sweeps from random lattices.  Buffer chains: ub chains (seed
     rbm_seed, ids 0..ub-1) from random lattices; each refresh is one
     uncorrected proposal of g Gibbs steps with the current parameters.
+    pre: keyword arguments of ``pretrain`` (n_random, seed, max_epochs,
+    order_seed and optionally patience, rel_tol): the pre-training step runs
+    first, from theta0, and the main loop starts from its parameters with a
+    fresh ADAM state (reading: the paper treats the two as separate steps).
     """
+    if pre is not None:
+        theta0 = pretrain(model, L, T, J, K, k, theta0, M=M, **pre, **adam)[0]
     beta = 1.0 / T
     zeroW, zh = np.zeros((K, k, k)), np.zeros(K)
     phys = chain.make_chains(model, zeroW, zh, 0.0, L, T, J, phys_seed, np.arange(n_phys))
@@ -150,3 +160,40 @@ def algorithm1(model, L, T, J, K, k, theta0, n_phys, phys_sweeps, phys_seed, n_t
         theta, ls = epoch(theta, st, x_tot, t_tot, wl.epoch_order(len(x_tot), order_seed, e), K, k, M, **adam)
         losses.append(ls.mean())
     return theta, st, np.array(losses)
+
+
+def pretrain(model, L, T, J, K, k, theta0, n_random, seed, max_epochs, order_seed, M=20, patience=1,
+             rel_tol=1e-4, **adam):
+    """Pre-training on random states (App. A; Sec. IV; App. D), at one temperature.
+
+    The n_random lattices are uniform: v_ij = [u < 1/2] from the init tag of
+    chains 0 .. n_random-1 of `seed` (``chain.random_init``); their targets
+    t = -log pi at T are computed once.  Epochs of minibatch ADAM steps
+    (``epoch``, visiting order ``wl.epoch_order(n_random, order_seed, e)``)
+    run until for `patience` consecutive epochs the epoch's loss -- the mean
+    of its minibatch losses -- has not fallen below (1 - rel_tol) times the
+    loss of the last epoch that did, or max_epochs have run.  Reading: the paper ends the
+    step once the loss stops falling, without a tolerance; the parameters kept
+    are those of the epoch with the lowest loss, the ADAM state the one after
+    the last epoch.
+    Returns (theta, adam state, epoch losses, epochs run).
+    """
+    x = chain.random_init(seed, np.arange(n_random), L)
+    t = targets_of(model, x, 1.0 / T, J)
+    theta = np.asarray(theta0, dtype=np.float64).copy()
+    st = Adam.zeros(len(theta))
+    best, best_theta = np.inf, theta.copy()       # lowest epoch loss and its parameters
+    level, stale, losses = np.inf, 0, []          # loss at the last decrease by more than rel_tol
+    for e in range(max_epochs):
+        theta, ls = epoch(theta, st, x, t, wl.epoch_order(n_random, order_seed, e), K, k, M, **adam)
+        loss = float(ls.mean())
+        losses.append(loss)
+        if loss < best:
+            best, best_theta = loss, theta.copy()
+        if loss < level * (1.0 - rel_tol):
+            level, stale = loss, 0
+        else:
+            stale += 1
+            if stale >= patience:
+                break
+    return best_theta, st, np.array(losses), len(losses)

@@ -65,8 +65,65 @@ def train_epochs(ctx: B.Context, problems, samples, targets, orders, batch=20, l
     return losses
 
 
+def pretrain(ctx: B.Context, kind, L, Ts, J, K, k, theta0, n_random, seed, max_epochs, order_fn, M=20, patience=1,
+             rel_tol=1e-4, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """Pre-training on random states (App. A; Sec. IV; App. D) for every
+    temperature of Ts side by side.
+
+    n_random uniform lattices, drawn on the device from the init tag of chains
+    0 .. n_random-1 of `seed`, serve every temperature; their targets
+    t = -log pi at each temperature come from one FP64 evaluation per
+    temperature.  Each epoch of all problems still training is one launch
+    (visiting order order_fn(n_random, epoch)); a problem stops once for
+    `patience` epochs its epoch loss (the mean of its minibatch losses) has
+    not fallen below (1 - rel_tol) times the loss of its last epoch that did,
+    or after max_epochs, and keeps the parameters of its lowest-loss epoch.  Returns
+    (problems, per-problem lists of epoch losses)."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    zero = ctx.load_model(kind, np.zeros((K, k, k)), 0.0, np.zeros(K))
+    x = ctx.new_job(zero, kind, L, np.full(n_random, Ts[0]), J, seed, 0, None, B.FP64)
+    bits, _ = x.state()
+    x.release()
+    xs = torch.tensor(bits.view(np.int32), device=dev)
+    ts = []
+    for T in Ts:
+        job = ctx.new_job(zero, kind, L, np.full(n_random, T), J, seed, 0, bits, B.FP64)
+        lp, _, _ = job.energies()
+        job.release()
+        ts.append(torch.tensor(-lp, device=dev))
+    probs = [Problem.new(ctx, K, k, L, theta0) for _ in Ts]
+    best = [np.inf] * len(Ts)                 # lowest epoch loss and its parameters
+    best_theta = [pr.theta.clone() for pr in probs]
+    level = [np.inf] * len(Ts)                # loss at the last decrease by more than rel_tol
+    stale = [0] * len(Ts)
+    active = [True] * len(Ts)
+    history = [[] for _ in Ts]
+    for e in range(max_epochs):
+        act = [i for i in range(len(Ts)) if active[i]]
+        if not act:
+            break
+        order = torch.tensor(np.asarray(order_fn(n_random, e), dtype=np.int32), device=dev)
+        losses = train_epochs(ctx, [probs[i] for i in act], [xs] * len(act), [ts[i] for i in act],
+                              [order] * len(act), M, lr, b1, b2, eps)
+        for i, ls in zip(act, losses):
+            loss = float(ls.mean())
+            history[i].append(loss)
+            if loss < best[i]:
+                best[i] = loss
+                best_theta[i] = probs[i].theta.clone()
+            if loss < level[i] * (1.0 - rel_tol):
+                level[i], stale[i] = loss, 0
+            else:
+                stale[i] += 1
+                active[i] = stale[i] < patience
+    for pr, th in zip(probs, best_theta):
+        pr.theta.copy_(th)
+    return probs, history
+
+
 def algorithm1(ctx: B.Context, kind, L, Ts, J, K, k, theta0, n_phys, phys_sweeps, phys_seed, n_train, ub, g,
-               rbm_seed, epochs, order_fn, M=20, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+               rbm_seed, epochs, order_fn, M=20, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, pre=None):
     """Algorithm 1 for every temperature of Ts side by side.
 
     Physical samples: the final lattices of n_phys local-Metropolis chains
@@ -76,13 +133,21 @@ def algorithm1(ctx: B.Context, kind, L, Ts, J, K, k, theta0, n_phys, phys_sweeps
     with the current parameters, its lattices put in front of the buffer,
     which is cut to n_train.  Each epoch: refresh, then one epoch over buffer
     + physical samples in the order order_fn(n, epoch).  theta0 gives the
-    initial parameters of every problem.  Returns (problems, mean loss per
-    epoch and temperature)."""
+    initial parameters of every problem; pre (keyword arguments of
+    ``pretrain``: n_random, seed, max_epochs, order_fn and optionally
+    patience, rel_tol) runs the pre-training step first, and each
+    temperature's main loop starts from its pre-trained parameters with a
+    fresh ADAM state.  Returns (problems, mean loss per epoch and
+    temperature)."""
     import torch
     dev = f"cuda:{ctx.device}"
+    theta0s = [theta0] * len(Ts)
+    if pre is not None:
+        pp, _ = pretrain(ctx, kind, L, Ts, J, K, k, theta0, M=M, lr=lr, b1=b1, b2=b2, eps=eps, **pre)
+        theta0s = [pr.theta.cpu().numpy() for pr in pp]
     zero = ctx.load_model(kind, np.zeros((K, k, k)), 0.0, np.zeros(K))
     probs, phys_bits, phys_t, bufs, rings = [], [], [], [], []
-    for T in Ts:
+    for T, th0 in zip(Ts, theta0s):
         x = ctx.new_job(zero, kind, L, np.full(n_phys, T), J, phys_seed, 0, None, B.FP64)
         x.local_run(phys_sweeps)
         bits, _ = x.state()
@@ -90,7 +155,7 @@ def algorithm1(ctx: B.Context, kind, L, Ts, J, K, k, theta0, n_phys, phys_sweeps
         phys_bits.append(bits)
         phys_t.append(-lp)
         x.release()
-        pr = Problem.new(ctx, K, k, L, theta0)
+        pr = Problem.new(ctx, K, k, L, th0)
         probs.append(pr)
         W, hb, vb = pr.params()
         mid = ctx.load_model(kind, W, vb, hb)

@@ -83,6 +83,50 @@ def test_algorithm1_matches_oracle(ctx, model):
         assert int(probs[i].t.item()) == st.t
 
 
+@pytest.mark.parametrize("model", ["ising", "kitaev"])
+def test_pretraining_matches_oracle(ctx, model):
+    """Pre-training on random states (App. A; Sec. IV; App. D): the random
+    lattices drawn on the device, their targets, the epochs and the stopping
+    rule give the oracle's epoch losses, stopping epoch and kept parameters at
+    every temperature."""
+    from oracle import chain, train
+    from paper_2008_05401_gb300 import ISING, KITAEV, trainer
+    if model == "ising":
+        kind, okind, L, Ts, J, K, k = ISING, chain.ISING, 6, [2.0, 2.5, 3.2], (1.0,), 2, 3
+    else:
+        kind, okind, L, Ts, J, K, k = KITAEV, chain.KITAEV, 4, [0.1, 0.5], (1.0, 1.0, 1.0), 2, 3
+    th0 = wl.init_train_params(K, k, seed=13)
+    kw = dict(n_random=1500, seed=21, max_epochs=12, M=20, patience=2, rel_tol=0.02)
+    probs, hist = trainer.pretrain(ctx, kind, L, Ts, J, K, k, th0, order_fn=lambda n, e: wl.epoch_order(n, 6, e),
+                                   **kw)
+    stopped_early = 0
+    for i, T in enumerate(Ts):
+        th, st, losses, n = train.pretrain(okind, L, T, J, K, k, th0, order_seed=6, **kw)
+        assert len(hist[i]) == n
+        stopped_early += n < kw["max_epochs"]
+        np.testing.assert_allclose(hist[i], losses, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(probs[i].theta.cpu().numpy(), th, rtol=1e-9, atol=1e-12)
+        assert losses.min() < losses[0]
+    if model == "ising":
+        assert stopped_early >= 1                    # the stopping rule itself is exercised
+
+
+def test_algorithm1_with_pretraining_matches_oracle(ctx):
+    from oracle import chain, train
+    from paper_2008_05401_gb300 import ISING, trainer
+    L, Ts, J, K, k = 4, [2.2, 3.0], (1.0,), 2, 3
+    th0 = wl.init_train_params(K, k, seed=11)
+    kw = dict(n_phys=24, phys_sweeps=6, phys_seed=5, n_train=30, ub=10, g=2, rbm_seed=6, epochs=3, M=8, lr=1e-2)
+    probs, hist = trainer.algorithm1(ctx, ISING, L, Ts, J, K, k, th0, order_fn=lambda n, e: wl.epoch_order(n, 4, e),
+                                     pre=dict(n_random=400, seed=31, max_epochs=6,
+                                              order_fn=lambda n, e: wl.epoch_order(n, 8, e)), **kw)
+    for i, T in enumerate(Ts):
+        th, st, losses = train.algorithm1(chain.ISING, L, T, J, K, k, th0, order_seed=4,
+                                          pre=dict(n_random=400, seed=31, max_epochs=6, order_seed=8), **kw)
+        np.testing.assert_allclose(probs[i].theta.cpu().numpy(), th, rtol=1e-8, atol=1e-11)
+        np.testing.assert_allclose(hist[:, i], losses, rtol=1e-8, atol=1e-11)
+
+
 def test_train_rejects_bad_shapes(ctx):
     import torch
     from paper_2008_05401_gb300 import CrbmError, trainer

@@ -121,3 +121,80 @@ def test_algorithm1_reduces_the_loss():
                                       order_seed=5, M=20, lr=1e-2)
     assert st.t == 30 * ((64 + 64 + 19) // 20)
     assert losses[-1] < 0.5 * losses[0]
+
+
+def _metropolis_states(L, T, n, seed, sweeps=200):
+    from oracle import metropolis
+    K = 1
+    ph = chain.make_chains(chain.ISING, np.zeros((K, 1, 1)), np.zeros(K), 0.0, L, T, (1.0,), seed, np.arange(n))
+    metropolis.run(ph, sweeps)
+    return ph.v.copy()
+
+
+def test_pretraining_fits_random_states_and_helps_on_physical_states():
+    """Pre-training (App. A; Sec. IV): epochs on 10^4 uniformly random lattices
+    lower their loss tenfold, and the pre-trained CRBM fits physical
+    (Metropolis) states far better than the initial one -- a target with the
+    wrong sign would fit the random states just as well, but not these."""
+    K, k, L, T = 2, 3, 6, 2.5
+    th0 = wl.init_train_params(K, k, seed=1)
+    th, st, losses, n = train.pretrain(chain.ISING, L, T, (1.0,), K, k, th0, n_random=10_000, seed=7,
+                                       max_epochs=12, order_seed=3, M=20)
+    assert n == len(losses) <= 12
+    assert losses.min() < 0.1 * losses[0], losses
+    x = _metropolis_states(L, T, 1000, 11)
+    t = train.targets_of(chain.ISING, x, 1 / T, (1.0,))
+    before, _ = train.loss_and_grad(x, t, th0, K, k)
+    after, _ = train.loss_and_grad(x, t, th, K, k)
+    assert after < 0.1 * before, (before, after)
+
+
+def test_pretraining_keeps_the_analytic_crbm():
+    """App. C's CRBM already has zero loss on every lattice: pre-training on
+    random states leaves it (up to ADAM's steps on rounding-level gradients)."""
+    T = 2.5
+    W, hb, vb = ising.analytic_crbm(1 / T, 2)
+    th0 = np.concatenate([W.ravel(), [vb], hb])
+    th, _, losses, n = train.pretrain(chain.ISING, 4, T, (1.0,), 2, 2, th0, n_random=10_000, seed=7,
+                                      max_epochs=6, order_seed=3)
+    assert losses.max() < 1e-4, losses
+    assert n < 6                                        # stops once the loss no longer falls
+    np.testing.assert_allclose(th, th0, atol=1e-4)
+
+
+def test_pretraining_stopping_rule_and_kept_parameters():
+    """With patience p the run stops p epochs after the last epoch that
+    lowered the loss by more than rel_tol (none of them below (1 - rel_tol)
+    times it) and returns the parameters of the lowest-loss epoch, which a
+    manual replay of the epochs reproduces."""
+    K, k, L, T = 1, 2, 4, 3.0
+    th0 = wl.init_train_params(K, k, seed=2)
+    p, tol = 2, 0.2
+    th, st, losses, n = train.pretrain(chain.ISING, L, T, (1.0,), K, k, th0, n_random=400, seed=5,
+                                       max_epochs=40, order_seed=8, M=20, patience=p, rel_tol=tol)
+    assert n < 40
+    j = n - p - 1                                   # the last epoch that lowered the loss by more than tol
+    assert losses[j] == losses[:j + 1].min()
+    assert all(l >= losses[j] * (1 - tol) for l in losses[j + 1:])
+    best = int(np.argmin(losses))
+    x = chain.random_init(5, np.arange(400), L)
+    t = train.targets_of(chain.ISING, x, 1 / T, (1.0,))
+    thr, s = th0.copy(), train.Adam.zeros(len(th0))
+    for e in range(best + 1):
+        thr, _ = train.epoch(thr, s, x, t, wl.epoch_order(400, 8, e), K, k, 20)
+    np.testing.assert_array_equal(th, thr)
+
+
+def test_algorithm1_starts_lower_after_pretraining():
+    """Algorithm 1 from pre-trained parameters starts (and ends) its epochs at
+    a lower loss than from the initial parameters (Sec. IV: pre-training
+    shortens the training)."""
+    K, k, L = 2, 3, 4
+    th0 = wl.init_train_params(K, k, seed=1)
+    args = dict(n_phys=64, phys_sweeps=20, phys_seed=3, n_train=64, ub=16, g=2, rbm_seed=4, epochs=5,
+                order_seed=5, M=20, lr=1e-2)
+    _, _, plain = train.algorithm1(chain.ISING, L, 2.5, (1.0,), K, k, th0, **args)
+    _, _, pre = train.algorithm1(chain.ISING, L, 2.5, (1.0,), K, k, th0,
+                                 pre=dict(n_random=2000, seed=9, max_epochs=20, order_seed=6), **args)
+    assert pre[0] < 0.5 * plain[0], (pre, plain)
+    assert pre[-1] < plain[-1], (pre, plain)
