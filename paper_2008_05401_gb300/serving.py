@@ -9,12 +9,15 @@ at each scheduling step:
      does not; the request then waits for memory to be released);
   2. groups the active jobs that can share a launch (same model kind,
      filter-bank shape and precision), at most 16 per launch; every group has
-     its own CUDA stream and, whenever its previous launch has finished
-     (polled through CUDA events, never by blocking), enqueues the next one,
-     running q = min(quantum, smallest remaining S of the launch) proposals.
-     The quantum adapts so that a launch takes about `target_launch_s`.  Slow
-     groups therefore never hold back fast ones, and groups overlap on the
-     device;
+     two CUDA streams and keeps up to two batches in flight, one per stream:
+     whenever a stream of the group is idle (polled through CUDA events,
+     never by blocking) it enqueues the group's jobs that are not in flight
+     -- a request that arrives while the group's batch runs starts at once on
+     the other stream instead of waiting for that batch's quantum --, running
+     q = min(quantum, smallest remaining S of the launch) proposals.  The
+     quantum adapts so that a launch takes about `target_launch_s`.  Slow
+     groups never hold back fast ones, and groups and batches overlap on the
+     device (the launch timeline is kept, see ``timeline``);
   3. retires finished jobs (results read back, memory released) as soon as
      their launch completes and records each request's latency.
 
@@ -80,15 +83,18 @@ class _Active:
 
 class _Group:
     """Jobs that can share a launch (same kind, filter shape, precision) and the
-    state of that group's stream: the launches in flight and an adaptive
-    quantum that aims each launch at `target_s` seconds."""
+    state of that group's two streams: the launches in flight on each and an
+    adaptive quantum that aims each launch at `target_s` seconds."""
 
-    def __init__(self, key, stream, quantum):
+    def __init__(self, key, streams, quantum):
         self.key = key
-        self.stream = stream
+        self.streams = streams
         self.quantum = quantum
-        self.in_flight = []          # [(end_event, start_event, chunk, q)]
-        self.finished = []           # jobs whose last launch completed, read back once the stream is idle
+        self.in_flight = []          # [(end_event, start_event, chunk, q, stream index)]
+        self.finished = []           # [(job, stream index)]: read back once that stream is idle
+
+    def busy(self, si):
+        return any(f[4] == si for f in self.in_flight)
 
 
 class Server:
@@ -109,10 +115,17 @@ class Server:
         self._groups: dict[tuple, _Group] = {}
         self.launches = 0
         self.proposals = 0
+        # every launch as (group key, stream index, start event, end event), and
+        # an event recorded when the server started, against which the
+        # device-side start and end times of the launches are measured
+        self.timeline = []
+        self.t0_event = torch.cuda.Event(enable_timing=True)
+        self.t0_event.record(torch.cuda.current_stream(device))
 
     def close(self):
         for g in self._groups.values():
-            g.stream.synchronize()
+            for st in g.streams:
+                st.synchronize()
         for a in self.active:
             a.job.release()
         self.active = []
@@ -153,14 +166,19 @@ class Server:
     # ---------------------------------------------------------------- scheduling
     def _group(self, key):
         if key not in self._groups:
-            self._groups[key] = _Group(key, self.torch.cuda.Stream(device=self.ctx.device), self.quantum)
+            dev = self.ctx.device
+            self._groups[key] = _Group(key, [self.torch.cuda.Stream(device=dev), self.torch.cuda.Stream(device=dev)],
+                                       self.quantum)
         return self._groups[key]
 
     def _complete(self, g: _Group):
-        """Retire the group's finished launches (non-blocking); True if any finished."""
+        """Retire the group's finished launches (non-blocking, in any order of
+        the two streams); True if any finished."""
         done_any = False
-        while g.in_flight and g.in_flight[0][0].query():
-            end, start, chunk, q = g.in_flight.pop(0)
+        done = [f for f in g.in_flight if f[0].query()]
+        g.in_flight = [f for f in g.in_flight if all(f is not d for d in done)]
+        for f in done:
+            end, start, chunk, q, si = f
             if self.adaptive:
                 dt = start.elapsed_time(end) * 1e-3
                 if dt > 0:
@@ -168,28 +186,33 @@ class Server:
             for a in chunk:
                 a.remaining -= q
                 if a.remaining <= 0:
-                    g.finished.append(a)
+                    g.finished.append((a, si))
             done_any = True
-        if not g.in_flight:
-            # reading a job back synchronises its stream: only once nothing is in flight on it
-            for a in g.finished:
+        # reading a job back synchronises its stream: only once nothing is in flight on it
+        keep = []
+        for a, si in g.finished:
+            if g.busy(si):
+                keep.append((a, si))
+            else:
                 self._retire(a)
-            g.finished = []
+        g.finished = keep
         return done_any
 
-    def _launch(self, g: _Group, members):
-        busy = {id(a) for _, _, chunk, _ in g.in_flight for a in chunk}
+    def _launch(self, g: _Group, members, si):
+        busy = {id(a) for f in g.in_flight for a in f[2]}
         ready = sorted((a for a in members if a.remaining > 0 and id(a) not in busy), key=lambda a: a.remaining)
         n = 0
+        stream = g.streams[si]
         for i in range(0, len(ready), self.max_per_launch):
             chunk = ready[i:i + self.max_per_launch]
             q = min(g.quantum, min(a.remaining for a in chunk))
             start = self.torch.cuda.Event(enable_timing=True)
             end = self.torch.cuda.Event(enable_timing=True)
-            start.record(g.stream)
-            self.ctx.run_batch([a.job for a in chunk], q, precision=g.key[-1], stream=g.stream)
-            end.record(g.stream)
-            g.in_flight.append((end, start, chunk, q))
+            start.record(stream)
+            self.ctx.run_batch([a.job for a in chunk], q, precision=g.key[-1], stream=stream)
+            end.record(stream)
+            g.in_flight.append((end, start, chunk, q, si))
+            self.timeline.append((g.key, si, start, end))
             self.proposals += q * sum(a.job.n for a in chunk)
             self.launches += 1
             n += 1
@@ -207,8 +230,10 @@ class Server:
         launched = 0
         for key, members in by_group.items():
             g = self._group(key)
-            if not g.in_flight:                 # one batch in flight per group keeps its stream busy
-                launched += self._launch(g, members)
+            for si in (0, 1):                   # an idle stream of the group takes the jobs not in flight
+                if not g.busy(si):
+                    launched += self._launch(g, members, si)
+                    break
         return launched + int(progressed)
 
     def _retire(self, a: _Active):
@@ -227,8 +252,10 @@ class Server:
                 return True
         for a in self.active:
             if a.req.rid == rid:
-                self._group(a.group).stream.synchronize()
-                self._complete(self._group(a.group))
+                g = self._group(a.group)
+                for st in g.streams:
+                    st.synchronize()
+                self._complete(g)
                 if a in self.active and a.remaining > 0:
                     a.job.release()
                     self.active.remove(a)
@@ -252,6 +279,14 @@ class Server:
                 time.sleep(0.0002)
         return self.results
 
+    def launch_intervals(self):
+        """Device-side (start, end) of every launch in seconds after the
+        server started, with its group key and stream index (after the work
+        has finished)."""
+        self.torch.cuda.synchronize(self.ctx.device)
+        return [(key, si, self.t0_event.elapsed_time(a) * 1e-3, self.t0_event.elapsed_time(b) * 1e-3)
+                for key, si, a, b in self.timeline]
+
     def stats(self, t_start: float | None = None):
         lat = np.array([r.latency for r in self.results.values()])
         if not len(lat):
@@ -260,7 +295,7 @@ class Server:
             t_start if t_start is not None else min(r.arrival for r in self.results.values()))
         return {"requests": len(lat), "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "proposals_per_s": self.proposals / span,
-                "launches": self.launches}
+                "launches": self.launches, "wall_s": span}
 
 
 def synthetic_requests(n: int, rate_hz: float = 200.0, seed: int = 2008054010, max_proposals: int = 10 ** 4,

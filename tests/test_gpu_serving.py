@@ -1,5 +1,6 @@
 """Continuous batching: results are the same alone and in the mix; admission
-waits for HBM; groups of different model kinds overlap on separate streams."""
+waits for HBM; groups of different model kinds, and two batches of one group,
+overlap on separate streams (CUDA event timestamps of the launches)."""
 import numpy as np
 import pytest
 
@@ -79,3 +80,26 @@ def test_a_failing_request_fails_alone():
     ref_srv.close()
     for rid in ref:
         _same(ref[rid], res[rid])
+
+
+def test_launches_of_different_groups_and_of_one_group_overlap():
+    """The Ising and Kitaev groups run on their own streams, and each group
+    keeps a second batch in flight for jobs that are not in its first: the
+    device-side intervals [start, end] of launches of the two groups intersect,
+    and so do those of two batches of one group."""
+    gpu_ctx().close()
+    from paper_2008_05401_gb300.serving import Server
+    reqs = _requests(24, seed=5, max_proposals=300)
+    for r in reqs[12:]:
+        r.arrival += 0.05                         # a second wave arrives while the first runs
+    srv = Server(quantum=37)
+    srv.run(reqs, realtime=True)
+    iv = srv.launch_intervals()
+    srv.close()
+    assert {key[0] for key, _, _, _ in iv} == {0, 1}
+
+    def meet(a, b):
+        return a[2] < b[3] and b[2] < a[3]
+
+    assert any(meet(a, b) for a in iv for b in iv if a[0][0] != b[0][0])
+    assert any(meet(a, b) for a in iv for b in iv if a[0] == b[0] and a[1] != b[1])
