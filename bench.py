@@ -315,7 +315,7 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False, clock
         base += n
     if graph:
         for L, _ in spec["jobs"]:
-            ctx.tune(mid, L, prec)            # autotuned tiles (Kitaev: one chain per CTA)
+            ctx.tune(mid, L, prec)            # autotuned tiles (Kitaev: chains, i.e. thread groups, per CTA)
     ms = time_jobs(ctx, jobs, spec["S"], prec, steps, 1, stream, dev, flush, graph=graph)
     n_chains = sum(n for _, n in spec["jobs"])
     sums = [j.observables() for j in jobs]

@@ -154,14 +154,16 @@ CRBM_API int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, 
 CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, int precision,
              void* cuda_stream);
 
-/* As crbm_run for n_jobs jobs in ONE kernel launch (chains of different L and
- * temperature side by side; Kitaev jobs run in CTAs whose size depends on
- * their lattice, one launch per size, forked from cuda_stream onto internal
- * side streams and joined back, so the call stays ordered on cuda_stream).
- * The jobs must share the model kind and the
- * filter-bank shape (K, k); their models may differ.  Each job keeps its own
- * step counter and random streams, so its result equals a crbm_run of that
- * job alone.  At most 16 jobs per call; a job may appear once. */
+/* As crbm_run for n_jobs jobs, chains of different L and temperature side
+ * by side: the jobs on the tensor-core form (crbm_set_tensor_cores) share ONE
+ * persistent launch whatever their sides; the other jobs share one launch of
+ * 256-thread CTAs (Kitaev chains in thread groups sized by their lattice,
+ * several per CTA for small ones); when both kinds of launch are needed they
+ * fork from cuda_stream onto internal side streams and join it again, so the
+ * call stays ordered on cuda_stream.  The jobs must share the model kind and
+ * the filter-bank shape (K, k); their models may differ.  Each job keeps its
+ * own step counter and random streams, so its result equals a crbm_run of
+ * that job alone.  At most 16 jobs per call; a job may appear once. */
 CRBM_API int crbm_run_batch(crbm_ctx* ctx, int n_jobs, const int* job_ids, int64_t S, int g,
                    int correct, int precision, void* cuda_stream);
 
@@ -335,8 +337,13 @@ CRBM_API int crbm_probe_peaks(crbm_ctx* ctx, double* fp32_tflops, double* fp64_t
  * lattice side L and `precision`: every admissible value is timed on a
  * temporary job that fills the GPU (device memory allocated and freed by this
  * call), and the fastest is used by every job of this (kind, L, K, k) created
- * afterwards in this context.  *best_nc / *best_us_per_proposal (may be NULL)
- * receive the choice and its time per chain-proposal in microseconds. */
+ * afterwards in this context.  For the Kitaev kind the value sets the threads
+ * of each chain's group (256 / chains, at least 32), which run its
+ * eigen-stage; a different group size changes the order of that stage's FP64
+ * sums (last bits of log pi), not the method.  Jobs of the tensor-core form
+ * (crbm_set_tensor_cores) keep their fixed tile of 128 / L chains.
+ * *best_nc / *best_us_per_proposal (may be NULL) receive the choice and its
+ * time per chain-proposal in microseconds. */
 CRBM_API int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc,
                        double* best_us_per_proposal);
 

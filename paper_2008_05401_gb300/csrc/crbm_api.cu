@@ -102,9 +102,11 @@ bool valid_L(int kind, int L) {
   return false;
 }
 
-// Chains per CTA: about two 4-site units per thread, a power of two in [1, 32].
+// Chains per CTA: Kitaev, 256 threads over the chain groups of
+// kitaev_group_threads; Ising, about two 4-site units per thread, a power of
+// two in [1, 32].
 int chains_per_tile(int kind, int L) {
-  if (kind == kKitaev) return 1;
+  if (kind == kKitaev) return kThreads / kitaev_group_threads(L * L);
   const int nblk = (L * L + 3) / 4;
   int nc = 1;
   while (nc < kThreads / 8 && (nc * 2) * nblk <= 2 * kThreads) nc *= 2;
@@ -256,12 +258,15 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
 }
 
 // Launch the fused kernel for a set of jobs (same kind and filter shape);
-// mode 1 = evaluate.  A job's CTA size depends only on its own lattice
-// (threads_for), so that its per-chain reduction order -- and hence every
-// bit of its results -- is the same alone or batched; jobs of different CTA
-// sizes go to separate launches on the same stream.
-static int launch_group(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g, int correct, int prec,
+// mode 1 = evaluate.  A job's chains per CTA (and so the threads of each
+// chain's group and its per-chain reduction order -- hence every bit of its
+// results) depend only on its own lattice, so the job gives the same results
+// alone or batched.  The jobs' tiles are laid out by decreasing lattice side,
+// so that the longest tiles start first and the short ones fill the end.
+static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int correct, int prec,
                         int mode, int nt, cudaStream_t st, const Job* partner = nullptr) {
+  if (!partner)
+    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ctx->jobs[a].L > ctx->jobs[b].L; });
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -1221,7 +1226,11 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
           smem_bytes(m.kind, precision, L, m.K, m.k, nc, m.K == 4 ? 4 : 0) <= 100 * 1024)
         cand.push_back(nc);
   } else {
-    cand.push_back(1);
+    // chain groups of 256 / nc threads (at least a warp), as many as fit the shared memory
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    for (int nc = 1; nc <= kThreads / 32; nc *= 2)
+      if (smem_bytes(m.kind, precision, L, m.K, m.k, nc, m.K == 4 ? 4 : 0) <= (size_t)optin) cand.push_back(nc);
   }
   // a temporary job large enough for every candidate to fill the GPU
   const int n_chains = 4 * sms * cand.back();

@@ -338,6 +338,38 @@ __device__ __forceinline__ void grp_reduce(double (&x)[NV], const Grp& g, double
   }
 }
 
+// Barrier of one chain's thread group (warp-aligned groups of 32 .. blockDim
+// threads): the CTA barrier when the group is the whole CTA, the warp's when it
+// is one warp, else a named barrier of its own (id 1 + group index; a CTA holds
+// at most 8 groups).  Only the group's threads take part, so groups may run
+// different branches between two of their barriers.
+__device__ __forceinline__ void grp_sync(const Grp& g) {
+  if (g.tpc == (int)blockDim.x) {
+    __syncthreads();
+  } else if (g.tpc == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;\n" :: "r"(1 + g.gl), "r"(g.tpc) : "memory");
+  }
+}
+
+// Deterministic sum over a chain's (warp-aligned) group, returned to every
+// thread of it: a butterfly within each warp, then the warps' partials added
+// in warp order -- the order of block_sum for a CTA of tpc threads, so a group
+// gives the same bits as a CTA of its size.  scratch: 32 doubles of the group.
+__device__ __forceinline__ double grp_sum(double x, const Grp& g, double* scratch) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
+  const int warp = g.r >> 5, nw = g.tpc >> 5;
+  grp_sync(g);
+  if ((g.r & 31) == 0) scratch[warp] = x;
+  grp_sync(g);
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += scratch[w];
+  grp_sync(g);
+  return s;
+}
+
 // Deterministic block-wide sum, result returned to every thread.
 __device__ __forceinline__ double block_sum(double x, double* scratch) {
 #pragma unroll
@@ -992,10 +1024,12 @@ __device__ __forceinline__ void thermal_add(double eps, double beta, double& lp,
 // eps_out (optional, device memory): the N energies eps, ascending.
 // open_cols: the lattice is open along j (the y-bonds from column L-1 to
 // column 0 are absent), the physics of the LCRBM's open boundary conditions.
-__device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J, double beta,
+// Run by the chain's thread group g (warp-aligned) with its own work areas wk;
+// every thread of the group calls, and only the group synchronises.
+__device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, const double* J, double beta,
                                const KitaevWork& wk, double (&res)[3], double* eps_out = nullptr,
                                bool open_cols = false) {
-  const int N = L * L, tid = threadIdx.x, nt = blockDim.x;
+  const int N = L * L, tid = g.r, nt = g.tpc;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double* A = wk.A;
   const double tx = 2.0 * J[0], ty = 2.0 * J[1], tz = 2.0 * J[2];
@@ -1021,7 +1055,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       if (wy <= w && !(open_cols && bj + 1 == L)) row[wy] += mw * ty;
     }
   }
-  __syncthreads();
+  grp_sync(g);
   // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1.
   // Only the lower triangle of the trailing block is read and updated.
   for (int j = 0; j < N - 2; ++j) {
@@ -1031,12 +1065,12 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       const double a = A[tri(i, j)];
       s += a * a;
     }
-    s = block_sum(s, wk.sc);
+    s = grp_sum(s, g, wk.sc);
     const double x0 = A[tri(j + 1, j)];
     if (tid == 0) wk.d[j] = A[tri(j, j)];
     if (s == 0.0) {
       if (tid == 0) wk.e[j] = x0;
-      __syncthreads();
+      grp_sync(g);
       continue;
     }
     const double nrm = sqrt(x0 * x0 + s);
@@ -1045,7 +1079,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     const double tau = 2.0 / (v0 * v0 + s);
     if (tid == 0) wk.e[j] = alpha;
     for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
-    __syncthreads();
+    grp_sync(g);
     // p = tau * A22 v from the lower triangle (row part c <= l, column part c > l), one warp per row
     for (int l = warp; l < m; l += nw) {
       double acc = 0.0;
@@ -1057,20 +1091,20 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
       if (lane == 0) wk.pw[l] = tau * acc;
     }
-    __syncthreads();
+    grp_sync(g);
     double pv = 0.0;
     for (int l = tid; l < m; l += nt) pv = fma(wk.pw[l], wk.vv[l], pv);
-    pv = block_sum(pv, wk.sc);
+    pv = grp_sum(pv, g, wk.sc);
     const double Kc = 0.5 * tau * pv;
     for (int l = tid; l < m; l += nt) wk.pw[l] = fma(-Kc, wk.vv[l], wk.pw[l]);
-    __syncthreads();
+    grp_sync(g);
     // lower triangle of A22 -= v w^T + w v^T
     for (int l = warp; l < m; l += nw) {
       double* row = A + tri(j + 1 + l, j + 1);
       const double vl = wk.vv[l], wl = wk.pw[l];
       for (int c = lane; c <= l; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
     }
-    __syncthreads();
+    grp_sync(g);
   }
   if (tid == 0) {
     wk.d[N - 2] = A[tri(N - 2, N - 2)];
@@ -1087,7 +1121,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     wk.sc[0] = lo;
     wk.sc[1] = hi;
   }
-  __syncthreads();
+  grp_sync(g);
   // squared off-diagonals for the Sturm recurrence (reuse vv), FP32 copies
   for (int i = tid; i < N; i += nt) {
     wk.vv[i] = wk.e[i] * wk.e[i];
@@ -1095,7 +1129,7 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     wk.e32[i] = (float)(wk.e[i] * wk.e[i]);
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
-  __syncthreads();
+  grp_sync(g);
   double lp = 0.0, en = 0.0, cf = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
     const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
@@ -1103,9 +1137,9 @@ __device__ inline void kitaev_logpi64(const uint32_t* v, int L, const double* J,
     if (eps_out) eps_out[idx] = eps;
     thermal_add(eps, beta, lp, en, cf);
   }
-  res[0] = block_sum(lp, wk.sc);
-  res[1] = block_sum(en, wk.sc);
-  res[2] = block_sum(cf, wk.sc);
+  res[0] = grp_sum(lp, g, wk.sc);
+  res[1] = grp_sum(en, g, wk.sc);
+  res[2] = grp_sum(cf, g, wk.sc);
 }
 
 }  // namespace crbm

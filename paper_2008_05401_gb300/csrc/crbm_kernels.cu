@@ -11,8 +11,7 @@ size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int n
              : (KC == 4 ? 3 * align16(nq * 16 * 8) + align16(nlut * 4) : 4 * align16(nlut * 4));
   b += align16(nc * sizeof(ChainSm));
   b += align16(64 * 8);
-  if (kind == kKitaev)
-    b += align16(N * (N + 1) / 2 * 8) + 4 * align16(N * 8) + align16(64 * 8) + 2 * align16(N * 4) + align16(N * 8);
+  if (kind == kKitaev) b += (size_t)nc * kitaev_work_bytes((int)N);
   b += align16((size_t)nc * (2 + K) * P * 4);
   return b;
 }
@@ -43,20 +42,8 @@ cudaError_t launch_kIsing_kMixed_256(int, int, const LaunchParams&, int, size_t,
 cudaError_t limit_kIsing_kMixed_256(size_t);
 cudaError_t launch_kKitaev_kFP64_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kKitaev_kFP64_256(size_t);
-cudaError_t launch_kKitaev_kFP64_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kFP64_128(size_t);
-cudaError_t launch_kKitaev_kFP64_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kFP64_64(size_t);
-cudaError_t launch_kKitaev_kFP64_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kFP64_32(size_t);
 cudaError_t launch_kKitaev_kMixed_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kKitaev_kMixed_256(size_t);
-cudaError_t launch_kKitaev_kMixed_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kMixed_128(size_t);
-cudaError_t launch_kKitaev_kMixed_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kMixed_64(size_t);
-cudaError_t launch_kKitaev_kMixed_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
-cudaError_t limit_kKitaev_kMixed_32(size_t);
 
 void specialisation(int K, int k, int& KC, int& kC) {
   KC = 0;
@@ -67,13 +54,15 @@ void specialisation(int K, int k, int& KC, int& kC) {
   }
 }
 
-// Kitaev CTA sizes measured on the Kitaev workloads: 32 threads up to 16
-// cells, 64 up to 64, 128 up to 100 and 256 above (per-column barriers of the
-// reduction cost less in small CTAs, of which more fit an SM).
-int threads_for(int kind, int max_N) {
-  if (kind != kKitaev) return 256;
-  return max_N <= 16 ? 32 : (max_N <= 64 ? 64 : (max_N <= 100 ? 128 : 256));
-}
+// Every job runs in CTAs of 256 threads, so jobs of any lattice side share one
+// launch.  A Kitaev chain's eigen-stage is run by a thread group of its own
+// (kitaev_group_threads), several groups per CTA for small matrices.
+int threads_for(int, int) { return 256; }
+
+// Threads of a Kitaev chain's group, measured on the Kitaev workloads when
+// they were CTA sizes: 32 up to 16 cells, 64 up to 64, 128 up to 100 and 256
+// above (the reduction's per-column barriers cost less in small groups).
+int kitaev_group_threads(int N) { return N <= 16 ? 32 : (N <= 64 ? 64 : (N <= 100 ? 128 : 256)); }
 
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
                         cudaStream_t st, bool generic) {
@@ -83,28 +72,15 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
   if (kind == kIsing)
     return prec == kFP64 ? launch_kIsing_kFP64_256(KC, kC, p, grid, smem, st)
                          : launch_kIsing_kMixed_256(KC, kC, p, grid, smem, st);
-  if (prec == kFP64) {
-    switch (nt) {
-      case 32: return launch_kKitaev_kFP64_32(KC, kC, p, grid, smem, st);
-      case 64: return launch_kKitaev_kFP64_64(KC, kC, p, grid, smem, st);
-      case 128: return launch_kKitaev_kFP64_128(KC, kC, p, grid, smem, st);
-      default: return launch_kKitaev_kFP64_256(KC, kC, p, grid, smem, st);
-    }
-  }
-  switch (nt) {
-    case 32: return launch_kKitaev_kMixed_32(KC, kC, p, grid, smem, st);
-    case 64: return launch_kKitaev_kMixed_64(KC, kC, p, grid, smem, st);
-    case 128: return launch_kKitaev_kMixed_128(KC, kC, p, grid, smem, st);
-    default: return launch_kKitaev_kMixed_256(KC, kC, p, grid, smem, st);
-  }
+  (void)nt;
+  return prec == kFP64 ? launch_kKitaev_kFP64_256(KC, kC, p, grid, smem, st)
+                       : launch_kKitaev_kMixed_256(KC, kC, p, grid, smem, st);
 }
 
 cudaError_t set_smem_limits(size_t bytes) {
   cudaError_t e = cudaSuccess;
   for (cudaError_t (*f)(size_t) : {limit_kIsing_kFP64_256, limit_kIsing_kMixed_256, limit_kKitaev_kFP64_256,
-                                   limit_kKitaev_kFP64_128, limit_kKitaev_kFP64_64, limit_kKitaev_kFP64_32,
-                                   limit_kKitaev_kMixed_256, limit_kKitaev_kMixed_128, limit_kKitaev_kMixed_64,
-                                   limit_kKitaev_kMixed_32})
+                                   limit_kKitaev_kMixed_256})
     if (e == cudaSuccess) e = f(bytes);
   return e;
 }

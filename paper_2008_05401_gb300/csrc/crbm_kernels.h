@@ -14,10 +14,12 @@ void specialisation(int K, int k, int& KC, int& kC);
 // Dynamic shared memory of one CTA of the fused kernel (ncls kernel classes
 // in the tables: 1 for a CRBM, 2 edge + 1 for an LCRBM).
 size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int ncls = 1);
-// Threads per CTA of a job whose lattice has max_N cells: 256 for the Ising
-// kind; for the Kitaev kind 32 up to 16 cells, 64 up to 64, 128 up to 100,
-// else 256 (measured: small CTAs wait less at the eigen-stage barriers).
+// Threads per CTA of a job: 256 for every kind and lattice.
 int threads_for(int kind, int max_N);
+// Default threads of one Kitaev chain's group (its eigen-stage): 32 up to 16
+// cells, 64 up to 64, 128 up to 100, else 256 (measured: small groups wait
+// less at the eigen-stage barriers).
+int kitaev_group_threads(int N);
 // Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch);
 // generic: use the runtime-shape variant even where a specialisation exists (LCRBM jobs).
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,

@@ -34,6 +34,15 @@ struct ChainSm {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Shared-memory work areas of one Kitaev chain (one per thread group of the
+// CTA): the packed lower triangle of A (N (N+1) / 2 FP64 or double-FP32
+// entries), d, e, vv, pw (N each), 64 doubles of reduction scratch, the FP32
+// tridiagonal copies (N each) and the proposed spectrum of a local sweep (N).
+__host__ __device__ inline size_t kitaev_work_bytes(int N) {
+  const size_t n = (size_t)N;
+  return align16(n * (n + 1) / 2 * 8) + 4 * align16(n * 8) + align16(64 * 8) + 2 * align16(n * 4) + align16(n * 8);
+}
+
 // The mixed path's FP64 free energy (rare), out of line to spare registers.
 static __device__ __noinline__ void free_energy64(const JobDev& jb, const Tabs& tb, const Grp& g,
                                                   const uint32_t* v, double* out) {
@@ -125,30 +134,8 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   sp += align16(jb.nc * sizeof(ChainSm));
   double* scratch = (double*)sp;
   sp += align16(64 * 8);
-  KitaevWork wk;
-  if (KIND == kKitaev) {
-    wk.A = (double*)sp;
-    sp += align16((size_t)N * (N + 1) / 2 * 8);
-    wk.d = (double*)sp;
-    sp += align16((size_t)N * 8);
-    wk.e = (double*)sp;
-    sp += align16((size_t)N * 8);
-    wk.vv = (double*)sp;
-    sp += align16((size_t)N * 8);
-    wk.pw = (double*)sp;
-    sp += align16((size_t)N * 8);
-    wk.sc = (double*)sp;
-    sp += align16(64 * 8);
-    wk.d32 = (float*)sp;
-    sp += align16((size_t)N * 4);
-    wk.e32 = (float*)sp;
-    sp += align16((size_t)N * 4);
-  }
-  double* eps_st = nullptr;     // Kitaev local sweeps: spectrum of the proposed lattice
-  if (KIND == kKitaev) {
-    eps_st = (double*)sp;
-    sp += align16((size_t)N * 8);
-  }
+  unsigned char* kwork = sp;     // Kitaev: the work areas of the CTA's nc chains
+  if (KIND == kKitaev) sp += (size_t)jb.nc * kitaev_work_bytes(N);
   uint32_t* planes = (uint32_t*)sp;
 
   Grp g;
@@ -158,6 +145,28 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   g.c = ltile * jb.nc + g.gl;
   g.active = g.c < jb.n_chains;
   g.cid = (uint32_t)(jb.cid_base + (uint64_t)g.c);
+  KitaevWork wk;
+  double* eps_st = nullptr;     // Kitaev local sweeps: spectrum of the proposed lattice
+  if (KIND == kKitaev) {
+    unsigned char* kp = kwork + (size_t)g.gl * kitaev_work_bytes(N);
+    wk.A = (double*)kp;
+    kp += align16((size_t)N * (N + 1) / 2 * 8);
+    wk.d = (double*)kp;
+    kp += align16((size_t)N * 8);
+    wk.e = (double*)kp;
+    kp += align16((size_t)N * 8);
+    wk.vv = (double*)kp;
+    kp += align16((size_t)N * 8);
+    wk.pw = (double*)kp;
+    kp += align16((size_t)N * 8);
+    wk.sc = (double*)kp;
+    kp += align16(64 * 8);
+    wk.d32 = (float*)kp;
+    kp += align16((size_t)N * 4);
+    wk.e32 = (float*)kp;
+    kp += align16((size_t)N * 4);
+    eps_st = (double*)kp;
+  }
   uint32_t* my = planes + (size_t)g.gl * (2 + K) * P;
   ChainSm& ch = cs[g.gl];
 
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
-      kitaev_logpi64(my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+      kitaev_logpi64(g, my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     if (g.active && g.r == 0) {
       double Fb = 0.0;
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
-      kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+      kitaev_logpi64(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     // the physical chain's lattice into the first hidden plane (free now)
     if (g.active)
@@ -408,23 +417,24 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         nacc += ising_colour(jb, g, v, step, 1, ch.thr);
         __syncthreads();
       } else {
-        // one chain per CTA: every branch below is CTA-uniform
+        // per chain group: every branch below is uniform in the group, and only
+        // the group synchronises (a short last tile has groups without a chain)
         for (int n = 0; n < N; ++n) {
           const uint32_t* v = my + ch.cur * P;
           uint32_t* vp = my + (ch.cur ^ 1) * P;
-          for (int w = tid; w < jb.Wd; w += NT) vp[w] = v[w] ^ ((w == (n >> 5)) ? (1u << (n & 31)) : 0u);
-          __syncthreads();
+          for (int w = g.r; w < jb.Wd; w += g.tpc) vp[w] = v[w] ^ ((w == (n >> 5)) ? (1u << (n & 31)) : 0u);
+          grp_sync(g);
           double kr[4] = {0.0, 0.0, 0.0, 0.0};
           if (PREC == kMixed) {
-            kitaev_logpi_df(vp, jb.L, jb.J, ch.beta, wk, kr, jb.lc_edge > 0);
+            kitaev_logpi_df(g, vp, jb.L, jb.J, ch.beta, wk, kr, jb.lc_edge > 0);
           } else {
             double k3[3];
-            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k3, eps_st, jb.lc_edge > 0);
+            kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k3, eps_st, jb.lc_edge > 0);
             kr[0] = k3[0];
             kr[1] = k3[1];
             kr[2] = k3[2];
           }
-          if (tid == 0) {
+          if (g.r == 0) {
             const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(n >> 2), kTagLocal, step, g.cid), jb.rk);
             const double logu = log(((double)pick(w, n & 3) + 0.5) * 0x1p-32);
             const double logr = kr[0] - ch.lp;
@@ -442,15 +452,15 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               else ch.flag_rec = 1;
             }
           }
-          __syncthreads();
+          grp_sync(g);
           if (PREC == kMixed && ch.flag_rec) {
             // the FP64 eigen-stage of the proposal (and of the current lattice
             // when its log-weight came from the df64 stage)
             double k1v[3], k0v[3] = {0.0, 0.0, 0.0};
             const bool redo_v = ch.lpb != 0.0;
-            kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st, jb.lc_edge > 0);
-            if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
-            if (tid == 0) {
+            kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st, jb.lc_edge > 0);
+            if (redo_v) kitaev_logpi64(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
+            if (g.r == 0) {
               ch.lpp = k1v[0];
               ch.lppb = 0.0;
               ch.Ep = k1v[1];
@@ -464,14 +474,14 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               ch.flag_acc = logu < ch.lpp - ch.lp;
               ch.rec_mh += 1ull;
             }
-            __syncthreads();
+            grp_sync(g);
           }
           if (ch.flag_acc) {
             // the spectrum cache follows the lattice when the proposal's came from the FP64 stage
-            if (PREC == kFP64 || ch.flag_rec)
-              for (int l = tid; l < N; l += NT) jb.eps[(size_t)g.c * N + l] = eps_st[l];
-            __syncthreads();
-            if (tid == 0) {
+            if (g.active && (PREC == kFP64 || ch.flag_rec))
+              for (int l = g.r; l < N; l += g.tpc) jb.eps[(size_t)g.c * N + l] = eps_st[l];
+            grp_sync(g);
+            if (g.r == 0) {
               ch.cur ^= 1;
               ch.lp = ch.lpp;
               ch.lpb = ch.lppb;
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               ch.acc += 1ull;
             }
           }
-          __syncthreads();
+          grp_sync(g);
         }
       }
       // observables of the lattice after the sweep
@@ -558,10 +568,10 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     double kr[4] = {0.0, 0.0, 0.0, 0.0};
     if (KIND == kKitaev) {
       if (PREC == kMixed) {
-        kitaev_logpi_df(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr, jb.lc_edge > 0);
+        kitaev_logpi_df(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr, jb.lc_edge > 0);
       } else {
         double k3[3];
-        kitaev_logpi64(vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3, nullptr, jb.lc_edge > 0);
+        kitaev_logpi64(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3, nullptr, jb.lc_edge > 0);
         kr[0] = k3[0];
         kr[1] = k3[1];
         kr[2] = k3[2];
@@ -655,12 +665,13 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         free_energy64(jb, tb64g, g3, v, f2);
         grp_reduce<4>(f2, g3, scratch);
         // Kitaev: the FP64 eigen-stage of v' (and of v when its log-weight
-        // came from the df64 stage); one chain per CTA, so this is CTA-uniform
+        // came from the df64 stage), run by every chain group of the CTA
+        // (`need` is CTA-wide; groups without a recompute discard the result)
         double k1v[3] = {0.0, 0.0, 0.0}, k0v[3] = {0.0, 0.0, 0.0};
         const bool redo_v = ch.lpb != 0.0;
         if (KIND == kKitaev) {
-          kitaev_logpi64(vp, jb.L, jb.J, ch.beta, wk, k1v, nullptr, jb.lc_edge > 0);
-          if (redo_v) kitaev_logpi64(v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
+          kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k1v, nullptr, jb.lc_edge > 0);
+          if (redo_v) kitaev_logpi64(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
         }
         if (g2.active && g.r == 0) {
           ch.Fp = -jb.vb * f1[2] - f1[0];

@@ -56,28 +56,57 @@ def test_batch_equals_each_job_alone(ctx, prec):
         b.release()
 
 
-def test_kitaev_batch_of_mixed_sizes_equals_alone(ctx):
-    """Kitaev jobs of small and large matrices (different CTA sizes) batched."""
-    from paper_2008_05401_gb300 import KITAEV, MIXED
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kitaev_batch_of_mixed_sizes_equals_alone(ctx, prec):
+    """Kitaev jobs of small and large matrices (chain groups of 32, 64, 128
+    and 256 threads; several chains per CTA and short last tiles) in one
+    launch give every job the results it has alone."""
+    from paper_2008_05401_gb300 import KITAEV
     W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=3)
     mid = ctx.load_model(KITAEV, W, vb, hb)
-    spec = [(4, 5, 0), (6, 7, 100), (10, 3, 200)]
+    spec = [(4, 5, 0), (6, 7, 100), (10, 3, 200), (12, 2, 300), (8, 9, 400)]
 
     def make():
         return [ctx.new_job(mid, KITAEV, L, wl.kitaev_ladder(n, 24), (1.0, 1.0, 1.0), SEED, base,
                             wl.pack_bits(wl.random_lattices(n, L, seed=L)), MIXED) for L, n, base in spec]
 
     batch = make()
-    ctx.run_batch(batch, 3, precision=MIXED)
+    ctx.run_batch(batch, 3, precision=prec)
     alone = make()
     for j in alone:
-        j.run(3, precision=MIXED)
+        j.run(3, precision=prec)
     for a, b in zip(batch, alone):
         sa, sb = _snapshot(a), _snapshot(b)
         for key in sa:
             np.testing.assert_array_equal(sa[key], sb[key], err_msg=key)
         a.release()
         b.release()
+
+
+@pytest.mark.parametrize("L,prec", [(6, 1), (4, 0)])
+def test_autotuned_kitaev_groups_keep_parity(ctx, L, prec):
+    """crbm_tune picks the chains (thread groups) per CTA of a Kitaev shape;
+    a job created afterwards, with a short last tile, reproduces the oracle."""
+    from _common import decisions_are_clear, oracle_chains, run_oracle
+    from paper_2008_05401_gb300 import KITAEV
+    W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=9)
+    mid = ctx.load_model(KITAEV, W, vb, hb)
+    nc, us = ctx.tune(mid, L, prec)
+    assert nc in (1, 2, 4, 8) and us > 0
+    n, S, J = 2 * nc + 3, 3, (1.0, 1.0, 1.0)
+    T = wl.kitaev_ladder(n, 24)
+    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=45))
+    job = ctx.new_job(mid, KITAEV, L, T, J, SEED, 0, bits0, prec)
+    job.run(S, precision=prec)
+    ref = oracle_chains("kitaev", W, hb, vb, L, T, J, SEED, n, bits0)
+    worst = run_oracle(ref, S)
+    if decisions_are_clear(worst):
+        np.testing.assert_array_equal(job.state()[0], wl.pack_bits(ref.v))
+        np.testing.assert_array_equal(job.observables()[1], ref.accepts)
+        lp, F, E = job.energies()
+        np.testing.assert_allclose(lp, ref.logpi, rtol=1e-10, atol=1e-9)
+        np.testing.assert_allclose(F, ref.F, rtol=1e-10, atol=1e-10)
+    job.release()
 
 
 def test_split_runs_and_checkpoint_resume(ctx):
