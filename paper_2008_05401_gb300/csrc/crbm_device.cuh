@@ -338,6 +338,12 @@ __device__ __forceinline__ void grp_reduce(double (&x)[NV], const Grp& g, double
   }
 }
 
+// grp_reduce for a warp-aligned group with scratch of its own (NV * tpc / 32
+// doubles), synchronising only the group: the same order of additions, the
+// result valid in the leader (r == 0).
+template <int NV>
+__device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, double* scratch);
+
 // Barrier of one chain's thread group (warp-aligned groups of 32 .. blockDim
 // threads): the CTA barrier when the group is the whole CTA, the warp's when it
 // is one warp, else a named barrier of its own (id 1 + group index; a CTA holds
@@ -368,6 +374,31 @@ __device__ __forceinline__ double grp_sum(double x, const Grp& g, double* scratc
   for (int w = 0; w < nw; ++w) s += scratch[w];
   grp_sync(g);
   return s;
+}
+
+template <int NV>
+__device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, double* scratch) {
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] += __shfl_xor_sync(kFull, x[v], o);
+  }
+  if (g.tpc > 32) {
+    const int warp = g.r >> 5;
+    if ((g.r & 31) == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) scratch[warp * NV + v] = x[v];
+    }
+    grp_sync(g);
+    if (g.r == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0;
+        for (int w = 0; w < g.tpc / 32; ++w) s += scratch[w * NV + v];
+        x[v] = s;
+      }
+    }
+    grp_sync(g);
+  }
 }
 
 // Deterministic block-wide sum, result returned to every thread.

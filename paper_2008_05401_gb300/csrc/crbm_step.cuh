@@ -544,6 +544,18 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   }
 
   if (AUX) return;
+  // The Kitaev kind's chain groups are warp-aligned and independent inside
+  // the proposal loop: they synchronise and reduce on their own (a group whose
+  // eigen-stage takes longer holds back no other chain of the CTA); the Ising
+  // kind's groups may be smaller than a warp and use the CTA barrier.
+  auto loop_sync = [&]() {
+    if (KIND == kKitaev) grp_sync(g);
+    else __syncthreads();
+  };
+  auto loop_reduce4 = [&](double (&x)[4], const Grp& gg) {
+    if (KIND == kKitaev) grp_reduce_local<4>(x, gg, wk.sc);
+    else grp_reduce<4>(x, gg, scratch);
+  };
   const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
   // the step counter lives in device memory (advanced by advance_steps after
   // the launch), so a captured CUDA graph can be replayed
@@ -557,14 +569,14 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     const uint32_t* src = v;
     for (int sub = 0; sub < prm.g; ++sub) {
       hidden_phase<PREC, KC, kC>(jb, tb, g, src, h, P, step, sub, nrec);
-      __syncthreads();
+      loop_sync();
       visible_phase<PREC, KC, kC>(jb, tb, g, h, vp, P, step, sub, nrec);
-      __syncthreads();
+      loop_sync();
       src = vp;
     }
     double fo[4];
     free_phase<PREC, KC, kC>(jb, tb, g, vp, fo);
-    grp_reduce<4>(fo, g, scratch);
+    loop_reduce4(fo, g);
     double kr[4] = {0.0, 0.0, 0.0, 0.0};
     if (KIND == kKitaev) {
       if (PREC == kMixed) {
@@ -646,7 +658,13 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
       }
     }
     if (PREC == kMixed) {
-      const int need = __syncthreads_or(g.active && g.r == 0 && ch.flag_rec);
+      int need;
+      if (KIND == kKitaev) {
+        loop_sync();                 // the leader's flag_rec, read by its whole group
+        need = g.active && ch.flag_rec;
+      } else {
+        need = __syncthreads_or(g.active && g.r == 0 && ch.flag_rec);
+      }
       if (need) {
         // the FP64 path's free energies of v' (and of v when only its FP32
         // value is known), computed by the same code and reduction order
@@ -658,15 +676,14 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         g2.active = g.active && ch.flag_rec;
         double f1[4];
         free_energy64(jb, tb64g, g2, vp, f1);
-        grp_reduce<4>(f1, g2, scratch);
+        loop_reduce4(f1, g2);
         Grp g3 = g2;
         g3.active = g2.active && ch.Fb != 0.0;
         double f2[4];
         free_energy64(jb, tb64g, g3, v, f2);
-        grp_reduce<4>(f2, g3, scratch);
+        loop_reduce4(f2, g3);
         // Kitaev: the FP64 eigen-stage of v' (and of v when its log-weight
-        // came from the df64 stage), run by every chain group of the CTA
-        // (`need` is CTA-wide; groups without a recompute discard the result)
+        // came from the df64 stage), by the group that needs it
         double k1v[3] = {0.0, 0.0, 0.0}, k0v[3] = {0.0, 0.0, 0.0};
         const bool redo_v = ch.lpb != 0.0;
         if (KIND == kKitaev) {
@@ -712,7 +729,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
       for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
       trace_store(jb, g.c, step0 + (uint64_t)s, ch.E);
     }
-    __syncthreads();
+    loop_sync();
   }
 
   if (nrec) atomicAdd(&ch.rec, (unsigned long long)nrec);

@@ -1,13 +1,14 @@
 // Exhaustive check of the special-function approximations the mixed-precision
-// path certifies its margins with (ex2, rcp, lg2 in crbm_device.cuh): every
-// float of the tested range is evaluated and the largest error against an
-// FP64 reference is returned.  Test-suite helper, not part of the library.
+// path certifies its margins with (ex2, rcp, lg2 in crbm_device.cuh), and of
+// the FP32 conditional sigma(x) they compose: every float of the tested range
+// is evaluated and the largest error against an FP64 reference is returned.
+// Test-suite helper, not part of the library.
 #include <cstdint>
 #include <cstring>
 #include "crbm_device.cuh"
 
 namespace {
-__device__ unsigned long long g_max[3];
+__device__ unsigned long long g_max[4];
 
 __device__ void fold(int slot, double err) {
   // non-negative doubles order like their bit patterns
@@ -27,8 +28,11 @@ __global__ void sweep(int which, uint32_t b0, uint32_t b1) {
     } else if (which == 1) {
       const double ref = 1.0 / (double)x;
       err = fabs((double)crbm::rcp_approx(x) - ref) / ref;
-    } else {
+    } else if (which == 2) {
       err = fabs((double)crbm::lg2_approx(x) - log2((double)x));
+    } else {
+      const double ref = 1.0 / (1.0 + exp(-(double)x));
+      err = fabs((double)crbm::sigmoid32(x) - ref) / ref;
     }
     worst = fmax(worst, err);
   }
@@ -37,11 +41,12 @@ __global__ void sweep(int which, uint32_t b0, uint32_t b1) {
 }  // namespace
 
 extern "C" int sfu_max_error(int which, uint32_t b0, uint32_t b1, double* out) {
-  unsigned long long zero[3] = {0, 0, 0};
+  if (which < 0 || which > 3) return -4;
+  unsigned long long zero[4] = {0, 0, 0, 0};
   if (cudaMemcpyToSymbol(g_max, zero, sizeof zero) != cudaSuccess) return -1;
   sweep<<<1216, 256>>>(which, b0, b1);
   if (cudaDeviceSynchronize() != cudaSuccess) return -2;
-  unsigned long long h[3];
+  unsigned long long h[4];
   if (cudaMemcpyFromSymbol(h, g_max, sizeof h) != cudaSuccess) return -3;
   std::memcpy(out, &h[which], sizeof(double));
   return 0;

@@ -68,7 +68,7 @@ def test_kitaev_batch_of_mixed_sizes_equals_alone(ctx, prec):
 
     def make():
         return [ctx.new_job(mid, KITAEV, L, wl.kitaev_ladder(n, 24), (1.0, 1.0, 1.0), SEED, base,
-                            wl.pack_bits(wl.random_lattices(n, L, seed=L)), MIXED) for L, n, base in spec]
+                            wl.pack_bits(wl.random_lattices(n, L, seed=L)), prec) for L, n, base in spec]
 
     batch = make()
     ctx.run_batch(batch, 3, precision=prec)

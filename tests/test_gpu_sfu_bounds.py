@@ -4,7 +4,9 @@ The library assumes (host constants of crbm_load_model): ex2.approx relative
 error <= 2^-22 on the arguments it receives, rcp.approx relative error <=
 2^-23, lg2.approx absolute error <= 2^-22 on [1, 2].  Each is checked here on
 EVERY float of its range against FP64, so the assumption is a measured fact
-of the device the tests run on.
+of the device the tests run on.  So is the precision of the mixed path's
+conditionals: the FP32 sigmoid those units compose is within 1e-6 relative of
+the FP64 one wherever sigma >= 1.1e-7, and within 1.1e-6 down to 2^-32.
 """
 import ctypes
 import os
@@ -60,3 +62,14 @@ def test_rcp_relative_error(lib):
 def test_lg2_absolute_error_on_1_2(lib):
     worst = _max_err(lib, 2, _bits(1.0), _bits(2.0) + 1)
     assert worst <= 2.0 ** -22, worst
+
+
+def test_fp32_conditional_relative_error(lib):
+    # every float of [-16, 40] (sigma >= 1.1e-7; above 40 both sides give 1):
+    # within 1e-6 relative.  Down to sigma = 2^-32 (x = -22.18; a uniform
+    # (w + 1/2) 2^-32 never falls below it) the FP32 product x log2(e) adds up
+    # to |x| 2^-24 ln 2 relative: within 1.1e-6.  (Decisions are certified on
+    # the absolute error and take the FP64 path's result either way.)
+    assert _max_err(lib, 3, _bits(0.0), _bits(40.0)) <= 1e-6
+    assert _max_err(lib, 3, _bits(-0.0), _bits(-16.0)) <= 1e-6
+    assert _max_err(lib, 3, _bits(-0.0), _bits(-22.18)) <= 1.1e-6
