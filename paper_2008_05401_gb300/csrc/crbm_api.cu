@@ -47,6 +47,7 @@ struct Layout {
 struct Job {
   bool live = false;
   int model = -1, kind = 0, L = 0, N = 0, Wd = 0, n = 0, nc = 1, tiles = 0;
+  int tpc = 0;   // Kitaev: threads of each chain's group (chains per CTA follow per launch)
   double J[3] = {1.0, 1.0, 1.0};
   uint64_t seed = 0, cid_base = 0, step = 0;
   unsigned char* mem = nullptr;
@@ -102,11 +103,10 @@ bool valid_L(int kind, int L) {
   return false;
 }
 
-// Chains per CTA: Kitaev, 256 threads over the chain groups of
-// kitaev_group_threads; Ising, about two 4-site units per thread, a power of
-// two in [1, 32].
+// Chains per CTA of an Ising job: about two 4-site units per thread, a power
+// of two in [1, 32].  (A Kitaev job's follow from its group size per launch.)
 int chains_per_tile(int kind, int L) {
-  if (kind == kKitaev) return kThreads / kitaev_group_threads(L * L);
+  if (kind == kKitaev) return 1;
   const int nblk = (L * L + 3) / 4;
   int nc = 1;
   while (nc < kThreads / 8 && (nc * 2) * nblk <= 2 * kThreads) nc *= 2;
@@ -258,15 +258,23 @@ static JobDev make_jobdev(const crbm_ctx* ctx, const Job& j) {
 }
 
 // Launch the fused kernel for a set of jobs (same kind and filter shape);
-// mode 1 = evaluate.  A job's chains per CTA (and so the threads of each
-// chain's group and its per-chain reduction order -- hence every bit of its
-// results) depend only on its own lattice, so the job gives the same results
-// alone or batched.  The jobs' tiles are laid out by decreasing lattice side,
-// so that the longest tiles start first and the short ones fill the end.
+// mode 1 = evaluate.  The threads of a chain's group (Ising: the job's chains
+// per 256-thread CTA; Kitaev: the job's group size) -- and so its per-chain
+// reduction order and every bit of its results -- depend only on the job, so
+// it gives the same results alone or batched.  A Kitaev launch takes CTAs of
+// the largest group size among its jobs, each job as many chains per CTA as
+// its groups fill: small matrices alone run in small CTAs, a batch of mixed
+// sizes in one launch.  The jobs' tiles are laid out by decreasing lattice
+// side, so that the longest tiles start first and the short ones fill the end.
 static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int correct, int prec,
                         int mode, int nt, cudaStream_t st, const Job* partner = nullptr) {
   if (!partner)
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ctx->jobs[a].L > ctx->jobs[b].L; });
+  const bool kitaev = !ids.empty() && ctx->jobs[ids[0]].kind == kKitaev;
+  if (kitaev) {
+    nt = 32;
+    for (int id : ids) nt = std::max(nt, ctx->jobs[id].tpc);
+  }
   LaunchParams p;
   memset(&p, 0, sizeof p);
   p.n_jobs = (int)ids.size();
@@ -285,7 +293,9 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
     kind = j.kind;
     p.tile_begin[i] = tiles;
     p.job[i] = make_jobdev(ctx, j);
-    tiles += j.tiles;
+    const int nc = kitaev ? nt / j.tpc : j.nc;
+    p.job[i].nc = nc;
+    tiles += kitaev ? (j.n + nc - 1) / nc : j.tiles;
     if (m.edge && prec != kFP64) return fail(ctx, CRBM_EINVAL, "LCRBM models run in CRBM_FP64 only");
     int KC, kC;
     specialisation(m.K, m.k, KC, kC);
@@ -293,7 +303,7 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
       KC = kC = 0;                // the class tables are read by the runtime-shape code
       generic = true;
     }
-    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, KC, m.ncls);
+    const size_t b = smem_bytes(j.kind, prec, j.L, m.K, m.k, nc, KC, m.ncls);
     if (b > smem) smem = b;
     K = m.K;
     k = m.k;
@@ -307,7 +317,7 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
     for (size_t i = 0; i < ids.size(); ++i) {
       const Job& j = ctx->jobs[ids[i]];
       const Model& m = ctx->models[j.model];
-      smem = std::max(smem, smem_bytes(j.kind, prec, j.L, m.K, m.k, j.nc, 0, m.ncls));
+      smem = std::max(smem, smem_bytes(j.kind, prec, j.L, m.K, m.k, p.job[i].nc, 0, m.ncls));
     }
   }
   CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st, generic), "kernel launch");
@@ -823,9 +833,11 @@ int crbm_init_chains(crbm_ctx* ctx, int model_id, int L, int n_chains, const dou
   j.Wd = (j.N + 31) / 32;
   j.n = n_chains;
   j.nc = chains_per_tile(m.kind, L);
+  if (m.kind == kKitaev) j.tpc = kitaev_group_threads(j.N);
   {
+    // crbm_tune's choice: chains per CTA (Ising) or the group size (Kitaev)
     const auto it = ctx->tuned.find(std::make_tuple(m.kind, L, m.K, m.k));
-    if (it != ctx->tuned.end()) j.nc = it->second;
+    if (it != ctx->tuned.end()) (m.kind == kKitaev ? j.tpc : j.nc) = it->second;
   }
   j.tiles = (n_chains + j.nc - 1) / j.nc;
   if (m.kind == kIsing) {
@@ -1226,11 +1238,9 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
           smem_bytes(m.kind, precision, L, m.K, m.k, nc, m.K == 4 ? 4 : 0) <= 100 * 1024)
         cand.push_back(nc);
   } else {
-    // chain groups of 256 / nc threads (at least a warp), as many as fit the shared memory
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    for (int nc = 1; nc <= kThreads / 32; nc *= 2)
-      if (smem_bytes(m.kind, precision, L, m.K, m.k, nc, m.K == 4 ? 4 : 0) <= (size_t)optin) cand.push_back(nc);
+    // group sizes 256 / nc threads (at least a warp); timed alone, a job runs
+    // one chain per CTA of its group size
+    for (int nc = 1; nc <= kThreads / 32; nc *= 2) cand.push_back(nc);
   }
   // a temporary job large enough for every candidate to fill the GPU
   const int n_chains = 4 * sms * cand.back();
@@ -1263,8 +1273,14 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
   float best_t = 1e30f;
   for (int nc : cand) {
     Job& jj = ctx->jobs[id];
-    jj.nc = nc;
-    jj.tiles = (n_chains + nc - 1) / nc;
+    if (m.kind == kKitaev) {
+      jj.tpc = kThreads / nc;
+      jj.nc = 1;
+      jj.tiles = n_chains;
+    } else {
+      jj.nc = nc;
+      jj.tiles = (n_chains + nc - 1) / nc;
+    }
     if ((rc = launch_jobs(ctx, {id}, 0, 1, 1, kFP64, 1, ctx->own))) break;        // F, log pi of the state
     if ((rc = launch_jobs(ctx, {id}, 2, 1, 1, precision, 0, ctx->own))) break;    // warm-up
     cudaEventRecord(e0, ctx->own);
@@ -1285,7 +1301,7 @@ int crbm_tune(crbm_ctx* ctx, int model_id, int L, int precision, int* best_nc, d
   ctx->jobs[id].live = false;
   cudaFree(mem);
   if (rc) return rc;
-  ctx->tuned[std::make_tuple(m.kind, L, m.K, m.k)] = best;
+  ctx->tuned[std::make_tuple(m.kind, L, m.K, m.k)] = m.kind == kKitaev ? kThreads / best : best;
   if (best_nc) *best_nc = best;
   if (best_ms) *best_ms = (double)best_t * 1e3 / 4.0;     // microseconds per chain-proposal
   return CRBM_OK;

@@ -42,8 +42,20 @@ cudaError_t launch_kIsing_kMixed_256(int, int, const LaunchParams&, int, size_t,
 cudaError_t limit_kIsing_kMixed_256(size_t);
 cudaError_t launch_kKitaev_kFP64_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kKitaev_kFP64_256(size_t);
+cudaError_t launch_kKitaev_kFP64_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_128(size_t);
+cudaError_t launch_kKitaev_kFP64_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_64(size_t);
+cudaError_t launch_kKitaev_kFP64_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_32(size_t);
 cudaError_t launch_kKitaev_kMixed_256(int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kKitaev_kMixed_256(size_t);
+cudaError_t launch_kKitaev_kMixed_128(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_128(size_t);
+cudaError_t launch_kKitaev_kMixed_64(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_64(size_t);
+cudaError_t launch_kKitaev_kMixed_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_32(size_t);
 
 void specialisation(int K, int k, int& KC, int& kC) {
   KC = 0;
@@ -54,9 +66,10 @@ void specialisation(int K, int k, int& KC, int& kC) {
   }
 }
 
-// Every job runs in CTAs of 256 threads, so jobs of any lattice side share one
-// launch.  A Kitaev chain's eigen-stage is run by a thread group of its own
-// (kitaev_group_threads), several groups per CTA for small matrices.
+// Ising jobs run in CTAs of 256 threads.  A Kitaev chain is run by a thread
+// group of its own (kitaev_group_threads or its tuned size); a launch of
+// Kitaev jobs takes CTAs of the largest group size among them, so jobs of
+// every lattice side share one launch, several small chains per CTA.
 int threads_for(int, int) { return 256; }
 
 // Threads of a Kitaev chain's group, measured on the Kitaev workloads when
@@ -72,15 +85,28 @@ cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchPa
   if (kind == kIsing)
     return prec == kFP64 ? launch_kIsing_kFP64_256(KC, kC, p, grid, smem, st)
                          : launch_kIsing_kMixed_256(KC, kC, p, grid, smem, st);
-  (void)nt;
-  return prec == kFP64 ? launch_kKitaev_kFP64_256(KC, kC, p, grid, smem, st)
-                       : launch_kKitaev_kMixed_256(KC, kC, p, grid, smem, st);
+  if (prec == kFP64) {
+    switch (nt) {
+      case 32: return launch_kKitaev_kFP64_32(KC, kC, p, grid, smem, st);
+      case 64: return launch_kKitaev_kFP64_64(KC, kC, p, grid, smem, st);
+      case 128: return launch_kKitaev_kFP64_128(KC, kC, p, grid, smem, st);
+      default: return launch_kKitaev_kFP64_256(KC, kC, p, grid, smem, st);
+    }
+  }
+  switch (nt) {
+    case 32: return launch_kKitaev_kMixed_32(KC, kC, p, grid, smem, st);
+    case 64: return launch_kKitaev_kMixed_64(KC, kC, p, grid, smem, st);
+    case 128: return launch_kKitaev_kMixed_128(KC, kC, p, grid, smem, st);
+    default: return launch_kKitaev_kMixed_256(KC, kC, p, grid, smem, st);
+  }
 }
 
 cudaError_t set_smem_limits(size_t bytes) {
   cudaError_t e = cudaSuccess;
   for (cudaError_t (*f)(size_t) : {limit_kIsing_kFP64_256, limit_kIsing_kMixed_256, limit_kKitaev_kFP64_256,
-                                   limit_kKitaev_kMixed_256})
+                                   limit_kKitaev_kFP64_128, limit_kKitaev_kFP64_64, limit_kKitaev_kFP64_32,
+                                   limit_kKitaev_kMixed_256, limit_kKitaev_kMixed_128, limit_kKitaev_kMixed_64,
+                                   limit_kKitaev_kMixed_32})
     if (e == cudaSuccess) e = f(bytes);
   return e;
 }

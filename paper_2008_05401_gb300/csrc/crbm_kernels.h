@@ -14,7 +14,8 @@ void specialisation(int K, int k, int& KC, int& kC);
 // Dynamic shared memory of one CTA of the fused kernel (ncls kernel classes
 // in the tables: 1 for a CRBM, 2 edge + 1 for an LCRBM).
 size_t smem_bytes(int kind, int prec, int L, int K, int k, int nc, int KC, int ncls = 1);
-// Threads per CTA of a job: 256 for every kind and lattice.
+// Threads per CTA of an Ising launch: 256 (a Kitaev launch takes the largest
+// group size of its jobs, see kitaev_group_threads).
 int threads_for(int kind, int max_N);
 // Default threads of one Kitaev chain's group (its eigen-stage): 32 up to 16
 // cells, 64 up to 64, 128 up to 100, else 256 (measured: small groups wait

@@ -1,0 +1,6 @@
+// Instantiations of the fused kernel for Kitaev / FP64, CTAs of 32 threads.
+#include "crbm_step.cuh"
+
+namespace crbm {
+CRBM_VARIANTS_NT(kKitaev, kFP64, 32)
+}  // namespace crbm

@@ -1,0 +1,6 @@
+// Instantiations of the fused kernel for Kitaev / Mixed, CTAs of 32 threads.
+#include "crbm_step.cuh"
+
+namespace crbm {
+CRBM_VARIANTS_NT(kKitaev, kMixed, 32)
+}  // namespace crbm
