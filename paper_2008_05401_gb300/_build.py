@@ -28,7 +28,9 @@ SOURCES = ["crbm_kernels.cu", "crbm_api.cu", "crbm_tempering.cu", "crbm_analysis
            "crbm_step_kitaev_mixed_t256.cu",
            "crbm_step_kitaev_mixed_t128.cu",
            "crbm_step_kitaev_mixed_t64.cu",
-           "crbm_step_kitaev_mixed_t32.cu"]
+           "crbm_step_kitaev_mixed_t32.cu",
+           "crbm_step_kitaev_fp64_t256_multi.cu",
+           "crbm_step_kitaev_mixed_t256_multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -271,9 +271,18 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
   if (!partner)
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ctx->jobs[a].L > ctx->jobs[b].L; });
   const bool kitaev = !ids.empty() && ctx->jobs[ids[0]].kind == kKitaev;
+  bool multi = false;
   if (kitaev) {
+    // one chain per CTA of its group size when every job has the same;
+    // otherwise CTAs of 256 threads holding several groups (proposals only:
+    // the other modes run one job at a time)
     nt = 32;
     for (int id : ids) nt = std::max(nt, ctx->jobs[id].tpc);
+    for (int id : ids) multi = multi || ctx->jobs[id].tpc != nt;
+    if (multi) {
+      if (mode != 0) return fail(ctx, CRBM_EINVAL, "jobs of different group sizes in a mode-%d launch", mode);
+      nt = kThreads;
+    }
   }
   LaunchParams p;
   memset(&p, 0, sizeof p);
@@ -320,7 +329,7 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
       smem = std::max(smem, smem_bytes(j.kind, prec, j.L, m.K, m.k, p.job[i].nc, 0, m.ncls));
     }
   }
-  CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st, generic), "kernel launch");
+  CK(launch_step(kind, prec, K, k, nt, p, tiles, smem, st, generic, multi), "kernel launch");
   return CRBM_OK;
 }
 

@@ -341,16 +341,19 @@ __device__ __forceinline__ void grp_reduce(double (&x)[NV], const Grp& g, double
 // grp_reduce for a warp-aligned group with scratch of its own (NV * tpc / 32
 // doubles), synchronising only the group: the same order of additions, the
 // result valid in the leader (r == 0).
-template <int NV>
+template <int NV, bool MULTI>
 __device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, double* scratch);
 
 // Barrier of one chain's thread group (warp-aligned groups of 32 .. blockDim
 // threads): the CTA barrier when the group is the whole CTA, the warp's when it
 // is one warp, else a named barrier of its own (id 1 + group index; a CTA holds
 // at most 8 groups).  Only the group's threads take part, so groups may run
-// different branches between two of their barriers.
+// different branches between two of their barriers.  MULTI = false: the
+// caller's CTAs hold one group each, and this is the CTA barrier (code without
+// named barriers, which would reserve all of the CTA's barrier slots).
+template <bool MULTI>
 __device__ __forceinline__ void grp_sync(const Grp& g) {
-  if (g.tpc == (int)blockDim.x) {
+  if (!MULTI || g.tpc == (int)blockDim.x) {
     __syncthreads();
   } else if (g.tpc == 32) {
     __syncwarp();
@@ -363,20 +366,22 @@ __device__ __forceinline__ void grp_sync(const Grp& g) {
 // thread of it: a butterfly within each warp, then the warps' partials added
 // in warp order -- the order of block_sum for a CTA of tpc threads, so a group
 // gives the same bits as a CTA of its size.  scratch: 32 doubles of the group.
+template <bool MULTI>
 __device__ __forceinline__ double grp_sum(double x, const Grp& g, double* scratch) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
-  const int warp = g.r >> 5, nw = g.tpc >> 5;
-  grp_sync(g);
-  if ((g.r & 31) == 0) scratch[warp] = x;
-  grp_sync(g);
+  const int r = MULTI ? g.r : (int)threadIdx.x, tpc = MULTI ? g.tpc : (int)blockDim.x;
+  const int warp = r >> 5, nw = tpc >> 5;
+  grp_sync<MULTI>(g);
+  if ((r & 31) == 0) scratch[warp] = x;
+  grp_sync<MULTI>(g);
   double s = 0.0;
   for (int w = 0; w < nw; ++w) s += scratch[w];
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   return s;
 }
 
-template <int NV>
+template <int NV, bool MULTI>
 __device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, double* scratch) {
   for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
@@ -388,7 +393,7 @@ __device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, 
 #pragma unroll
       for (int v = 0; v < NV; ++v) scratch[warp * NV + v] = x[v];
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     if (g.r == 0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -397,7 +402,7 @@ __device__ __forceinline__ void grp_reduce_local(double (&x)[NV], const Grp& g, 
         x[v] = s;
       }
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
   }
 }
 
@@ -1056,11 +1061,13 @@ __device__ __forceinline__ void thermal_add(double eps, double beta, double& lp,
 // open_cols: the lattice is open along j (the y-bonds from column L-1 to
 // column 0 are absent), the physics of the LCRBM's open boundary conditions.
 // Run by the chain's thread group g (warp-aligned) with its own work areas wk;
-// every thread of the group calls, and only the group synchronises.
+// every thread of the group calls, and only the group synchronises (MULTI:
+// see grp_sync).
+template <bool MULTI>
 __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, const double* J, double beta,
                                const KitaevWork& wk, double (&res)[3], double* eps_out = nullptr,
                                bool open_cols = false) {
-  const int N = L * L, tid = g.r, nt = g.tpc;
+  const int N = L * L, tid = MULTI ? g.r : (int)threadIdx.x, nt = MULTI ? g.tpc : (int)blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   double* A = wk.A;
   const double tx = 2.0 * J[0], ty = 2.0 * J[1], tz = 2.0 * J[2];
@@ -1086,7 +1093,7 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
       if (wy <= w && !(open_cols && bj + 1 == L)) row[wy] += mw * ty;
     }
   }
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1.
   // Only the lower triangle of the trailing block is read and updated.
   for (int j = 0; j < N - 2; ++j) {
@@ -1096,12 +1103,12 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
       const double a = A[tri(i, j)];
       s += a * a;
     }
-    s = grp_sum(s, g, wk.sc);
+    s = grp_sum<MULTI>(s, g, wk.sc);
     const double x0 = A[tri(j + 1, j)];
     if (tid == 0) wk.d[j] = A[tri(j, j)];
     if (s == 0.0) {
       if (tid == 0) wk.e[j] = x0;
-      grp_sync(g);
+      grp_sync<MULTI>(g);
       continue;
     }
     const double nrm = sqrt(x0 * x0 + s);
@@ -1110,7 +1117,7 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     const double tau = 2.0 / (v0 * v0 + s);
     if (tid == 0) wk.e[j] = alpha;
     for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     // p = tau * A22 v from the lower triangle (row part c <= l, column part c > l), one warp per row
     for (int l = warp; l < m; l += nw) {
       double acc = 0.0;
@@ -1122,20 +1129,20 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
       if (lane == 0) wk.pw[l] = tau * acc;
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     double pv = 0.0;
     for (int l = tid; l < m; l += nt) pv = fma(wk.pw[l], wk.vv[l], pv);
-    pv = grp_sum(pv, g, wk.sc);
+    pv = grp_sum<MULTI>(pv, g, wk.sc);
     const double Kc = 0.5 * tau * pv;
     for (int l = tid; l < m; l += nt) wk.pw[l] = fma(-Kc, wk.vv[l], wk.pw[l]);
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     // lower triangle of A22 -= v w^T + w v^T
     for (int l = warp; l < m; l += nw) {
       double* row = A + tri(j + 1 + l, j + 1);
       const double vl = wk.vv[l], wl = wk.pw[l];
       for (int c = lane; c <= l; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
   }
   if (tid == 0) {
     wk.d[N - 2] = A[tri(N - 2, N - 2)];
@@ -1152,7 +1159,7 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     wk.sc[0] = lo;
     wk.sc[1] = hi;
   }
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   // squared off-diagonals for the Sturm recurrence (reuse vv), FP32 copies
   for (int i = tid; i < N; i += nt) {
     wk.vv[i] = wk.e[i] * wk.e[i];
@@ -1160,7 +1167,7 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     wk.e32[i] = (float)(wk.e[i] * wk.e[i]);
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   double lp = 0.0, en = 0.0, cf = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
     const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
@@ -1168,9 +1175,9 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     if (eps_out) eps_out[idx] = eps;
     thermal_add(eps, beta, lp, en, cf);
   }
-  res[0] = grp_sum(lp, g, wk.sc);
-  res[1] = grp_sum(en, g, wk.sc);
-  res[2] = grp_sum(cf, g, wk.sc);
+  res[0] = grp_sum<MULTI>(lp, g, wk.sc);
+  res[1] = grp_sum<MULTI>(en, g, wk.sc);
+  res[2] = grp_sum<MULTI>(cf, g, wk.sc);
 }
 
 }  // namespace crbm

@@ -352,9 +352,10 @@ __device__ inline double eigen_idx_df(const KitaevWork& wk, const df* d, const d
 // eigenvalue mu = eps^2 by at most dmu, and (ii) the slope of
 // log 2cosh(beta sqrt(mu)/2) in mu, at most min(beta^2/8, beta/(4 sqrt(mu))).
 // Run by the chain's thread group g with its own work areas, like kitaev_logpi64.
+template <bool MULTI>
 __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, const double* J, double beta,
                                        const KitaevWork& wk, double (&res)[4], bool open_cols = false) {
-  const int N = L * L, tid = g.r, nt = g.tpc;
+  const int N = L * L, tid = MULTI ? g.r : (int)threadIdx.x, nt = MULTI ? g.tpc : (int)blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   df* A = reinterpret_cast<df*>(wk.A);        // same footprint as the FP64 matrix
   df* dv = reinterpret_cast<df*>(wk.vv);       // Householder vector
@@ -388,8 +389,8 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     }
     for (int c = 0; c <= w; ++c) fro = fmaf((c == w ? 1.0f : 2.0f) * row[c].hi, row[c].hi, fro);
   }
-  const double fro_all = grp_sum((double)fro, g, wk.sc);
-  grp_sync(g);
+  const double fro_all = grp_sum<MULTI>((double)fro, g, wk.sc);
+  grp_sync<MULTI>(g);
   for (int j = 0; j < N - 2; ++j) {
     const int m = N - j - 1;
     df s = {0.0f, 0.0f};
@@ -398,12 +399,12 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
       s = df_fma(a, a, s);
     }
     // block sum of df partials (through doubles: exact enough, 2^-53)
-    const double sd = grp_sum(df_to_double(s), g, wk.sc);
+    const double sd = grp_sum<MULTI>(df_to_double(s), g, wk.sc);
     const df x0 = A[tri(j + 1, j)];
     if (tid == 0) wk.d[j] = df_to_double(A[tri(j, j)]);
     if (sd == 0.0) {
       if (tid == 0) wk.e[j] = df_to_double(x0);
-      grp_sync(g);
+      grp_sync<MULTI>(g);
       continue;
     }
     const float sh = (float)sd;
@@ -414,7 +415,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     const df tau = df_div({2.0f, 0.0f}, df_add(df_mul(v0, v0), ss));
     if (tid == 0) wk.e[j] = df_to_double(alpha);
     for (int l = tid; l < m; l += nt) dv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     for (int l = warp; l < m; l += nw) {
       df acc = {0.0f, 0.0f};
       for (int c = lane; c < m; c += 32) {
@@ -428,21 +429,21 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
       }
       if (lane == 0) pw[l] = df_mul(tau, acc);
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     df pv = {0.0f, 0.0f};
     for (int l = tid; l < m; l += nt) pv = df_fma(pw[l], dv[l], pv);
-    const double pvd = grp_sum(df_to_double(pv), g, wk.sc);
+    const double pvd = grp_sum<MULTI>(df_to_double(pv), g, wk.sc);
     const float ph = (float)pvd;
     const df Kc = df_mul(df_mul({0.5f, 0.0f}, tau), {ph, (float)(pvd - (double)ph)});
     for (int l = tid; l < m; l += nt) pw[l] = df_add(pw[l], df_neg(df_mul(Kc, dv[l])));
-    grp_sync(g);
+    grp_sync<MULTI>(g);
     for (int l = warp; l < m; l += nw) {
       df* row = A + tri(j + 1 + l, j + 1);
       const df vl = dv[l], wl = pw[l];
       for (int c = lane; c <= l; c += 32)
         row[c] = df_add(row[c], df_neg(df_add(df_mul(vl, pw[c]), df_mul(wl, dv[c]))));
     }
-    grp_sync(g);
+    grp_sync<MULTI>(g);
   }
   if (tid == 0) {
     wk.d[N - 2] = df_to_double(A[tri(N - 2, N - 2)]);
@@ -458,7 +459,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     wk.sc[0] = lo;
     wk.sc[1] = hi;
   }
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   // the df64 matrix is no longer needed: vv/pw hold FP64 Sturm data again
   // the matrix is reduced: its storage now holds the df64 tridiagonal (d, e^2)
   df* ddf = reinterpret_cast<df*>(wk.A);
@@ -471,7 +472,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     edf[i] = df_of(wk.e[i] * wk.e[i]);
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
-  grp_sync(g);
+  grp_sync<MULTI>(g);
   // reduction backward error of this stage and of the FP64 stage it stands in
   // for, the FP64 eigenvalue solver's own error on the FP64 path's tridiagonal,
   // and this stage's df64 solver (Sturm backward error and Newton tolerance)
@@ -487,10 +488,10 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     const double slope = (mlo > 0.0) ? fmin(0.125 * beta * beta, 0.25 * beta / sqrt(mlo)) : 0.125 * beta * beta;
     bd += slope * dmu;
   }
-  res[0] = grp_sum(lp, g, wk.sc);
-  res[1] = grp_sum(en, g, wk.sc);
-  res[2] = grp_sum(cf, g, wk.sc);
-  res[3] = grp_sum(bd, g, wk.sc) * 1.01 + 1e-12 * fabs(res[0]) + 1e-300;
+  res[0] = grp_sum<MULTI>(lp, g, wk.sc);
+  res[1] = grp_sum<MULTI>(en, g, wk.sc);
+  res[2] = grp_sum<MULTI>(cf, g, wk.sc);
+  res[3] = grp_sum<MULTI>(bd, g, wk.sc) * 1.01 + 1e-12 * fabs(res[0]) + 1e-300;
 }
 
 }  // namespace crbm

@@ -56,6 +56,10 @@ cudaError_t launch_kKitaev_kMixed_64(int, int, const LaunchParams&, int, size_t,
 cudaError_t limit_kKitaev_kMixed_64(size_t);
 cudaError_t launch_kKitaev_kMixed_32(int, int, const LaunchParams&, int, size_t, cudaStream_t);
 cudaError_t limit_kKitaev_kMixed_32(size_t);
+cudaError_t launch_kKitaev_kFP64_256_multi(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kFP64_256_multi(size_t);
+cudaError_t launch_kKitaev_kMixed_256_multi(int, int, const LaunchParams&, int, size_t, cudaStream_t);
+cudaError_t limit_kKitaev_kMixed_256_multi(size_t);
 
 void specialisation(int K, int k, int& KC, int& kC) {
   KC = 0;
@@ -78,10 +82,13 @@ int threads_for(int, int) { return 256; }
 int kitaev_group_threads(int N) { return N <= 16 ? 32 : (N <= 64 ? 64 : (N <= 100 ? 128 : 256)); }
 
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
-                        cudaStream_t st, bool generic) {
+                        cudaStream_t st, bool generic, bool multi) {
   int KC, kC;
   specialisation(K, k, KC, kC);
   if (generic) KC = kC = 0;
+  if (multi)
+    return prec == kFP64 ? launch_kKitaev_kFP64_256_multi(KC, kC, p, grid, smem, st)
+                         : launch_kKitaev_kMixed_256_multi(KC, kC, p, grid, smem, st);
   if (kind == kIsing)
     return prec == kFP64 ? launch_kIsing_kFP64_256(KC, kC, p, grid, smem, st)
                          : launch_kIsing_kMixed_256(KC, kC, p, grid, smem, st);
@@ -106,7 +113,8 @@ cudaError_t set_smem_limits(size_t bytes) {
   for (cudaError_t (*f)(size_t) : {limit_kIsing_kFP64_256, limit_kIsing_kMixed_256, limit_kKitaev_kFP64_256,
                                    limit_kKitaev_kFP64_128, limit_kKitaev_kFP64_64, limit_kKitaev_kFP64_32,
                                    limit_kKitaev_kMixed_256, limit_kKitaev_kMixed_128, limit_kKitaev_kMixed_64,
-                                   limit_kKitaev_kMixed_32})
+                                   limit_kKitaev_kMixed_32, limit_kKitaev_kFP64_256_multi,
+                                   limit_kKitaev_kMixed_256_multi})
     if (e == cudaSuccess) e = f(bytes);
   return e;
 }

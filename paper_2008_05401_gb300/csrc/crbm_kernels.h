@@ -22,9 +22,10 @@ int threads_for(int kind, int max_N);
 // less at the eigen-stage barriers).
 int kitaev_group_threads(int N);
 // Launch the fused kernel: grid = total tiles of all jobs in p (one filter shape per launch);
-// generic: use the runtime-shape variant even where a specialisation exists (LCRBM jobs).
+// generic: use the runtime-shape variant even where a specialisation exists (LCRBM jobs);
+// multi: Kitaev proposals (mode 0) in 256-thread CTAs holding several chain groups.
 cudaError_t launch_step(int kind, int prec, int K, int k, int nt, const LaunchParams& p, int grid, size_t smem,
-                        cudaStream_t st, bool generic = false);
+                        cudaStream_t st, bool generic = false, bool multi = false);
 // Raise the dynamic shared-memory limit of every fused-kernel instantiation.
 cudaError_t set_smem_limits(size_t bytes);
 // Tensor-core form of the proposal kernel (crbm_step_tc.cu): Ising kind, mixed

@@ -81,8 +81,10 @@ __device__ inline void store_evaluation(const JobDev& jb, int c, double beta, co
 
 // AUX = 0: the proposal loop (mode 0) only; AUX = 1: modes 1-3.  Two kernels,
 // so that the hot proposal loop carries none of the other modes' code and
-// registers (with them it spilled).
-template <int KIND, int PREC, int KC, int kC, int NT, int AUX>
+// registers (with them it spilled).  MULTI (Kitaev, mode 0 only): CTAs hold
+// several chain groups, which synchronise on named barriers of their own;
+// without it every CTA holds one chain and uses the CTA barrier only.
+template <int KIND, int PREC, int KC, int kC, int NT, int AUX, bool MULTI = false>
 __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kernel(const __grid_constant__ LaunchParams prm) {
   int jid = 0;
   while (jid + 1 < prm.n_jobs && (int)blockIdx.x >= prm.tile_begin[jid + 1]) ++jid;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   KitaevWork wk;
   double* eps_st = nullptr;     // Kitaev local sweeps: spectrum of the proposed lattice
   if (KIND == kKitaev) {
-    unsigned char* kp = kwork + (size_t)g.gl * kitaev_work_bytes(N);
+    unsigned char* kp = MULTI ? kwork + (size_t)g.gl * kitaev_work_bytes(N) : kwork;
     wk.A = (double*)kp;
     kp += align16((size_t)N * (N + 1) / 2 * 8);
     wk.d = (double*)kp;
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
-      kitaev_logpi64(g, my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+      kitaev_logpi64<MULTI>(g, my, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     if (g.active && g.r == 0) {
       double Fb = 0.0;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     grp_reduce<4>(fo, g, scratch);
     double kr[3] = {0.0, 0.0, 0.0};
     if (KIND == kKitaev)
-      kitaev_logpi64(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
+      kitaev_logpi64<MULTI>(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr,
                      g.active ? jb.eps + (size_t)g.c * N : nullptr, jb.lc_edge > 0);
     // the physical chain's lattice into the first hidden plane (free now)
     if (g.active)
@@ -423,13 +425,13 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
           const uint32_t* v = my + ch.cur * P;
           uint32_t* vp = my + (ch.cur ^ 1) * P;
           for (int w = g.r; w < jb.Wd; w += g.tpc) vp[w] = v[w] ^ ((w == (n >> 5)) ? (1u << (n & 31)) : 0u);
-          grp_sync(g);
+          grp_sync<MULTI>(g);
           double kr[4] = {0.0, 0.0, 0.0, 0.0};
           if (PREC == kMixed) {
-            kitaev_logpi_df(g, vp, jb.L, jb.J, ch.beta, wk, kr, jb.lc_edge > 0);
+            kitaev_logpi_df<MULTI>(g, vp, jb.L, jb.J, ch.beta, wk, kr, jb.lc_edge > 0);
           } else {
             double k3[3];
-            kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k3, eps_st, jb.lc_edge > 0);
+            kitaev_logpi64<MULTI>(g, vp, jb.L, jb.J, ch.beta, wk, k3, eps_st, jb.lc_edge > 0);
             kr[0] = k3[0];
             kr[1] = k3[1];
             kr[2] = k3[2];
@@ -452,14 +454,14 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               else ch.flag_rec = 1;
             }
           }
-          grp_sync(g);
+          grp_sync<MULTI>(g);
           if (PREC == kMixed && ch.flag_rec) {
             // the FP64 eigen-stage of the proposal (and of the current lattice
             // when its log-weight came from the df64 stage)
             double k1v[3], k0v[3] = {0.0, 0.0, 0.0};
             const bool redo_v = ch.lpb != 0.0;
-            kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st, jb.lc_edge > 0);
-            if (redo_v) kitaev_logpi64(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
+            kitaev_logpi64<MULTI>(g, vp, jb.L, jb.J, ch.beta, wk, k1v, eps_st, jb.lc_edge > 0);
+            if (redo_v) kitaev_logpi64<MULTI>(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
             if (g.r == 0) {
               ch.lpp = k1v[0];
               ch.lppb = 0.0;
@@ -474,13 +476,13 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               ch.flag_acc = logu < ch.lpp - ch.lp;
               ch.rec_mh += 1ull;
             }
-            grp_sync(g);
+            grp_sync<MULTI>(g);
           }
           if (ch.flag_acc) {
             // the spectrum cache follows the lattice when the proposal's came from the FP64 stage
             if (g.active && (PREC == kFP64 || ch.flag_rec))
               for (int l = g.r; l < N; l += g.tpc) jb.eps[(size_t)g.c * N + l] = eps_st[l];
-            grp_sync(g);
+            grp_sync<MULTI>(g);
             if (g.r == 0) {
               ch.cur ^= 1;
               ch.lp = ch.lpp;
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
               ch.acc += 1ull;
             }
           }
-          grp_sync(g);
+          grp_sync<MULTI>(g);
         }
       }
       // observables of the lattice after the sweep
@@ -549,11 +551,11 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
   // eigen-stage takes longer holds back no other chain of the CTA); the Ising
   // kind's groups may be smaller than a warp and use the CTA barrier.
   auto loop_sync = [&]() {
-    if (KIND == kKitaev) grp_sync(g);
+    if (KIND == kKitaev && MULTI) grp_sync<MULTI>(g);
     else __syncthreads();
   };
   auto loop_reduce4 = [&](double (&x)[4], const Grp& gg) {
-    if (KIND == kKitaev) grp_reduce_local<4>(x, gg, wk.sc);
+    if (KIND == kKitaev && MULTI) grp_reduce_local<4, MULTI>(x, gg, wk.sc);
     else grp_reduce<4>(x, gg, scratch);
   };
   const uint32_t k0 = (uint32_t)jb.seed, k1 = (uint32_t)(jb.seed >> 32);
@@ -580,10 +582,10 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     double kr[4] = {0.0, 0.0, 0.0, 0.0};
     if (KIND == kKitaev) {
       if (PREC == kMixed) {
-        kitaev_logpi_df(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr, jb.lc_edge > 0);
+        kitaev_logpi_df<MULTI>(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, kr, jb.lc_edge > 0);
       } else {
         double k3[3];
-        kitaev_logpi64(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3, nullptr, jb.lc_edge > 0);
+        kitaev_logpi64<MULTI>(g, vp, jb.L, jb.J, g.active ? ch.beta : 1.0, wk, k3, nullptr, jb.lc_edge > 0);
         kr[0] = k3[0];
         kr[1] = k3[1];
         kr[2] = k3[2];
@@ -659,7 +661,7 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
     }
     if (PREC == kMixed) {
       int need;
-      if (KIND == kKitaev) {
+      if (KIND == kKitaev && MULTI) {
         loop_sync();                 // the leader's flag_rec, read by its whole group
         need = g.active && ch.flag_rec;
       } else {
@@ -687,8 +689,8 @@ __global__ void __launch_bounds__(NT, CRBM_MIN_BLOCKS * 256 / NT) crbm_step_kern
         double k1v[3] = {0.0, 0.0, 0.0}, k0v[3] = {0.0, 0.0, 0.0};
         const bool redo_v = ch.lpb != 0.0;
         if (KIND == kKitaev) {
-          kitaev_logpi64(g, vp, jb.L, jb.J, ch.beta, wk, k1v, nullptr, jb.lc_edge > 0);
-          if (redo_v) kitaev_logpi64(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
+          kitaev_logpi64<MULTI>(g, vp, jb.L, jb.J, ch.beta, wk, k1v, nullptr, jb.lc_edge > 0);
+          if (redo_v) kitaev_logpi64<MULTI>(g, v, jb.L, jb.J, ch.beta, wk, k0v, nullptr, jb.lc_edge > 0);
         }
         if (g2.active && g.r == 0) {
           ch.Fp = -jb.vb * f1[2] - f1[0];
@@ -761,11 +763,16 @@ static __global__ void advance_steps_kernel(const __grid_constant__ LaunchParams
   if (i < p.n_jobs) *p.job[i].step += (unsigned long long)p.S;
 }
 
-// Launch one instantiation; raise its dynamic shared-memory limit.
-template <int KIND, int PREC, int KC, int kC, int NT>
+// Launch one instantiation; raise its dynamic shared-memory limit.  MULTI
+// launches run mode 0 only.
+template <int KIND, int PREC, int KC, int kC, int NT, bool MULTI = false>
 cudaError_t launch_inst(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  if (p.mode == 0) crbm_step_kernel<KIND, PREC, KC, kC, NT, 0><<<grid, NT, smem, st>>>(p);
-  else crbm_step_kernel<KIND, PREC, KC, kC, NT, 1><<<grid, NT, smem, st>>>(p);
+  if constexpr (MULTI) {
+    crbm_step_kernel<KIND, PREC, KC, kC, NT, 0, true><<<grid, NT, smem, st>>>(p);
+  } else {
+    if (p.mode == 0) crbm_step_kernel<KIND, PREC, KC, kC, NT, 0><<<grid, NT, smem, st>>>(p);
+    else crbm_step_kernel<KIND, PREC, KC, kC, NT, 1><<<grid, NT, smem, st>>>(p);
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && p.mode != 1 && p.S > 0) {
     advance_steps_kernel<<<1, kMaxJobs, 0, st>>>(p);
@@ -799,6 +806,23 @@ cudaError_t limit_nt(size_t bytes) {
   return e;
 }
 
+// The several-chains-per-CTA proposal kernel (mixed-size Kitaev batches).
+template <int KIND, int PREC, int NT>
+cudaError_t launch_multi(int KC, int kC, const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (KC == 4 && kC == 5) return launch_inst<KIND, PREC, 4, 5, NT, true>(p, grid, smem, st);
+  if (KC == 4 && kC == 3) return launch_inst<KIND, PREC, 4, 3, NT, true>(p, grid, smem, st);
+  return launch_inst<KIND, PREC, 0, 0, NT, true>(p, grid, smem, st);
+}
+
+template <int KIND, int PREC, int NT>
+cudaError_t limit_multi(size_t bytes) {
+  cudaError_t e = cudaSuccess;
+  for (auto f : {crbm_step_kernel<KIND, PREC, 4, 5, NT, 0, true>, crbm_step_kernel<KIND, PREC, 4, 3, NT, 0, true>,
+                 crbm_step_kernel<KIND, PREC, 0, 0, NT, 0, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
+}
+
 // One translation unit per (kind, precision, CTA size) instantiates the
 // (K, k) variants (4, 5), (4, 3) and runtime: CTAs of 256 threads, plus 128,
 // 64 and 32 threads for the Kitaev kind (small matrices); every CTA size gets
@@ -809,5 +833,12 @@ cudaError_t limit_nt(size_t bytes) {
     return launch_nt<KIND, PREC, NT>(KC, kC, p, grid, smem, st);                               \
   }                                                                                            \
   cudaError_t limit_##KIND##_##PREC##_##NT(size_t bytes) { return limit_nt<KIND, PREC, NT>(bytes); }
+
+#define CRBM_VARIANTS_MULTI(KIND, PREC, NT)                                                    \
+  cudaError_t launch_##KIND##_##PREC##_##NT##_multi(int KC, int kC, const LaunchParams& p, int grid, \
+                                                    size_t smem, cudaStream_t st) {            \
+    return launch_multi<KIND, PREC, NT>(KC, kC, p, grid, smem, st);                            \
+  }                                                                                            \
+  cudaError_t limit_##KIND##_##PREC##_##NT##_multi(size_t bytes) { return limit_multi<KIND, PREC, NT>(bytes); }
 
 }  // namespace crbm

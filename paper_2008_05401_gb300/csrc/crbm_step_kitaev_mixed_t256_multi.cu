@@ -1,0 +1,7 @@
+// Instantiations of the fused proposal kernel for Kitaev / Mixed, CTAs of 256
+// threads holding several chain groups (batches of mixed lattice sizes).
+#include "crbm_step.cuh"
+
+namespace crbm {
+CRBM_VARIANTS_MULTI(kKitaev, kMixed, 256)
+}  // namespace crbm

@@ -7,8 +7,9 @@
   with the analytic CRBM of App. C, and <E>, C_v of the small Ising workload
   (its own filters, MH corrected) with binned errors;
 * the small Ising workload exactly as specified, replayed by the oracle;
-* full-size parity: the 4096-chain L = 128 launch of the batch workload on
-  its CD-1 filters, every chain with an MH recompute replayed by the oracle.
+* full-size parity: the batch workload in the bench's launch configuration
+  (four sides x 4096 chains, one launch) on its CD-1 filters, every chain with
+  an MH recompute replayed by the oracle.
 """
 import os
 
@@ -124,64 +125,71 @@ def _cd1_bank():
 
 
 def test_full_size_batch_launch_replays_every_recompute(ctx):
-    """The L = 128 job of the batch workload in the bench's launch
-    configuration: 4096 chains, the CD-1 filter bank, mixed precision (the
-    tensor-core kernel).  After 20 proposals (the regime the bench measures)
-    the state is read; then S = 3 proposals.  Every chain whose MH decision went
-    to the second level (double-FP32 free energies, then FP64 if still
-    undecided), chains with FP64 Bernoulli redos, and 16 random chains are
-    replayed by the oracle from that state: lattices, accepts and energy sums
-    identical, log pi and F (read back in FP64) within 1e-10."""
+    """The batch Ising workload in the bench's launch configuration: L = 128,
+    64, 32 and 16, 4096 chains each, the CD-1 filter bank, mixed precision, all
+    four sides in one batched call (one persistent tensor-core launch).  After
+    20 proposals (the regime the bench measures) the state is read; then S = 3
+    proposals.  From every side, every chain whose MH decision went to the
+    second level (double-FP32 free energies, then FP64 if still undecided),
+    chains with FP64 Bernoulli redos and random chains are replayed by the
+    oracle from that state: lattices, accepts and energy sums identical, log pi
+    and F (read back in FP64) within 1e-10."""
     from oracle import chain
     from paper_2008_05401_gb300 import ISING, MIXED
-    L, n, S0, S = 128, 4096, 20, 3
+    n, S0, S = 4096, 20, 3
     W, hb, vb = _cd1_bank()
     T = wl.ising_ladder(n, 32)
     mid = ctx.load_model(ISING, W, vb, hb)
-    job = ctx.new_job(mid, ISING, L, T, (1.0,), SEED, 0, wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)),
-                      MIXED)
-    job.run(S0, precision=MIXED)
-    bits0, step0 = job.state()
-    sums0, acc0, rec0 = job.observables()
-    job.run(S, precision=MIXED)
-    bits, step = job.state()
-    lp, F, E = job.energies()
-    sums, acc, rec = job.observables()
-    assert step == S0 + S
-    d_acc, d_rec, d_sums = acc - acc0, rec - rec0, sums - sums0
-    mh = np.nonzero(d_rec[:, 1])[0]
-    bern = np.nonzero(d_rec[:, 0])[0]
-    rand = np.random.default_rng(5).choice(n, 16, replace=False)
-    sel = np.unique(np.concatenate([mh, bern[:48], rand]))
-    assert mh.size >= 1, "no MH decision reached the second level: the replay would not check it"
-    compared, in_margin = [], []
-    for g0 in range(0, len(sel), 32):
-        cs = sel[g0:g0 + 32]
-        ref = chain.make_chains(chain.ISING, W, hb, vb, L, T[cs], (1.0,), SEED, cs, v0=wl.unpack_bits(bits0[cs], L))
-        ref.step = step0
-        bm = np.full(len(cs), np.inf)
-        mm = np.full(len(cs), np.inf)
+    sides = (128, 64, 32, 16)
+    jobs = [ctx.new_job(mid, ISING, L, T, (1.0,), SEED, base, wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)),
+                        MIXED) for L, base in zip(sides, (0, n, 2 * n, 3 * n))]
+    ctx.run_batch(jobs, S0, precision=MIXED)
+    before = [(j.state(), j.observables()) for j in jobs]
+    ctx.run_batch(jobs, S, precision=MIXED)
+    total_mh = total_mh_compared = 0
+    for L, base, j, ((bits0, step0), (sums0, acc0, rec0)) in zip(sides, (0, n, 2 * n, 3 * n), jobs, before):
+        bits, step = j.state()
+        lp, F, E = j.energies()
+        sums, acc, rec = j.observables()
+        assert step == S0 + S
+        d_acc, d_rec, d_sums = acc - acc0, rec - rec0, sums - sums0
+        mh = np.nonzero(d_rec[:, 1])[0]
+        bern = np.nonzero(d_rec[:, 0])[0]
+        rand = np.random.default_rng(L).choice(n, 16 if L == 128 else 64, replace=False)
+        cap = 48 if L == 128 else 256                # oracle time: the L = 128 chains dominate
+        sel = np.unique(np.concatenate([mh, bern[:cap], rand]))
+        compared, in_margin = [], []
+        for g0 in range(0, len(sel), 32):
+            cs = sel[g0:g0 + 32]
+            ref = chain.make_chains(chain.ISING, W, hb, vb, L, T[cs], (1.0,), SEED, base + cs,
+                                    v0=wl.unpack_bits(bits0[cs], L))
+            ref.step = step0
+            bm = np.full(len(cs), np.inf)
+            mm = np.full(len(cs), np.inf)
 
-        def rec_margins(c, d):
-            bm[:] = np.minimum(bm, d["bernoulli_margin"])
-            mm[:] = np.minimum(mm, d["mh_margin"] / d["mh_scale"])
+            def rec_margins(c, d):
+                bm[:] = np.minimum(bm, d["bernoulli_margin"])
+                mm[:] = np.minimum(mm, d["mh_margin"] / d["mh_scale"])
 
-        chain.run(ref, S, record=rec_margins)
-        for q, c in enumerate(cs):
-            if bm[q] <= 1e-12 or mm[q] <= 1e-10:    # both sides may legitimately differ there
-                in_margin.append(int(c))
-                continue
-            np.testing.assert_array_equal(bits[c], wl.pack_bits(ref.v[q:q + 1])[0], err_msg=f"chain {c}")
-            assert d_acc[c] == ref.accepts[q], c
-            np.testing.assert_allclose(E[c], ref.E_phys[q], rtol=1e-12)
-            np.testing.assert_allclose(lp[c], ref.logpi[q], rtol=1e-10)
-            np.testing.assert_allclose(F[c], ref.F[q], rtol=1e-10)
-            np.testing.assert_allclose(d_sums[c], ref.obs[q], rtol=1e-10, atol=1e-9)
-            compared.append(int(c))
-    assert len(compared) >= len(sel) - 2, (len(compared), len(sel), in_margin)
-    assert set(mh.tolist()) <= set(compared) | set(in_margin)
-    assert len(set(mh.tolist()) & set(compared)) >= 1
-    job.release()
+            chain.run(ref, S, record=rec_margins)
+            for q, c in enumerate(cs):
+                if bm[q] <= 1e-12 or mm[q] <= 1e-10:    # both sides may legitimately differ there
+                    in_margin.append(int(c))
+                    continue
+                np.testing.assert_array_equal(bits[c], wl.pack_bits(ref.v[q:q + 1])[0], err_msg=f"L={L} chain {c}")
+                assert d_acc[c] == ref.accepts[q], (L, c)
+                np.testing.assert_allclose(E[c], ref.E_phys[q], rtol=1e-12)
+                np.testing.assert_allclose(lp[c], ref.logpi[q], rtol=1e-10)
+                np.testing.assert_allclose(F[c], ref.F[q], rtol=1e-10)
+                np.testing.assert_allclose(d_sums[c], ref.obs[q], rtol=1e-10, atol=1e-9)
+                compared.append(int(c))
+        assert len(compared) >= len(sel) - 2, (L, len(compared), len(sel), in_margin)
+        assert set(mh.tolist()) <= set(compared) | set(in_margin)
+        total_mh += mh.size
+        total_mh_compared += len(set(mh.tolist()) & set(compared))
+    assert total_mh >= 1 and total_mh_compared >= 1, "no MH decision reached the second level"
+    for j in jobs:
+        j.release()
 
 
 def _binned(x, nb):
