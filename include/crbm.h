@@ -156,9 +156,10 @@ CRBM_API int crbm_run(crbm_ctx* ctx, int job_id, int64_t S, int g, int correct, 
 
 /* As crbm_run for n_jobs jobs, chains of different L and temperature side
  * by side: the jobs on the tensor-core form (crbm_set_tensor_cores) share ONE
- * persistent launch whatever their sides; the other jobs share one launch of
- * 256-thread CTAs (Kitaev chains in thread groups sized by their lattice,
- * several per CTA for small ones); when both kinds of launch are needed they
+ * persistent launch whatever their sides; the other jobs share one launch
+ * (Kitaev: one chain per CTA of its thread-group size when the jobs' group
+ * sizes agree, else 256-thread CTAs holding several chain groups); when both
+ * kinds of launch are needed they
  * fork from cuda_stream onto internal side streams and join it again, so the
  * call stays ordered on cuda_stream.  The jobs must share the model kind and
  * the filter-bank shape (K, k); their models may differ.  Each job keeps its
