@@ -563,20 +563,23 @@ static int build_tc(crbm_ctx* ctx, Model& m, int K, int k, const double* W, doub
   m.tq2 = (float)std::ldexp(qf, 22);
   m.tq1 = (float)std::ldexp(qf, 11);
   m.tq0 = (float)qf;
-  // decisions (decide32 units of 2^-32): x = fl(fl(c2-sum q2 + fl(c1-sum q1 +
-  // c0-sum q0)) + b32) is within quantisation (k^2 or K k^2) qf / 2, the low
-  // digits' rounding 2^-24 T1 and 2^-24 (2 |x| + 2 |b|) of the exact
-  // pre-activation, the FP64 path's own sum within 2^-50 S; slope of sigma
-  // <= 1/4; factor 2 of safety
+  // decisions (decide32 units of 2^-32): x = fl(c2-sum q2 + fl(c1-sum q1 +
+  // fl(c0-sum q0 + b32))) (three fused multiply-adds; the products are exact)
+  // is within quantisation (k^2 or K k^2) qf / 2, the two inner roundings
+  // 2^-24 (|c0 part| + |b|) + 2^-24 (|c1 part| + |c0 part| + |b|) <= 2^-24
+  // (2 T1 + 2 |b|) and the outer one 2^-24 |x| (budgeted 2^-23 |x|) of the
+  // exact pre-activation, the FP64 path's own sum within 2^-50 S; slope of
+  // sigma <= 1/4; factor 2 of safety
   const double u24 = std::ldexp(1.0, -24), u50 = std::ldexp(1.0, -50);
   const double eqh = 0.5 * k * k * qf, eqv = 0.5 * K * k * k * qf;
-  m.tc0h = (float)std::ldexp(2.0 * (common + 0.25 * (eqh + u24 * t1 + 2.0 * u24 * maxhb + u50 * sh)) + 1e-14, 32);
+  m.tc0h = (float)std::ldexp(2.0 * (common + 0.25 * (eqh + 2.0 * u24 * t1 + 2.0 * u24 * maxhb + u50 * sh)) + 1e-14, 32);
   m.tc0v = (float)std::ldexp(
-      2.0 * (common + 0.25 * (eqv + u24 * t1v + 2.0 * u24 * std::fabs(v_bias) + u50 * sv)) + 1e-14, 32);
+      2.0 * (common + 0.25 * (eqv + 2.0 * u24 * t1v + 2.0 * u24 * std::fabs(v_bias) + u50 * sv)) + 1e-14, 32);
   m.tc1 = (float)std::ldexp(2.0 * (std::ldexp(1.0, -25) + 0.25 * 2.0 * u24), 32);
   // free energy, per unit beyond the 2^-23 |x| the kernel sums: quantisation
-  // k^2 qf / 2, rounding of the low digits 2^-24 T1, of hb 3 2^-24 |hb|; factor 1.5
-  m.tcft = (float)(1.5 * (0.5 * k * k * qf + u24 * t1 + 3.0 * u24 * maxhb + u50 * sh));
+  // k^2 qf / 2, the two inner roundings 2^-24 (2 T1 + 2 |hb|) (budgeted
+  // 3 2^-24 |hb|); factor 1.5
+  m.tcft = (float)(1.5 * (0.5 * k * k * qf + 2.0 * u24 * t1 + 3.0 * u24 * maxhb + u50 * sh));
   if (alloc) CK(cudaMalloc(&m.d_tc, bytes), "cudaMalloc tensor-core images");
   else if (!m.d_tc || m.tc_bytes != bytes) return fail(ctx, CRBM_EINVAL, "tensor-core image size changed");
   m.tc_bytes = bytes;

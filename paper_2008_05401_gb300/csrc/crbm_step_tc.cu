@@ -167,15 +167,20 @@ __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.
 // the launch's error flag and returns false; once the abort flag is up every
 // wait of the CTA returns false at once, so that the CTA runs to its end
 // instead of stalling wait after wait (its results are void and the host
-// reports CRBM_ETIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit, volatile int* abort,
-                                          int* err) {
+// reports CRBM_ETIMEOUT).  The first probe is inline; the polling loop with its
+// clock reads is out of line, so that a phase already complete costs one probe
+// and no branch-heavy code at every call site.
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+  return done != 0;
+}
+static __device__ __noinline__ bool mbar_poll(uint32_t mbar, uint32_t parity, long long limit, volatile int* abort,
+                                              int* err) {
   const long long t0 = clock64();
   while (true) {
-    uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, parity)) return true;
     if (abort != nullptr && *abort != 0) return false;
     if (clock64() - t0 > limit) {
       if (abort != nullptr) *abort = 1;
@@ -183,6 +188,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
       return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit, volatile int* abort,
+                                          int* err) {
+  if (mbar_try(mbar, parity)) return true;
+  return mbar_poll(mbar, parity, limit, abort, err);
 }
 
 // CTA barrier with the tensor-memory and proxy fences around it.
@@ -198,6 +208,12 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(mbar) : "memory");
+}
+// Arrive from the lanes where `on` holds, as a predicated instruction (no
+// branch around it).
+__device__ __forceinline__ void mbar_arrive_if(uint32_t mbar, bool on) {
+  asm volatile("{\n.reg .pred p;\n.reg .b64 st;\nsetp.ne.u32 p, %1, 0;\n@p mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n"
+               :: "r"(mbar), "r"((uint32_t)on) : "memory");
 }
 
 enum { kStH = 0, kStV = 1, kStF = 2 };
@@ -343,7 +359,7 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
   uint32_t byte = 0u, amb = 0u;
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    const float x = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, s0[jj] * jb.tq0)) + hb;
+    const float x = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, fmaf(s0[jj], jb.tq0, hb)));
     uint32_t bit, a;
     decide32_split(x, pick(jj < 4 ? w0 : w1, jj & 3), jb.tc0h, jb.tc1, bit, a);
     byte |= bit << jj;
@@ -400,7 +416,7 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
   uint32_t nib = 0u, amb = 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const float x = fmaf(s2[t], jb.tq2, fmaf(s1[t], jb.tq1, s0[t] * jb.tq0)) + jb.vb32;
+    const float x = fmaf(s2[t], jb.tq2, fmaf(s1[t], jb.tq1, fmaf(s0[t], jb.tq0, jb.vb32)));
     uint32_t bit, a;
     decide32_split(x, pick(w, t), jb.tc0v, jb.tc1, bit, a);
     nib |= bit << t;
@@ -440,8 +456,7 @@ __device__ __forceinline__ void epi_free(const JobDev& jb, const float (&s2)[8],
   float sp[8];
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    const float xn = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, s0[jj] * jb.tq0));
-    const float x = xn + hb;
+    const float x = fmaf(s2[jj], jb.tq2, fmaf(s1[jj], jb.tq1, fmaf(s0[jj], jb.tq0, hb)));
     sp[jj] = softplus32(x);
     sabs += fabsf(x);
   }
@@ -692,13 +707,13 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
   auto epi_release = [&]() {
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar(kBarEmpty + (zc & (kNbuf - 1))));
+    mbar_arrive_if(bar(kBarEmpty + (zc & (kNbuf - 1))), lane == 0);
   };
   // epilogue warp: its generic-proxy operand writes visible to later MMAs, then arrive
   auto epi_publish = [&](uint32_t b) {
     proxy_fence();
     __syncwarp();
-    if (lane == 0) mbar_arrive(b);
+    mbar_arrive_if(b, lane == 0);
   };
 
   for (int s = 0; s < prm.S; ++s) {
