@@ -879,6 +879,13 @@ __device__ void free_phase(const JobDev& jb, const Tabs& tb, const Grp& g, const
 // Sturm counts, and log pi = sum_l log 2cosh(beta eps_l / 2).
 // Packed lower triangle of a symmetric N x N matrix: element (i, c), c <= i.
 __device__ __forceinline__ int tri(int i, int c) { return i * (i + 1) / 2 + c; }
+// Lanes per row of a group's matrix-vector product over m rows with nt
+// threads: the largest power of two H <= 32 with H m <= nt (at least 1).
+__device__ __forceinline__ int row_split(int m, int nt) {
+  int H = 1;
+  while (H < 32 && 2 * H * m <= nt) H <<= 1;
+  return H;
+}
 
 struct KitaevWork {
   double* A;       // packed lower triangle, N (N+1) / 2 entries
@@ -1094,55 +1101,134 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     }
   }
   grp_sync<MULTI>(g);
-  // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1.
-  // Only the lower triangle of the trailing block is read and updated.
-  for (int j = 0; j < N - 2; ++j) {
-    const int m = N - j - 1;
-    double s = 0.0;
-    for (int i = j + 2 + tid; i < N; i += nt) {
-      const double a = A[tri(i, j)];
-      s += a * a;
+  // Householder tridiagonalisation, column j: x = A[j+1:, j] -> alpha e_1 by
+  // H = I - tau u u^T, u = x - alpha e_1.  Only the lower triangle of the
+  // trailing block A22 (rows and columns j+1..N-1, m of them) is read and
+  // updated; the product with A22 reads u from column j itself (u_0 = x_0 -
+  // alpha, u_c = A[j+1+c][j]), which the step does not change, and stores it
+  // in vv for the update.  Three group barriers per column: p = tau A22 u
+  // with H lanes per row and, per warp, the partial of p^T u; then w = p -
+  // (tau p^T u / 2) u; then A22 -= u w^T + w u^T, its first column (with
+  // per-warp partials of the next step's s, the sum of squares below the
+  // subdiagonal) and the rest of the packed triangle element by element in
+  // turn over the group's threads.  sc[0..31]: p^T u partials, sc[32..63]: s.
+  double* scP = wk.sc;
+  double* scS = wk.sc + 32;
+  double s;
+  {
+    double s0 = 0.0;
+    for (int i = 2 + tid; i < N; i += nt) {
+      const double a = A[tri(i, 0)];
+      s0 = fma(a, a, s0);
     }
-    s = grp_sum<MULTI>(s, g, wk.sc);
-    const double x0 = A[tri(j + 1, j)];
+    s = grp_sum<MULTI>(s0, g, wk.sc);
+  }
+  for (int j = 0; j < N - 2; ++j) {
+    const int m = N - j - 1, j1 = j + 1;
+    const double x0 = A[tri(j1, j)];
     if (tid == 0) wk.d[j] = A[tri(j, j)];
     if (s == 0.0) {
+      // column already reduced: no reflection; s of the next column directly
       if (tid == 0) wk.e[j] = x0;
-      grp_sync<MULTI>(g);
+      double s2 = 0.0;
+      for (int i = j + 3 + tid; i < N; i += nt) {
+        const double a = A[tri(i, j1)];
+        s2 = fma(a, a, s2);
+      }
+      s = grp_sum<MULTI>(s2, g, wk.sc);
       continue;
     }
     const double nrm = sqrt(x0 * x0 + s);
     const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double tau = 2.0 / (v0 * v0 + s);
+    const double u0 = x0 - alpha;
+    const double tau = 2.0 / (u0 * u0 + s);
     if (tid == 0) wk.e[j] = alpha;
-    for (int l = tid; l < m; l += nt) wk.vv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
-    grp_sync<MULTI>(g);
-    // p = tau * A22 v from the lower triangle (row part c <= l, column part c > l), one warp per row
-    for (int l = warp; l < m; l += nw) {
-      double acc = 0.0;
-      for (int c = lane; c < m; c += 32) {
-        const int off = (c <= l) ? tri(j + 1 + l, j + 1 + c) : tri(j + 1 + c, j + 1 + l);
-        acc = fma(A[off], wk.vv[c], acc);
+    // p_l = tau sum_c A22[l][c] u_c, u_c = A[tri(j1 + c, j)] (c >= 1): H lanes
+    // of a warp per row (H = 1, 2, 4, .. while H m still fits the group), lane
+    // h of a row taking the columns c = h mod H -- the row part c <= l
+    // (contiguous), then the column part c > l -- alternately into two
+    // accumulators, the H lanes' sums then added by a butterfly
+    const int H = row_split(m, nt), h = lane & (H - 1);
+    double part = 0.0;
+    for (int l0 = 0; l0 < m; l0 += nt / H) {
+      const int l = l0 + warp * (32 / H) + lane / H;
+      double e0 = 0.0, e1 = 0.0;
+      if (l < m) {
+        const double* row = A + tri(j1 + l, j1);
+        int c = h;
+        if (c == 0) {
+          e0 = row[0] * u0;
+          c = H;
+        }
+        for (; c + H <= l; c += 2 * H) {
+          e1 = fma(row[c], A[tri(j1 + c, j)], e1);
+          e0 = fma(row[c + H], A[tri(j1 + c + H, j)], e0);
+        }
+        if (c <= l) {
+          e1 = fma(row[c], A[tri(j1 + c, j)], e1);
+          c += H;
+        }
+        for (; c + H < m; c += 2 * H) {
+          const int b1 = tri(j1 + c, 0), b2 = tri(j1 + c + H, 0);
+          e0 = fma(A[b1 + j1 + l], A[b1 + j], e0);
+          e1 = fma(A[b2 + j1 + l], A[b2 + j], e1);
+        }
+        if (c < m) {
+          const int b1 = tri(j1 + c, 0);
+          e0 = fma(A[b1 + j1 + l], A[b1 + j], e0);
+        }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-      if (lane == 0) wk.pw[l] = tau * acc;
+      double e = e0 + e1;
+      for (int o = 1; o < H; o <<= 1) e += __shfl_xor_sync(kFull, e, o);
+      if (l < m && h == 0) {
+        const double p = tau * e, ul = l == 0 ? u0 : A[tri(j1 + l, j)];
+        wk.pw[l] = p;
+        wk.vv[l] = ul;
+        part = fma(p, ul, part);
+      }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (lane == 0) scP[warp] = part;
     grp_sync<MULTI>(g);
     double pv = 0.0;
-    for (int l = tid; l < m; l += nt) pv = fma(wk.pw[l], wk.vv[l], pv);
-    pv = grp_sum<MULTI>(pv, g, wk.sc);
+    for (int w = 0; w < nw; ++w) pv += scP[w];
     const double Kc = 0.5 * tau * pv;
     for (int l = tid; l < m; l += nt) wk.pw[l] = fma(-Kc, wk.vv[l], wk.pw[l]);
     grp_sync<MULTI>(g);
-    // lower triangle of A22 -= v w^T + w v^T
-    for (int l = warp; l < m; l += nw) {
-      double* row = A + tri(j + 1 + l, j + 1);
-      const double vl = wk.vv[l], wl = wk.pw[l];
-      for (int c = lane; c <= l; c += 32) row[c] = fma(-vl, wk.pw[c], fma(-wl, wk.vv[c], row[c]));
+    // A22 -= u w^T + w u^T (u in vv, w in pw): column 0 of A22 -- the next
+    // step's column -- row r by thread r mod nt, with the partials of s; then
+    // the rest of the packed triangle (rows and columns 1..m-1), element
+    // q = tri(r, c) of it by thread q mod nt
+    const double* uu = wk.vv;
+    const double* ww = wk.pw;
+    double sp = 0.0;
+    for (int r = tid; r < m; r += nt) {
+      double* a = A + tri(j1 + r, j1);
+      const double x = fma(-uu[r], ww[0], fma(-ww[r], u0, *a));
+      *a = x;
+      if (r >= 2) sp = fma(x, x, sp);
     }
+    const int ntri = (m - 1) * m / 2;
+    int q = tid, r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= q) ++r;
+    while (r * (r + 1) / 2 > q) --r;
+    int c = q - r * (r + 1) / 2;
+    for (; q < ntri; q += nt) {
+      double* a = A + tri(j1 + 1 + r, j1 + 1 + c);
+      *a = fma(-uu[r + 1], ww[c + 1], fma(-ww[r + 1], uu[c + 1], *a));
+      c += nt;
+      while (c > r) {
+        c -= r + 1;
+        ++r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(kFull, sp, o);
+    if (lane == 0) scS[warp] = sp;
     grp_sync<MULTI>(g);
+    s = 0.0;
+    for (int w = 0; w < nw; ++w) s += scS[w];
   }
   if (tid == 0) {
     wk.d[N - 2] = A[tri(N - 2, N - 2)];

@@ -343,6 +343,35 @@ __device__ inline double eigen_idx_df(const KitaevWork& wk, const df* d, const d
   return x;
 }
 
+// Sum of a df64 value over a warp (butterfly; df_add is commutative, so every
+// lane ends with the same value).
+__device__ __forceinline__ df warp_sum_df(df x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df y = {__shfl_xor_sync(kFull, x.hi, o), __shfl_xor_sync(kFull, x.lo, o)};
+    x = df_add(x, y);
+  }
+  return x;
+}
+
+// Deterministic df64 sum over a chain's (warp-aligned) group, returned to
+// every thread of it: warp sums, then the warps' partials in warp order.
+// scratch: at least 32 doubles of the group.
+template <bool MULTI>
+__device__ __forceinline__ df grp_sum_df(df x, const Grp& g, double* scratch) {
+  x = warp_sum_df(x);
+  const int r = MULTI ? g.r : (int)threadIdx.x, tpc = MULTI ? g.tpc : (int)blockDim.x;
+  const int warp = r >> 5, nw = tpc >> 5;
+  df* sd = reinterpret_cast<df*>(scratch);
+  grp_sync<MULTI>(g);
+  if ((r & 31) == 0) sd[warp] = x;
+  grp_sync<MULTI>(g);
+  df s = sd[0];
+  for (int w = 1; w < nw; ++w) s = df_add(s, sd[w]);
+  grp_sync<MULTI>(g);
+  return s;
+}
+
 // Kitaev log-weight with the Householder tridiagonalisation of A = M^T M in
 // df64 and the eigenvalues (FP32 isolation + FP64 Newton, as in the FP64
 // stage) and sums in FP64.  res = {log pi, e, c_f, bound}: |log pi - exact| <=
@@ -358,8 +387,8 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   const int N = L * L, tid = MULTI ? g.r : (int)threadIdx.x, nt = MULTI ? g.tpc : (int)blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   df* A = reinterpret_cast<df*>(wk.A);        // same footprint as the FP64 matrix
-  df* dv = reinterpret_cast<df*>(wk.vv);       // Householder vector
   df* pw = reinterpret_cast<df*>(wk.pw);       // p, then w
+  df* uu = reinterpret_cast<df*>(wk.vv);       // Householder vector u
   auto split = [](double x) -> df {
     const float h = (float)x;
     return {h, (float)(x - (double)h)};
@@ -391,59 +420,119 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   }
   const double fro_all = grp_sum<MULTI>((double)fro, g, wk.sc);
   grp_sync<MULTI>(g);
-  for (int j = 0; j < N - 2; ++j) {
-    const int m = N - j - 1;
-    df s = {0.0f, 0.0f};
-    for (int i = j + 2 + tid; i < N; i += nt) {
-      const df a = A[tri(i, j)];
-      s = df_fma(a, a, s);
+  // Householder tridiagonalisation in df64, organised as the FP64 stage's
+  // (kitaev_logpi64): u read from column j, three group barriers per column,
+  // p = tau A22 u one thread per row, the rank-2 update element by element
+  // over the packed triangle.  Every reduction stays in df64 on the FP32 pipe
+  // (an FP64 instruction costs tens of cycles of the SMSP's FP64 pipe on
+  // GB300).  sc[0..31]: per-warp df64 partials of p^T u, sc[32..63]: of s.
+  df* scP = reinterpret_cast<df*>(wk.sc);
+  df* scS = reinterpret_cast<df*>(wk.sc + 32);
+  df s;
+  {
+    df s0 = {0.0f, 0.0f};
+    for (int i = 2 + tid; i < N; i += nt) {
+      const df a = A[tri(i, 0)];
+      s0 = df_fma(a, a, s0);
     }
-    // block sum of df partials (through doubles: exact enough, 2^-53)
-    const double sd = grp_sum<MULTI>(df_to_double(s), g, wk.sc);
-    const df x0 = A[tri(j + 1, j)];
+    s = grp_sum_df<MULTI>(s0, g, wk.sc);
+  }
+  for (int j = 0; j < N - 2; ++j) {
+    const int m = N - j - 1, j1 = j + 1;
+    const df x0 = A[tri(j1, j)];
     if (tid == 0) wk.d[j] = df_to_double(A[tri(j, j)]);
-    if (sd == 0.0) {
+    if (s.hi == 0.0f) {
+      // column already reduced: no reflection; s of the next column directly
       if (tid == 0) wk.e[j] = df_to_double(x0);
-      grp_sync<MULTI>(g);
+      df s2 = {0.0f, 0.0f};
+      for (int i = j + 3 + tid; i < N; i += nt) {
+        const df a = A[tri(i, j1)];
+        s2 = df_fma(a, a, s2);
+      }
+      s = grp_sum_df<MULTI>(s2, g, wk.sc);
       continue;
     }
-    const float sh = (float)sd;
-    const df ss = {sh, (float)(sd - (double)sh)};
-    const df nrm = df_sqrt(df_add(df_mul(x0, x0), ss));
+    const df nrm = df_sqrt(df_add(df_mul(x0, x0), s));
     const df alpha = (x0.hi >= 0.0f) ? df_neg(nrm) : nrm;
-    const df v0 = df_add(x0, df_neg(alpha));
-    const df tau = df_div({2.0f, 0.0f}, df_add(df_mul(v0, v0), ss));
+    const df u0 = df_add(x0, df_neg(alpha));
+    const df tau = df_div({2.0f, 0.0f}, df_add(df_mul(u0, u0), s));
     if (tid == 0) wk.e[j] = df_to_double(alpha);
-    for (int l = tid; l < m; l += nt) dv[l] = (l == 0) ? v0 : A[tri(j + 1 + l, j)];
-    grp_sync<MULTI>(g);
-    for (int l = warp; l < m; l += nw) {
-      df acc = {0.0f, 0.0f};
-      for (int c = lane; c < m; c += 32) {
-        const int off = (c <= l) ? tri(j + 1 + l, j + 1 + c) : tri(j + 1 + c, j + 1 + l);
-        acc = df_fma(A[off], dv[c], acc);
+    // p_l = tau sum_c A22[l][c] u_c with H lanes per row, as in the FP64 stage
+    const int H = row_split(m, nt), h = lane & (H - 1);
+    df part = {0.0f, 0.0f};
+    for (int l0 = 0; l0 < m; l0 += nt / H) {
+      const int l = l0 + warp * (32 / H) + lane / H;
+      df e0 = {0.0f, 0.0f}, e1 = {0.0f, 0.0f};
+      if (l < m) {
+        const df* row = A + tri(j1 + l, j1);
+        int c = h;
+        if (c == 0) {
+          e0 = df_mul(row[0], u0);
+          c = H;
+        }
+        for (; c + H <= l; c += 2 * H) {
+          e1 = df_fma(row[c], A[tri(j1 + c, j)], e1);
+          e0 = df_fma(row[c + H], A[tri(j1 + c + H, j)], e0);
+        }
+        if (c <= l) {
+          e1 = df_fma(row[c], A[tri(j1 + c, j)], e1);
+          c += H;
+        }
+        for (; c + H < m; c += 2 * H) {
+          const int b1 = tri(j1 + c, 0), b2 = tri(j1 + c + H, 0);
+          e0 = df_fma(A[b1 + j1 + l], A[b1 + j], e0);
+          e1 = df_fma(A[b2 + j1 + l], A[b2 + j], e1);
+        }
+        if (c < m) {
+          const int b1 = tri(j1 + c, 0);
+          e0 = df_fma(A[b1 + j1 + l], A[b1 + j], e0);
+        }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const df other = {__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)};
-        acc = df_add(acc, other);
+      df e = df_add(e0, e1);
+      for (int o = 1; o < H; o <<= 1) e = df_add(e, {__shfl_xor_sync(kFull, e.hi, o), __shfl_xor_sync(kFull, e.lo, o)});
+      if (l < m && h == 0) {
+        const df p = df_mul(tau, e), ul = l == 0 ? u0 : A[tri(j1 + l, j)];
+        pw[l] = p;
+        uu[l] = ul;
+        part = df_fma(p, ul, part);
       }
-      if (lane == 0) pw[l] = df_mul(tau, acc);
     }
+    part = warp_sum_df(part);
+    if (lane == 0) scP[warp] = part;
     grp_sync<MULTI>(g);
-    df pv = {0.0f, 0.0f};
-    for (int l = tid; l < m; l += nt) pv = df_fma(pw[l], dv[l], pv);
-    const double pvd = grp_sum<MULTI>(df_to_double(pv), g, wk.sc);
-    const float ph = (float)pvd;
-    const df Kc = df_mul(df_mul({0.5f, 0.0f}, tau), {ph, (float)(pvd - (double)ph)});
-    for (int l = tid; l < m; l += nt) pw[l] = df_add(pw[l], df_neg(df_mul(Kc, dv[l])));
+    df pv = scP[0];
+    for (int w = 1; w < nw; ++w) pv = df_add(pv, scP[w]);
+    const df Kc = df_mul(df_mul({0.5f, 0.0f}, tau), pv);
+    for (int l = tid; l < m; l += nt) pw[l] = df_add(pw[l], df_neg(df_mul(Kc, uu[l])));
     grp_sync<MULTI>(g);
-    for (int l = warp; l < m; l += nw) {
-      df* row = A + tri(j + 1 + l, j + 1);
-      const df vl = dv[l], wl = pw[l];
-      for (int c = lane; c <= l; c += 32)
-        row[c] = df_add(row[c], df_neg(df_add(df_mul(vl, pw[c]), df_mul(wl, dv[c]))));
+    // A22 -= u w^T + w u^T (u in uu, w in pw): column 0 of A22 with the
+    // partials of s, then the rest of the packed triangle, as in the FP64 stage
+    df sp = {0.0f, 0.0f};
+    for (int r = tid; r < m; r += nt) {
+      df* a = A + tri(j1 + r, j1);
+      const df x = df_add(*a, df_neg(df_add(df_mul(uu[r], pw[0]), df_mul(pw[r], u0))));
+      *a = x;
+      if (r >= 2) sp = df_fma(x, x, sp);
     }
+    const int ntri = (m - 1) * m / 2;
+    int q = tid, r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= q) ++r;
+    while (r * (r + 1) / 2 > q) --r;
+    int c = q - r * (r + 1) / 2;
+    for (; q < ntri; q += nt) {
+      df* a = A + tri(j1 + 1 + r, j1 + 1 + c);
+      *a = df_add(*a, df_neg(df_add(df_mul(uu[r + 1], pw[c + 1]), df_mul(pw[r + 1], uu[c + 1]))));
+      c += nt;
+      while (c > r) {
+        c -= r + 1;
+        ++r;
+      }
+    }
+    sp = warp_sum_df(sp);
+    if (lane == 0) scS[warp] = sp;
     grp_sync<MULTI>(g);
+    s = scS[0];
+    for (int w = 1; w < nw; ++w) s = df_add(s, scS[w]);
   }
   if (tid == 0) {
     wk.d[N - 2] = df_to_double(A[tri(N - 2, N - 2)]);
