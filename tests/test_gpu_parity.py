@@ -127,6 +127,30 @@ def test_kitaev_matches_oracle(ctx, L, K, k, n, correct):
     jm.release()
 
 
+@pytest.mark.parametrize("J", [(0.0, 0.0, 1.0), (0.7, 0.0, 1.2), (0.0, 0.9, 1.1)])
+@pytest.mark.parametrize("L", [4, 6])
+def test_kitaev_degenerate_couplings_match_oracle(ctx, L, J):
+    """Vanishing couplings: with J_x = J_y = 0 the matrix M^T M is diagonal,
+    so every column of the Householder reduction is already reduced (the
+    step without a reflection) and the spectrum is N-fold degenerate; with
+    one of them zero the lattice falls apart into chains (repeated
+    eigenvalues, columns that vanish part-way through the reduction).  Both
+    precisions against the oracle's singular values."""
+    from paper_2008_05401_gb300 import FP64, KITAEV, MIXED
+    W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=L + 29)
+    n, S = 24, 3
+    T = wl.kitaev_ladder(n, 24)
+    bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=L + 11))
+    ref = oracle_chains("kitaev", W, hb, vb, L, T, J, SEED, n, bits0)
+    worst = run_oracle(ref, S)
+    mid = ctx.load_model(KITAEV, W, vb, hb)
+    for prec in (FP64, MIXED):
+        job = ctx.new_job(mid, KITAEV, L, T, J, SEED, 0, bits0, prec)
+        job.run(S, precision=prec)
+        _compare(job, ref, worst, S)
+        job.release()
+
+
 def test_random_init_matches_oracle(ctx):
     """init = 0 draws the lattices from the stream's init tag on the device."""
     from oracle import chain
