@@ -28,8 +28,10 @@ struct ChainSm {
   double beta;
   double thr[5];         // local Ising sweeps: e^{-beta dE} 2^32 for 0..4 unequal neighbours
   double logu;           // tensor-core kernel: log u of the current proposal's MH draw
+  double cst, mgs;       // tensor-core kernel: the tile's constant margin terms, the
+                         // current state's margin terms (both off the MH thread's path)
   unsigned long long acc, rec, rec_mh;
-  int cur, flag_rec, flag_acc, pad;
+  int cur, flag_rec, flag_acc, onesp;   // onesp: set units of the proposal (tensor-core kernel)
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }

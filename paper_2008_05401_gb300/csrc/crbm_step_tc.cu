@@ -659,6 +659,11 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
       ch.os[o] = on ? jb.obs[(size_t)c * kNobs + o] : 0.0;
     }
     ch.beta = on ? 1.0 / jb.T[c] : 1.0;
+    // margin terms that do not depend on the proposal: the tile's constants
+    // (the fixed-point conversion rounds each thread's sum by <= 2^-33) and
+    // those of the current state, renewed whenever the state changes
+    ch.cst = (double)K * (double)(LT * LT) * ((double)jb.csp + (double)jb.tcft) + (double)(kEpi / CH) * 0x1p-33;
+    ch.mgs = ((ch.Fb + ch.lpb) + 1e-12 * (fabs(ch.lp) + fabs(ch.F))) + (ch.cst + 1e-300);
     ch.acc = 0ull;
     ch.rec_mh = 0ull;
     ch.flag_rec = 0;
@@ -925,6 +930,9 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
     }
     __syncthreads();
     // thread c < CH: the MH decision of chain c0 + c
+    // after the decision, by a lane of warp 1 per chain (beside the accept
+    // copies): the accepted state, its observables, the running sums and
+    // the state's margin terms for the next decision
     auto settle = [&](ChainSm& ch, int c) {
       if (ch.flag_acc) {
         ch.F = ch.Fp;
@@ -932,9 +940,15 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
         ch.lp = ch.lpp;
         ch.lpb = ch.lppb;
         ch.E = ch.Ep;
-        for (int o = 0; o < kNobs; ++o) ch.ot[o] = ch.otp[o];
+        const double M = (double)(2 * ch.onesp - LT * LT);
+        ch.ot[0] = ch.Ep;
+        ch.ot[1] = ch.Ep * ch.Ep;
+        ch.ot[2] = fabs(M);
+        ch.ot[3] = M * M;
         ch.acc += 1ull;
       }
+      // (a second-level recompute may also have tightened F(v) of a rejected proposal)
+      ch.mgs = ((ch.Fb + ch.lpb) + 1e-12 * (fabs(ch.lp) + fabs(ch.F))) + (ch.cst + 1e-300);
       for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
       if (c0 + c < jb.n_chains) trace_store(jb, c0 + c, step0 + (uint64_t)s, ch.E);
     };
@@ -956,22 +970,20 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
           ones += redc[w] & 0xFFFFu;
           pairs += redc[w] >> 16;
         }
-      // the fixed-point conversion rounds each thread's sum by <= 2^-33; the FP32
-      // sums of the non-negative bound terms over 512 / CH threads and then over
-      // 16 warps lose < 26 2^-24 relative, inside the factor 1.001
+      // the FP32 sums of the non-negative bound terms over 512 / CH threads and
+      // then over 16 warps lose < 26 2^-24 relative, inside the factor 1.001
       constexpr int kN = LT * LT;
-      // margin terms known before this proposal's sums, off the dependent chain
-      const double cst = (double)K * (double)kN * ((double)jb.csp + (double)jb.tcft) + (512.0 / CH) * 0x1p-33;
-      const double mg0 = ((Fb + lpb) + 1e-12 * (fabs(lp) + fabs(F))) + (cst + 1e-300);
+      // the margin terms known before this proposal's sums come precomputed
+      // (ch.cst, ch.mgs); the observables wait for the decision
+      const double cst = ch.cst, mg0 = ch.mgs;
       const double Fdata = (double)bnd * 1.001;
       const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
-      const double M = (double)(2 * (int)ones - kN);
       const double lpp = -beta * E;
       const double Fp = fma((double)fs, -0x1p-32, -jb.vb * (double)ones);
       const double Bp = (Fdata + cst) + 1e-12 * fabs(Fp);
       ch.Ep = E;
       ch.lpp = lpp;
-      ch.otp[0] = E; ch.otp[1] = E * E; ch.otp[2] = fabs(M); ch.otp[3] = M * M;
+      ch.onesp = (int)ones;
       ch.lppb = 0.0;
       ch.Fp = Fp;
       ch.Bp = Bp;
@@ -986,13 +998,12 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
         else if (logu - logr > Mg) ch.flag_acc = 0;
         else ch.flag_rec = 1;
       }
-      if (!ch.flag_rec) settle(ch, tid);
     }
     if (__syncthreads_or(tid < CH && ch_of(tid).flag_rec)) {
       mh_redo<LT>(jb, &ch_of(0), scratch, pv, vbits, step, c0);
-      if (tid < CH && ch_of(tid).flag_rec) settle(ch_of(tid), tid);
       __syncthreads();
     }
+    if (warp == 1 && lane < CH) settle(ch_of(lane), lane);
     // accepted: v' becomes v (packed, and its operand rows into operand 0 when
     // they are in operand 1); rejected after several Gibbs steps: operand 0
     // was overwritten, so v is expanded again
