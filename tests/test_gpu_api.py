@@ -83,7 +83,7 @@ def test_kitaev_batch_of_mixed_sizes_equals_alone(ctx, prec):
         b.release()
 
 
-@pytest.mark.parametrize("L,prec", [(6, 1), (4, 0)])
+@pytest.mark.parametrize("L,prec", [(6, 1), (6, 0), (4, 0)])
 def test_autotuned_kitaev_groups_keep_parity(ctx, L, prec):
     """crbm_tune picks the chains (thread groups) per CTA of a Kitaev shape;
     a job created afterwards, with a short last tile, reproduces the oracle."""
