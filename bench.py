@@ -300,9 +300,10 @@ def time_jobs(ctx, jobs, S, prec, steps, warmup, stream, dev, flush, graph=False
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
-def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False, clocks=None):
+def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False, clocks=None, tune=None):
     """Proposals/s of another workload or precision (no e2e, no clocks); graph:
-    replay a captured CUDA graph of the batched run."""
+    replay a captured CUDA graph of the batched run; tune (default: with the
+    graph): autotuned tiles first."""
     from paper_2008_05401_gb300 import MIXED
     spec = workload(name)
     ctx = ctx_cls(dev)
@@ -313,7 +314,7 @@ def secondary(ctx_cls, name, prec, steps, dev, stream, flush, graph=False, clock
         jobs.append(ctx.new_job(mid, spec["kind"], L, spec["T"](n), spec["J"], SEED, base,
                                 wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec))
         base += n
-    if graph:
+    if graph if tune is None else tune:
         for L, _ in spec["jobs"]:
             ctx.tune(mid, L, prec)            # autotuned tiles (Kitaev: chains, i.e. thread groups, per CTA)
     ms = time_jobs(ctx, jobs, spec["S"], prec, steps, 1, stream, dev, flush, graph=graph)
@@ -741,6 +742,8 @@ def main():
     if rank == 0 and not args.no_secondary and args.workload == "ising-batch":
         line["secondary"] = [
             secondary(Context, "ising-batch", FP64, 2, dev, stream, flush),
+            # the persistent tensor-core launch of the whole batch, replayed from a captured graph
+            secondary(Context, "ising-batch", MIXED, 3, dev, stream, flush, graph=True, clocks=clocks, tune=False),
             secondary(Context, "kitaev-small", FP64, 3, dev, stream, flush),
             secondary(Context, "kitaev-small", MIXED, 3, dev, stream, flush, clocks=clocks),
             secondary(Context, "kitaev-batch", FP64, 2, dev, stream, flush),
