@@ -597,7 +597,7 @@ __device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t byt
 // wait has run out; the launch's results are then void).
 template <int LT, int KT, int kT>
 __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& jb, int c0, unsigned char* smem,
-                                        uint32_t bar0, uint32_t tmem, volatile int* abort) {
+                                        uint32_t bar0, uint32_t tmem, volatile int* abort, uint8_t* stab) {
   using G = Geo<LT>;
   constexpr int CH = G::CH, WPC = G::WPC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -616,6 +616,13 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
   const int nval = jb.n_chains - c0 < CH ? jb.n_chains - c0 : CH;   // chains of this tile
   const uint32_t vbytes = (uint32_t)(nval * WPC * 4);               // their packed lattices
 
+  // the stage order of a Gibbs step as a table (type | tile << 2), read by
+  // the issuing and the epilogue warps at every stage
+  if (tid < G::NHV) {
+    int ty, tl;
+    hv_stage<LT>(tid, ty, tl);
+    stab[tid] = (uint8_t)(ty | (tl << 2));
+  }
   if (tid == 0) {
     for (int b = 0; b < kNbuf; ++b) {
       mbar_init(bar(kBarFull + b), 2);
@@ -746,8 +753,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
       const uint32_t zbase = zc;
       if (issuer) {
         for (int z = 0; z < G::NHV; ++z, ++zc) {
-          int ty, tl;
-          hv_stage<LT>(z, ty, tl);
+          const int ty = stab[z] & 3, tl = stab[z] >> 2;
           const uint32_t d = mma_claim();
           if (ty == kStV) {
             wait_bar(bar(kBarH + ((2 * tl + G::NT - 1) % G::NT)), gs & 1u);
@@ -760,8 +766,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
         }
       } else if (epi) {
         for (int z = 0; z < G::NHV; ++z, ++zc) {
-          int ty, tl;
-          hv_stage<LT>(z, ty, tl);
+          const int ty = stab[z] & 3, tl = stab[z] >> 2;
           // this stage's Philox words do not depend on its MMAs: drawn before
           // waiting for them, so the counter-based generator overlaps the
           // tensor-core work and the accumulator loads
@@ -1066,6 +1071,7 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
   __shared__ __align__(8) unsigned long long s_bar[kNbar];
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_abort;
+  __shared__ uint8_t s_stage[32];
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) s_abort = 0;
   if (warp == 16) {
@@ -1087,10 +1093,10 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     while (jid + 1 < prm.n_jobs && item >= prm.tile_begin[jid + 1]) ++jid;
     const JobDev& jb = prm.job[jid];
     const int t = item - prm.tile_begin[jid];
-    if (jb.L == 128) tc_tile<128, KT, kT>(prm, jb, t, smem, bar0, tmem, abort);
-    else if (jb.L == 64) tc_tile<64, KT, kT>(prm, jb, 2 * t, smem, bar0, tmem, abort);
-    else if (jb.L == 32) tc_tile<32, KT, kT>(prm, jb, 4 * t, smem, bar0, tmem, abort);
-    else tc_tile<16, KT, kT>(prm, jb, 8 * t, smem, bar0, tmem, abort);
+    if (jb.L == 128) tc_tile<128, KT, kT>(prm, jb, t, smem, bar0, tmem, abort, s_stage);
+    else if (jb.L == 64) tc_tile<64, KT, kT>(prm, jb, 2 * t, smem, bar0, tmem, abort, s_stage);
+    else if (jb.L == 32) tc_tile<32, KT, kT>(prm, jb, 4 * t, smem, bar0, tmem, abort, s_stage);
+    else tc_tile<16, KT, kT>(prm, jb, 8 * t, smem, bar0, tmem, abort, s_stage);
   }
   tc_fence_before();
   __syncthreads();
