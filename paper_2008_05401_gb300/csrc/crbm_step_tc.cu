@@ -86,7 +86,7 @@ struct Geo {
 };
 
 struct TcLayout {
-  uint32_t opv[2], vbuf, plast, hold, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, total;
+  uint32_t opv[2], vbuf, plast, hold, bh, bv, vbits, pb[2], hbits, scratch, ch, misc, lut, total;
 };
 
 template <int LT>
@@ -108,6 +108,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int k) {
   l.scratch = o; o += 256 * 8;
   l.ch = o; o += (uint32_t)align16(G::CH * sizeof(ChainSm));
   l.misc = o; o += G::MISC;           // mbarriers, TMEM address, counters, reduction slots
+  l.lut = o; o += 256 * 16;            // fp16 operand images of the 256 bytes of units
   l.total = o;
   return l;
 }
@@ -375,9 +376,7 @@ __device__ __forceinline__ void epi_hidden(const JobDev& jb, unsigned char* smem
       }
   }
   smem[hbc + (uint32_t)f * (G::WPC * 4) + (uint32_t)(n0 >> 3)] = (unsigned char)byte;
-  const uint32_t z = byte | (byte << 15);     // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
-  const uint4 h4 = make_uint4(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u,
-                              ((z >> 4) & 0x10001u) * 0x3C00u, ((z >> 6) & 0x10001u) * 0x3C00u);
+  const uint4 h4 = *(const uint4*)(smem + ly.lut + byte * 16u);   // the 8 units as fp16 0 / 1
   // operand rows m + HH of the V operands; rows 128-HH..127 also as rows -HH..-1
   const uint32_t r0 = (uint32_t)(m + G::HH) * 16, r1 = (uint32_t)(m - (128 - G::HH)) * 16;
   auto put = [&](uint32_t base) {
@@ -410,7 +409,7 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
                                             const float (&s1)[4], const float (&s0)[4], int m, int i, int cq,
                                             int u, const uint4& w, uint32_t* dbc, uint32_t opv,
                                             const uint32_t* hbc, uint32_t hbar, uint32_t parity, long long limit,
-                                            volatile int* abort, int* err, unsigned& nrec) {
+                                            volatile int* abort, int* err, unsigned& nrec, uint32_t lut) {
   using G = Geo<LT>;
   const int j0 = 16 * u + 4 * cq, n0 = i * LT + j0;
   uint32_t nib = 0u, amb = 0u;
@@ -435,8 +434,7 @@ __device__ __forceinline__ void epi_visible(const JobDev& jb, unsigned char* sme
       }
   }
   atomicOr(dbc + (n0 >> 5), nib << (n0 & 31));
-  const uint32_t z = nib | (nib << 15);
-  const uint2 h2 = make_uint2(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u);
+  const uint2 h2 = *(const uint2*)(smem + lut + nib * 16u);        // the 4 units as fp16 0 / 1
   const uint32_t off = opv + (uint32_t)(j0 >> 3) * G::LBO + (uint32_t)(j0 & 7) * 2;
   *(uint2*)(smem + off + (uint32_t)m * 16) = h2;
   if (m < G::HH) *(uint2*)(smem + off + (uint32_t)(m + 128) * 16) = h2;
@@ -646,6 +644,11 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
   // V buffers zeroed: the groups of filters f >= K are read (with zero weights)
   // by the last K-step when 3K is odd, and must hold finite values
   for (int q = tid; q < 2 * G::VBUF / 16; q += kThr) ((uint4*)(smem + ly.vbuf))[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (int q = tid; q < 256; q += kThr) {
+    const uint32_t z = (uint32_t)q | ((uint32_t)q << 15);   // bit b at b and b + 15: pairs (2p, 2p+1) at 2p and 2p + 16
+    ((uint4*)(smem + ly.lut))[q] = make_uint4(((z >> 0) & 0x10001u) * 0x3C00u, ((z >> 2) & 0x10001u) * 0x3C00u,
+                                              ((z >> 4) & 0x10001u) * 0x3C00u, ((z >> 6) & 0x10001u) * 0x3C00u);
+  }
   for (int w = tid; w < CH * WPC; w += kThr) {
     if (w >= nval * WPC) vbits[w] = 0u;       // empty chain slots of a short last tile
     ((uint32_t*)(smem + ly.pb[0]))[w] = 0u;
@@ -843,7 +846,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
             epi_release();
             epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
                             (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.wait_limit, abort,
-                            prm.err, nrec);
+                            prm.err, nrec, ly.lut);
             if (tl == G::NV - 1) epi_publish(bar(kBarV));
           }
         }
