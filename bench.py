@@ -139,10 +139,10 @@ def peaks():
 
 # DRAM bytes (read + write) of one full-size launch of the persistent
 # tensor-core kernel on the batch Ising workload (the timed step after three
-# warm-up steps, L2 flushed before it), from an ncu capture: 14,972,416 B read,
-# 73,472 B written (the lattices and state written back stay in the 129 MB L2
+# warm-up steps, L2 flushed before it), from an ncu capture: 14,549,248 B read,
+# 60,416 B written (the lattices and state written back stay in the 129 MB L2
 # until after the launch).
-BATCH_ISING_TC_TRAFFIC_BYTES = 14_972_416 + 73_472
+BATCH_ISING_TC_TRAFFIC_BYTES = 14_549_248 + 60_416
 
 
 def _sm_mhz(clocks):
