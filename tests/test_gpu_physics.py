@@ -192,6 +192,72 @@ def test_full_size_batch_launch_replays_every_recompute(ctx):
         j.release()
 
 
+def test_full_size_kitaev_batch_replays_sampled_chains(ctx):
+    """The Kitaev batch workload in the bench's launch configuration: 683, 683
+    and 682 chains of L = 8, 10 and 12 (N = 64, 100, 144) over the 24-point
+    ladder T in [0.005, 1], K = 4 filters 3 x 3 N(0, 0.05^2), mixed precision,
+    all three sizes in one batched call (one launch).  After 2 proposals the
+    state is read; then 2 more.  From every size, every chain whose MH
+    decision was redone with the FP64 eigen-stage, chains with FP64 Bernoulli
+    redos and random chains are replayed by the oracle from that state:
+    lattices and accepts identical, log pi and F (read back in FP64) within
+    1e-10, e and the observable sums within 1e-9."""
+    from oracle import chain
+    from paper_2008_05401_gb300 import KITAEV, MIXED
+    W, hb, vb = wl.gaussian_crbm(4, 3, 0.05)
+    sizes = ((8, 683), (10, 683), (12, 682))
+    J = (1.0, 1.0, 1.0)
+    mid = ctx.load_model(KITAEV, W, vb, hb)
+    jobs, bases, base = [], [], 0
+    for L, n in sizes:
+        jobs.append(ctx.new_job(mid, KITAEV, L, wl.kitaev_ladder(n, 24), J, SEED, base,
+                                wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), MIXED))
+        bases.append(base)
+        base += n
+    S0, S = 2, 2
+    ctx.run_batch(jobs, S0, precision=MIXED)
+    before = [(j.state(), j.observables()) for j in jobs]
+    ctx.run_batch(jobs, S, precision=MIXED)
+    for (L, n), b0, j, ((bits0, step0), (sums0, acc0, rec0)) in zip(sizes, bases, jobs, before):
+        T = wl.kitaev_ladder(n, 24)
+        bits, step = j.state()
+        lp, F, E = j.energies()
+        sums, acc, rec = j.observables()
+        assert step == S0 + S
+        d_acc, d_rec, d_sums = acc - acc0, rec - rec0, sums - sums0
+        mh = np.nonzero(d_rec[:, 1])[0]
+        bern = np.nonzero(d_rec[:, 0])[0]
+        rand = np.random.default_rng(L).choice(n, 24, replace=False)
+        sel = np.unique(np.concatenate([mh, bern[:24], rand]))
+        compared = []
+        for g0 in range(0, len(sel), 32):
+            cs = sel[g0:g0 + 32]
+            ref = chain.make_chains(chain.KITAEV, W, hb, vb, L, T[cs], J, SEED, b0 + cs,
+                                    v0=wl.unpack_bits(bits0[cs], L))
+            ref.step = step0
+            bm = np.full(len(cs), np.inf)
+            mm = np.full(len(cs), np.inf)
+
+            def rec_margins(c, d):
+                bm[:] = np.minimum(bm, d["bernoulli_margin"])
+                mm[:] = np.minimum(mm, d["mh_margin"] / d["mh_scale"])
+
+            chain.run(ref, S, record=rec_margins)
+            for q, c in enumerate(cs):
+                if bm[q] <= 1e-12 or mm[q] <= 1e-10:    # both sides may legitimately differ there
+                    continue
+                np.testing.assert_array_equal(bits[c], wl.pack_bits(ref.v[q:q + 1])[0], err_msg=f"L={L} chain {c}")
+                assert d_acc[c] == ref.accepts[q], (L, c)
+                np.testing.assert_allclose(lp[c], ref.logpi[q], rtol=1e-10, atol=1e-9)
+                np.testing.assert_allclose(F[c], ref.F[q], rtol=1e-10, atol=1e-10)
+                np.testing.assert_allclose(E[c], ref.E_phys[q], rtol=1e-9, atol=1e-9)
+                np.testing.assert_allclose(d_sums[c], ref.obs[q], rtol=1e-9, atol=1e-9)
+                compared.append(int(c))
+        assert len(compared) >= len(sel) - 2, (L, len(compared), len(sel))
+    for j in jobs:
+        j.release()
+
+
 def _binned(x, nb):
     """Means of nb consecutive blocks along axis 1 of (chains, steps) x, flattened."""
     C, n = x.shape
