@@ -192,32 +192,36 @@ def test_full_size_batch_launch_replays_every_recompute(ctx):
         j.release()
 
 
-def test_full_size_kitaev_batch_replays_sampled_chains(ctx):
-    """The Kitaev batch workload in the bench's launch configuration: 683, 683
-    and 682 chains of L = 8, 10 and 12 (N = 64, 100, 144) over the 24-point
-    ladder T in [0.005, 1], K = 4 filters 3 x 3 N(0, 0.05^2), mixed precision,
-    all three sizes in one batched call (one launch).  After 2 proposals the
-    state is read; then 2 more.  From every size, every chain whose MH
-    decision was redone with the FP64 eigen-stage, chains with FP64 Bernoulli
-    redos and random chains are replayed by the oracle from that state:
-    lattices and accepts identical, log pi and F (read back in FP64) within
-    1e-10, e and the observable sums within 1e-9."""
+KITAEV_WORKLOADS = [((8, 683), (10, 683), (12, 682)), ((6, 1024),)]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("sizes", KITAEV_WORKLOADS)
+def test_full_size_kitaev_batch_replays_sampled_chains(ctx, sizes, prec):
+    """The Kitaev workloads in the bench's launch configuration -- the batch of
+    683, 683 and 682 chains of L = 8, 10 and 12 (N = 64, 100, 144) in one
+    batched call (one launch), and 1024 chains of L = 6 -- over the 24-point
+    ladder T in [0.005, 1], K = 4 filters 3 x 3 N(0, 0.05^2), mixed precision
+    and FP64.  After 2 proposals the state is read; then 2 more.  From every
+    size, every chain whose MH decision was redone with the FP64 eigen-stage,
+    chains with FP64 Bernoulli redos and random chains are replayed by the
+    oracle from that state: lattices and accepts identical, log pi and F (read
+    back in FP64) within 1e-10, e and the observable sums within 1e-9."""
     from oracle import chain
-    from paper_2008_05401_gb300 import KITAEV, MIXED
+    from paper_2008_05401_gb300 import KITAEV
     W, hb, vb = wl.gaussian_crbm(4, 3, 0.05)
-    sizes = ((8, 683), (10, 683), (12, 682))
     J = (1.0, 1.0, 1.0)
     mid = ctx.load_model(KITAEV, W, vb, hb)
     jobs, bases, base = [], [], 0
     for L, n in sizes:
         jobs.append(ctx.new_job(mid, KITAEV, L, wl.kitaev_ladder(n, 24), J, SEED, base,
-                                wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), MIXED))
+                                wl.pack_bits(wl.random_lattices(n, L, seed=SEED + L)), prec))
         bases.append(base)
         base += n
     S0, S = 2, 2
-    ctx.run_batch(jobs, S0, precision=MIXED)
+    ctx.run_batch(jobs, S0, precision=prec)
     before = [(j.state(), j.observables()) for j in jobs]
-    ctx.run_batch(jobs, S, precision=MIXED)
+    ctx.run_batch(jobs, S, precision=prec)
     for (L, n), b0, j, ((bits0, step0), (sums0, acc0, rec0)) in zip(sizes, bases, jobs, before):
         T = wl.kitaev_ladder(n, 24)
         bits, step = j.state()
