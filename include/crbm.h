@@ -420,6 +420,19 @@ CRBM_API int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t
  * either way.  Errors: CRBM_EINVAL (null bits, step >= 2^32, precision). */
 CRBM_API int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step, int precision);
 
+/* crbm_write_state for several jobs at once (no counterpart in the paper: a
+ * batching convenience of this library).  Job i's lattices are read from
+ * bits[i] (host memory, n_chains * ceil(L*L/32) words; may be NULL for an
+ * empty job) and its step counter set to steps[i]; then every listed job is
+ * re-evaluated as crbm_write_state does, in ONE launch (jobs of every side
+ * together) followed by one synchronisation, instead of one launch and one
+ * synchronisation per job.  Host buffers are read during the call only.
+ * Results are identical to crbm_write_state job by job.  Errors: CRBM_EINVAL
+ * (n_jobs outside 0..16, a bad or repeated job id, null pointers, a step >=
+ * 2^32, bad precision), CRBM_ECUDA. */
+CRBM_API int crbm_write_states(crbm_ctx* ctx, int n_jobs, const int* job_ids, const uint32_t* const* bits,
+                               const uint64_t* steps, int precision);
+
 /* Forget a job (its dev_mem may be freed afterwards) and return its bytes to
  * the context's budget. */
 CRBM_API int crbm_release(crbm_ctx* ctx, int job_id);

@@ -77,6 +77,7 @@ _SIGS = {
     "crbm_read_observables": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
     "crbm_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_int]),
+    "crbm_write_states": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "crbm_release": (C.c_int, [C.c_void_p, C.c_int]),
 }
 EXPORTS = tuple(_SIGS)
@@ -286,6 +287,16 @@ def crbm_write_state(ctx, job_id, bits, step, precision=FP64):
     _check(ctx, load().crbm_write_state(ctx, job_id, _ptr(bits), step, precision))
 
 
+def crbm_write_states(ctx, job_ids, bits_list, steps, precision=FP64):
+    """crbm_write_state for several jobs, one evaluation launch for all."""
+    n = len(job_ids)
+    arrs = [np.ascontiguousarray(b, dtype=np.uint32) for b in bits_list]
+    ids = (C.c_int * n)(*job_ids)
+    ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+    st = (C.c_uint64 * n)(*steps)
+    _check(ctx, load().crbm_write_states(ctx, n, ids, ptrs, st, precision))
+
+
 def crbm_release(ctx, job_id):
     _check(ctx, load().crbm_release(ctx, job_id))
 
@@ -420,6 +431,12 @@ class Context:
         series = series.contiguous()
         return crbm_autocorr(self.h, series.data_ptr(), series.shape[1], series.shape[0], c,
                              _stream_handle(stream))
+
+    def write_states(self, jobs, bits_list, steps, precision=FP64):
+        """Job.write_state for several jobs of this context, one evaluation launch."""
+        crbm_write_states(self.h, [j.id for j in jobs], bits_list, steps, precision)
+        for j, st in zip(jobs, steps):
+            j.step = st
 
     def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
         crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))

@@ -1426,6 +1426,66 @@ int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t s
   return evaluate(ctx, job_id, precision);
 }
 
+int crbm_write_states(crbm_ctx* ctx, int n_jobs, const int* job_ids, const uint32_t* const* bits,
+                      const uint64_t* steps, int precision) {
+  if (!ctx) return CRBM_EINVAL;
+  if (n_jobs < 0 || n_jobs > kMaxJobs) return fail(ctx, CRBM_EINVAL, "n_jobs must be 0..%d", kMaxJobs);
+  if (n_jobs > 0 && (!job_ids || !bits || !steps)) return fail(ctx, CRBM_EINVAL, "null job_ids, bits or steps");
+  if (precision != CRBM_FP64 && precision != CRBM_MIXED) return fail(ctx, CRBM_EINVAL, "bad precision");
+  std::vector<int> ids;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  for (int i = 0; i < n_jobs; ++i) {
+    Job* j = get_job(ctx, job_ids[i]);
+    if (!j) return fail(ctx, CRBM_EINVAL, "bad job id %d", job_ids[i]);
+    for (int q = 0; q < i; ++q)
+      if (job_ids[q] == job_ids[i]) return fail(ctx, CRBM_EINVAL, "job %d listed twice", job_ids[i]);
+    if (!bits[i] && j->n > 0) return fail(ctx, CRBM_EINVAL, "null bits for job %d", job_ids[i]);
+    if (steps[i] >= (1ull << 32)) return fail(ctx, CRBM_EINVAL, "step must stay below 2^32");
+  }
+  for (int i = 0; i < n_jobs; ++i) {
+    const int rc = crbm_sync(ctx, job_ids[i]);
+    if (rc) return rc;
+  }
+  // the steps stay in host memory until the copies have run (synchronised below)
+  std::vector<unsigned long long> st(steps, steps + n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    Job& j = ctx->jobs[job_ids[i]];
+    j.step = steps[i];
+    if (j.n == 0) continue;
+    CK(cudaMemcpyAsync(j.mem + j.lay.bits, bits[i], (size_t)j.n * j.Wd * 4, cudaMemcpyHostToDevice, ctx->own),
+       "copy bits");
+    CK(cudaMemcpyAsync(j.mem + j.lay.step, &st[i], 8, cudaMemcpyHostToDevice, ctx->own), "copy step");
+    ids.push_back(job_ids[i]);
+  }
+  if (ids.empty()) return CRBM_OK;
+  // one evaluation launch per (model kind, filter shape): the table kernel
+  // takes jobs of every side of a shape in one launch
+  std::vector<bool> done(ids.size(), false);
+  for (size_t a = 0; a < ids.size(); ++a) {
+    if (done[a]) continue;
+    const Job& ja = ctx->jobs[ids[a]];
+    const Model& ma = ctx->models[ja.model];
+    std::vector<int> grp;
+    for (size_t b = a; b < ids.size(); ++b) {
+      const Job& jb = ctx->jobs[ids[b]];
+      const Model& mb = ctx->models[jb.model];
+      if (!done[b] && jb.kind == ja.kind && mb.K == ma.K && mb.k == ma.k) {
+        grp.push_back(ids[b]);
+        done[b] = true;
+      }
+    }
+    const int rc = launch_jobs(ctx, grp, 0, 1, 1, precision, 1, ctx->own);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(ctx->own), "evaluate");
+  for (int id : ids) {
+    ctx->jobs[id].exact = true;
+    ctx->jobs[id].fexact = (precision == kFP64);
+    ctx->jobs[id].f64vals = (precision == kFP64);
+  }
+  return CRBM_OK;
+}
+
 int crbm_release(crbm_ctx* ctx, int job_id) {
   Job* j = get_job(ctx, job_id);
   if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;

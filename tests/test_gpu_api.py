@@ -147,6 +147,49 @@ def test_split_runs_and_checkpoint_resume(ctx):
         j.release()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_write_states_equals_write_state_job_by_job(ctx, prec):
+    """crbm_write_states (several jobs, one evaluation launch) leaves every job
+    exactly as crbm_write_state does job by job -- jobs of several sides, an
+    empty job and a Kitaev job of another filter shape in one call -- and the
+    chains then continue identically; a repeated job id is rejected."""
+    from paper_2008_05401_gb300 import ISING, KITAEV, CrbmError
+    mid = _ising_model(ctx)
+    W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=5)
+    kid = ctx.load_model(KITAEV, W, vb, hb)
+    specs = [(mid, ISING, 16, 40, (1.0,)), (mid, ISING, 64, 9, (1.0,)), (mid, ISING, 8, 0, (1.0,)),
+             (kid, KITAEV, 4, 10, (1.0, 1.0, 1.0))]
+
+    def make(seed):
+        out = []
+        for m, kind, L, n, J in specs:
+            T = wl.ising_ladder(n, 4) if kind == ISING else wl.kitaev_ladder(n, 24)
+            out.append(ctx.new_job(m, kind, L, T, J, SEED, 100, wl.pack_bits(wl.random_lattices(n, L, seed=seed)),
+                                   prec))
+        return out
+
+    a, b = make(1), make(1)
+    new_bits = [wl.pack_bits(wl.random_lattices(n, L, seed=L + 50)) for _, _, L, n, _ in specs]
+    steps = [7, 3, 0, 11]
+    ctx.write_states(a, new_bits, steps, prec)
+    for j, bits, st in zip(b, new_bits, steps):
+        j.write_state(bits, st, prec)
+    for ja, jb in zip(a, b):
+        sa, sb = _snapshot(ja), _snapshot(jb)
+        for key in sa:
+            np.testing.assert_array_equal(sa[key], sb[key], err_msg=key)
+    for ja, jb in zip(a, b):
+        ja.run(4, precision=prec)
+        jb.run(4, precision=prec)
+        sa, sb = _snapshot(ja), _snapshot(jb)
+        for key in sa:
+            np.testing.assert_array_equal(sa[key], sb[key], err_msg=key)
+    with pytest.raises(CrbmError):
+        ctx.write_states([a[0], a[0]], [new_bits[0], new_bits[0]], [1, 1], prec)
+    for j in a + b:
+        j.release()
+
+
 def test_empty_job_and_zero_steps(ctx):
     from paper_2008_05401_gb300 import FP64, ISING, KITAEV
     mid = _ising_model(ctx)
