@@ -338,14 +338,16 @@ static int launch_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int c
 // are the same alone or batched.
 static bool on_tc(const crbm_ctx* ctx, const Job& j, int prec, int mode) {
   const Model& m = ctx->models[j.model];
-  return ctx->use_tc && ctx->tc_ok && mode == 0 && m.d_tc && !m.edge && tc_supported(j.kind, prec, j.L, m.K, m.k);
+  return ctx->use_tc && ctx->tc_ok && (mode == 0 || mode == 1) && m.d_tc && !m.edge &&
+         tc_supported(j.kind, prec, j.L, m.K, m.k);
 }
 
 // One persistent launch of the tensor-core kernel for the given jobs (any of
 // the four sides): a tile of 128 / L chains per work item, the jobs ordered by
 // decreasing L so that the longest items go first; the work-queue counter is
 // the first job's.
-static int launch_tc_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int correct, cudaStream_t st) {
+static int launch_tc_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, int correct, int mode,
+                           cudaStream_t st) {
   std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return ctx->jobs[a].L > ctx->jobs[b].L; });
   LaunchParams p;
   memset(&p, 0, sizeof p);
@@ -353,7 +355,7 @@ static int launch_tc_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, in
   p.S = S;
   p.g = g;
   p.correct = correct;
-  p.mode = 0;
+  p.mode = mode;                 // 0: proposals, 1: evaluation of the current lattices
   p.err = ctx->d_err;
   p.wait_limit = ctx->wait_limit;
   int tiles = 0;
@@ -369,7 +371,7 @@ static int launch_tc_group(crbm_ctx* ctx, std::vector<int> ids, int S, int g, in
   }
   p.tile_begin[ids.size()] = tiles;
   p.total_items = tiles;
-  if (tiles == 0 || S == 0) return CRBM_OK;
+  if (tiles == 0 || (S == 0 && mode == 0)) return CRBM_OK;
   const Job& lead = ctx->jobs[ids[0]];
   p.queue = (int*)(lead.mem + lead.lay.sched);
   CK(launch_tc(p, std::min(tiles, ctx->sms), smem, st), "kernel launch");
@@ -391,7 +393,7 @@ static int launch_jobs(crbm_ctx* ctx, const std::vector<int>& ids, int S, int g,
     if (!part.empty()) parts.emplace_back(nt, part);
   }
   auto launch_part = [&](const std::pair<int, std::vector<int>>& pt, cudaStream_t s) {
-    return pt.first < 0 ? launch_tc_group(ctx, pt.second, S, g, correct, s)
+    return pt.first < 0 ? launch_tc_group(ctx, pt.second, S, g, correct, mode, s)
                         : launch_group(ctx, pt.second, S, g, correct, prec, mode, pt.first, s, partner);
   };
   if (parts.size() <= 1) {

@@ -593,7 +593,7 @@ __device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t byt
 // memory at column tmem; bar0: shared address of the CTA's mbarriers (set
 // up here, invalidated at the end).  abort: the CTA's abort flag (up once a
 // wait has run out; the launch's results are then void).
-template <int LT, int KT, int kT>
+template <int LT, int KT, int kT, bool EVAL>
 __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& jb, int c0, unsigned char* smem,
                                         uint32_t bar0, uint32_t tmem, volatile int* abort, uint8_t* stab) {
   using G = Geo<LT>;
@@ -731,151 +731,16 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
     mbar_arrive_if(b, lane == 0);
   };
 
-  for (int s = 0; s < prm.S; ++s) {
-    const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
-    if (warp == 17 && lane >= 1 && lane <= CH && prm.correct) {
-      // the MH draws of this proposal, ahead of the decisions (read after the
-      // barriers of the proposal's end).  In FP32, within 2^-20 (1 + |log u|)
-      // of the FP64 log u, which the decision adds to its margin: the FP64 log
-      // would hold this warp's issuing lane, whose commits every stage waits
-      // for, for thousands of cycles on the 1/64-rate FP64 pipe
-      const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, (uint32_t)(jb.cid_base + (uint64_t)(c0 + lane - 1))),
-                                       jb.rk);
-      ch_of(lane - 1).logu = (double)log_u32(w.x);
-    }
-    // Gibbs step sub reads operand sub % 2 and writes the other: v is in
-    // operand 0 at the start of a proposal, v' in operand g % 2 at its end
-    for (int sub = 0; sub < prm.g; ++sub, ++gs) {
-      const int src = sub & 1;
-      const uint32_t pbs = ly.pb[0] + (uint32_t)(sub & 1) * (CH * WPC * 4);
-      uint32_t* dbc = (uint32_t*)(smem + pbs) + cm * WPC;
-      const uint32_t* sbc =
-          sub == 0 ? vb_m : (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub - 1) & 1) * (CH * WPC * 4)) + cm * WPC;
-      const uint32_t taghid = (uint32_t)(sub * (K + 1)), tagvis = (uint32_t)(sub * (K + 1) + K);
-      const uint32_t opv_dst = ly.opv[0] + (uint32_t)(src ^ 1) * G::OPV;
-      const uint32_t zbase = zc;
-      if (issuer) {
-        for (int z = 0; z < G::NHV; ++z, ++zc) {
-          const int ty = stab[z] & 3, tl = stab[z] >> 2;
-          const uint32_t d = mma_claim();
-          if (ty == kStV) {
-            wait_bar(bar(kBarH + ((2 * tl + G::NT - 1) % G::NT)), gs & 1u);
-            wait_bar(bar(kBarH + 2 * tl), gs & 1u);
-            wait_bar(bar(kBarH + 2 * tl + 1), gs & 1u);
-            tc_fence_after();
-          }
-          issue_stage<LT, KT, kT>(role, ty, tl, d, dopv0 + (uint32_t)(src * (G::OPV >> 4)), dvbuf, dbh, dbv, K,
-                                  k, bar(kBarFull + (zc & (kNbuf - 1))));
-        }
-      } else if (epi) {
-        for (int z = 0; z < G::NHV; ++z, ++zc) {
-          const int ty = stab[z] & 3, tl = stab[z] >> 2;
-          // this stage's Philox words do not depend on its MMAs: drawn before
-          // waiting for them, so the counter-based generator overlaps the
-          // tensor-core work and the accumulator loads
-          uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
-          if (ty == kStH) {
-            if (fq < K) {
-              const uint32_t q0 = (uint32_t)((i * LT + 8 * tl) >> 2), tag = taghid + (uint32_t)fq;
-              w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
-              w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
-            }
-          } else {
-            w0 = philox4x32_10_rk(make_uint4((uint32_t)((i * LT + 16 * tl + 4 * fq) >> 2), tagvis, step, cid),
-                                  jb.rk);
-            w1 = w0;
-          }
-          const uint32_t tcol = epi_claim();
-          if (ty == kStH) {
-            if (fq < K) {
-              float s2[8], s1[8], s0[8];
-              tm_ld8(tcol + 8 * fq, s2);
-              tm_ld8(tcol + 32 + 8 * fq, s1);
-              tm_ld8(tcol + 64 + 8 * fq, s0);
-              tm_wait();
-              tm_tie(s2);
-              tm_tie(s1);
-              tm_tie(s0);
-              epi_release();
-              epi_hidden<LT>(jb, smem, ly, s2, s1, s0, m, i, fq, tl, w0, w1, sbc, hbc, nrec);
-            } else {
-              epi_release();
-            }
-            if (tl == G::NT - 2 && fq < K) {
-              // this thread's rows of the last hidden tile (written by it at the
-              // first H stage) into the last slot of the last V tile's buffer,
-              // read last by V_{NV-3}, whose MMAs this warp has waited for
-              const uint32_t dst = ly.vbuf + (uint32_t)((G::NV - 1) & 1) * G::VBUF + (uint32_t)fq * G::PLANE3 +
-                                   2 * G::LBO,
-                             pl = ly.plast + (uint32_t)fq * G::LBO;
-              const uint32_t r0 = (uint32_t)(m + G::HH) * 16, r1 = (uint32_t)(m - (128 - G::HH)) * 16;
-              *(uint4*)(smem + dst + r0) = *(const uint4*)(smem + pl + r0);
-              if (m >= 128 - G::HH) *(uint4*)(smem + dst + r1) = *(const uint4*)(smem + pl + r1);
-            }
-            epi_publish(bar(kBarH + tl));
-          } else {
-            float s2[4], s1[4], s0[4];
-            tm_ld4(tcol + 4 * fq, s2);
-            tm_ld4(tcol + 16 + 4 * fq, s1);
-            tm_ld4(tcol + 32 + 4 * fq, s0);
-            if (K > 2) {
-              // K-steps 3.. from the second issuer's accumulator (integer sums: exact)
-              float t2[4], t1[4], t0[4];
-              tm_ld4(tcol + 48 + 4 * fq, t2);
-              tm_ld4(tcol + 64 + 4 * fq, t1);
-              tm_ld4(tcol + 80 + 4 * fq, t0);
-              tm_wait();
-              tm_tie(s2);
-              tm_tie(s1);
-              tm_tie(s0);
-              tm_tie(t2);
-              tm_tie(t1);
-              tm_tie(t0);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                s2[q] += t2[q];
-                s1[q] += t1[q];
-                s0[q] += t0[q];
-              }
-            } else {
-              tm_wait();
-              tm_tie(s2);
-              tm_tie(s1);
-              tm_tie(s0);
-            }
-            epi_release();
-            epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
-                            (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.wait_limit, abort,
-                            prm.err, nrec, ly.lut);
-            if (tl == G::NV - 1) epi_publish(bar(kBarV));
-          }
-        }
-      }
-      zc = zbase + G::NHV;
-      if (sub + 1 < prm.g) {
-        // next Gibbs step: its source is this step's v' (every write done), and
-        // the proposal buffer it fills is cleared
-        cta_sync();
-        for (int w = tid; w < CH * WPC; w += kThr)
-          ((uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub + 1) & 1) * (CH * WPC * 4)))[w] = 0u;
-        __syncthreads();
-      }
-    }
-    const int fin = prm.g & 1;                                     // operand holding v'
-    const uint32_t* pv = (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((prm.g - 1) & 1) * (CH * WPC * 4));
-
-    // free energy of v' from the F tiles
+  if constexpr (EVAL) {
+    // evaluation of the current lattices (the values a mixed proposal leaves
+    // for an accepted state): the F tiles on operand 0 (v) with the certified
+    // FP32 bound, the lattice counts, then F, its bound, log pi = -beta E and
+    // the observables; sums, accepts and the step counter are untouched
     float s32 = 0.f, c32 = 0.f, sabs = 0.f, ssp = 0.f;
-    const uint32_t zbase = zc;
     if (issuer) {
       for (int t = 0; t < G::NT; ++t, ++zc) {
         const uint32_t d = mma_claim();
-        if (t == 0) {
-          wait_bar(bar(kBarV), (gs - 1) & 1u);
-          tc_fence_after();
-        }
-        issue_stage<LT, KT, kT>(role, kStF, t, d, dopv0 + (uint32_t)(fin * (G::OPV >> 4)), dvbuf, dbh, dbv, K, k,
-                                bar(kBarFull + (zc & (kNbuf - 1))));
+        issue_stage<LT, KT, kT>(role, kStF, t, d, dopv0, dvbuf, dbh, dbv, K, k, bar(kBarFull + (zc & (kNbuf - 1))));
       }
     } else if (epi) {
       for (int t = 0; t < G::NT; ++t, ++zc) {
@@ -896,15 +761,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
         }
       }
     }
-    zc = zbase + G::NT;
-
-    // per-warp sums: F as an exact 2^-32 fixed-point integer and its
-    // error-bound part in FP32 per chain (a thread's units are all of its
-    // chain cm: lane parity for CH = 2), ones and unequal nearest-neighbour
-    // pairs of the count-pass words (every warp's v' writes done: vrdy,
-    // completed before the F stages)
     if (epi) {
-      wait_bar(bar(kBarV), (gs - 1) & 1u);
       long long fs = __float2ll_rn(s32 * 0x1p32f);
       float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
 #pragma unroll
@@ -918,15 +775,15 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
       }
       uint32_t cnt = 0;
       if (tid < CH * WPC) {
-        const uint32_t* p = pv + (tid / WPC) * WPC;
+        const uint32_t* p = vbits + (tid / WPC) * WPC;
         const int w = tid % WPC;
         const uint32_t x = p[w];
         uint32_t right, down;
-        if constexpr (LT >= 32) {          // whole rows of WPR words
+        if constexpr (LT >= 32) {
           const uint32_t xr = p[(w & ~(G::WPR - 1)) | ((w + 1) & (G::WPR - 1))];
           right = (x >> 1) | (xr << 31);
           down = p[(w + G::WPR) % WPC];
-        } else {                           // L = 16: two rows per word
+        } else {
           right = ((x >> 1) & 0x7FFF7FFFu) | ((x << 15) & 0x80008000u);
           down = (x >> 16) | (p[(w + 1) % WPC] << 16);
         }
@@ -934,38 +791,11 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
       }
 #pragma unroll
       for (int o = G::SPAN / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
-      if (tid % G::SPAN == 0 && tid < 16 * G::SPAN) redc[tid / G::SPAN] = cnt;   // part = chain's words
+      if (tid % G::SPAN == 0 && tid < 16 * G::SPAN) redc[tid / G::SPAN] = cnt;
     }
     __syncthreads();
-    // thread c < CH: the MH decision of chain c0 + c
-    // after the decision, by a lane of warp 1 per chain (beside the accept
-    // copies): the accepted state, its observables, the running sums and
-    // the state's margin terms for the next decision
-    auto settle = [&](ChainSm& ch, int c) {
-      if (ch.flag_acc) {
-        ch.F = ch.Fp;
-        ch.Fb = ch.Bp;
-        ch.lp = ch.lpp;
-        ch.lpb = ch.lppb;
-        ch.E = ch.Ep;
-        const double M = (double)(2 * ch.onesp - LT * LT);
-        ch.ot[0] = ch.Ep;
-        ch.ot[1] = ch.Ep * ch.Ep;
-        ch.ot[2] = fabs(M);
-        ch.ot[3] = M * M;
-        ch.acc += 1ull;
-      }
-      // (a second-level recompute may also have tightened F(v) of a rejected proposal)
-      ch.mgs = ((ch.Fb + ch.lpb) + 1e-12 * (fabs(ch.lp) + fabs(ch.F))) + (ch.cst + 1e-300);
-      for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
-      if (c0 + c < jb.n_chains) trace_store(jb, c0 + c, step0 + (uint64_t)s, ch.E);
-    };
     if (tid < CH) {
-      // one thread per chain; each FP64 instruction (conversions included)
-      // holds the SMSP's slow FP64 pipe for tens of cycles, so FP64 work is
-      // kept small: partial sums in integers and FP32, values in registers
       ChainSm& ch = ch_of(tid);
-      const double lp = ch.lp, F = ch.F, Fb = ch.Fb, lpb = ch.lpb, beta = ch.beta, logu = ch.logu;
       long long fs = 0;
       float bnd = 0.0f;
       uint32_t ones = 0, pairs = 0;
@@ -978,56 +808,317 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
           ones += redc[w] & 0xFFFFu;
           pairs += redc[w] >> 16;
         }
-      // the FP32 sums of the non-negative bound terms over 512 / CH threads and
-      // then over 16 warps lose < 26 2^-24 relative, inside the factor 1.001
       constexpr int kN = LT * LT;
-      // the margin terms known before this proposal's sums come precomputed
-      // (ch.cst, ch.mgs); the observables wait for the decision
-      const double cst = ch.cst, mg0 = ch.mgs;
       const double Fdata = (double)bnd * 1.001;
       const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
-      const double lpp = -beta * E;
-      const double Fp = fma((double)fs, -0x1p-32, -jb.vb * (double)ones);
-      const double Bp = (Fdata + cst) + 1e-12 * fabs(Fp);
-      ch.Ep = E;
-      ch.lpp = lpp;
-      ch.onesp = (int)ones;
-      ch.lppb = 0.0;
-      ch.Fp = Fp;
-      ch.Bp = Bp;
-      ch.flag_rec = 0;
-      if (!prm.correct) {
-        ch.flag_acc = 1;
-      } else {
-        const double logr = (lpp - lp) + (Fp - F);
-        // = Bp + Fb + lpb + 1e-12 (|lpp| + |lp| + |Fp| + |F|) + 1e-300
-        const double Mg = (Fdata + mg0) + 1e-12 * (2.0 * fabs(Fp) + fabs(lpp)) + 0x1p-20 * (1.0 + fabs(logu));
-        if (logr - logu > Mg) ch.flag_acc = 1;
-        else if (logu - logr > Mg) ch.flag_acc = 0;
-        else ch.flag_rec = 1;
-      }
+      const double M = (double)(2 * (int)ones - kN);
+      const double Fv = fma((double)fs, -0x1p-32, -jb.vb * (double)ones);
+      ch.F = Fv;
+      ch.Fb = (Fdata + ch.cst) + 1e-12 * fabs(Fv);
+      ch.lp = -ch.beta * E;
+      ch.lpb = 0.0;
+      ch.E = E;
+      ch.ot[0] = E; ch.ot[1] = E * E; ch.ot[2] = fabs(M); ch.ot[3] = M * M;
     }
-    if (__syncthreads_or(tid < CH && ch_of(tid).flag_rec)) {
-      mh_redo<LT>(jb, &ch_of(0), scratch, pv, vbits, step, c0);
+  } else {
+    for (int s = 0; s < prm.S; ++s) {
+      const uint32_t step = (uint32_t)(step0 + (uint64_t)s);
+      if (warp == 17 && lane >= 1 && lane <= CH && prm.correct) {
+        // the MH draws of this proposal, ahead of the decisions (read after the
+        // barriers of the proposal's end).  In FP32, within 2^-20 (1 + |log u|)
+        // of the FP64 log u, which the decision adds to its margin: the FP64 log
+        // would hold this warp's issuing lane, whose commits every stage waits
+        // for, for thousands of cycles on the 1/64-rate FP64 pipe
+        const uint4 w = philox4x32_10_rk(make_uint4(0u, kTagAcc, step, (uint32_t)(jb.cid_base + (uint64_t)(c0 + lane - 1))),
+                                         jb.rk);
+        ch_of(lane - 1).logu = (double)log_u32(w.x);
+      }
+      // Gibbs step sub reads operand sub % 2 and writes the other: v is in
+      // operand 0 at the start of a proposal, v' in operand g % 2 at its end
+      for (int sub = 0; sub < prm.g; ++sub, ++gs) {
+        const int src = sub & 1;
+        const uint32_t pbs = ly.pb[0] + (uint32_t)(sub & 1) * (CH * WPC * 4);
+        uint32_t* dbc = (uint32_t*)(smem + pbs) + cm * WPC;
+        const uint32_t* sbc =
+            sub == 0 ? vb_m : (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub - 1) & 1) * (CH * WPC * 4)) + cm * WPC;
+        const uint32_t taghid = (uint32_t)(sub * (K + 1)), tagvis = (uint32_t)(sub * (K + 1) + K);
+        const uint32_t opv_dst = ly.opv[0] + (uint32_t)(src ^ 1) * G::OPV;
+        const uint32_t zbase = zc;
+        if (issuer) {
+          for (int z = 0; z < G::NHV; ++z, ++zc) {
+            const int ty = stab[z] & 3, tl = stab[z] >> 2;
+            const uint32_t d = mma_claim();
+            if (ty == kStV) {
+              wait_bar(bar(kBarH + ((2 * tl + G::NT - 1) % G::NT)), gs & 1u);
+              wait_bar(bar(kBarH + 2 * tl), gs & 1u);
+              wait_bar(bar(kBarH + 2 * tl + 1), gs & 1u);
+              tc_fence_after();
+            }
+            issue_stage<LT, KT, kT>(role, ty, tl, d, dopv0 + (uint32_t)(src * (G::OPV >> 4)), dvbuf, dbh, dbv, K,
+                                    k, bar(kBarFull + (zc & (kNbuf - 1))));
+          }
+        } else if (epi) {
+          for (int z = 0; z < G::NHV; ++z, ++zc) {
+            const int ty = stab[z] & 3, tl = stab[z] >> 2;
+            // this stage's Philox words do not depend on its MMAs: drawn before
+            // waiting for them, so the counter-based generator overlaps the
+            // tensor-core work and the accumulator loads
+            uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+            if (ty == kStH) {
+              if (fq < K) {
+                const uint32_t q0 = (uint32_t)((i * LT + 8 * tl) >> 2), tag = taghid + (uint32_t)fq;
+                w0 = philox4x32_10_rk(make_uint4(q0, tag, step, cid), jb.rk);
+                w1 = philox4x32_10_rk(make_uint4(q0 + 1u, tag, step, cid), jb.rk);
+              }
+            } else {
+              w0 = philox4x32_10_rk(make_uint4((uint32_t)((i * LT + 16 * tl + 4 * fq) >> 2), tagvis, step, cid),
+                                    jb.rk);
+              w1 = w0;
+            }
+            const uint32_t tcol = epi_claim();
+            if (ty == kStH) {
+              if (fq < K) {
+                float s2[8], s1[8], s0[8];
+                tm_ld8(tcol + 8 * fq, s2);
+                tm_ld8(tcol + 32 + 8 * fq, s1);
+                tm_ld8(tcol + 64 + 8 * fq, s0);
+                tm_wait();
+                tm_tie(s2);
+                tm_tie(s1);
+                tm_tie(s0);
+                epi_release();
+                epi_hidden<LT>(jb, smem, ly, s2, s1, s0, m, i, fq, tl, w0, w1, sbc, hbc, nrec);
+              } else {
+                epi_release();
+              }
+              if (tl == G::NT - 2 && fq < K) {
+                // this thread's rows of the last hidden tile (written by it at the
+                // first H stage) into the last slot of the last V tile's buffer,
+                // read last by V_{NV-3}, whose MMAs this warp has waited for
+                const uint32_t dst = ly.vbuf + (uint32_t)((G::NV - 1) & 1) * G::VBUF + (uint32_t)fq * G::PLANE3 +
+                                     2 * G::LBO,
+                               pl = ly.plast + (uint32_t)fq * G::LBO;
+                const uint32_t r0 = (uint32_t)(m + G::HH) * 16, r1 = (uint32_t)(m - (128 - G::HH)) * 16;
+                *(uint4*)(smem + dst + r0) = *(const uint4*)(smem + pl + r0);
+                if (m >= 128 - G::HH) *(uint4*)(smem + dst + r1) = *(const uint4*)(smem + pl + r1);
+              }
+              epi_publish(bar(kBarH + tl));
+            } else {
+              float s2[4], s1[4], s0[4];
+              tm_ld4(tcol + 4 * fq, s2);
+              tm_ld4(tcol + 16 + 4 * fq, s1);
+              tm_ld4(tcol + 32 + 4 * fq, s0);
+              if (K > 2) {
+                // K-steps 3.. from the second issuer's accumulator (integer sums: exact)
+                float t2[4], t1[4], t0[4];
+                tm_ld4(tcol + 48 + 4 * fq, t2);
+                tm_ld4(tcol + 64 + 4 * fq, t1);
+                tm_ld4(tcol + 80 + 4 * fq, t0);
+                tm_wait();
+                tm_tie(s2);
+                tm_tie(s1);
+                tm_tie(s0);
+                tm_tie(t2);
+                tm_tie(t1);
+                tm_tie(t0);
+  #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  s2[q] += t2[q];
+                  s1[q] += t1[q];
+                  s0[q] += t0[q];
+                }
+              } else {
+                tm_wait();
+                tm_tie(s2);
+                tm_tie(s1);
+                tm_tie(s0);
+              }
+              epi_release();
+              epi_visible<LT>(jb, smem, s2, s1, s0, m, i, fq, tl, w0, dbc, opv_dst,
+                              (const uint32_t*)(smem + hbc), bar(kBarH), gs & 1u, prm.wait_limit, abort,
+                              prm.err, nrec, ly.lut);
+              if (tl == G::NV - 1) epi_publish(bar(kBarV));
+            }
+          }
+        }
+        zc = zbase + G::NHV;
+        if (sub + 1 < prm.g) {
+          // next Gibbs step: its source is this step's v' (every write done), and
+          // the proposal buffer it fills is cleared
+          cta_sync();
+          for (int w = tid; w < CH * WPC; w += kThr)
+            ((uint32_t*)(smem + ly.pb[0] + (uint32_t)((sub + 1) & 1) * (CH * WPC * 4)))[w] = 0u;
+          __syncthreads();
+        }
+      }
+      const int fin = prm.g & 1;                                     // operand holding v'
+      const uint32_t* pv = (const uint32_t*)(smem + ly.pb[0] + (uint32_t)((prm.g - 1) & 1) * (CH * WPC * 4));
+
+      // free energy of v' from the F tiles
+      float s32 = 0.f, c32 = 0.f, sabs = 0.f, ssp = 0.f;
+      const uint32_t zbase = zc;
+      if (issuer) {
+        for (int t = 0; t < G::NT; ++t, ++zc) {
+          const uint32_t d = mma_claim();
+          if (t == 0) {
+            wait_bar(bar(kBarV), (gs - 1) & 1u);
+            tc_fence_after();
+          }
+          issue_stage<LT, KT, kT>(role, kStF, t, d, dopv0 + (uint32_t)(fin * (G::OPV >> 4)), dvbuf, dbh, dbv, K, k,
+                                  bar(kBarFull + (zc & (kNbuf - 1))));
+        }
+      } else if (epi) {
+        for (int t = 0; t < G::NT; ++t, ++zc) {
+          const uint32_t tcol = epi_claim();
+          if (fq < K) {
+            float s2[8], s1[8], s0[8];
+            tm_ld8(tcol + 8 * fq, s2);
+            tm_ld8(tcol + 32 + 8 * fq, s1);
+            tm_ld8(tcol + 64 + 8 * fq, s0);
+            tm_wait();
+            tm_tie(s2);
+            tm_tie(s1);
+            tm_tie(s0);
+            epi_release();
+            epi_free(jb, s2, s1, s0, fq, s32, c32, sabs, ssp);
+          } else {
+            epi_release();
+          }
+        }
+      }
+      zc = zbase + G::NT;
+
+      // per-warp sums: F as an exact 2^-32 fixed-point integer and its
+      // error-bound part in FP32 per chain (a thread's units are all of its
+      // chain cm: lane parity for CH = 2), ones and unequal nearest-neighbour
+      // pairs of the count-pass words (every warp's v' writes done: vrdy,
+      // completed before the F stages)
+      if (epi) {
+        wait_bar(bar(kBarV), (gs - 1) & 1u);
+        long long fs = __float2ll_rn(s32 * 0x1p32f);
+        float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
+  #pragma unroll
+        for (int o = 16; o >= CH; o >>= 1) {
+          fs += __shfl_xor_sync(kFull, fs, o);
+          bnd += __shfl_xor_sync(kFull, bnd, o);
+        }
+        if (lane < CH) {
+          *(long long*)(redf + 16 * (warp * CH + lane)) = fs;
+          *(float*)(redf + 16 * (warp * CH + lane) + 8) = bnd;
+        }
+        uint32_t cnt = 0;
+        if (tid < CH * WPC) {
+          const uint32_t* p = pv + (tid / WPC) * WPC;
+          const int w = tid % WPC;
+          const uint32_t x = p[w];
+          uint32_t right, down;
+          if constexpr (LT >= 32) {          // whole rows of WPR words
+            const uint32_t xr = p[(w & ~(G::WPR - 1)) | ((w + 1) & (G::WPR - 1))];
+            right = (x >> 1) | (xr << 31);
+            down = p[(w + G::WPR) % WPC];
+          } else {                           // L = 16: two rows per word
+            right = ((x >> 1) & 0x7FFF7FFFu) | ((x << 15) & 0x80008000u);
+            down = (x >> 16) | (p[(w + 1) % WPC] << 16);
+          }
+          cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ right) + __popc(x ^ down)) << 16);
+        }
+  #pragma unroll
+        for (int o = G::SPAN / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+        if (tid % G::SPAN == 0 && tid < 16 * G::SPAN) redc[tid / G::SPAN] = cnt;   // part = chain's words
+      }
       __syncthreads();
-    }
-    if (warp == 1 && lane < CH) settle(ch_of(lane), lane);
-    // accepted: v' becomes v (packed, and its operand rows into operand 0 when
-    // they are in operand 1); rejected after several Gibbs steps: operand 0
-    // was overwritten, so v is expanded again
-    for (int c = 0; c < CH; ++c) {
-      const bool acc = ch_of(c).flag_acc != 0;
-      for (int w = tid; w < WPC; w += kThr) {
-        uint32_t* pvw = (uint32_t*)pv + c * WPC;
-        if (acc) vbits[c * WPC + w] = pvw[w];
-        pvw[w] = 0u;                              // cleared for the next proposal
+      // thread c < CH: the MH decision of chain c0 + c
+      // after the decision, by a lane of warp 1 per chain (beside the accept
+      // copies): the accepted state, its observables, the running sums and
+      // the state's margin terms for the next decision
+      auto settle = [&](ChainSm& ch, int c) {
+        if (ch.flag_acc) {
+          ch.F = ch.Fp;
+          ch.Fb = ch.Bp;
+          ch.lp = ch.lpp;
+          ch.lpb = ch.lppb;
+          ch.E = ch.Ep;
+          const double M = (double)(2 * ch.onesp - LT * LT);
+          ch.ot[0] = ch.Ep;
+          ch.ot[1] = ch.Ep * ch.Ep;
+          ch.ot[2] = fabs(M);
+          ch.ot[3] = M * M;
+          ch.acc += 1ull;
+        }
+        // (a second-level recompute may also have tightened F(v) of a rejected proposal)
+        ch.mgs = ((ch.Fb + ch.lpb) + 1e-12 * (fabs(ch.lp) + fabs(ch.F))) + (ch.cst + 1e-300);
+        for (int o = 0; o < kNobs; ++o) ch.os[o] += ch.ot[o];
+        if (c0 + c < jb.n_chains) trace_store(jb, c0 + c, step0 + (uint64_t)s, ch.E);
+      };
+      if (tid < CH) {
+        // one thread per chain; each FP64 instruction (conversions included)
+        // holds the SMSP's slow FP64 pipe for tens of cycles, so FP64 work is
+        // kept small: partial sums in integers and FP32, values in registers
+        ChainSm& ch = ch_of(tid);
+        const double lp = ch.lp, F = ch.F, Fb = ch.Fb, lpb = ch.lpb, beta = ch.beta, logu = ch.logu;
+        long long fs = 0;
+        float bnd = 0.0f;
+        uint32_t ones = 0, pairs = 0;
+        for (int w = 0; w < 16; ++w) {
+          fs += *(const long long*)(redf + 16 * (w * CH + tid));
+          bnd += *(const float*)(redf + 16 * (w * CH + tid) + 8);
+        }
+        for (int w = 0; w < 16; ++w)
+          if (w * G::SPAN < CH * WPC && (w * G::SPAN) / WPC == tid) {
+            ones += redc[w] & 0xFFFFu;
+            pairs += redc[w] >> 16;
+          }
+        // the FP32 sums of the non-negative bound terms over 512 / CH threads and
+        // then over 16 warps lose < 26 2^-24 relative, inside the factor 1.001
+        constexpr int kN = LT * LT;
+        // the margin terms known before this proposal's sums come precomputed
+        // (ch.cst, ch.mgs); the observables wait for the decision
+        const double cst = ch.cst, mg0 = ch.mgs;
+        const double Fdata = (double)bnd * 1.001;
+        const double E = -jb.J[0] * (double)(2 * kN - 2 * (int)pairs);
+        const double lpp = -beta * E;
+        const double Fp = fma((double)fs, -0x1p-32, -jb.vb * (double)ones);
+        const double Bp = (Fdata + cst) + 1e-12 * fabs(Fp);
+        ch.Ep = E;
+        ch.lpp = lpp;
+        ch.onesp = (int)ones;
+        ch.lppb = 0.0;
+        ch.Fp = Fp;
+        ch.Bp = Bp;
+        ch.flag_rec = 0;
+        if (!prm.correct) {
+          ch.flag_acc = 1;
+        } else {
+          const double logr = (lpp - lp) + (Fp - F);
+          // = Bp + Fb + lpb + 1e-12 (|lpp| + |lp| + |Fp| + |F|) + 1e-300
+          const double Mg = (Fdata + mg0) + 1e-12 * (2.0 * fabs(Fp) + fabs(lpp)) + 0x1p-20 * (1.0 + fabs(logu));
+          if (logr - logu > Mg) ch.flag_acc = 1;
+          else if (logu - logr > Mg) ch.flag_acc = 0;
+          else ch.flag_rec = 1;
+        }
       }
-      if (acc && fin == 1) copy_chain_rows<LT>(smem, ly.opv[0], ly.opv[1], c, tid, kThr);
+      if (__syncthreads_or(tid < CH && ch_of(tid).flag_rec)) {
+        mh_redo<LT>(jb, &ch_of(0), scratch, pv, vbits, step, c0);
+        __syncthreads();
+      }
+      if (warp == 1 && lane < CH) settle(ch_of(lane), lane);
+      // accepted: v' becomes v (packed, and its operand rows into operand 0 when
+      // they are in operand 1); rejected after several Gibbs steps: operand 0
+      // was overwritten, so v is expanded again
+      for (int c = 0; c < CH; ++c) {
+        const bool acc = ch_of(c).flag_acc != 0;
+        for (int w = tid; w < WPC; w += kThr) {
+          uint32_t* pvw = (uint32_t*)pv + c * WPC;
+          if (acc) vbits[c * WPC + w] = pvw[w];
+          pvw[w] = 0u;                              // cleared for the next proposal
+        }
+        if (acc && fin == 1) copy_chain_rows<LT>(smem, ly.opv[0], ly.opv[1], c, tid, kThr);
+      }
+      __syncthreads();
+      for (int c = 0; c < CH; ++c)
+        if (!ch_of(c).flag_acc && prm.g > 1) expand_lattice<LT>(smem, ly.opv[0], vbits, tid, kThr, c);
+      cta_sync();
     }
-    __syncthreads();
-    for (int c = 0; c < CH; ++c)
-      if (!ch_of(c).flag_acc && prm.g > 1) expand_lattice<LT>(smem, ly.opv[0], vbits, tid, kThr, c);
-    cta_sync();
   }
 
   if (nrec) atomicAdd(nrec_sm + cm, (unsigned long long)nrec);
@@ -1068,7 +1159,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
 // and a tile that takes longer (an MH recompute) delays only its own CTA's
 // next pick instead of the end of a wave.  Tensor memory is allocated once
 // per CTA; after an abort the CTA takes no further item.
-template <int KT, int kT>
+template <int KT, int kT, bool EVAL>
 __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant__ LaunchParams prm) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_bar[kNbar];
@@ -1096,10 +1187,10 @@ __global__ void __launch_bounds__(kThr, 1) crbm_tc_kernel(const __grid_constant_
     while (jid + 1 < prm.n_jobs && item >= prm.tile_begin[jid + 1]) ++jid;
     const JobDev& jb = prm.job[jid];
     const int t = item - prm.tile_begin[jid];
-    if (jb.L == 128) tc_tile<128, KT, kT>(prm, jb, t, smem, bar0, tmem, abort, s_stage);
-    else if (jb.L == 64) tc_tile<64, KT, kT>(prm, jb, 2 * t, smem, bar0, tmem, abort, s_stage);
-    else if (jb.L == 32) tc_tile<32, KT, kT>(prm, jb, 4 * t, smem, bar0, tmem, abort, s_stage);
-    else tc_tile<16, KT, kT>(prm, jb, 8 * t, smem, bar0, tmem, abort, s_stage);
+    if (jb.L == 128) tc_tile<128, KT, kT, EVAL>(prm, jb, t, smem, bar0, tmem, abort, s_stage);
+    else if (jb.L == 64) tc_tile<64, KT, kT, EVAL>(prm, jb, 2 * t, smem, bar0, tmem, abort, s_stage);
+    else if (jb.L == 32) tc_tile<32, KT, kT, EVAL>(prm, jb, 4 * t, smem, bar0, tmem, abort, s_stage);
+    else tc_tile<16, KT, kT, EVAL>(prm, jb, 8 * t, smem, bar0, tmem, abort, s_stage);
   }
   tc_fence_before();
   __syncthreads();
@@ -1134,9 +1225,9 @@ __global__ void wait_probe_kernel(long long limit, int arrive, int* err) {
   mbar_wait(b, 0u, limit, &ab, err);
 }
 
-template <int KT, int kT>
+template <int KT, int kT, bool EVAL>
 cudaError_t tc_limit_inst(size_t bytes) {
-  return cudaFuncSetAttribute(crbm_tc_kernel<KT, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(crbm_tc_kernel<KT, kT, EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -1156,12 +1247,19 @@ bool tc_supported(int kind, int prec, int L, int K, int k) {
 }
 
 // One persistent launch for the jobs of p (one filter shape; any of the four
-// sides), then the step counters and the queue counter.
+// sides), then the step counters and the queue counter.  p.mode 1: the
+// evaluation of the current lattices (no proposal; step counters unchanged).
 cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t st) {
-  if (p.S <= 0 || p.total_items <= 0) return cudaSuccess;
+  const bool eval = p.mode == 1;
+  if ((!eval && p.S <= 0) || p.total_items <= 0) return cudaSuccess;
   const bool k45 = p.job[0].K == 4 && p.job[0].k == 5;
-  if (k45) crbm_tc_kernel<4, 5><<<grid, kThr, smem, st>>>(p);
-  else crbm_tc_kernel<0, 0><<<grid, kThr, smem, st>>>(p);
+  if (eval) {
+    if (k45) crbm_tc_kernel<4, 5, true><<<grid, kThr, smem, st>>>(p);
+    else crbm_tc_kernel<0, 0, true><<<grid, kThr, smem, st>>>(p);
+  } else {
+    if (k45) crbm_tc_kernel<4, 5, false><<<grid, kThr, smem, st>>>(p);
+    else crbm_tc_kernel<0, 0, false><<<grid, kThr, smem, st>>>(p);
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     tc_advance_kernel<<<1, kMaxJobs, 0, st>>>(p);
@@ -1172,8 +1270,10 @@ cudaError_t launch_tc(const LaunchParams& p, int grid, size_t smem, cudaStream_t
 
 cudaError_t tc_set_smem_limit() {
   const size_t b = tc_layout<128>(4, 5).total;
-  cudaError_t e = tc_limit_inst<4, 5>(b);
-  if (e == cudaSuccess) e = tc_limit_inst<0, 0>(b);
+  cudaError_t e = tc_limit_inst<4, 5, false>(b);
+  if (e == cudaSuccess) e = tc_limit_inst<0, 0, false>(b);
+  if (e == cudaSuccess) e = tc_limit_inst<4, 5, true>(b);
+  if (e == cudaSuccess) e = tc_limit_inst<0, 0, true>(b);
   return e;
 }
 
