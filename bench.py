@@ -655,13 +655,14 @@ def main():
 
     # end to end through the C ABI with host buffers: upload lattices (pinned)
     # and re-evaluate the chains (crbm_write_states), run, read lattices and
-    # observable sums back
+    # observable sums back (crbm_read_states)
     host_bits = []
     for j in jobs:
         b = torch.empty(j.state()[0].shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
         b[:] = j.state()[0]
         host_bits.append(b)
     out_bits = [torch.empty(b.shape, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32) for b in host_bits]
+    out_sums = [torch.empty((j.n, 4), dtype=torch.float64, pin_memory=True).numpy() for j in jobs]
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -670,10 +671,8 @@ def main():
         ctx.write_states(jobs, host_bits, [j.step for j in jobs], prec)      # one evaluation launch
         h2d += sum(hbits.nbytes for hbits in host_bits)
         ctx.run_batch(jobs, S, precision=prec, stream=stream)
-        for j, obits in zip(jobs, out_bits):
-            bits, _ = j.state(out=obits)
-            sums, _, _ = j.observables()
-            d2h += bits.nbytes + sums.nbytes
+        ctx.read_states(jobs, out_bits, out_sums)                           # one synchronisation
+        d2h += sum(b.nbytes + x.nbytes for b, x in zip(out_bits, out_sums))
     e2e_s = time.perf_counter() - t0
     e2e = None if not e2e_steps else {
         "value": n_chains * S * e2e_steps * world / e2e_s, "unit": "proposals/s",

@@ -412,6 +412,18 @@ CRBM_API int crbm_read_observables(crbm_ctx* ctx, int job_id, double* sums, int6
  * ids this is a complete checkpoint. */
 CRBM_API int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step);
 
+/* crbm_read_state and the observable sums of crbm_read_observables for
+ * several jobs with one synchronisation (no counterpart in the paper: a
+ * batching convenience of this library).  For job i: bits[i] receives its
+ * packed lattices (n_chains * ceil(L*L/32) words), steps[i] its step counter,
+ * sums[i] its observable sums (n_chains * CRBM_NOBS doubles); the arrays
+ * bits, steps and sums, and any bits[i] or sums[i], may be NULL (not read
+ * back).  Host buffers are written during the call.  Errors: CRBM_EINVAL
+ * (n_jobs outside 0..16, a bad job id), CRBM_ETIMEOUT as crbm_sync,
+ * CRBM_ECUDA. */
+CRBM_API int crbm_read_states(crbm_ctx* ctx, int n_jobs, const int* job_ids, uint32_t* const* bits,
+                              uint64_t* steps, double* const* sums);
+
 /* Restore a checkpoint (or upload new lattices): overwrite the lattices and
  * the step counter, then re-evaluate log pi and the observables in FP64 and
  * F in `precision` (CRBM_MIXED: the FP32 value with its certified bound, as

@@ -78,6 +78,7 @@ _SIGS = {
     "crbm_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_uint64)]),
     "crbm_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_int]),
     "crbm_write_states": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "crbm_read_states": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crbm_release": (C.c_int, [C.c_void_p, C.c_int]),
 }
 EXPORTS = tuple(_SIGS)
@@ -297,6 +298,25 @@ def crbm_write_states(ctx, job_ids, bits_list, steps, precision=FP64):
     _check(ctx, load().crbm_write_states(ctx, n, ids, ptrs, st, precision))
 
 
+def crbm_read_states(ctx, job_ids, bits_out, sums_out):
+    """Lattices into bits_out[i] and observable sums into sums_out[i] (C-contiguous
+    uint32 / float64 arrays of the jobs' shapes, or None) for several jobs,
+    one synchronisation; returns the step counters."""
+    n = len(job_ids)
+    for b in bits_out:
+        if b is not None and (b.dtype != np.uint32 or not b.flags.c_contiguous):
+            raise ValueError("bits_out entries must be C-contiguous uint32 arrays")
+    for x in sums_out:
+        if x is not None and (x.dtype != np.float64 or not x.flags.c_contiguous):
+            raise ValueError("sums_out entries must be C-contiguous float64 arrays")
+    ids = (C.c_int * n)(*job_ids)
+    bp = (C.c_void_p * n)(*[None if b is None else b.ctypes.data for b in bits_out])
+    sp = (C.c_void_p * n)(*[None if x is None else x.ctypes.data for x in sums_out])
+    st = (C.c_uint64 * n)()
+    _check(ctx, load().crbm_read_states(ctx, n, ids, bp, st, sp))
+    return [int(v) for v in st]
+
+
 def crbm_release(ctx, job_id):
     _check(ctx, load().crbm_release(ctx, job_id))
 
@@ -437,6 +457,17 @@ class Context:
         crbm_write_states(self.h, [j.id for j in jobs], bits_list, steps, precision)
         for j, st in zip(jobs, steps):
             j.step = st
+
+    def read_states(self, jobs, bits_out, sums_out):
+        """Lattices and observable sums of several jobs into the given arrays
+        (shapes (n, ceil(L*L/32)) uint32 and (n, NOBS) float64; None skips),
+        one synchronisation; returns the step counters."""
+        for j, b, x in zip(jobs, bits_out, sums_out):
+            if b is not None and b.shape != (j.n, (j.L * j.L + 31) // 32):
+                raise ValueError("bits_out shape")
+            if x is not None and x.shape != (j.n, NOBS):
+                raise ValueError("sums_out shape")
+        return crbm_read_states(self.h, [j.id for j in jobs], bits_out, sums_out)
 
     def run_batch(self, jobs, S, g=1, correct=True, precision=FP64, stream=None):
         crbm_run_batch(self.h, [j.id for j in jobs], S, g, int(correct), precision, _stream_handle(stream))

@@ -1411,6 +1411,35 @@ int crbm_read_state(crbm_ctx* ctx, int job_id, uint32_t* bits, uint64_t* step) {
   return read_back(ctx, j, bits, j->lay.bits, (size_t)j->n * j->Wd * 4);
 }
 
+int crbm_read_states(crbm_ctx* ctx, int n_jobs, const int* job_ids, uint32_t* const* bits, uint64_t* steps,
+                     double* const* sums) {
+  if (!ctx) return CRBM_EINVAL;
+  if (n_jobs < 0 || n_jobs > kMaxJobs) return fail(ctx, CRBM_EINVAL, "n_jobs must be 0..%d", kMaxJobs);
+  if (n_jobs > 0 && !job_ids) return fail(ctx, CRBM_EINVAL, "null job_ids");
+  for (int i = 0; i < n_jobs; ++i)
+    if (!get_job(ctx, job_ids[i])) return fail(ctx, CRBM_EINVAL, "bad job id %d", job_ids[i]);
+  if (n_jobs == 0) return CRBM_OK;
+  // every job's stream, then the error flag once (crbm_sync of the first job
+  // reads it after its own stream; the others are synchronised before)
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  for (int i = 1; i < n_jobs; ++i) CK(cudaStreamSynchronize(ctx->jobs[job_ids[i]].stream), "stream sync");
+  int rc = crbm_sync(ctx, job_ids[0]);
+  if (rc) return rc;
+  for (int i = 0; i < n_jobs; ++i) {
+    Job& j = ctx->jobs[job_ids[i]];
+    if (steps) steps[i] = j.step;
+    if (j.n == 0) continue;
+    if (bits && bits[i])
+      CK(cudaMemcpyAsync(bits[i], j.mem + j.lay.bits, (size_t)j.n * j.Wd * 4, cudaMemcpyDeviceToHost, ctx->own),
+         "device to host copy");
+    if (sums && sums[i])
+      CK(cudaMemcpyAsync(sums[i], j.mem + j.lay.os, (size_t)j.n * 8 * kNobs, cudaMemcpyDeviceToHost, ctx->own),
+         "device to host copy");
+  }
+  CK(cudaStreamSynchronize(ctx->own), "device to host copy");
+  return CRBM_OK;
+}
+
 int crbm_write_state(crbm_ctx* ctx, int job_id, const uint32_t* bits, uint64_t step, int precision) {
   Job* j = get_job(ctx, job_id);
   if (!j) return ctx ? fail(ctx, CRBM_EINVAL, "bad job id %d", job_id) : CRBM_EINVAL;

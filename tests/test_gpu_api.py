@@ -190,6 +190,30 @@ def test_write_states_equals_write_state_job_by_job(ctx, prec):
         j.release()
 
 
+def test_read_states_equals_job_by_job_reads(ctx):
+    """crbm_read_states returns every job's lattices, step counter and
+    observable sums as crbm_read_state and crbm_read_observables do, for jobs
+    of several sides and an empty one; None entries are skipped."""
+    from paper_2008_05401_gb300 import ISING, MIXED, NOBS
+    mid = _ising_model(ctx)
+    specs = [(16, 40), (64, 9), (8, 0), (32, 12)]
+    jobs = [ctx.new_job(mid, ISING, L, wl.ising_ladder(n, 4), (1.0,), SEED, 0,
+                        wl.pack_bits(wl.random_lattices(n, L, seed=L)), MIXED) for L, n in specs]
+    ctx.run_batch(jobs, 5, precision=MIXED)
+    bits = [np.empty((n, (L * L + 31) // 32), dtype=np.uint32) for L, n in specs]
+    sums = [np.empty((n, NOBS)) for _, n in specs]
+    bits[3] = None
+    steps = ctx.read_states(jobs, bits, sums)
+    for q, j in enumerate(jobs):
+        b, st = j.state()
+        assert steps[q] == st == 5
+        if bits[q] is not None:
+            np.testing.assert_array_equal(bits[q], b)
+        np.testing.assert_array_equal(sums[q], j.observables()[0])
+    for j in jobs:
+        j.release()
+
+
 def test_empty_job_and_zero_steps(ctx):
     from paper_2008_05401_gb300 import FP64, ISING, KITAEV
     mid = _ising_model(ctx)
