@@ -921,7 +921,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
                 tm_tie(t2);
                 tm_tie(t1);
                 tm_tie(t0);
-  #pragma unroll
+#pragma unroll
                 for (int q = 0; q < 4; ++q) {
                   s2[q] += t2[q];
                   s1[q] += t1[q];
@@ -997,7 +997,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
         wait_bar(bar(kBarV), (gs - 1) & 1u);
         long long fs = __float2ll_rn(s32 * 0x1p32f);
         float bnd = sabs * 0x1p-23f + ssp * (8.0f * 0x1p-24f);
-  #pragma unroll
+#pragma unroll
         for (int o = 16; o >= CH; o >>= 1) {
           fs += __shfl_xor_sync(kFull, fs, o);
           bnd += __shfl_xor_sync(kFull, bnd, o);
@@ -1022,7 +1022,7 @@ __device__ __forceinline__ void tc_tile(const LaunchParams& prm, const JobDev& j
           }
           cnt = (uint32_t)__popc(x) | ((uint32_t)(__popc(x ^ right) + __popc(x ^ down)) << 16);
         }
-  #pragma unroll
+#pragma unroll
         for (int o = G::SPAN / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
         if (tid % G::SPAN == 0 && tid < 16 * G::SPAN) redc[tid / G::SPAN] = cnt;   // part = chain's words
       }
