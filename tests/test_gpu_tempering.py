@@ -177,3 +177,52 @@ def test_pt_rejects_mismatched_jobs(ctx):
         ctx.pt_run(a, b, 1, g=0)
     for j in (a, b, c):
         j.release()
+
+
+def _cd1_bank():
+    import os
+    from _common import ROOT
+    d = np.load(os.path.join(ROOT, "paper_2008_05401_gb300", "data", "ising_cd1_L16_K4_k5.npz"))
+    return d["W"], d["hb"], float(d["vb"])
+
+
+FULL_PT = [
+    # model, L, chains per side, g, warm-up cycles, compared cycles
+    ("ising", 16, 4096, 1, 2, 3),
+    ("kitaev", 6, 1024, 1, 2, 4),
+    ("kitaev", 8, 1024, 4, 2, 2),     # k = 4 Gibbs steps per correction (Table II)
+]
+
+
+@pytest.mark.parametrize("model,L,n,g,warm,cycles", FULL_PT)
+def test_full_size_pt_matches_oracle(ctx, model, L, n, g, warm, cycles):
+    """The tempering configurations the bench times, at their full size and in
+    their launch configuration: the Ising L = 16 ladder of 4096 physical plus
+    4096 RBM chains on the CD-1 filter bank (32 temperatures in [1.5, 3.5]),
+    and the Kitaev L = 6 and L = 8 (g = 4) ladders of 1024 + 1024 chains over
+    24 temperatures in [0.005, 1], mixed precision.  Job x (seed s, chain ids
+    0..n-1) and job y (seed s + 1, ids n..2n-1) run warm-up cycles and then
+    more in a second call; the oracle runs the same cycles from the same
+    lattices.  Both lattices, swap counts, step counters, observable sums and
+    FP64 energies must match as in the small cases."""
+    import paper_2008_05401_gb300 as P
+    if model == "ising":
+        W, hb, vb = _cd1_bank()
+        T, J, kind = wl.ising_ladder(n, 32), (1.0,), P.ISING
+    else:
+        W, hb, vb = wl.gaussian_crbm(4, 3, 0.05)
+        T, J, kind = wl.kitaev_ladder(n, 24), (1.0, 1.0, 1.0), P.KITAEV
+    bx = wl.pack_bits(wl.random_lattices(n, L, seed=SEED_X + L))
+    by = wl.pack_bits(wl.random_lattices(n, L, seed=SEED_X + L + 1))
+    px = oracle_chains(model, W, hb, vb, L, T, J, SEED_X, n, bx)
+    py = oracle_chains(model, W, hb, vb, L, T, J, SEED_X + 1, n, by, cid_base=n)
+    mid = ctx.load_model(kind, W, vb, hb)
+    jx = ctx.new_job(mid, kind, L, T, J, SEED_X, 0, bx, P.MIXED)
+    jy = ctx.new_job(mid, kind, L, T, J, SEED_X + 1, n, by, P.MIXED)
+    worst = _run_oracle_pt(px, py, g, warm + cycles)
+    ctx.pt_run(jx, jy, warm, g=g, precision=P.MIXED)
+    ctx.pt_run(jx, jy, cycles, g=g, precision=P.MIXED)
+    _compare(jx, jy, px, py, worst)
+    assert px.accepts.sum() > 0
+    jx.release()
+    jy.release()
