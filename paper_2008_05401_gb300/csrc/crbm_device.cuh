@@ -887,6 +887,35 @@ __device__ __forceinline__ int row_split(int m, int nt) {
   return H;
 }
 
+// Thread tid of nt visiting a packed triangle of R rows (row r: columns
+// 0..r) with stride nt: rows p and R-1-p side by side form folded row p,
+// R+1 long, so the thread's next element is a fixed step away in the folded
+// rows (for odd R the middle row is the last folded row's first half).
+// Every element is visited once, neighbouring threads take neighbouring
+// elements, and no walk across the short rows is needed.
+struct FoldWalk {
+  int R, p, o, dp, dq;
+  __device__ __forceinline__ FoldWalk(int rows, int tid, int nt) : R(rows) {
+    p = tid / (rows + 1);
+    o = tid - p * (rows + 1);
+    dp = nt / (rows + 1);
+    dq = nt - dp * (rows + 1);
+  }
+  __device__ __forceinline__ void rc(int& r, int& c) const {
+    const bool first = o <= p;
+    r = first ? p : R - 1 - p;
+    c = first ? o : o - p - 1;
+  }
+  __device__ __forceinline__ void next() {
+    o += dq;
+    p += dp;
+    if (o > R) {
+      o -= R + 1;
+      ++p;
+    }
+  }
+};
+
 struct KitaevWork {
   double* A;       // packed lower triangle, N (N+1) / 2 entries
   double* d;       // N
@@ -1198,8 +1227,8 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
     grp_sync<MULTI>(g);
     // A22 -= u w^T + w u^T (u in vv, w in pw): column 0 of A22 -- the next
     // step's column -- row r by thread r mod nt, with the partials of s; then
-    // the rest of the packed triangle (rows and columns 1..m-1), element
-    // q = tri(r, c) of it by thread q mod nt
+    // the rest of the packed triangle (rows and columns 1..m-1), in the
+    // folded order of FoldWalk
     const double* uu = wk.vv;
     const double* ww = wk.pw;
     double sp = 0.0;
@@ -1210,18 +1239,12 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
       if (r >= 2) sp = fma(x, x, sp);
     }
     const int ntri = (m - 1) * m / 2;
-    int q = tid, r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-    while ((r + 1) * (r + 2) / 2 <= q) ++r;
-    while (r * (r + 1) / 2 > q) --r;
-    int c = q - r * (r + 1) / 2;
-    for (; q < ntri; q += nt) {
+    FoldWalk fw(m - 1, tid, nt);
+    for (int q = tid; q < ntri; q += nt, fw.next()) {
+      int r, c;
+      fw.rc(r, c);
       double* a = A + tri(j1 + 1 + r, j1 + 1 + c);
       *a = fma(-uu[r + 1], ww[c + 1], fma(-ww[r + 1], uu[c + 1], *a));
-      c += nt;
-      while (c > r) {
-        c -= r + 1;
-        ++r;
-      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(kFull, sp, o);

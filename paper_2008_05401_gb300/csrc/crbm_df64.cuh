@@ -515,18 +515,12 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
       if (r >= 2) sp = df_fma(x, x, sp);
     }
     const int ntri = (m - 1) * m / 2;
-    int q = tid, r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-    while ((r + 1) * (r + 2) / 2 <= q) ++r;
-    while (r * (r + 1) / 2 > q) --r;
-    int c = q - r * (r + 1) / 2;
-    for (; q < ntri; q += nt) {
+    FoldWalk fw(m - 1, tid, nt);
+    for (int q = tid; q < ntri; q += nt, fw.next()) {
+      int r, c;
+      fw.rc(r, c);
       df* a = A + tri(j1 + 1 + r, j1 + 1 + c);
       *a = df_add(*a, df_neg(df_add(df_mul(uu[r + 1], pw[c + 1]), df_mul(pw[r + 1], uu[c + 1]))));
-      c += nt;
-      while (c > r) {
-        c -= r + 1;
-        ++r;
-      }
     }
     sp = warp_sum_df(sp);
     if (lane == 0) scS[warp] = sp;
