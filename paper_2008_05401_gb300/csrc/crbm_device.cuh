@@ -991,6 +991,49 @@ __device__ __forceinline__ int sturm_count32(const float* d, const float* e2, in
   return cnt;
 }
 
+// Shared start of the eigenvalues' FP32 bisections: G points strictly inside
+// the (FP32) Gershgorin interval, point k at lo + (k + 1) h with
+// h = (hi - lo) / (G + 1), and the FP32 Sturm count at each, one point per
+// thread of the group.  The count at a point is the number of eigenvalues
+// below it, so eigenvalue idx lies between the last point whose count is
+// <= idx and the next one: about log2(G + 1) rounds of bisection that every
+// eigenvalue would otherwise repeat on its own are taken in one round.  The
+// counts live in the reduced matrix's storage, free by then beyond the
+// first 2N doubles (at most N^2 - 3N ints).
+struct EigGrid {
+  const int* cnt;
+  int G;
+  float lo, hi, h;
+  __device__ __forceinline__ float x(int k) const { return __fmaf_rn((float)(k + 1), h, lo); }
+  // [lo32, hi32]: neighbouring grid points (or interval ends) with
+  // count(lo32) <= idx < count(hi32) as computed; the bisection goes on from
+  // there, and the verification after it falls back to the Gershgorin interval
+  // should the FP32 counts not be monotone
+  __device__ __forceinline__ void bracket(int idx, float& lo32, float& hi32) const {
+    int a = 0, b = G;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (cnt[mid] > idx) b = mid; else a = mid + 1;
+    }
+    lo32 = a == 0 ? lo : x(a - 1);
+    hi32 = a == G ? hi : x(a);
+  }
+};
+
+// Fill the grid (every thread of the group calls; the caller syncs the group
+// before the counts are read).  d32 / e32 and the interval must be final.
+__device__ __forceinline__ EigGrid eig_grid(const KitaevWork& wk, int N, double glo, double ghi, int tid, int nt) {
+  EigGrid gr;
+  int* cnt = reinterpret_cast<int*>(wk.A + 2 * N);
+  gr.cnt = cnt;
+  gr.G = min(nt, N * N - 3 * N);
+  gr.lo = (float)glo;
+  gr.hi = (float)ghi;
+  gr.h = (gr.hi - gr.lo) / (float)(gr.G + 1);
+  if (tid < gr.G) cnt[tid] = sturm_count32(wk.d32, wk.e32, N, gr.x(tid));
+  return gr;
+}
+
 // FP64 Sturm count together with p_N(x) and p_N'(x) (for a Newton step):
 // p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}', all four values of a
 // step rescaled together.  Five FP64 operations per step.
@@ -1041,9 +1084,11 @@ __device__ __forceinline__ SturmNewton sturm_newton(const double* d, const doubl
 // interval), then safeguarded Newton steps on p_N refine it in FP64; every
 // iterate updates the bracket through its Sturm count, and a step that leaves
 // the bracket is replaced by bisection.
-__device__ __forceinline__ double eigen_idx(const KitaevWork& wk, int N, int idx, double glo, double ghi) {
+__device__ __forceinline__ double eigen_idx(const KitaevWork& wk, const EigGrid& gr, int N, int idx, double glo,
+                                           double ghi) {
   const double range = fmax(ghi - glo, 1e-300);
-  float lo32 = (float)glo, hi32 = (float)ghi;
+  float lo32, hi32;
+  gr.bracket(idx, lo32, hi32);
   const float w32 = (float)(range * 0x1p-20);
   for (int it = 0; it < 48 && hi32 - lo32 > w32; ++it) {
     const float mid = 0.5f * (lo32 + hi32);
@@ -1277,9 +1322,11 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
   grp_sync<MULTI>(g);
+  const EigGrid gr = eig_grid(wk, N, glo, ghi, tid, nt);
+  grp_sync<MULTI>(g);
   double lp = 0.0, en = 0.0, cf = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
-    const double mu = fmax(eigen_idx(wk, N, idx, glo, ghi), 0.0);
+    const double mu = fmax(eigen_idx(wk, gr, N, idx, glo, ghi), 0.0);
     const double eps = sqrt(mu);
     if (eps_out) eps_out[idx] = eps;
     thermal_add(eps, beta, lp, en, cf);

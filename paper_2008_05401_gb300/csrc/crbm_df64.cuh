@@ -304,10 +304,11 @@ __device__ inline SturmNewtonDf sturm_df(const df* d, const df* e2, int N, df x)
 // Eigenvalue idx (ascending) of the tridiagonal (d, e^2) in df64: FP32
 // bisection (wk.d32 / wk.e32), df64 verification of the padded bracket
 // (falling back to the Gershgorin interval), safeguarded df64 Newton.
-__device__ inline double eigen_idx_df(const KitaevWork& wk, const df* d, const df* e2, int N, int idx, double glo,
-                                      double ghi) {
+__device__ inline double eigen_idx_df(const KitaevWork& wk, const EigGrid& gr, const df* d, const df* e2, int N,
+                                      int idx, double glo, double ghi) {
   const double range = fmax(ghi - glo, 1e-300);
-  float lo32 = (float)glo, hi32 = (float)ghi;
+  float lo32, hi32;
+  gr.bracket(idx, lo32, hi32);
   const float w32 = (float)(range * 0x1p-20);
   for (int it = 0; it < 48 && hi32 - lo32 > w32; ++it) {
     const float mid = 0.5f * (lo32 + hi32);
@@ -556,6 +557,8 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   }
   const double glo = wk.sc[0], ghi = wk.sc[1];
   grp_sync<MULTI>(g);
+  const EigGrid gr = eig_grid(wk, N, glo, ghi, tid, nt);
+  grp_sync<MULTI>(g);
   // reduction backward error of this stage and of the FP64 stage it stands in
   // for, the FP64 eigenvalue solver's own error on the FP64 path's tridiagonal,
   // and this stage's df64 solver (Sturm backward error and Newton tolerance)
@@ -565,7 +568,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
                       16.0 * 0x1p-46 * scale + 2.0 * 0x1p-42 * (ghi - glo + fabs(glo))) * 1.01;
   double lp = 0.0, en = 0.0, cf = 0.0, bd = 0.0;
   for (int idx = tid; idx < N; idx += nt) {
-    const double mu = fmax(eigen_idx_df(wk, ddf, edf, N, idx, glo, ghi), 0.0);
+    const double mu = fmax(eigen_idx_df(wk, gr, ddf, edf, N, idx, glo, ghi), 0.0);
     thermal_add(sqrt(mu), beta, lp, en, cf);
     const double mlo = fmax(mu - dmu, 0.0);
     const double slope = (mlo > 0.0) ? fmin(0.125 * beta * beta, 0.25 * beta / sqrt(mlo)) : 0.125 * beta * beta;
