@@ -42,7 +42,32 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
   return fast_two_sum(p.hi, p.lo);
 }
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+// c + a b with one normalisation (the reduction's inner loops): a.hi b.hi
+// exact by two_prod, its low part with the cross terms and c.lo in FP32, the
+// high parts added by TwoSum.  Dropped a.lo b.lo and the FP32 roundings of
+// the low sum give |error| <= 13 2^-48 |a b| + 3 2^-48 |c| < 2^-44 (|a b| +
+// |c|) -- an absolute bound in the operands' size (no relative bound under
+// cancellation), which is the form the backward-error analysis of the
+// reduction uses (about 1.6 times the bound of df_mul then df_add).
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+  const df p = two_prod(a.hi, b.hi);
+  const float t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)) + c.lo;
+  const df s = two_sum(c.hi, p.hi);
+  return fast_two_sum(s.hi, s.lo + t);
+}
+// a - (x1 y1 + x2 y2) with one normalisation (the rank-2 update): the two
+// high products exact, their low parts and the four cross terms summed in
+// FP32, the high parts taken from a.hi by two TwoSums; |error| <= 2^-48
+// (6 |a| + 21 |x1 y1| + 23 |x2 y2|) < 2^-43 (|a| + |x1 y1| + |x2 y2|), the
+// same form as df_fma's (about 2.3 times the bound of two df_mul and two
+// df_add).
+__device__ __forceinline__ df df_sub_dot2(df a, df x1, df y1, df x2, df y2) {
+  const df p1 = two_prod(x1.hi, y1.hi), p2 = two_prod(x2.hi, y2.hi);
+  const float c = fmaf(x1.hi, y1.lo, fmaf(x1.lo, y1.hi, fmaf(x2.hi, y2.lo, fmaf(x2.lo, y2.hi, p1.lo + p2.lo))));
+  const df s1 = two_sum(a.hi, -p1.hi);
+  const df s2 = two_sum(s1.hi, -p2.hi);
+  return fast_two_sum(s2.hi, ((a.lo - c) + s1.lo) + s2.lo);
+}
 __device__ __forceinline__ df df_div(df a, df b) {
   const float q1 = a.hi / b.hi;
   const df r = df_add(a, df_neg(df_mul(b, {q1, 0.0f})));
@@ -511,7 +536,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     df sp = {0.0f, 0.0f};
     for (int r = tid; r < m; r += nt) {
       df* a = A + tri(j1 + r, j1);
-      const df x = df_add(*a, df_neg(df_add(df_mul(uu[r], pw[0]), df_mul(pw[r], u0))));
+      const df x = df_sub_dot2(*a, uu[r], pw[0], pw[r], u0);
       *a = x;
       if (r >= 2) sp = df_fma(x, x, sp);
     }
@@ -521,7 +546,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
       int r, c;
       fw.rc(r, c);
       df* a = A + tri(j1 + 1 + r, j1 + 1 + c);
-      *a = df_add(*a, df_neg(df_add(df_mul(uu[r + 1], pw[c + 1]), df_mul(pw[r + 1], uu[c + 1]))));
+      *a = df_sub_dot2(*a, uu[r + 1], pw[c + 1], pw[r + 1], uu[c + 1]);
     }
     sp = warp_sum_df(sp);
     if (lane == 0) scS[warp] = sp;
@@ -559,11 +584,13 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   grp_sync<MULTI>(g);
   const EigGrid gr = eig_grid(wk, N, glo, ghi, tid, nt);
   grp_sync<MULTI>(g);
-  // reduction backward error of this stage and of the FP64 stage it stands in
-  // for, the FP64 eigenvalue solver's own error on the FP64 path's tridiagonal,
+  // reduction backward error of this stage (constant 32: 8 for safety times
+  // about 4 for the one-normalisation df_fma / df_sub_dot2 of the reduction's
+  // loops) and of the FP64 stage it stands in for (8), the FP64 eigenvalue
+  // solver's own error on the FP64 path's tridiagonal,
   // and this stage's df64 solver (Sturm backward error and Newton tolerance)
   const double scale = ghi - glo + fabs(glo) + fabs(ghi);
-  const double dmu = (8.0 * (double)N * (double)N * (0x1p-46 + 0x1p-53) * sqrt(fro_all) +
+  const double dmu = ((double)N * (double)N * (32.0 * 0x1p-46 + 8.0 * 0x1p-53) * sqrt(fro_all) +
                       4.0 * (double)N * 0x1p-52 * (ghi - glo + fabs(glo)) +
                       16.0 * 0x1p-46 * scale + 2.0 * 0x1p-42 * (ghi - glo + fabs(glo))) * 1.01;
   double lp = 0.0, en = 0.0, cf = 0.0, bd = 0.0;
