@@ -179,11 +179,12 @@ def roofline(kernel_ms, clocks, K, k, n_sites, traffic=None):
                                "note": "direct-FP32-equivalent of the three convolutions the kernel computes"}}
 
 
-# FP32 instructions of one double-FP32 multiply-add (df_mul: two_prod 2, two
-# FMAs, fast_two_sum 3; df_add: two two_sums of 6, two adds, two
-# fast_two_sums of 3): the mixed Kitaev path emulates each FP64 multiply-add
-# of the reduction with them on the FP32 pipe
-DF64_FP32_OPS_PER_FMA = 27
+# FP32 instructions of one double-FP32 multiply-add with one normalisation
+# (df_fma: two_prod 2, two cross-term FMAs and an add, two_sum 6, an add,
+# fast_two_sum 3; the rank-2 update's a - (x1 y1 + x2 y2) takes 27 for two):
+# the mixed Kitaev path emulates each FP64 multiply-add of the reduction with
+# them on the FP32 pipe
+DF64_FP32_OPS_PER_FMA = 15
 
 
 def kitaev_roofline(spec, ms, steps, prec, clocks):
@@ -191,7 +192,7 @@ def kitaev_roofline(spec, ms, steps, prec, clocks):
     flops per proposal ((4/3) N^3 multiply-adds: a Golub-Kahan
     bidiagonalisation of M, values only).  FP64 path: against the FP64 FMA
     peak the library's probe measures.  Mixed path: those multiply-adds run as
-    double-FP32 on the FP32 pipe, 27 FP32 instructions each, against the FP32
+    double-FP32 on the FP32 pipe, 15 FP32 instructions each, against the FP32
     pipe's instruction rate from unit counts (152 SMs x 128 lanes) at the
     sampled SM clock."""
     fmas = sum(n * (4.0 / 3.0) * (L * L) ** 3 for L, n in spec["jobs"]) * spec["S"] * steps
