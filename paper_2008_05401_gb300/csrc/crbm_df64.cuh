@@ -37,6 +37,13 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+// a + b with one normalisation (the reduction's sums of partials): TwoSum of
+// the high parts, the low parts added in FP32; |error| <= 3 2^-48 (|a| + |b|)
+// (no relative bound under cancellation).  Commutative, as df_add.
+__device__ __forceinline__ df df_add_fast(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
 __device__ __forceinline__ df df_mul(df a, df b) {
   df p = two_prod(a.hi, b.hi);
   p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
@@ -378,13 +385,13 @@ __device__ inline double eigen_idx_df(const KitaevWork& wk, const EigGrid& gr, c
   return x;
 }
 
-// Sum of a df64 value over a warp (butterfly; df_add is commutative, so every
-// lane ends with the same value).
+// Sum of a df64 value over a warp (butterfly; df_add_fast is commutative, so
+// every lane ends with the same value).
 __device__ __forceinline__ df warp_sum_df(df x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const df y = {__shfl_xor_sync(kFull, x.hi, o), __shfl_xor_sync(kFull, x.lo, o)};
-    x = df_add(x, y);
+    x = df_add_fast(x, y);
   }
   return x;
 }
@@ -402,7 +409,7 @@ __device__ __forceinline__ df grp_sum_df(df x, const Grp& g, double* scratch) {
   if ((r & 31) == 0) sd[warp] = x;
   grp_sync<MULTI>(g);
   df s = sd[0];
-  for (int w = 1; w < nw; ++w) s = df_add(s, sd[w]);
+  for (int w = 1; w < nw; ++w) s = df_add_fast(s, sd[w]);
   grp_sync<MULTI>(g);
   return s;
 }
@@ -523,8 +530,9 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
           e0 = df_fma(A[b1 + j1 + l], A[b1 + j], e0);
         }
       }
-      df e = df_add(e0, e1);
-      for (int o = 1; o < H; o <<= 1) e = df_add(e, {__shfl_xor_sync(kFull, e.hi, o), __shfl_xor_sync(kFull, e.lo, o)});
+      df e = df_add_fast(e0, e1);
+      for (int o = 1; o < H; o <<= 1)
+        e = df_add_fast(e, {__shfl_xor_sync(kFull, e.hi, o), __shfl_xor_sync(kFull, e.lo, o)});
       if (l < m && h == 0) {
         const df p = df_mul(tau, e), ul = l == 0 ? u0 : A[tri(j1 + l, j)];
         pw[l] = p;
@@ -536,9 +544,9 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     if (lane == 0) scP[warp] = part;
     grp_sync<MULTI>(g);
     df pv = scP[0];
-    for (int w = 1; w < nw; ++w) pv = df_add(pv, scP[w]);
+    for (int w = 1; w < nw; ++w) pv = df_add_fast(pv, scP[w]);
     const df Kc = df_mul(df_mul({0.5f, 0.0f}, tau), pv);
-    for (int l = tid; l < m; l += nt) pw[l] = df_add(pw[l], df_neg(df_mul(Kc, uu[l])));
+    for (int l = tid; l < m; l += nt) pw[l] = df_fma(df_neg(Kc), uu[l], pw[l]);
     grp_sync<MULTI>(g);
     // A22 -= u w^T + w u^T (u in uu, w in pw): column 0 of A22 with the
     // partials of s, then the rest of the packed triangle, as in the FP64 stage
@@ -561,7 +569,7 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
     if (lane == 0) scS[warp] = sp;
     grp_sync<MULTI>(g);
     s = scS[0];
-    for (int w = 1; w < nw; ++w) s = df_add(s, scS[w]);
+    for (int w = 1; w < nw; ++w) s = df_add_fast(s, scS[w]);
   }
   if (tid == 0) {
     wk.d[N - 2] = df_to_double(A[tri(N - 2, N - 2)]);
@@ -594,8 +602,8 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   const EigGrid gr = eig_grid(wk, N, glo, ghi, tid, nt);
   grp_sync<MULTI>(g);
   // reduction backward error of this stage (constant 32: 8 for safety times
-  // about 4 for the one-normalisation df_fma / df_sub_dot2 of the reduction's
-  // loops) and of the FP64 stage it stands in for (8), the FP64 eigenvalue
+  // about 4 for the one-normalisation df_fma / df_sub_dot2 / df_add_fast of the
+  // reduction's loops and sums) and of the FP64 stage it stands in for (8), the FP64 eigenvalue
   // solver's own error on the FP64 path's tridiagonal,
   // and this stage's df64 solver (Sturm backward error and Newton tolerance)
   const double scale = ghi - glo + fabs(glo) + fabs(ghi);
