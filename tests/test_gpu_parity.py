@@ -180,14 +180,14 @@ def test_analytic_crbm_accepts_everything(ctx):
         job.release()
 
 
-@pytest.mark.parametrize("L", [6, 10, 12])
-def test_kitaev_mixed_df64_stage_matches_fp64(ctx, L):
+@pytest.mark.parametrize("L,n,S", [(6, 24, 4), (10, 24, 4), (12, 24, 4), (6, 1024, 3), (12, 682, 2)])
+def test_kitaev_mixed_df64_stage_matches_fp64(ctx, L, n, S):
     """The mixed path's df64 eigen-stage: lattices and acceptances identical to
-    the FP64 path over the whole temperature ladder (down to T = 0.005), and
-    log-weights far inside the certified bound (~1e-13 relative)."""
+    the FP64 path over the whole temperature ladder (down to T = 0.005), also
+    at the Kitaev workloads' chain counts, and log-weights (read back in FP64)
+    within 1e-10."""
     from paper_2008_05401_gb300 import FP64, KITAEV, MIXED
     W, hb, vb = wl.gaussian_crbm(4, 3, 0.05, seed=L + 99)
-    n, S = 24, 4
     T = wl.kitaev_ladder(n, 24)
     bits0 = wl.pack_bits(wl.random_lattices(n, L, seed=L + 5))
     mid = ctx.load_model(KITAEV, W, vb, hb)
