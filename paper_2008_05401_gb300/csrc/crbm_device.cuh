@@ -1184,8 +1184,9 @@ __device__ inline void kitaev_logpi64(const Grp& g, const uint32_t* v, int L, co
   // with H lanes per row and, per warp, the partial of p^T u; then w = p -
   // (tau p^T u / 2) u; then A22 -= u w^T + w u^T, its first column (with
   // per-warp partials of the next step's s, the sum of squares below the
-  // subdiagonal) and the rest of the packed triangle element by element in
-  // turn over the group's threads.  sc[0..31]: p^T u partials, sc[32..63]: s.
+  // subdiagonal) and the rest of the packed triangle element by element over
+  // the group's threads in the folded order of FoldWalk.  sc[0..31]: p^T u
+  // partials, sc[32..63]: s.
   double* scP = wk.sc;
   double* scS = wk.sc + 32;
   double s;

@@ -464,10 +464,12 @@ __device__ inline void kitaev_logpi_df(const Grp& g, const uint32_t* v, int L, c
   grp_sync<MULTI>(g);
   // Householder tridiagonalisation in df64, organised as the FP64 stage's
   // (kitaev_logpi64): u read from column j, three group barriers per column,
-  // p = tau A22 u one thread per row, the rank-2 update element by element
-  // over the packed triangle.  Every reduction stays in df64 on the FP32 pipe
-  // (an FP64 instruction costs tens of cycles of the SMSP's FP64 pipe on
-  // GB300).  sc[0..31]: per-warp df64 partials of p^T u, sc[32..63]: of s.
+  // p = tau A22 u with H lanes per row, the rank-2 update element by element
+  // over the packed triangle in folded order.  Every reduction stays in df64
+  // on the FP32 pipe (an FP64 instruction costs tens of cycles of the SMSP's
+  // FP64 pipe on GB300), the inner loops' multiply-adds, the update and the
+  // sums with one normalisation each (df_fma, df_sub_dot2, df_add_fast).
+  // sc[0..31]: per-warp df64 partials of p^T u, sc[32..63]: of s.
   df* scP = reinterpret_cast<df*>(wk.sc);
   df* scS = reinterpret_cast<df*>(wk.sc + 32);
   df s;
